@@ -1,0 +1,228 @@
+"""FP64 CPU oracle for the fluctuating two-species lattice Boltzmann update
+(arXiv 1410.5584, Sec. V, Eqs. algorithm and lattice finalstep).
+
+TEST INFRASTRUCTURE ONLY: the yardstick the CUDA library is checked against.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  The product package never imports it and shares no
+code with it; the C source is ``flbm_oracle.c`` beside this file.
+
+This module builds the C source with gcc (plain ``-O2``, IEEE semantics, no fast
+math) into ``oracle/_build/`` and binds it with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "flbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+D2Q9, D3Q19 = 0, 1
+
+# option keys (same numbers as the public C-ABI's keys)
+OPT_LAMBDA_D = 2
+OPT_SDF = 3
+OPT_RHO0_A = 4
+OPT_RHO0_B = 5
+OPT_NOISE_RHO = 7
+OPT_FORCE_VELOCITY = 8
+OPT_LAMBDA_MODE = 1000  # + 100 * species + mode
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liborc.so (skipped when up to date)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-std=c11", "-D_DEFAULT_SOURCE", "-O2", "-fPIC", "-shared",
+                    "-fopenmp", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            vp, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int, ctypes.c_long,
+                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            up = ctypes.POINTER(ctypes.c_uint32)
+            L.orc_create.restype = vp
+            L.orc_create.argtypes = [i32, i32, i32, i32, dbl, dbl, dbl, dbl, u64]
+            L.orc_destroy.argtypes = [vp]
+            L.orc_set_option.argtypes = [vp, i32, dbl]
+            L.orc_init.argtypes = [vp, dp, dp]
+            L.orc_set_f.argtypes = [vp, dp, i64]
+            L.orc_get_f.argtypes = [vp, dp]
+            L.orc_set_threads.argtypes = [vp, i32]
+            L.orc_get_step.restype = i64
+            L.orc_get_step.argtypes = [vp]
+            L.orc_step.argtypes = [vp, i64]
+            L.orc_moments.argtypes = [vp, dp, dp, dp, dp]
+            L.orc_sf_sample.argtypes = [vp, i32, i32]
+            L.orc_structure_factor.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long)]
+            L.orc_sf_reset.argtypes = [vp]
+            L.orc_tables.argtypes = [i32, ip, ip, ip, dp, dp, dp]
+            L.orc_meq.argtypes = [i32, dbl, dp, dp]
+            L.orc_phi.argtypes = [i32, dbl, dp, dp, dp]
+            L.orc_philox4x32_10.argtypes = [up, up, up]
+            L.orc_gaussian.restype = dbl
+            L.orc_gaussian.argtypes = [u64, u32, u32, u32, u32]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def tables(lattice: int):
+    """(c [Q,3] int, w [Q], T [Q,Q] with T[a,i], N [Q]) as built by the oracle."""
+    D = ctypes.c_int()
+    Q = ctypes.c_int()
+    c = np.zeros(19 * 3, dtype=np.int32)
+    w = np.zeros(19)
+    T = np.zeros(19 * 19)
+    N = np.zeros(19)
+    rc = lib().orc_tables(lattice, ctypes.byref(D), ctypes.byref(Q),
+                          c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(w), _dp(T), _dp(N))
+    assert rc == 0
+    q = Q.value
+    return c[:q * 3].reshape(q, 3), w[:q].copy(), T[:q * q].reshape(q, q), N[:q].copy()
+
+
+def meq(lattice: int, rho: float, u) -> np.ndarray:
+    u3 = np.zeros(3)
+    u3[:len(u)] = u
+    out = np.zeros(19)
+    lib().orc_meq(lattice, rho, _dp(u3), _dp(out))
+    return out[:19 if lattice == D3Q19 else 9]
+
+
+def phi(lattice: int, rho: float, acc, v) -> np.ndarray:
+    a3 = np.zeros(3)
+    a3[:len(acc)] = acc
+    v3 = np.zeros(3)
+    v3[:len(v)] = v
+    out = np.zeros(19)
+    lib().orc_phi(lattice, rho, _dp(a3), _dp(v3), _dp(out))
+    return out[:19 if lattice == D3Q19 else 9]
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def gaussian(seed: int, site: int, step: int, species: int, mode: int) -> float:
+    return lib().orc_gaussian(seed, site, step, species, mode)
+
+
+class Oracle:
+    """Handle on one oracle lattice (two species, periodic box)."""
+
+    def __init__(self, lattice, nx, ny, nz, tau_a, tau_b, kT, G, seed, **options):
+        self.lattice = lattice
+        self.nx, self.ny = nx, ny
+        self.nz = 1 if lattice == D2Q9 else nz
+        self.D = 2 if lattice == D2Q9 else 3
+        self.Q = 9 if lattice == D2Q9 else 19
+        self.N = self.nx * self.ny * self.nz
+        self._h = lib().orc_create(lattice, nx, ny, self.nz, tau_a, tau_b, kT, G, seed)
+        if not self._h:
+            raise MemoryError("orc_create failed")
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def set_threads(self, n: int):
+        """OpenMP threads for the site loops (the arithmetic is unchanged)."""
+        lib().orc_set_threads(self._h, int(n))
+
+    def set_option(self, key, value):
+        if isinstance(key, str):
+            key = {"lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF, "rho0_a": OPT_RHO0_A,
+                   "rho0_b": OPT_RHO0_B, "noise_rho": OPT_NOISE_RHO,
+                   "force_velocity": OPT_FORCE_VELOCITY}[key]
+        if lib().orc_set_option(self._h, int(key), float(value)) != 0:
+            raise ValueError(f"bad oracle option {key}")
+
+    def set_mode_rate(self, species, mode, lam):
+        self.set_option(OPT_LAMBDA_MODE + 100 * species + mode, lam)
+
+    def init(self, rho_a=None, rho_b=None):
+        ra = None if rho_a is None else np.ascontiguousarray(rho_a, dtype=np.float64).ravel()
+        rb = None if rho_b is None else np.ascontiguousarray(rho_b, dtype=np.float64).ravel()
+        lib().orc_init(self._h, _dp(ra), _dp(rb))
+
+    def step(self, n=1):
+        rc = lib().orc_step(self._h, int(n))
+        if rc != 0:
+            raise FloatingPointError(f"oracle step failed with status {rc}")
+
+    @property
+    def step_count(self):
+        return lib().orc_get_step(self._h)
+
+    def get_f(self) -> np.ndarray:
+        """Populations, natural layout [species][i][z][y][x]."""
+        f = np.zeros(2 * self.Q * self.N)
+        lib().orc_get_f(self._h, _dp(f))
+        return f.reshape(2, self.Q, self.nz, self.ny, self.nx)
+
+    def set_f(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        assert f.size == 2 * self.Q * self.N
+        lib().orc_set_f(self._h, _dp(f), int(step))
+
+    def moments(self):
+        ra = np.zeros(self.N)
+        rb = np.zeros(self.N)
+        u = np.zeros(self.D * self.N)
+        cons = np.zeros(5)
+        lib().orc_moments(self._h, _dp(ra), _dp(rb), _dp(u), _dp(cons))
+        shp = (self.nz, self.ny, self.nx)
+        return ra.reshape(shp), rb.reshape(shp), u.reshape((self.D,) + shp), cons
+
+    def sf_sample(self, axis=0, nk=None):
+        n_axis = (self.nx, self.ny, self.nz)[axis]
+        nk = n_axis // 2 if nk is None else nk
+        self._sf_nk = nk
+        if lib().orc_sf_sample(self._h, axis, nk) != 0:
+            raise ValueError("bad structure-factor axis or nk")
+
+    def structure_factor(self):
+        nk = self._sf_nk
+        out = [np.zeros(nk) for _ in range(4)]
+        n = ctypes.c_long()
+        lib().orc_structure_factor(self._h, *[_dp(o) for o in out], ctypes.byref(n))
+        return (*out, n.value)
+
+    def sf_reset(self):
+        lib().orc_sf_reset(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
