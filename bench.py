@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the fluctuating two-species lattice Boltzmann update on GB300.
+
+One "step" is one full lattice update (density pass + fused force, moment
+collision, noise and streaming) of both species on the whole box.  Default
+workload: D3Q19 256^3 periodic box, FP32 populations, rho_A = rho_B = 1,
+G rho0 = 0.9, tau = 1, kT = 1e-5 (the 2.55 GB population array is far larger
+than L2, so no flush is needed between steps).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead, on bounded samples of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "d3q19-256": dict(lattice=1, nx=256, ny=256, nz=256, storage="f32", tau=(1.0, 1.0), kT=1e-5, G=0.9,
+                      rho0=1.0, desc="D3Q19 256^3 periodic two-species Shan-Chen mixture, FP32 populations, "
+                                     "rho_A=rho_B=1, G*rho0=0.9, tau=1.0, kT=1e-5"),
+    "d3q19-256-f16": dict(lattice=1, nx=256, ny=256, nz=256, storage="f16", tau=(1.0, 1.0), kT=1e-5, G=0.9,
+                          rho0=1.0, desc="D3Q19 256^3 mixture, populations stored as FP16 deviations from "
+                                         "w_i*rho0, FP32 collision"),
+    "d3q19-256-bf16": dict(lattice=1, nx=256, ny=256, nz=256, storage="bf16", tau=(1.0, 1.0), kT=1e-5, G=0.9,
+                           rho0=1.0, desc="D3Q19 256^3 mixture, populations stored as BF16 deviations from "
+                                          "w_i*rho0, FP32 collision"),
+    "d2q9-512": dict(lattice=0, nx=512, ny=512, nz=1, storage="f32", tau=(0.8, 1.0), kT=1e-5, G=0.9,
+                     rho0=1.0, desc="D2Q9 512^2 periodic Shan-Chen mixture, FP32, G*rho0=0.9, tau=0.8/1.0, "
+                                    "kT=1e-5 (fits in L2)"),
+}
+BYTES_PER_POP = {"f32": 4, "f16": 2, "bf16": 2}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d3q19-256")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sources_digest():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1410_5584_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload, sites):
+    """DRAM bytes per collide launch from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    rec = d.get(workload)
+    if not rec or rec.get("sources_sha256") != sources_digest():
+        return None
+    return rec["dram_bytes_per_launch"] * sites / rec["sites"]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, seed, budget_s=15.0):
+    """The FP64 oracle, single-threaded as it stands, on a bounded sample: the
+    same lattice and parameters on a smaller periodic box."""
+    import numpy as np
+
+    import oracle
+
+    side = 64 if wl["lattice"] == 1 else 512
+    shape = (side, side, side) if wl["lattice"] == 1 else (1, side, side)
+    nz, ny, nx = shape
+    o = oracle.Oracle(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed)
+    o.set_threads(1)
+    o.init(np.full(nx * ny * nz, wl["rho0"]), np.full(nx * ny * nz, wl["rho0"]))
+    t0 = time.perf_counter()
+    o.step(1)
+    dt1 = time.perf_counter() - t0
+    n = max(1, min(50, int(budget_s / max(dt1, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    sites = nx * ny * nz
+    o.close()
+    return {"value": sites * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{'D3Q19' if wl['lattice'] == 1 else 'D2Q9'} {nx}x{ny}x{nz} periodic box, same tau/kT/G/rho0, "
+                      f"{n} steps timed after 1, FP64, 1 thread"}
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 oracle on the host cores; each step is one
+    oracle step on a small periodic box of the same workload, sized so the
+    whole run stays within a few minutes."""
+    import numpy as np
+
+    import oracle
+
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    lat = wl["lattice"]
+
+    def make(side):
+        shape = (side, side, side) if lat == 1 else (1, side, side)
+        nz, ny, nx = shape
+        o = oracle.Oracle(lat, nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], args.seed)
+        o.set_threads(1)
+        o.init(np.full(nx * ny * nz, wl["rho0"]), np.full(nx * ny * nz, wl["rho0"]))
+        return o, nx * ny * nz, shape
+
+    o, sites, _ = make(8 if lat == 1 else 32)
+    t0 = time.perf_counter()
+    o.step(2)
+    rate = 2 * sites / (time.perf_counter() - t0)
+    o.close()
+    budget = 150.0
+    side = 4 if lat == 1 else 8
+    for cand in range(4, 257):
+        if (cand ** 3 if lat == 1 else cand * cand) * (args.steps + args.warmup) / rate <= budget:
+            side = cand
+    o, sites, shape = make(side)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    value = sites * args.steps / dt / 1e6
+    sample = (f"{'D3Q19' if lat == 1 else 'D2Q9'} {shape[2]}x{shape[1]}x{shape[0]} periodic box per step "
+              f"(same tau/kT/G/rho0), FP64, 1 thread")
+    line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"], "reference_sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    from paper_1410_5584_gb300 import Lattice
+    from paper_1410_5584_gb300.replicas import aggregate, replica_seed
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    seed = replica_seed(args.seed, rank)
+    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
+    sites = nx * ny * nz
+    Q = 19 if wl["lattice"] == 1 else 9
+    lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
+                  storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"])
+    lat.init()
+    lat.step(args.warmup)
+    lat.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-timed region: inputs resident in HBM ----
+    lat.set_option("kernel_timing", 1)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(device)
+    with ClockSampler(local) as clk:
+        start.record(lat.stream)
+        lat.step(args.steps)
+        end.record(lat.stream)
+        torch.cuda.synchronize(device)
+    barrier()
+    lat.sync()
+    t_local = start.elapsed_time(end) / 1e3
+    kms, kn = lat.kernel_times()
+    lat.set_option("kernel_timing", 0)
+    t_max, units = aggregate(t_local, sites * args.steps, device=device)
+    value = units / t_max / 1e6
+
+    # ---- end to end through the C-ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        ra = np.full(sites, wl["rho0"])
+        rb = np.full(sites, wl["rho0"])
+        out_a, out_b = np.empty(sites), np.empty(sites)
+        D = 3 if wl["lattice"] == 1 else 2
+        out_u = np.empty(D * sites)
+        import ctypes
+
+        from paper_1410_5584_gb300 import flbm as F
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cons = np.empty(5)
+        barrier()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        F.check(lat._h, F.lib().flbm_init(lat._h, dp(ra), dp(rb)))
+        F.check(lat._h, F.lib().flbm_step(lat._h, args.steps))
+        F.check(lat._h, F.lib().flbm_moments(lat._h, dp(out_a), dp(out_b), dp(out_u), dp(cons)))
+        t1 = time.perf_counter()
+        barrier()
+        te, ue = aggregate(t1 - t0, sites * args.steps, device=device)
+        h2d = 2 * sites * 4  # the two density planes, as float, from pinned staging
+        d2h = (2 + D) * sites * 8 + 5 * 8
+        e2e = {"value": ue / te / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps,
+               "note": "flbm_init from host densities + K steps + flbm_moments to host, per-step averages"}
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    bpp = BYTES_PER_POP[wl["storage"]]
+    alg_bytes = sites * 2 * Q * 2 * bpp  # populations read + written once per step
+    coll_ms = kms["collide"] / max(kn["collide"], 1)
+    achieved = alg_bytes / (coll_ms / 1e3) / 1e9
+    traffic = recorded_traffic(args.workload, sites)
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "lattice": "D3Q19" if wl["lattice"] == 1 else "D2Q9",
+                   "nx": nx, "ny": ny, "nz": nz, "storage": wl["storage"], "replicas": world,
+                   "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2"},
+        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "step_hbm_frac": alg_bytes / (t_max / args.steps) / 1e9 / peak,
+        "kernel_ms": {"density": kms["density"] / max(kn["density"], 1), "collide": coll_ms},
+        "gpu_launches": kn["density"] + kn["collide"],
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.seed)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+    world, _, _ = dist_env()
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

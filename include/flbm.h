@@ -1,0 +1,216 @@
+/*
+ * flbm.h -- C-ABI of the GB300 (sm_103a) library for the fluctuating two-species
+ * lattice Boltzmann update of Belardinelli, Sbragaglia, Biferale, Gross and
+ * Varnik, "Fluctuating multicomponent lattice Boltzmann model" (arXiv 1410.5584).
+ *
+ * The update is the paper's lattice algorithm (Sec. V B, Eqs. algorithm and
+ * lattice finalstep), applied per site r and step n to both species:
+ *   fbar_i(r + c_i, n+1) = fbar_i(r, n) + w_i sum_a T_ai R_a(r, n) / N_a,
+ *   R_a = lambdabar_a (m^eq_a(rho, vbar_b + a_b/2) - mbar_a) + Phibar_a + xibar_a,
+ * with the Shan-Chen inter-species force a(r) = -G sum_i w_i rho'(r + c_i) c_i
+ * (Sec. VI, Eq. FORCESTRUCTURE), the D2Q9 basis of Table I, and Gaussian noise
+ * with the covariances of Eq. new-noise (opposite on the two species' momenta,
+ * local densities, Sec. VII).
+ *
+ * Conventions for every call:
+ *   - Every call returns an flbm_status and never aborts or throws.  After an
+ *     error, flbm_last_error() gives a one-line reason.
+ *   - Lattice units: Delta t = Delta r = 1, k_B = 1, c_s^2 = 1/3.  The box is
+ *     fully periodic.
+ *   - Site index: site = (z * ny + y) * nx + x, x fastest.  Host arrays of one
+ *     value per site are row-major [z][y][x], caller-owned, and are read or
+ *     written only during the call.
+ *   - Populations, where exposed, are in the natural layout
+ *     [species][i][z][y][x]; species 0 = A, 1 = B; i indexes the velocity set:
+ *       D2Q9 : (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *       D3Q19: (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1)
+ *              (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1)
+ *              (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *   - flbm_step is asynchronous on the context's stream.  Faults detected on
+ *     the device (a density that is not positive and finite) are reported by
+ *     the next synchronising call: flbm_sync, flbm_moments, flbm_sf_sample,
+ *     flbm_structure_factor, flbm_get_populations, flbm_checkpoint.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef FLBM_H
+#define FLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flbm_ctx flbm_ctx; /* opaque; created and freed by the library */
+
+typedef enum {
+    FLBM_OK = 0,
+    FLBM_EINVAL = 1,       /* an argument is out of range or inconsistent */
+    FLBM_ENOMEM = 2,       /* a host or device allocation failed */
+    FLBM_ECUDA = 3,        /* a CUDA runtime call failed (reason in flbm_last_error) */
+    FLBM_ENONFINITE = 4,   /* a density became non-positive or non-finite on the device */
+    FLBM_ETIMEOUT = 5,     /* a bounded device wait gave up */
+    FLBM_EUNSUPPORTED = 6, /* valid request that this build does not support */
+    FLBM_ESTATE = 7        /* call out of order (e.g. step before init) */
+} flbm_status;
+
+typedef enum { FLBM_D2Q9 = 0, FLBM_D3Q19 = 1 } flbm_lattice;
+
+/* Population storage formats (option FLBM_OPT_STORAGE). */
+typedef enum {
+    FLBM_STORE_F32 = 0,  /* populations stored as float */
+    FLBM_STORE_F16 = 1,  /* stored as half deviations from w_i * rho0^s; collided in float */
+    FLBM_STORE_BF16 = 2  /* stored as bfloat16 deviations from w_i * rho0^s; collided in float */
+} flbm_storage;
+
+/* Option keys for flbm_set_option. */
+enum {
+    FLBM_OPT_STORAGE = 1,        /* flbm_storage; only before flbm_init / flbm_attach_buffers */
+    FLBM_OPT_LAMBDA_D = 2,       /* common momentum rate lambdabar_d, 0 < value < 2 (Sec. III,
+                                    Eq. diffusionrelaxation); default 1/tau if tau_A = tau_B,
+                                    else 2/(tau_A + tau_B) */
+    FLBM_OPT_SDF = 3,            /* 1 (default): noise on the species momenta ("sdf");
+                                    0: switched off ("no-sdf" control of Sec. VI A) */
+    FLBM_OPT_RHO0_A = 4,         /* reference density of A: uniform init and 16-bit deviation base;
+                                    default 1 */
+    FLBM_OPT_RHO0_B = 5,         /* same for B */
+    FLBM_OPT_NOISE_RHO = 7,      /* 0 (default): local densities in the noise amplitudes
+                                    (Sec. VII); 1: the reference densities rho0 (Eq. new-noise,
+                                    homogeneous form) */
+    FLBM_OPT_FORCE_VELOCITY = 8, /* species velocity inside Phi: 0 (default) rho v = jbar + R_j/2
+                                    (Eq. alg-mom, equivalent to Eq. 2system); 1: v = vbar + a/2 */
+    FLBM_OPT_SF_AXIS = 9,        /* axis of the structure-factor wavevector (0 x, 1 y, 2 z);
+                                    changing it clears the accumulators; default 0 */
+    FLBM_OPT_KERNEL_TIMING = 10, /* 1: flbm_step records CUDA events around each kernel on the
+                                    context's stream (see flbm_kernel_times); 0 (default): off.
+                                    Switching it clears the accumulated times */
+    FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
+                                    non-conserved mode, 0 < value < 2; default 1/tau_species */
+};
+
+/*
+ * Create a context for an nx * ny * nz periodic box of two species (nz = 1 for
+ * D2Q9).  tau_a, tau_b: relaxation times; every non-conserved mode of species s
+ * relaxes with lambdabar = 1/tau_s (the lattice rate of Eq. lattice-freq), the
+ * momenta with the common lambdabar_d (see FLBM_OPT_LAMBDA_D).  kT: fluctuation
+ * temperature (k_B T, lattice units, >= 0).  G: inter-species coupling of
+ * Eq. FORCESTRUCTURE (G > 0 repels).  seed: the 64-bit key of the
+ * Philox4x32-10 noise generator.
+ * Noise: the Gaussian for mode a of species s at (site, step n) is lane a mod 4
+ * of Box-Muller on Philox4x32-10 with key (seed low, seed high) and counter
+ * (site, n, s, a/4); u1 = ((x>>8)+1) 2^-24, u2 = (y>>8) 2^-24,
+ * (g0, g1) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2) on lanes (0,1) and (2,3).
+ * The species momenta use species 0's draws for B as well, with the opposite sign.
+ * No device memory is allocated here.
+ * Errors: FLBM_EINVAL if lat is unknown, nx/ny/nz < 2 (nz != 1 for D2Q9),
+ * ny or nz > 65535, nx*ny*nz >= 2^31, tau <= 0.5, kT < 0, or out == NULL.
+ */
+flbm_status flbm_create(flbm_lattice lat, int nx, int ny, int nz, double tau_a, double tau_b,
+                        double kT, double G, uint64_t seed, flbm_ctx **out);
+
+/* Set one option (keys above).  FLBM_EINVAL for an unknown key or a value out of
+ * range; FLBM_ESTATE for FLBM_OPT_STORAGE after the buffers exist. */
+flbm_status flbm_set_option(flbm_ctx *ctx, int key, double value);
+
+/* Run the context's work on `stream` (a cudaStream_t, NULL = the library's own
+ * non-blocking stream).  The caller keeps ownership of the stream and must keep
+ * it alive while the context uses it. */
+flbm_status flbm_set_stream(flbm_ctx *ctx, void *stream);
+
+/* Bytes of device memory the context needs for its populations and its density
+ * field, for the current storage option.  Either pointer may be NULL. */
+flbm_status flbm_buffer_bytes(const flbm_ctx *ctx, size_t *pop_bytes, size_t *rho_bytes);
+
+/* Use caller-owned device buffers for the populations (pop_bytes as reported by
+ * flbm_buffer_bytes, 256-byte aligned) and the density field.  The library
+ * never frees them; they must outlive the context.  Without this call,
+ * flbm_init allocates its own.  FLBM_ESTATE if buffers already exist. */
+flbm_status flbm_attach_buffers(flbm_ctx *ctx, void *pop, size_t pop_bytes, void *rho,
+                                size_t rho_bytes);
+
+/* Rest-state initialisation f_i = w_i rho^s(r) (f^eq at zero velocity, Sec. V B).
+ * rho_a, rho_b: host arrays of N doubles each, or NULL for the uniform
+ * reference densities.  Resets the step counter to 0.  Allocates the buffers
+ * if none are attached (FLBM_ENOMEM on failure). */
+flbm_status flbm_init(flbm_ctx *ctx, const double *rho_a, const double *rho_b);
+
+/* Advance n >= 0 steps (asynchronous).  Step n uses noise counter n.
+ * FLBM_ESTATE before flbm_init; FLBM_ECUDA if a launch fails. */
+flbm_status flbm_step(flbm_ctx *ctx, int64_t n);
+
+/* Wait for the context's stream and report device-detected faults
+ * (FLBM_ENONFINITE once a density was not positive and finite). */
+flbm_status flbm_sync(flbm_ctx *ctx);
+
+/* Accumulated device time of the kernels launched by flbm_step while
+ * FLBM_OPT_KERNEL_TIMING was on, in milliseconds, per kernel kind:
+ * ms[0] density pass, ms[1] fused collide-and-stream; launches[k] the number of
+ * launches timed.  Either array may be NULL.  Synchronising. */
+flbm_status flbm_kernel_times(flbm_ctx *ctx, double ms[2], int64_t launches[2]);
+
+/* Steps taken since flbm_init (or the restored checkpoint's count). */
+flbm_status flbm_get_step(const flbm_ctx *ctx, int64_t *step);
+
+/*
+ * Observables of the current state (Eq. lattice-vb): per-site rho^A, rho^B and
+ * the baricentric velocity u_b = (jbar^A + jbar^B + (F^A + F^B)/2) / rho_t with
+ * F^s = rho^s a^s, as host arrays (rho_a, rho_b: N doubles; u: D * N doubles,
+ * component-major [d][z][y][x]); cons (5 doubles) = FP64 totals
+ * [sum rho^A, sum rho^B, sum (jbar_t + F_t/2)_x, _y, _z] (z entry 0 for D2Q9).
+ * Any pointer may be NULL.  Synchronising.
+ */
+flbm_status flbm_moments(flbm_ctx *ctx, double *rho_a, double *rho_b, double *u, double *cons);
+
+/* Add one snapshot of the axis structure factors to the FP64 accumulators:
+ * for k_m = 2 pi m / n_axis, m = 1 .. n_axis/2, along the axis of
+ * FLBM_OPT_SF_AXIS: |rhohat_A|^2/N, Re(rhohat_A conj rhohat_B)/N, |rhohat_B|^2/N and
+ * (1/D) sum_d |uhat_d|^2/N, rhohat(k) = sum_r rho(r) e^{-i k r_axis} (Sec. VI A).
+ * Synchronising. */
+flbm_status flbm_sf_sample(flbm_ctx *ctx);
+
+/* Ensemble means over the snapshots taken so far, for m = 1..nk (nk <= n_axis/2)
+ * along `axis` (must equal FLBM_OPT_SF_AXIS): S_aa, S_ab, S_bb, S_uu are host
+ * arrays of nk doubles (any may be NULL); *nsamples = snapshot count.
+ * FLBM_ESTATE if no snapshot was taken. */
+flbm_status flbm_structure_factor(flbm_ctx *ctx, int axis, int nk, double *S_aa, double *S_ab,
+                                  double *S_bb, double *S_uu, int64_t *nsamples);
+
+/* Clear the structure-factor accumulators. */
+flbm_status flbm_sf_reset(flbm_ctx *ctx);
+
+/* Copy the populations, natural layout [2][Q][N], to / from host doubles
+ * (2 * Q * N values).  get: synchronising; set: converts to the storage format
+ * and sets the step counter to `step`. */
+flbm_status flbm_get_populations(flbm_ctx *ctx, double *f);
+flbm_status flbm_set_populations(flbm_ctx *ctx, const double *f, int64_t step);
+
+/* Natural-layout populations of `nsites` sites (indices in [0, N)), out = host
+ * [nsites][2][Q] doubles.  For sampled checks on large boxes.  Synchronising. */
+flbm_status flbm_get_site_populations(flbm_ctx *ctx, const int64_t *sites, int64_t nsites,
+                                      double *out);
+
+/* Checkpoint: the full state (parameters, options, step counter, populations)
+ * as an opaque byte image.  With buf == NULL, *bytes receives the size needed;
+ * otherwise *bytes must be at least that size.  Restoring into a context created
+ * with the same lattice and box continues bit-identically (the noise is keyed on
+ * the step).  FLBM_EINVAL on a size, lattice or box mismatch or a corrupt image. */
+flbm_status flbm_checkpoint(flbm_ctx *ctx, void *buf, size_t *bytes);
+flbm_status flbm_restore(flbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* One-line reason of the last error on this context ("" if none).  The string
+ * is owned by the context.  Never NULL (ctx may be NULL). */
+const char *flbm_last_error(const flbm_ctx *ctx);
+
+/* Free the context and the device memory it owns (never attached buffers).
+ * NULL is a no-op. */
+void flbm_destroy(flbm_ctx *ctx);
+
+/* Library version string, e.g. "flbm 0.1 sm_103a". */
+const char *flbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLBM_H */

@@ -68,6 +68,7 @@ def lib():
             L.orc_set_f.argtypes = [vp, dp, i64]
             L.orc_get_f.argtypes = [vp, dp]
             L.orc_set_threads.argtypes = [vp, i32]
+            L.orc_set_rng_origin.argtypes = [vp, i64, i64, i64, i64, i64, i64]
             L.orc_get_step.restype = i64
             L.orc_get_step.argtypes = [vp]
             L.orc_step.argtypes = [vp, i64]
@@ -153,6 +154,13 @@ class Oracle:
     def set_threads(self, n: int):
         """OpenMP threads for the site loops (the arithmetic is unchanged)."""
         lib().orc_set_threads(self._h, int(n))
+
+    def set_rng_origin(self, global_shape, origin):
+        """Draw the noise of local site (x, y, z) with the index of site
+        (x, y, z) + origin of a periodic box of shape (nz, ny, nx)."""
+        gnz, gny, gnx = global_shape
+        oz, oy, ox = origin
+        lib().orc_set_rng_origin(self._h, gnx, gny, gnz, ox, oy, oz)
 
     def set_option(self, key, value):
         if isinstance(key, str):

@@ -80,6 +80,10 @@ typedef struct {
     double *rho[2]; /* density field of the current step */
     long step;
     int threads; /* OpenMP threads for the site loops (1 = serial) */
+    /* noise site numbering: by default the site's own index; for a block cut
+     * out of a larger box, the index the site has in that box */
+    int rng_global;
+    long gnx, gny, gnz, ox, oy, oz;
     /* structure-factor accumulators, index m-1 for k_m = 2 pi m / n_axis */
     int sf_axis, sf_nk;
     double *sf_aa, *sf_ab, *sf_bb, *sf_uu;
@@ -472,6 +476,29 @@ long orc_get_step(const orc_t *o) { return o->step; }
 
 void orc_set_threads(orc_t *o, int n) { o->threads = n > 0 ? n : 1; }
 
+/* Treat this box as the block of a periodic gnx * gny * gnz box whose local
+ * site (0,0,0) sits at (ox, oy, oz): the noise of a site is then drawn with
+ * its index in the large box, so a block's update can be checked against a
+ * run on the large box. */
+void orc_set_rng_origin(orc_t *o, long gnx, long gny, long gnz, long ox, long oy, long oz)
+{
+    o->rng_global = 1;
+    o->gnx = gnx;
+    o->gny = gny;
+    o->gnz = gnz;
+    o->ox = ox;
+    o->oy = oy;
+    o->oz = oz;
+}
+
+static uint32_t rng_site(const orc_t *o, long site)
+{
+    if (!o->rng_global) return (uint32_t)site;
+    long x = site % o->nx, y = (site / o->nx) % o->ny, z = site / ((long)o->nx * o->ny);
+    long gx = (x + o->ox) % o->gnx, gy = (y + o->oy) % o->gny, gz = (z + o->oz) % o->gnz;
+    return (uint32_t)((gz * o->gny + gy) * o->gnx + gx);
+}
+
 /* site index r + c (periodic) */
 static long neighbour(const orc_t *o, long site, const int c[3])
 {
@@ -541,7 +568,7 @@ static int collide_site(const orc_t *o, long site, double R[2][ORC_MAXQ])
         double var_j = (2.0 * lam_d - lam_d * lam_d) * o->kT * nr[0] * nr[1] / (nr[0] + nr[1]);
         double sj = o->sdf ? sqrt(var_j) : 0.0;
         for (int d = 0; d < D; d++) {
-            double g = orc_gaussian(o->seed, (uint32_t)site, (uint32_t)o->step, 0u, (uint32_t)(1 + d));
+            double g = orc_gaussian(o->seed, rng_site(o, site), (uint32_t)o->step, 0u, (uint32_t)(1 + d));
             xi[0][1 + d] = sj * g;
             xi[1][1 + d] = -xi[0][1 + d];
         }
@@ -550,7 +577,7 @@ static int collide_site(const orc_t *o, long site, double R[2][ORC_MAXQ])
         for (int a = D + 1; a < Q; a++) {
             double lam = o->lam[s][a];
             double var = (2.0 * lam - lam * lam) * L->N[a] * mu * nr[s];
-            double g = orc_gaussian(o->seed, (uint32_t)site, (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
+            double g = orc_gaussian(o->seed, rng_site(o, site), (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
             xi[s][a] = sqrt(var) * g;
         }
     /* momentum modes: R_alpha (Eq. finalstep, m^eq_alpha = rho u_alpha, Phi_alpha = rho a_alpha) */

@@ -1,0 +1,810 @@
+// flbm_api.cu -- the C-ABI of include/flbm.h: context, argument checks, buffer
+// ownership, the step loop, observables, checkpoints and error reporting.
+// Every entry point catches its own failures and returns an flbm_status.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "flbm_internal.h"
+#include "flbm_lattice.cuh"
+
+using namespace flbm;
+
+struct flbm_ctx {
+    // problem
+    int lat = 0, D = 2, Q = 9;
+    int nx = 0, ny = 0, nz = 1;
+    int64_t N = 0;
+    double tau[2] = {1.0, 1.0}, kT = 0.0, G = 0.0;
+    uint64_t seed = 0;
+    // options
+    double lam[2][kMaxQ] = {};
+    int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
+    double rho0[2] = {1.0, 1.0};
+    // state
+    int64_t step = 0;
+    int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
+    bool initialised = false;
+    bool faulted = false;
+    // device buffers
+    void *pop = nullptr;
+    size_t pop_bytes = 0;
+    float *rho = nullptr;
+    size_t rho_bytes = 0;
+    bool own_buffers = false;
+    unsigned *d_status = nullptr;
+    double *d_obs = nullptr;      // (2 + D) * N doubles: rho_a, rho_b, u
+    double *d_partials = nullptr; // per-block totals
+    size_t partials_cap = 0;
+    double *d_cons = nullptr;     // 5 doubles
+    double *d_sf = nullptr;       // 4 * n_axis/2 accumulators
+    double *d_profile = nullptr;  // (2 + D) * n_axis
+    int64_t sf_count = 0;
+    float *h_stage = nullptr;     // pinned staging, 2 * N floats
+    // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;      // recorded in order: start, after density, after collide, ...
+    size_t ev_used = 0;
+    double kernel_ms[2] = {0.0, 0.0};
+    int64_t kernel_launches[2] = {0, 0};
+    // stream
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char err[512] = {0};
+};
+
+namespace {
+
+const char *kNoError = "";
+
+flbm_status fail(flbm_ctx *c, flbm_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+flbm_status cuda_fail(flbm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, FLBM_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define FLBM_CUDA(ctx, call, what)                                \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, what); \
+    } while (0)
+
+double lat_w(int lat, int i) { return lat == FLBM_D2Q9 ? D2Q9::wd(i) : D3Q19::wd(i); }
+double lat_N(int lat, int a) { return lat == FLBM_D2Q9 ? D2Q9::Nd(a) : D3Q19::Nd(a); }
+int lat_c(int lat, int i, int d)
+{
+    if (lat == FLBM_D2Q9) return d == 0 ? D2Q9::cx(i) : (d == 1 ? D2Q9::cy(i) : 0);
+    return d == 0 ? D3Q19::cx(i) : (d == 1 ? D3Q19::cy(i) : D3Q19::cz(i));
+}
+int lat_opp(int lat, int i) { return lat == FLBM_D2Q9 ? D2Q9::opp(i) : D3Q19::opp(i); }
+
+void default_rates(flbm_ctx *c)
+{
+    const double lam_d = c->tau[0] == c->tau[1] ? 1.0 / c->tau[0] : 2.0 / (c->tau[0] + c->tau[1]);
+    for (int s = 0; s < 2; s++)
+        for (int a = 0; a < kMaxQ; a++) c->lam[s][a] = a == 0 ? 0.0 : (a <= c->D ? lam_d : 1.0 / c->tau[s]);
+}
+
+StepParams make_params(const flbm_ctx *c)
+{
+    StepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nz = c->nz;
+    p.N = (int)c->N;
+    p.G = (float)c->G;
+    const double mu = 3.0 * c->kT; // k_B T / c_s^2
+    for (int s = 0; s < 2; s++)
+        for (int a = 0; a < c->Q; a++) {
+            const double lb = c->lam[s][a];
+            p.lam[s][a] = (float)lb;
+            p.hlam[s][a] = (float)(1.0 - 0.5 * lb);
+            p.noise_amp[s][a] = a > c->D ? (float)std::sqrt((2.0 * lb - lb * lb) * lat_N(c->lat, a) * mu) : 0.0f;
+        }
+    const double lb_d = c->lam[0][1];
+    p.noise_amp_j = c->sdf ? (float)std::sqrt((2.0 * lb_d - lb_d * lb_d) * c->kT) : 0.0f;
+    p.rho0[0] = (float)c->rho0[0];
+    p.rho0[1] = (float)c->rho0[1];
+    p.noise_ref = c->noise_ref;
+    p.force_velocity = c->force_velocity;
+    p.key0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
+    p.key1 = (uint32_t)(c->seed >> 32);
+    p.step = (uint32_t)c->step;
+    return p;
+}
+
+flbm_status ensure_stream(flbm_ctx *c)
+{
+    if (!c->stream) {
+        FLBM_CUDA(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    return FLBM_OK;
+}
+
+size_t pop_bytes_of(const flbm_ctx *c) { return (size_t)2 * c->Q * (size_t)c->N * storage_bytes(c->storage); }
+size_t rho_bytes_of(const flbm_ctx *c) { return (size_t)2 * (size_t)c->N * sizeof(float); }
+
+flbm_status ensure_status(flbm_ctx *c)
+{
+    if (!c->d_status) {
+        FLBM_CUDA(c, cudaMalloc(&c->d_status, sizeof(unsigned)), "cudaMalloc(status)");
+        FLBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "cudaMemset(status)");
+    }
+    return FLBM_OK;
+}
+
+flbm_status ensure_buffers(flbm_ctx *c)
+{
+    flbm_status st = ensure_stream(c);
+    if (st != FLBM_OK) return st;
+    if (!c->pop) {
+        c->pop_bytes = pop_bytes_of(c);
+        c->rho_bytes = rho_bytes_of(c);
+        cudaError_t e = cudaMalloc(&c->pop, c->pop_bytes);
+        if (e != cudaSuccess) {
+            c->pop = nullptr;
+            return fail(c, FLBM_ENOMEM, "cudaMalloc of %zu population bytes failed: %s", c->pop_bytes, cudaGetErrorString(e));
+        }
+        e = cudaMalloc((void **)&c->rho, c->rho_bytes);
+        if (e != cudaSuccess) {
+            cudaFree(c->pop);
+            c->pop = nullptr;
+            c->rho = nullptr;
+            return fail(c, FLBM_ENOMEM, "cudaMalloc of %zu density bytes failed: %s", c->rho_bytes, cudaGetErrorString(e));
+        }
+        c->own_buffers = true;
+    }
+    return ensure_status(c);
+}
+
+flbm_status ensure_stage(flbm_ctx *c)
+{
+    if (!c->h_stage) {
+        cudaError_t e = cudaMallocHost((void **)&c->h_stage, (size_t)2 * c->N * sizeof(float));
+        if (e != cudaSuccess) {
+            c->h_stage = nullptr;
+            return fail(c, FLBM_ENOMEM, "cudaMallocHost of the staging buffer failed: %s", cudaGetErrorString(e));
+        }
+    }
+    return FLBM_OK;
+}
+
+flbm_status ensure_obs(flbm_ctx *c)
+{
+    if (!c->d_obs) {
+        cudaError_t e = cudaMalloc((void **)&c->d_obs, (size_t)(2 + c->D) * c->N * sizeof(double));
+        if (e != cudaSuccess) {
+            c->d_obs = nullptr;
+            return fail(c, FLBM_ENOMEM, "cudaMalloc of the observables buffer failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!c->d_cons) FLBM_CUDA(c, cudaMalloc((void **)&c->d_cons, 5 * sizeof(double)), "cudaMalloc(cons)");
+    const size_t nb = (size_t)((c->nx + 127) / 128) * c->ny * c->nz;
+    if (c->partials_cap < nb) {
+        cudaFree(c->d_partials);
+        c->d_partials = nullptr;
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_partials, nb * 5 * sizeof(double)), "cudaMalloc(partials)");
+        c->partials_cap = nb;
+    }
+    return FLBM_OK;
+}
+
+int axis_len(const flbm_ctx *c, int axis) { return axis == 0 ? c->nx : (axis == 1 ? c->ny : c->nz); }
+
+flbm_status ensure_sf(flbm_ctx *c)
+{
+    if (!c->d_sf) {
+        const int n = axis_len(c, c->sf_axis);
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_sf, (size_t)4 * (n / 2) * sizeof(double)), "cudaMalloc(sf)");
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_profile, (size_t)(2 + c->D) * n * sizeof(double)), "cudaMalloc(profile)");
+        FLBM_CUDA(c, cudaMemsetAsync(c->d_sf, 0, (size_t)4 * (n / 2) * sizeof(double), c->stream), "cudaMemset(sf)");
+        c->sf_count = 0;
+    }
+    return FLBM_OK;
+}
+
+void free_sf(flbm_ctx *c)
+{
+    if (c->d_sf) cudaFree(c->d_sf);
+    if (c->d_profile) cudaFree(c->d_profile);
+    c->d_sf = nullptr;
+    c->d_profile = nullptr;
+    c->sf_count = 0;
+}
+
+// wait for the stream, then report device-side faults
+flbm_status sync_and_check(flbm_ctx *c)
+{
+    FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (c->d_status) {
+        unsigned h = 0;
+        FLBM_CUDA(c, cudaMemcpy(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost), "status read");
+        if (h & kStatusNonFinite) c->faulted = true;
+    }
+    if (c->faulted)
+        return fail(c, FLBM_ENONFINITE, "a density became non-positive or non-finite on the device (step <= %lld)",
+                    (long long)c->step);
+    return FLBM_OK;
+}
+
+// fold the recorded events into the per-kernel totals and recycle them
+flbm_status drain_timing(flbm_ctx *c)
+{
+    if (c->ev_used == 0) return FLBM_OK;
+    FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    // events come in triples: before density, between the kernels, after collide
+    for (size_t k = 0; k + 2 < c->ev_used; k += 3) {
+        float a = 0.0f, b = 0.0f;
+        FLBM_CUDA(c, cudaEventElapsedTime(&a, c->ev_pool[k], c->ev_pool[k + 1]), "cudaEventElapsedTime");
+        FLBM_CUDA(c, cudaEventElapsedTime(&b, c->ev_pool[k + 1], c->ev_pool[k + 2]), "cudaEventElapsedTime");
+        c->kernel_ms[0] += a;
+        c->kernel_ms[1] += b;
+        c->kernel_launches[0]++;
+        c->kernel_launches[1]++;
+    }
+    c->ev_used = 0;
+    return FLBM_OK;
+}
+
+flbm_status next_event(flbm_ctx *c, cudaEvent_t *ev)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        FLBM_CUDA(c, cudaEventCreate(&e), "cudaEventCreate");
+        c->ev_pool.push_back(e);
+    }
+    *ev = c->ev_pool[c->ev_used++];
+    return FLBM_OK;
+}
+
+flbm_status density_now(flbm_ctx *c, const StepParams &p)
+{
+    FLBM_CUDA(c, launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream), "density kernel launch");
+    return FLBM_OK;
+}
+
+// natural-layout population f_i(site) of species s from a raw host copy
+double raw_to_natural(const flbm_ctx *c, const std::vector<unsigned char> &raw, int s, int i, int64_t site)
+{
+    int64_t src = site;
+    int slot = i;
+    if (c->parity == 1) {
+        const int x = (int)(site % c->nx), y = (int)((site / c->nx) % c->ny), z = (int)(site / ((int64_t)c->nx * c->ny));
+        const int xs = (x - lat_c(c->lat, i, 0) + c->nx) % c->nx;
+        const int ys = (y - lat_c(c->lat, i, 1) + c->ny) % c->ny;
+        const int zs = (z - lat_c(c->lat, i, 2) + c->nz) % c->nz;
+        src = ((int64_t)zs * c->ny + ys) * c->nx + xs;
+        slot = lat_opp(c->lat, i);
+    }
+    const size_t idx = (size_t)(s * c->Q + slot) * (size_t)c->N + (size_t)src;
+    const float base = (float)lat_w(c->lat, i) * (float)c->rho0[s];
+    if (c->storage == FLBM_STORE_F32) {
+        float v;
+        std::memcpy(&v, raw.data() + idx * 4, 4);
+        return (double)v;
+    }
+    uint16_t bits;
+    std::memcpy(&bits, raw.data() + idx * 2, 2);
+    float dev;
+    if (c->storage == FLBM_STORE_F16) {
+        __half_raw hr;
+        hr.x = bits;
+        dev = __half2float(__half(hr));
+    } else {
+        __nv_bfloat16_raw br;
+        br.x = bits;
+        dev = __bfloat162float(__nv_bfloat16(br));
+    }
+    return (double)base + (double)dev;
+}
+
+uint64_t fnv1a(const unsigned char *p, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t k = 0; k < n; k++) {
+        h ^= p[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t lat, nx, ny, nz, storage, parity, sdf, noise_ref, force_velocity, sf_axis;
+    int64_t step;
+    uint64_t seed;
+    double tau[2], kT, G, rho0[2];
+    double lam[2][kMaxQ];
+    uint64_t payload_bytes;
+    uint64_t payload_hash;
+};
+
+} // namespace
+
+extern "C" {
+
+const char *flbm_version(void) { return "flbm 0.1 sm_103a"; }
+
+const char *flbm_last_error(const flbm_ctx *ctx) { return ctx ? ctx->err : kNoError; }
+
+flbm_status flbm_create(flbm_lattice lat, int nx, int ny, int nz, double tau_a, double tau_b, double kT,
+                        double G, uint64_t seed, flbm_ctx **out)
+{
+    if (!out) return FLBM_EINVAL;
+    *out = nullptr;
+    if (lat != FLBM_D2Q9 && lat != FLBM_D3Q19) return FLBM_EINVAL;
+    if (nx < 2 || ny < 2 || ny > 65535) return FLBM_EINVAL;
+    if (lat == FLBM_D2Q9 ? nz != 1 : (nz < 2 || nz > 65535)) return FLBM_EINVAL;
+    if ((int64_t)nx * ny * nz >= (int64_t(1) << 31)) return FLBM_EINVAL;
+    if (!(tau_a > 0.5) || !(tau_b > 0.5) || !std::isfinite(tau_a) || !std::isfinite(tau_b)) return FLBM_EINVAL;
+    if (!(kT >= 0.0) || !std::isfinite(kT) || !std::isfinite(G)) return FLBM_EINVAL;
+    flbm_ctx *c = new (std::nothrow) flbm_ctx();
+    if (!c) return FLBM_ENOMEM;
+    c->lat = lat;
+    c->D = lat == FLBM_D2Q9 ? 2 : 3;
+    c->Q = lat == FLBM_D2Q9 ? 9 : 19;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = (int64_t)nx * ny * nz;
+    c->tau[0] = tau_a;
+    c->tau[1] = tau_b;
+    c->kT = kT;
+    c->G = G;
+    c->seed = seed;
+    default_rates(c);
+    *out = c;
+    return FLBM_OK;
+}
+
+flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
+{
+    if (!c) return FLBM_EINVAL;
+    if (key == FLBM_OPT_STORAGE) {
+        if (c->pop) return fail(c, FLBM_ESTATE, "the storage format is fixed once the buffers exist");
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, FLBM_EINVAL, "storage must be 0 (f32), 1 (f16) or 2 (bf16)");
+        c->storage = (int)v;
+    } else if (key == FLBM_OPT_LAMBDA_D) {
+        if (!(v > 0.0 && v < 2.0)) return fail(c, FLBM_EINVAL, "lambda_d must lie in (0, 2)");
+        for (int s = 0; s < 2; s++)
+            for (int a = 1; a <= c->D; a++) c->lam[s][a] = v;
+    } else if (key == FLBM_OPT_SDF) {
+        c->sdf = v != 0.0;
+    } else if (key == FLBM_OPT_RHO0_A || key == FLBM_OPT_RHO0_B) {
+        if (!(v > 0.0) || !std::isfinite(v)) return fail(c, FLBM_EINVAL, "reference densities must be positive");
+        if (c->pop && c->storage != FLBM_STORE_F32)
+            return fail(c, FLBM_ESTATE, "the deviation base of 16-bit storage is fixed once the buffers exist");
+        c->rho0[key == FLBM_OPT_RHO0_A ? 0 : 1] = v;
+    } else if (key == FLBM_OPT_NOISE_RHO) {
+        c->noise_ref = v != 0.0;
+    } else if (key == FLBM_OPT_FORCE_VELOCITY) {
+        c->force_velocity = v != 0.0;
+    } else if (key == FLBM_OPT_SF_AXIS) {
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, FLBM_EINVAL, "axis must be 0, 1 or 2");
+        if ((int)v >= c->D) return fail(c, FLBM_EINVAL, "axis %d does not exist on this lattice", (int)v);
+        if ((int)v != c->sf_axis) {
+            free_sf(c);
+            c->sf_axis = (int)v;
+        }
+    } else if (key == FLBM_OPT_KERNEL_TIMING) {
+        if (c->stream) {
+            flbm_status st = drain_timing(c);
+            if (st != FLBM_OK) return st;
+        }
+        c->timing = v != 0.0;
+        c->kernel_ms[0] = c->kernel_ms[1] = 0.0;
+        c->kernel_launches[0] = c->kernel_launches[1] = 0;
+    } else if (key >= FLBM_OPT_LAMBDA_MODE && key < FLBM_OPT_LAMBDA_MODE + 200) {
+        const int s = (key - FLBM_OPT_LAMBDA_MODE) / 100, a = (key - FLBM_OPT_LAMBDA_MODE) % 100;
+        if (a <= c->D || a >= c->Q) return fail(c, FLBM_EINVAL, "mode %d is not a non-conserved mode", a);
+        if (!(v > 0.0 && v < 2.0)) return fail(c, FLBM_EINVAL, "rates must lie in (0, 2)");
+        c->lam[s][a] = v;
+    } else {
+        return fail(c, FLBM_EINVAL, "unknown option key %d", key);
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_set_stream(flbm_ctx *c, void *stream)
+{
+    if (!c) return FLBM_EINVAL;
+    if (c->own_stream && c->stream) {
+        cudaStreamSynchronize(c->stream);
+        cudaStreamDestroy(c->stream);
+    }
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->own_stream = false;
+    if (!stream) return ensure_stream(c);
+    return FLBM_OK;
+}
+
+flbm_status flbm_buffer_bytes(const flbm_ctx *c, size_t *pop_bytes, size_t *rho_bytes)
+{
+    if (!c) return FLBM_EINVAL;
+    if (pop_bytes) *pop_bytes = pop_bytes_of(c);
+    if (rho_bytes) *rho_bytes = rho_bytes_of(c);
+    return FLBM_OK;
+}
+
+flbm_status flbm_attach_buffers(flbm_ctx *c, void *pop, size_t pop_bytes, void *rho, size_t rho_bytes)
+{
+    if (!c) return FLBM_EINVAL;
+    if (c->pop) return fail(c, FLBM_ESTATE, "buffers already exist");
+    if (!pop || !rho) return fail(c, FLBM_EINVAL, "NULL buffer");
+    if (pop_bytes < pop_bytes_of(c) || rho_bytes < rho_bytes_of(c))
+        return fail(c, FLBM_EINVAL, "buffers too small: need %zu and %zu bytes", pop_bytes_of(c), rho_bytes_of(c));
+    if (((uintptr_t)pop % 256) != 0 || ((uintptr_t)rho % 256) != 0)
+        return fail(c, FLBM_EINVAL, "buffers must be 256-byte aligned");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, pop) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(c, FLBM_EINVAL, "population buffer is not device memory");
+    }
+    if (cudaPointerGetAttributes(&at, rho) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(c, FLBM_EINVAL, "density buffer is not device memory");
+    }
+    c->pop = pop;
+    c->pop_bytes = pop_bytes;
+    c->rho = static_cast<float *>(rho);
+    c->rho_bytes = rho_bytes;
+    c->own_buffers = false;
+    flbm_status st = ensure_stream(c);
+    if (st != FLBM_OK) return st;
+    return ensure_status(c);
+}
+
+flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
+{
+    if (!c) return FLBM_EINVAL;
+    flbm_status st = ensure_buffers(c);
+    if (st != FLBM_OK) return st;
+    if ((st = ensure_stage(c)) != FLBM_OK) return st;
+    // previous asynchronous work may still read the staging buffer
+    FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    const double *in[2] = {rho_a, rho_b};
+    for (int s = 0; s < 2; s++)
+        for (int64_t k = 0; k < c->N; k++) {
+            const double r = in[s] ? in[s][k] : c->rho0[s];
+            if (!(r > 0.0) || !std::isfinite(r)) return fail(c, FLBM_EINVAL, "initial density %g at site %lld is not positive", r, (long long)k);
+            c->h_stage[s * c->N + k] = (float)r;
+        }
+    FLBM_CUDA(c, cudaMemcpyAsync(c->rho, c->h_stage, (size_t)2 * c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream), "H2D densities");
+    const StepParams p = make_params(c);
+    FLBM_CUDA(c, launch_init_rest(c->lat, c->storage, p, c->rho, c->pop, c->stream), "init kernel launch");
+    FLBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "status reset");
+    c->step = 0;
+    c->parity = 0;
+    c->faulted = false;
+    c->initialised = true;
+    return FLBM_OK;
+}
+
+flbm_status flbm_step(flbm_ctx *c, int64_t n)
+{
+    if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
+    if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
+    StepParams p = make_params(c);
+    for (int64_t t = 0; t < n; t++) {
+        p.step = (uint32_t)c->step;
+        cudaEvent_t ev[3];
+        if (c->timing) {
+            // bound the number of outstanding events
+            if (c->ev_used + 3 > 3 * 4096) {
+                flbm_status st = drain_timing(c);
+                if (st != FLBM_OK) return st;
+            }
+            for (int k = 0; k < 3; k++) {
+                flbm_status st = next_event(c, &ev[k]);
+                if (st != FLBM_OK) return st;
+            }
+            FLBM_CUDA(c, cudaEventRecord(ev[0], c->stream), "cudaEventRecord");
+        }
+        cudaError_t e = launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
+        if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
+        e = launch_collide(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
+        if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[2], c->stream), "cudaEventRecord");
+        c->step++;
+        c->parity ^= 1;
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_sync(flbm_ctx *c)
+{
+    if (!c) return FLBM_EINVAL;
+    if (!c->stream) return FLBM_OK;
+    return sync_and_check(c);
+}
+
+flbm_status flbm_kernel_times(flbm_ctx *c, double ms[2], int64_t launches[2])
+{
+    if (!c) return FLBM_EINVAL;
+    if (c->stream) {
+        flbm_status st = drain_timing(c);
+        if (st != FLBM_OK) return st;
+    }
+    for (int k = 0; k < 2; k++) {
+        if (ms) ms[k] = c->kernel_ms[k];
+        if (launches) launches[k] = c->kernel_launches[k];
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_get_step(const flbm_ctx *c, int64_t *step)
+{
+    if (!c || !step) return FLBM_EINVAL;
+    *step = c->step;
+    return FLBM_OK;
+}
+
+flbm_status flbm_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, double *cons)
+{
+    if (!c) return FLBM_EINVAL;
+    if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_moments before flbm_init");
+    flbm_status st = ensure_obs(c);
+    if (st != FLBM_OK) return st;
+    const StepParams p = make_params(c);
+    if ((st = density_now(c, p)) != FLBM_OK) return st;
+    double *ra = c->d_obs, *rb = c->d_obs + c->N, *uu = c->d_obs + 2 * c->N;
+    int nb = 0;
+    FLBM_CUDA(c, launch_observables(c->lat, c->storage, c->parity, p, c->pop, c->rho, rho_a ? ra : nullptr,
+                                    rho_b ? rb : nullptr, u ? uu : nullptr, c->d_partials, &nb, c->stream),
+              "observables kernel launch");
+    FLBM_CUDA(c, launch_sum_partials(c->d_partials, nb, c->d_cons, c->stream), "reduction kernel launch");
+    if ((st = sync_and_check(c)) != FLBM_OK) return st;
+    if (rho_a) FLBM_CUDA(c, cudaMemcpy(rho_a, ra, c->N * sizeof(double), cudaMemcpyDeviceToHost), "D2H rho_a");
+    if (rho_b) FLBM_CUDA(c, cudaMemcpy(rho_b, rb, c->N * sizeof(double), cudaMemcpyDeviceToHost), "D2H rho_b");
+    if (u) FLBM_CUDA(c, cudaMemcpy(u, uu, (size_t)c->D * c->N * sizeof(double), cudaMemcpyDeviceToHost), "D2H u");
+    if (cons) FLBM_CUDA(c, cudaMemcpy(cons, c->d_cons, 5 * sizeof(double), cudaMemcpyDeviceToHost), "D2H cons");
+    return FLBM_OK;
+}
+
+flbm_status flbm_sf_sample(flbm_ctx *c)
+{
+    if (!c) return FLBM_EINVAL;
+    if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_sf_sample before flbm_init");
+    flbm_status st = ensure_obs(c);
+    if (st != FLBM_OK) return st;
+    if ((st = ensure_sf(c)) != FLBM_OK) return st;
+    const StepParams p = make_params(c);
+    if ((st = density_now(c, p)) != FLBM_OK) return st;
+    int nb = 0;
+    FLBM_CUDA(c, launch_observables(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_obs, c->d_obs + c->N,
+                                    c->d_obs + 2 * c->N, c->d_partials, &nb, c->stream),
+              "observables kernel launch");
+    FLBM_CUDA(c, launch_sf_accumulate(c->D, c->nx, c->ny, c->nz, c->sf_axis, c->d_obs, c->d_profile, c->d_sf, c->stream),
+              "structure-factor kernel launch");
+    if ((st = sync_and_check(c)) != FLBM_OK) return st;
+    c->sf_count++;
+    return FLBM_OK;
+}
+
+flbm_status flbm_structure_factor(flbm_ctx *c, int axis, int nk, double *S_aa, double *S_ab, double *S_bb,
+                                  double *S_uu, int64_t *nsamples)
+{
+    if (!c) return FLBM_EINVAL;
+    if (axis != c->sf_axis) return fail(c, FLBM_EINVAL, "axis %d differs from the sampled axis %d", axis, c->sf_axis);
+    const int half = axis_len(c, axis) / 2;
+    if (nk < 1 || nk > half) return fail(c, FLBM_EINVAL, "nk must lie in [1, %d]", half);
+    if (nsamples) *nsamples = c->sf_count;
+    if (!c->d_sf || c->sf_count == 0) return fail(c, FLBM_ESTATE, "no structure-factor snapshot taken");
+    flbm_status st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    std::vector<double> h((size_t)4 * half);
+    FLBM_CUDA(c, cudaMemcpy(h.data(), c->d_sf, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "D2H sf");
+    double *outs[4] = {S_aa, S_ab, S_bb, S_uu};
+    for (int q = 0; q < 4; q++)
+        if (outs[q])
+            for (int m = 0; m < nk; m++) outs[q][m] = h[(size_t)q * half + m] / (double)c->sf_count;
+    return FLBM_OK;
+}
+
+flbm_status flbm_sf_reset(flbm_ctx *c)
+{
+    if (!c) return FLBM_EINVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_sf(c);
+    return FLBM_OK;
+}
+
+flbm_status flbm_get_populations(flbm_ctx *c, double *f)
+{
+    if (!c || !f) return FLBM_EINVAL;
+    if (!c->initialised) return fail(c, FLBM_ESTATE, "no populations before flbm_init");
+    flbm_status st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    const size_t bytes = pop_bytes_of(c);
+    std::vector<unsigned char> raw(bytes);
+    FLBM_CUDA(c, cudaMemcpy(raw.data(), c->pop, bytes, cudaMemcpyDeviceToHost), "D2H populations");
+    for (int s = 0; s < 2; s++)
+        for (int i = 0; i < c->Q; i++)
+            for (int64_t site = 0; site < c->N; site++)
+                f[((size_t)s * c->Q + i) * c->N + site] = raw_to_natural(c, raw, s, i, site);
+    return FLBM_OK;
+}
+
+flbm_status flbm_set_populations(flbm_ctx *c, const double *f, int64_t step)
+{
+    if (!c || !f || step < 0) return FLBM_EINVAL;
+    flbm_status st = ensure_buffers(c);
+    if (st != FLBM_OK) return st;
+    FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    const size_t n = (size_t)2 * c->Q * c->N;
+    std::vector<unsigned char> raw(n * storage_bytes(c->storage));
+    for (int s = 0; s < 2; s++)
+        for (int i = 0; i < c->Q; i++) {
+            const float base = (float)lat_w(c->lat, i) * (float)c->rho0[s];
+            for (int64_t site = 0; site < c->N; site++) {
+                const size_t idx = ((size_t)s * c->Q + i) * c->N + site;
+                const double v = f[idx];
+                if (!std::isfinite(v)) return fail(c, FLBM_EINVAL, "non-finite population at index %zu", idx);
+                if (c->storage == FLBM_STORE_F32) {
+                    const float x = (float)v;
+                    std::memcpy(raw.data() + idx * 4, &x, 4);
+                } else if (c->storage == FLBM_STORE_F16) {
+                    const __half h = __float2half_rn((float)(v - (double)base));
+                    const __half_raw hr = h;
+                    std::memcpy(raw.data() + idx * 2, &hr.x, 2);
+                } else {
+                    const __nv_bfloat16 b = __float2bfloat16_rn((float)(v - (double)base));
+                    const __nv_bfloat16_raw br = b;
+                    std::memcpy(raw.data() + idx * 2, &br.x, 2);
+                }
+            }
+        }
+    FLBM_CUDA(c, cudaMemcpy(c->pop, raw.data(), raw.size(), cudaMemcpyHostToDevice), "H2D populations");
+    FLBM_CUDA(c, cudaMemset(c->d_status, 0, sizeof(unsigned)), "status reset");
+    c->step = step;
+    c->parity = 0;
+    c->faulted = false;
+    c->initialised = true;
+    return FLBM_OK;
+}
+
+flbm_status flbm_get_site_populations(flbm_ctx *c, const int64_t *sites, int64_t nsites, double *out)
+{
+    if (!c || (!sites && nsites) || (!out && nsites) || nsites < 0) return FLBM_EINVAL;
+    if (!c->initialised) return fail(c, FLBM_ESTATE, "no populations before flbm_init");
+    for (int64_t k = 0; k < nsites; k++)
+        if (sites[k] < 0 || sites[k] >= c->N) return fail(c, FLBM_EINVAL, "site index %lld out of range", (long long)sites[k]);
+    flbm_status st = sync_and_check(c);
+    if (st != FLBM_OK || nsites == 0) return st;
+    int64_t *d_sites = nullptr;
+    double *d_out = nullptr;
+    const size_t out_n = (size_t)nsites * 2 * c->Q;
+    cudaError_t e = cudaMalloc((void **)&d_sites, nsites * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_out, out_n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(d_sites, sites, nsites * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_gather_sites(c->lat, c->storage, c->parity, make_params(c), c->pop, d_sites, nsites, d_out, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, out_n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d_sites);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(c, e, "site gather");
+    return FLBM_OK;
+}
+
+flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
+{
+    if (!c || !bytes) return FLBM_EINVAL;
+    const size_t payload = pop_bytes_of(c);
+    const size_t need = sizeof(CkptHeader) + payload;
+    if (!buf) {
+        *bytes = need;
+        return FLBM_OK;
+    }
+    if (*bytes < need) return fail(c, FLBM_EINVAL, "checkpoint buffer too small: need %zu bytes", need);
+    if (!c->initialised) return fail(c, FLBM_ESTATE, "nothing to checkpoint before flbm_init");
+    flbm_status st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "FLBMCKP1", 8);
+    h.version = 1;
+    h.lat = c->lat;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.storage = c->storage;
+    h.parity = c->parity;
+    h.sdf = c->sdf;
+    h.noise_ref = c->noise_ref;
+    h.force_velocity = c->force_velocity;
+    h.sf_axis = c->sf_axis;
+    h.step = c->step;
+    h.seed = c->seed;
+    std::memcpy(h.tau, c->tau, sizeof(h.tau));
+    h.kT = c->kT;
+    h.G = c->G;
+    std::memcpy(h.rho0, c->rho0, sizeof(h.rho0));
+    std::memcpy(h.lam, c->lam, sizeof(h.lam));
+    h.payload_bytes = payload;
+    unsigned char *dst = static_cast<unsigned char *>(buf);
+    FLBM_CUDA(c, cudaMemcpy(dst + sizeof(CkptHeader), c->pop, payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
+    h.payload_hash = fnv1a(dst + sizeof(CkptHeader), payload);
+    std::memcpy(dst, &h, sizeof(h));
+    *bytes = need;
+    return FLBM_OK;
+}
+
+flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
+{
+    if (!c || !buf) return FLBM_EINVAL;
+    if (bytes < sizeof(CkptHeader)) return fail(c, FLBM_EINVAL, "checkpoint image too small");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 1) return fail(c, FLBM_EINVAL, "not a checkpoint image");
+    if (h.lat != c->lat || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz)
+        return fail(c, FLBM_EINVAL, "checkpoint lattice or box differs from this context");
+    if (c->pop && h.storage != c->storage) return fail(c, FLBM_EINVAL, "checkpoint storage format differs");
+    const size_t payload = (size_t)2 * c->Q * (size_t)c->N * storage_bytes(h.storage);
+    if (h.payload_bytes != payload || bytes < sizeof(CkptHeader) + payload)
+        return fail(c, FLBM_EINVAL, "checkpoint image truncated");
+    const unsigned char *src = static_cast<const unsigned char *>(buf) + sizeof(CkptHeader);
+    if (fnv1a(src, payload) != h.payload_hash) return fail(c, FLBM_EINVAL, "checkpoint image corrupt (hash mismatch)");
+    c->storage = h.storage;
+    std::memcpy(c->rho0, h.rho0, sizeof(h.rho0));
+    flbm_status st = ensure_buffers(c);
+    if (st != FLBM_OK) return st;
+    FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    FLBM_CUDA(c, cudaMemcpy(c->pop, src, payload, cudaMemcpyHostToDevice), "H2D checkpoint");
+    FLBM_CUDA(c, cudaMemset(c->d_status, 0, sizeof(unsigned)), "status reset");
+    c->parity = h.parity;
+    c->step = h.step;
+    c->seed = h.seed;
+    c->tau[0] = h.tau[0];
+    c->tau[1] = h.tau[1];
+    c->kT = h.kT;
+    c->G = h.G;
+    c->sdf = h.sdf;
+    c->noise_ref = h.noise_ref;
+    c->force_velocity = h.force_velocity;
+    std::memcpy(c->lam, h.lam, sizeof(h.lam));
+    if (h.sf_axis != c->sf_axis) {
+        free_sf(c);
+        c->sf_axis = h.sf_axis;
+    }
+    c->faulted = false;
+    c->initialised = true;
+    return FLBM_OK;
+}
+
+void flbm_destroy(flbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own_buffers) {
+        if (c->pop) cudaFree(c->pop);
+        if (c->rho) cudaFree(c->rho);
+    }
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->d_obs) cudaFree(c->d_obs);
+    if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_cons) cudaFree(c->d_cons);
+    free_sf(c);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+} // extern "C"

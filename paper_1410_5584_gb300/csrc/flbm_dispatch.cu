@@ -1,0 +1,71 @@
+// flbm_dispatch.cu -- run-time dispatch from (lattice, storage) to the kernel
+// instances of flbm_kernels.cuh.
+#include "flbm_launch.h"
+
+namespace flbm {
+
+namespace {
+
+template <template <class, class> class F, class... A>
+cudaError_t dispatch(int lat, int storage, A &&...args)
+{
+    if (lat == FLBM_D2Q9) {
+        if (storage == FLBM_STORE_F32) return F<D2Q9, StoreF32>::run(args...);
+        if (storage == FLBM_STORE_F16) return F<D2Q9, StoreF16>::run(args...);
+        return F<D2Q9, StoreBF16>::run(args...);
+    }
+    if (storage == FLBM_STORE_F32) return F<D3Q19, StoreF32>::run(args...);
+    if (storage == FLBM_STORE_F16) return F<D3Q19, StoreF16>::run(args...);
+    return F<D3Q19, StoreBF16>::run(args...);
+}
+
+template <class L, class S> struct DensityF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::density(a...); }
+};
+template <class L, class S> struct CollideF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::collide(a...); }
+};
+template <class L, class S> struct InitF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::init_rest(a...); }
+};
+template <class L, class S> struct GatherF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::gather(a...); }
+};
+template <class L, class S> struct ObsF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::observables(a...); }
+};
+
+} // namespace
+
+cudaError_t launch_density(int lat, int storage, int parity, const StepParams &p, const void *pop, float *rho,
+                           cudaStream_t stream)
+{
+    return dispatch<DensityF>(lat, storage, parity, p, pop, rho, stream);
+}
+
+cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop, const float *rho,
+                           unsigned *status, cudaStream_t stream)
+{
+    return dispatch<CollideF>(lat, storage, parity, p, pop, rho, status, stream);
+}
+
+cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in, void *pop,
+                             cudaStream_t stream)
+{
+    return dispatch<InitF>(lat, storage, p, rho_in, pop, stream);
+}
+
+cudaError_t launch_gather_sites(int lat, int storage, int parity, const StepParams &p, const void *pop,
+                                const int64_t *sites, int64_t nsites, double *out, cudaStream_t stream)
+{
+    return dispatch<GatherF>(lat, storage, parity, p, pop, sites, nsites, out, stream);
+}
+
+cudaError_t launch_observables(int lat, int storage, int parity, const StepParams &p, const void *pop,
+                               const float *rho, double *rho_a, double *rho_b, double *u, double *partials,
+                               int *nblocks, cudaStream_t stream)
+{
+    return dispatch<ObsF>(lat, storage, parity, p, pop, rho, rho_a, rho_b, u, partials, nblocks, stream);
+}
+
+} // namespace flbm

@@ -1,0 +1,118 @@
+// flbm_internal.h -- shared definitions of the CUDA library (not installed).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "flbm.h"
+
+namespace flbm {
+
+constexpr int kMaxQ = 19;
+
+// Everything one step kernel needs, passed by value (kernel parameter space).
+struct StepParams {
+    int nx, ny, nz;
+    int N;                     // nx * ny * nz  (< 2^31)
+    float G;                   // inter-species coupling, Eq. FORCESTRUCTURE
+    float lam[2][kMaxQ];       // lambdabar_a per species (lam[s][1..D] = lambdabar_d)
+    float hlam[2][kMaxQ];      // 1 - lambdabar_a / 2  (Eq. forcerenorm)
+    float noise_amp[2][kMaxQ]; // a > D: sqrt((2 lb_a - lb_a^2) N_a kT / c_s^2); times sqrt(rho^s)
+    float noise_amp_j;         // sqrt((2 lb_d - lb_d^2) kT); times sqrt(rho rho'/rho_t); 0 = no-sdf
+    float rho0[2];             // reference densities: 16-bit deviation base, noise reference
+    int noise_ref;             // 1: noise amplitudes from rho0 instead of the local densities
+    int force_velocity;        // 0: rho v = jbar + R_j/2 ; 1: v = vbar + a/2
+    uint32_t key0, key1;       // Philox key (seed low, seed high)
+    uint32_t step;             // noise counter word for this step
+};
+
+// Device status bits (ORed by kernels, read by the host at sync points).
+constexpr unsigned kStatusNonFinite = 1u;
+
+// ---------------------------------------------------------------------------
+// Population storage.  Kernels work with deviations delta_i = f_i - w_i rho0^s:
+// for float storage the subtraction is (nearly always) exact and keeps the
+// small non-conserved moments free of cancellation; the 16-bit formats store
+// the deviation itself.
+// ---------------------------------------------------------------------------
+struct StoreF32 {
+    using T = float;
+    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
+    {
+        return __ldg(p + idx) - base;
+    }
+    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float base)
+    {
+        p[idx] = base + dev;
+    }
+};
+
+struct StoreF16 {
+    using T = __half;
+    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float)
+    {
+        return __half2float(p[idx]);
+    }
+    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float)
+    {
+        p[idx] = __float2half_rn(dev);
+    }
+};
+
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float)
+    {
+        return __bfloat162float(p[idx]);
+    }
+    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float)
+    {
+        p[idx] = __float2bfloat16_rn(dev);
+    }
+};
+
+inline size_t storage_bytes(int storage) { return storage == FLBM_STORE_F32 ? 4 : 2; }
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files).  All are asynchronous on `stream` and
+// return the launch error.
+// ---------------------------------------------------------------------------
+
+// Density pass: rho[s * N + site] = rho0^s + sum_i delta_i^s(site), reading the
+// populations according to the in-place streaming parity.
+cudaError_t launch_density(int lat, int storage, int parity, const StepParams &p, const void *pop,
+                           float *rho, cudaStream_t stream);
+
+// Fused force + moment collision + noise + in-place streaming of one step.
+cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop,
+                           const float *rho, unsigned *status, cudaStream_t stream);
+
+// Per-site observables in double: rho_a, rho_b, u (D planes), any may be NULL,
+// plus per-block FP64 partial totals [nblocks][5] into `partials`; returns the
+// block count in *nblocks.  Needs the density field of the current state.
+cudaError_t launch_observables(int lat, int storage, int parity, const StepParams &p,
+                               const void *pop, const float *rho, double *rho_a, double *rho_b,
+                               double *u, double *partials, int *nblocks, cudaStream_t stream);
+
+// Fixed-order sum of [nblocks][5] partials into out[5].
+cudaError_t launch_sum_partials(const double *partials, int nblocks, double *out,
+                                cudaStream_t stream);
+
+// Structure-factor snapshot: profiles of (rho_a, rho_b, u_0..u_{D-1}) along
+// `axis` (per-site doubles in `obs`, component-major), their DFT at
+// k_m = 2 pi m / n_axis, m = 1..n_axis/2, accumulated into acc[4][n_axis/2].
+cudaError_t launch_sf_accumulate(int D, int nx, int ny, int nz, int axis, const double *obs,
+                                 double *profile, double *acc, cudaStream_t stream);
+
+// Rest-state populations from a float density field (two planes of N).
+cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in,
+                             void *pop, cudaStream_t stream);
+
+// Natural-layout gather of selected sites: out[k][s][i] (doubles).
+cudaError_t launch_gather_sites(int lat, int storage, int parity, const StepParams &p,
+                                const void *pop, const int64_t *sites, int64_t nsites, double *out,
+                                cudaStream_t stream);
+
+} // namespace flbm

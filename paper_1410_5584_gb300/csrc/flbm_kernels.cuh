@@ -1,0 +1,393 @@
+// flbm_kernels.cuh -- kernel templates of the library, instantiated once per
+// (lattice, storage) pair in the inst_*.cu translation units.
+//
+// The per-step update is the fluctuating two-species lattice Boltzmann
+// equation of arXiv 1410.5584 (Sec. V B, Eqs. algorithm and lattice
+// finalstep) with in-place "AA" streaming:
+//   parity 0 (natural layout, A[s][i][x] = f_i(x)):   read A[s][i][x],
+//       write the post-collision f*_i(x) to A[s][opp i][x] (same site);
+//   parity 1 (swapped layout, A[s][opp i][x] = f*_i(x) of the previous step):
+//       read f_i(x) = A[s][opp i][x - c_i], write f*_i(x) to A[s][i][x + c_i].
+// After a parity-1 step the array is back in the natural layout.  Every array
+// slot is read and written by exactly one thread, so the update is race-free.
+#pragma once
+#include "flbm_internal.h"
+#include "flbm_lattice.cuh"
+#include "flbm_launch.h"
+#include "flbm_noise.cuh"
+
+namespace flbm {
+namespace kern {
+
+constexpr int kObsBlock = 128;
+
+
+// periodic neighbour indices of one site
+struct Nbr {
+    int xs[3], ys[3], zs[3];
+    int nx, ny;
+    __device__ __forceinline__ int at(int dx, int dy, int dz) const
+    {
+        return (zs[dz + 1] * ny + ys[dy + 1]) * nx + xs[dx + 1];
+    }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const StepParams &p, int x, int y, int z)
+{
+    Nbr n;
+    n.nx = p.nx;
+    n.ny = p.ny;
+    n.xs[0] = x == 0 ? p.nx - 1 : x - 1;
+    n.xs[1] = x;
+    n.xs[2] = x == p.nx - 1 ? 0 : x + 1;
+    n.ys[0] = y == 0 ? p.ny - 1 : y - 1;
+    n.ys[1] = y;
+    n.ys[2] = y == p.ny - 1 ? 0 : y + 1;
+    n.zs[0] = z == 0 ? p.nz - 1 : z - 1;
+    n.zs[1] = z;
+    n.zs[2] = z == p.nz - 1 ? 0 : z + 1;
+    return n;
+}
+
+template <class L> __device__ __forceinline__ constexpr float wf(int i) { return (float)L::wd(i); }
+template <class L> __device__ __forceinline__ constexpr float invNf(int a) { return (float)(1.0 / L::Nd(a)); }
+
+// array index of the population f_i(site) that the current step reads
+template <class L, int PARITY>
+__device__ __forceinline__ size_t read_index(const Nbr &nb, size_t NN, int s, int i)
+{
+    if (PARITY == 0) return (size_t)(s * L::Q + i) * NN + nb.at(0, 0, 0);
+    return (size_t)(s * L::Q + L::opp(i)) * NN + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+}
+
+// array index where the post-collision f*_i(site) is written
+template <class L, int PARITY>
+__device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s, int i)
+{
+    if (PARITY == 0) return (size_t)(s * L::Q + L::opp(i)) * NN + nb.at(0, 0, 0);
+    return (size_t)(s * L::Q + i) * NN + nb.at(L::cx(i), L::cy(i), L::cz(i));
+}
+
+// deviation moments m_a = sum_i T_ai delta_i (m_0 = rho - rho0)
+template <class L>
+__device__ __forceinline__ void project(const float *d, float *m)
+{
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) {
+            if (L::T(a, i) == 1) s += d[i];
+            else if (L::T(a, i) == -1) s -= d[i];
+            else if (L::T(a, i) != 0) s += (float)L::T(a, i) * d[i];
+        }
+        m[a] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// density pass
+// ---------------------------------------------------------------------------
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_density(const StepParams p, const typename S::T *__restrict__ pop,
+                                                 float *__restrict__ rho)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+    const size_t NN = (size_t)p.N;
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            sum += S::load_dev(pop, read_index<L, PARITY>(nb, NN, s, i), wf<L>(i) * p.rho0[s]);
+        rho[(size_t)s * NN + nb.at(0, 0, 0)] = p.rho0[s] + sum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused force + moment collision + noise + streaming
+// ---------------------------------------------------------------------------
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S::T *__restrict__ pop,
+                                                 const float *__restrict__ rho, unsigned *__restrict__ status)
+{
+    constexpr int Q = L::Q, D = L::D;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+    const size_t NN = (size_t)p.N;
+    const int site = nb.at(0, 0, 0);
+
+    // 1. moments of both species (Eq. modes-discrete), density rho = rhobar
+    float m[2][Q], rs[2];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        float d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; i++) d[i] = S::load_dev(pop, read_index<L, PARITY>(nb, NN, s, i), wf<L>(i) * p.rho0[s]);
+        project<L>(d, m[s]);
+        rs[s] = p.rho0[s] + m[s][0];
+    }
+
+    // 2. Shan-Chen force from the other species' neighbour densities (Eq. FORCESTRUCTURE)
+    float acc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const int ns = nb.at(L::cx(i), L::cy(i), L::cz(i));
+        const float ra = __ldg(rho + ns), rb = __ldg(rho + NN + ns);
+        const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            if (c[d] != 0) {
+                acc[0][d] += (float)c[d] * wf<L>(i) * rb;
+                acc[1][d] += (float)c[d] * wf<L>(i) * ra;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int d = 0; d < D; d++) acc[s][d] *= -p.G;
+
+    // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
+    const float rt = rs[0] + rs[1];
+    const float irt = 1.0f / rt;
+    float u[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int d = 0; d < D; d++)
+        u[d] = (m[0][1 + d] + m[1][1 + d] + 0.5f * (rs[0] * acc[0][d] + rs[1] * acc[1][d])) * irt;
+    if (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt)) atomicOr(status, kStatusNonFinite);
+
+    // 4. noise amplitudes of Eq. new-noise (local or reference densities)
+    const float n0 = p.noise_ref ? p.rho0[0] : rs[0];
+    const float n1 = p.noise_ref ? p.rho0[1] : rs[1];
+    float g[2][Q];
+    draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, g[0]);
+    draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, g[1]);
+    const float amp_j = p.noise_amp_j * sqrtf(n0 * n1 / (n0 + n1));
+    const float sq[2] = {sqrtf(n0), sqrtf(n1)};
+
+    // 5. momentum modes: common rate, opposite noise; species velocity for Phi
+    float v[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const float irs = 1.0f / rs[s];
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            const int a = 1 + d;
+            const float xi = (s == 0 ? amp_j : -amp_j) * g[0][a];
+            const float R = p.lam[s][a] * (rs[s] * u[d] - m[s][a]) + p.hlam[s][a] * rs[s] * acc[s][d] + xi;
+            v[s][d] = p.force_velocity ? m[s][a] * irs + 0.5f * acc[s][d] : (m[s][a] + 0.5f * R) * irs;
+            m[s][a] += R;
+        }
+    }
+
+    // 6. transport and ghost modes, then back-projection and streaming
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        float meq[Q], phi[Q];
+        Closure<L>::eq_force(rs[s], u, acc[s], v[s], meq, phi);
+#pragma unroll
+        for (int a = D + 1; a < Q; a++)
+            m[s][a] += p.lam[s][a] * (meq[a] - m[s][a]) + p.hlam[s][a] * phi[a] +
+                       p.noise_amp[s][a] * sq[s] * g[s][a];
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            float acc_i = 0.0f;
+#pragma unroll
+            for (int a = 0; a < Q; a++) {
+                if (L::T(a, i) != 0) acc_i += (float)L::T(a, i) * invNf<L>(a) * m[s][a];
+            }
+            S::store_dev(pop, write_index<L, PARITY>(nb, NN, s, i), wf<L>(i) * acc_i, wf<L>(i) * p.rho0[s]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// rest-state initialisation and site gather
+// ---------------------------------------------------------------------------
+template <class L, class S>
+__global__ void k_init_rest(const StepParams p, const float *__restrict__ rho_in, typename S::T *__restrict__ pop)
+{
+    const size_t NN = (size_t)p.N;
+    for (size_t site = blockIdx.x * (size_t)blockDim.x + threadIdx.x; site < NN; site += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const float r = rho_in[(size_t)s * NN + site];
+#pragma unroll
+            for (int i = 0; i < L::Q; i++)
+                S::store_dev(pop, (size_t)(s * L::Q + i) * NN + site, wf<L>(i) * (r - p.rho0[s]), wf<L>(i) * p.rho0[s]);
+        }
+    }
+}
+
+template <class L, class S, int PARITY>
+__global__ void k_gather_sites(const StepParams p, const typename S::T *__restrict__ pop,
+                               const int64_t *__restrict__ sites, int64_t nsites, double *__restrict__ out)
+{
+    const size_t NN = (size_t)p.N;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nsites; k += (int64_t)gridDim.x * blockDim.x) {
+        const int site = (int)sites[k];
+        const int x = site % p.nx, y = (site / p.nx) % p.ny, z = site / (p.nx * p.ny);
+        const Nbr nb = make_nbr(p, x, y, z);
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int i = 0; i < L::Q; i++) {
+                const float base = wf<L>(i) * p.rho0[s];
+                const float dev = S::load_dev(pop, read_index<L, PARITY>(nb, NN, s, i), base);
+                out[(k * 2 + s) * L::Q + i] = (double)base + (double)dev;
+            }
+    }
+}
+
+
+// fixed-order block reduction of NV doubles per thread; result valid in thread 0
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV])
+{
+    const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+#pragma unroll
+    for (int k = 0; k < NV; k++) sh[t][k] = v[k];
+    __syncthreads();
+    for (int stride = NT / 2; stride > 0; stride >>= 1) {
+        if (t < stride)
+#pragma unroll
+            for (int k = 0; k < NV; k++) sh[t][k] += sh[t + stride][k];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = sh[0][k];
+}
+
+template <class L> __device__ __forceinline__ constexpr double wdd(int i) { return L::wd(i); }
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, const typename S::T *__restrict__ pop,
+                                                           const float *__restrict__ rho, double *__restrict__ rho_a,
+                                                           double *__restrict__ rho_b, double *__restrict__ u,
+                                                           double *__restrict__ partials)
+{
+    constexpr int Q = L::Q, D = L::D;
+    __shared__ double sh[kObsBlock][5];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (x < p.nx) {
+        const int xs[3] = {x == 0 ? p.nx - 1 : x - 1, x, x == p.nx - 1 ? 0 : x + 1};
+        const int ys[3] = {y == 0 ? p.ny - 1 : y - 1, y, y == p.ny - 1 ? 0 : y + 1};
+        const int zs[3] = {z == 0 ? p.nz - 1 : z - 1, z, z == p.nz - 1 ? 0 : z + 1};
+        auto at = [&](int dx, int dy, int dz) { return (zs[dz + 1] * p.ny + ys[dy + 1]) * p.nx + xs[dx + 1]; };
+        const size_t NN = (size_t)p.N;
+        const int site = at(0, 0, 0);
+        double r[2], j[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, a[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            double sum = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const size_t idx = PARITY == 0
+                                       ? (size_t)(s * Q + i) * NN + site
+                                       : (size_t)(s * Q + L::opp(i)) * NN + at(-L::cx(i), -L::cy(i), -L::cz(i));
+                const double dv = (double)S::load_dev(pop, idx, (float)L::wd(i) * p.rho0[s]);
+                sum += dv;
+                j[s][0] += L::cx(i) * dv;
+                j[s][1] += L::cy(i) * dv;
+                j[s][2] += L::cz(i) * dv;
+            }
+            r[s] = (double)p.rho0[s] + sum;
+        }
+        // force with the density field (the same values the step kernel uses)
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+            const int ns = at(L::cx(i), L::cy(i), L::cz(i));
+            const double ra = rho[ns], rb = rho[NN + ns];
+            a[0][0] += wdd<L>(i) * L::cx(i) * rb;
+            a[0][1] += wdd<L>(i) * L::cy(i) * rb;
+            a[0][2] += wdd<L>(i) * L::cz(i) * rb;
+            a[1][0] += wdd<L>(i) * L::cx(i) * ra;
+            a[1][1] += wdd<L>(i) * L::cy(i) * ra;
+            a[1][2] += wdd<L>(i) * L::cz(i) * ra;
+        }
+        const double ra0 = rho[site], rb0 = rho[NN + site];
+        const double rt = r[0] + r[1];
+        if (rho_a) rho_a[site] = r[0];
+        if (rho_b) rho_b[site] = r[1];
+        tot[0] = r[0];
+        tot[1] = r[1];
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            const double Ft = -(double)p.G * (ra0 * a[0][d] + rb0 * a[1][d]);
+            const double jt = j[0][d] + j[1][d] + 0.5 * Ft;
+            if (u) u[(size_t)d * NN + site] = jt / rt;
+            tot[2 + d] = jt;
+        }
+    }
+    block_sum<5, kObsBlock>(tot, sh);
+    if (threadIdx.x == 0) {
+        const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+#pragma unroll
+        for (int k = 0; k < 5; k++) partials[b * 5 + k] = tot[k];
+    }
+}
+
+
+inline dim3 site_block(int nx) { return dim3(nx >= 128 ? 128 : ((nx + 31) / 32) * 32); }
+inline dim3 site_grid(const StepParams &p, dim3 blk) { return dim3((p.nx + blk.x - 1) / blk.x, p.ny, p.nz); }
+
+} // namespace kern
+
+template <class L, class S>
+cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *pop, float *rho, cudaStream_t st)
+{
+    const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
+    auto *ptr = static_cast<const typename S::T *>(pop);
+    if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, ptr, rho);
+    else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, ptr, rho);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, const float *rho, unsigned *status,
+                                  cudaStream_t st)
+{
+    const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
+    auto *ptr = static_cast<typename S::T *>(pop);
+    if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, ptr, rho, status);
+    else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, ptr, rho, status);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st)
+{
+    kern::k_init_rest<L, S><<<1024, 256, 0, st>>>(p, rho_in, static_cast<typename S::T *>(pop));
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::gather(int parity, const StepParams &p, const void *pop, const int64_t *sites, int64_t n,
+                                 double *out, cudaStream_t st)
+{
+    auto *ptr = static_cast<const typename S::T *>(pop);
+    const int blocks = (int)((n + 127) / 128);
+    if (parity == 0) kern::k_gather_sites<L, S, 0><<<blocks, 128, 0, st>>>(p, ptr, sites, n, out);
+    else kern::k_gather_sites<L, S, 1><<<blocks, 128, 0, st>>>(p, ptr, sites, n, out);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::observables(int parity, const StepParams &p, const void *pop, const float *rho, double *ra,
+                                      double *rb, double *u, double *partials, int *nblocks, cudaStream_t st)
+{
+    const dim3 b(kern::kObsBlock), g((p.nx + kern::kObsBlock - 1) / kern::kObsBlock, p.ny, p.nz);
+    *nblocks = (int)(g.x * g.y * g.z);
+    auto *ptr = static_cast<const typename S::T *>(pop);
+    if (parity == 0) kern::k_observables<L, S, 0><<<g, b, 0, st>>>(p, ptr, rho, ra, rb, u, partials);
+    else kern::k_observables<L, S, 1><<<g, b, 0, st>>>(p, ptr, rho, ra, rb, u, partials);
+    return cudaGetLastError();
+}
+
+} // namespace flbm

@@ -1,0 +1,171 @@
+// flbm_lattice.cuh -- velocity sets, moment bases and closed-form equilibrium and
+// forcing moments of the two lattices (compile-time constants).
+//
+// D2Q9: the basis of Table I (arXiv 1410.5584, Sec. VI), c_s^2 = 1/3.
+// D3Q19: not in the paper.  Standard D3Q19 velocities and weights; rows 0-9 are
+// the Hermite modes of order <= 2 (Eq. setofT: 1, c, c c - c_s^2 I in the
+// bulk/shear combinations below), rows 10-18 an orthogonal ghost completion.
+//
+// Everything here is constexpr so that, inside fully unrolled loops, the
+// 0/+-1/+-2 structure of T folds into straight-line adds.
+#pragma once
+
+namespace flbm {
+
+struct D2Q9 {
+    static constexpr int D = 2;
+    static constexpr int Q = 9;
+    // velocity order: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+    __host__ __device__ static constexpr int cx(int i)
+    {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i)
+    {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    // opposite pairs: 1-3, 2-4, 5-7, 6-8
+    __host__ __device__ static constexpr int opp(int i)
+    {
+        return i == 0 ? 0 : (i <= 4 ? (i <= 2 ? i + 2 : i - 2) : (i <= 6 ? i + 2 : i - 2));
+    }
+    // Gauss-Hermite weights: 4/9 rest, 1/9 axis, 1/36 diagonal
+    __host__ __device__ static constexpr double wd(int i)
+    {
+        return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    // rows of Table I, integer valued
+    __host__ __device__ static constexpr int T(int a, int i)
+    {
+        const int x = cx(i), y = cy(i), c2 = x * x + y * y;
+        return a == 0 ? 1
+             : a == 1 ? x
+             : a == 2 ? y
+             : a == 3 ? 3 * c2 - 2
+             : a == 4 ? 2 * x * x - c2
+             : a == 5 ? x * y
+             : a == 6 ? (3 * c2 - 4) * x
+             : a == 7 ? (3 * c2 - 4) * y
+             :          9 * c2 * c2 - 15 * c2 + 2;
+    }
+    // squared norms of Table I
+    __host__ __device__ static constexpr double Nd(int a)
+    {
+        return a == 0 ? 1.0
+             : a <= 2 ? 1.0 / 3.0
+             : a == 3 ? 4.0
+             : a == 4 ? 4.0 / 9.0
+             : a == 5 ? 1.0 / 9.0
+             : a <= 7 ? 2.0 / 3.0
+             :          16.0;
+    }
+};
+
+struct D3Q19 {
+    static constexpr int D = 3;
+    static constexpr int Q = 19;
+    // velocity order: rest; +-x, +-y, +-z; then the 12 edges in opposite pairs
+    __host__ __device__ static constexpr int cx(int i)
+    {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+             : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int i)
+    {
+        return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+             : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int i)
+    {
+        return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+             : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+    }
+    // opposite directions are stored in adjacent pairs (1,2), (3,4), ..., (17,18)
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    __host__ __device__ static constexpr double wd(int i)
+    {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+    __host__ __device__ static constexpr int T(int a, int i)
+    {
+        const int x = cx(i), y = cy(i), z = cz(i);
+        const int c2 = x * x + y * y + z * z;
+        return a == 0  ? 1
+             : a == 1  ? x
+             : a == 2  ? y
+             : a == 3  ? z
+             : a == 4  ? c2 - 1
+             : a == 5  ? 2 * x * x - y * y - z * z
+             : a == 6  ? y * y - z * z
+             : a == 7  ? x * y
+             : a == 8  ? y * z
+             : a == 9  ? x * z
+             : a == 10 ? (3 * c2 - 5) * x
+             : a == 11 ? (3 * c2 - 5) * y
+             : a == 12 ? (3 * c2 - 5) * z
+             : a == 13 ? x * (y * y - z * z)
+             : a == 14 ? y * (z * z - x * x)
+             : a == 15 ? z * (x * x - y * y)
+             : a == 16 ? 3 * c2 * c2 - 6 * c2 + 1
+             : a == 17 ? (2 * c2 - 3) * (2 * x * x - y * y - z * z)
+             :           (2 * c2 - 3) * (y * y - z * z);
+    }
+    // N_a = sum_i w_i T_ai^2, evaluated at compile time
+    __host__ __device__ static constexpr double Nd(int a)
+    {
+        double s = 0.0;
+        for (int i = 0; i < Q; i++) s += wd(i) * T(a, i) * T(a, i);
+        return s;
+    }
+};
+
+// Closed-form equilibrium moments m^eq_a(rho, u) of the second-order Hermite
+// equilibrium (Table I column for D2Q9; for D3Q19 the Hermite rows give
+// rho, rho u, rho |u|^2, rho (2ux^2 - uy^2 - uz^2), rho (uy^2 - uz^2), rho u_a u_b),
+// and forcing moments Phi_a(rho, a, v) of Eq. hermite-for truncated at second
+// order: Phi_ab = rho (a_a v_b + v_a a_b) projected on the same rows; ghosts 0.
+// Only rows a > D are produced (the momentum rows are handled separately).
+template <class L> struct Closure;
+
+template <> struct Closure<D2Q9> {
+    __device__ __forceinline__ static void eq_force(float rho, const float *u, const float *a,
+                                                    const float *v, float *meq, float *phi)
+    {
+        const float uxx = u[0] * u[0], uyy = u[1] * u[1];
+        meq[3] = 3.0f * rho * (uxx + uyy);
+        meq[4] = rho * (uxx - uyy);
+        meq[5] = rho * u[0] * u[1];
+        meq[6] = meq[7] = meq[8] = 0.0f;
+        const float axvx = a[0] * v[0], ayvy = a[1] * v[1];
+        phi[3] = 6.0f * rho * (axvx + ayvy);
+        phi[4] = 2.0f * rho * (axvx - ayvy);
+        phi[5] = rho * (a[0] * v[1] + a[1] * v[0]);
+        phi[6] = phi[7] = phi[8] = 0.0f;
+    }
+};
+
+template <> struct Closure<D3Q19> {
+    __device__ __forceinline__ static void eq_force(float rho, const float *u, const float *a,
+                                                    const float *v, float *meq, float *phi)
+    {
+        const float uxx = u[0] * u[0], uyy = u[1] * u[1], uzz = u[2] * u[2];
+        meq[4] = rho * (uxx + uyy + uzz);
+        meq[5] = rho * (2.0f * uxx - uyy - uzz);
+        meq[6] = rho * (uyy - uzz);
+        meq[7] = rho * u[0] * u[1];
+        meq[8] = rho * u[1] * u[2];
+        meq[9] = rho * u[0] * u[2];
+        const float pxx = 2.0f * a[0] * v[0], pyy = 2.0f * a[1] * v[1], pzz = 2.0f * a[2] * v[2];
+        phi[4] = rho * (pxx + pyy + pzz);
+        phi[5] = rho * (2.0f * pxx - pyy - pzz);
+        phi[6] = rho * (pyy - pzz);
+        phi[7] = rho * (a[0] * v[1] + a[1] * v[0]);
+        phi[8] = rho * (a[1] * v[2] + a[2] * v[1]);
+        phi[9] = rho * (a[0] * v[2] + a[2] * v[0]);
+#pragma unroll
+        for (int k = 10; k < 19; k++) meq[k] = phi[k] = 0.0f;
+    }
+};
+
+} // namespace flbm

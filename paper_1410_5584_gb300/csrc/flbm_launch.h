@@ -1,0 +1,27 @@
+// flbm_launch.h -- per-(lattice, storage) launchers; defined in
+// flbm_kernels.cuh and explicitly instantiated in the inst_*.cu files.
+#pragma once
+#include "flbm_internal.h"
+#include "flbm_lattice.cuh"
+
+namespace flbm {
+
+template <class L, class S> struct Launch {
+    static cudaError_t density(int parity, const StepParams &p, const void *pop, float *rho, cudaStream_t st);
+    static cudaError_t collide(int parity, const StepParams &p, void *pop, const float *rho, unsigned *status,
+                               cudaStream_t st);
+    static cudaError_t init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st);
+    static cudaError_t gather(int parity, const StepParams &p, const void *pop, const int64_t *sites, int64_t n,
+                              double *out, cudaStream_t st);
+    static cudaError_t observables(int parity, const StepParams &p, const void *pop, const float *rho, double *ra,
+                                   double *rb, double *u, double *partials, int *nblocks, cudaStream_t st);
+};
+
+extern template struct Launch<D2Q9, StoreF32>;
+extern template struct Launch<D2Q9, StoreF16>;
+extern template struct Launch<D2Q9, StoreBF16>;
+extern template struct Launch<D3Q19, StoreF32>;
+extern template struct Launch<D3Q19, StoreF16>;
+extern template struct Launch<D3Q19, StoreBF16>;
+
+} // namespace flbm

@@ -1,0 +1,81 @@
+// flbm_noise.cuh -- counter-based Gaussian noise on the device.
+//
+// Philox4x32-10 (J. K. Salmon, M. A. Moraes, R. O. Dror, D. E. Shaw, "Parallel
+// random numbers: as easy as 1, 2, 3", SC'11): a 10-round bijection of a
+// 128-bit counter under a 64-bit key; each round multiplies two words by fixed
+// odd constants, swaps halves and mixes in the key, which is advanced by the
+// Weyl constants between rounds.  Gaussians come from the Box-Muller transform
+// (the paper's generator, Sec. VI A) on pairs of output words.
+#pragma once
+#include <cstdint>
+
+namespace flbm {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
+        const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
+        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+        k0 += W0;
+        k1 += W1;
+    }
+    return x;
+}
+
+// Box-Muller on one pair of words: u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and
+// u2 = (b >> 8) 2^-24 in [0, 1) are exact in float; g0 = r cos(2 pi u2),
+// g1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
+{
+    const float u1 = (float)((a >> 8) + 1u) * 0x1.0p-24f;
+    const float u2 = (float)(b >> 8) * 0x1.0p-24f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    g0 = r * c;
+    g1 = r * s;
+}
+
+// Does species S use the Gaussian of mode a?  Non-conserved modes a > D of
+// each species have their own draws; the momenta (1..D) are drawn once, for
+// species 0, and used with the opposite sign for species 1 (Sec. IV A).
+template <class L, int S>
+__host__ __device__ constexpr bool uses_mode(int a)
+{
+    return a < L::Q && (a > L::D || (S == 0 && a >= 1 && a <= L::D));
+}
+
+// Fill g[a] with the standard Gaussian of mode a for every mode species S uses:
+// counter (site, step, S, a/4), lane a mod 4.  Only the needed Philox blocks
+// and Box-Muller pairs are evaluated.
+template <class L, int S>
+__device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uint32_t k0,
+                                               uint32_t k1, float *g)
+{
+#pragma unroll
+    for (int slot = 0; slot * 4 < L::Q; slot++) {
+        const bool p0 = uses_mode<L, S>(4 * slot) || uses_mode<L, S>(4 * slot + 1);
+        const bool p1 = uses_mode<L, S>(4 * slot + 2) || uses_mode<L, S>(4 * slot + 3);
+        if (p0 || p1) {
+            const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)slot), k0, k1);
+            if (p0) {
+                float g0, g1;
+                box_muller(x.x, x.y, g0, g1);
+                if (uses_mode<L, S>(4 * slot)) g[4 * slot] = g0;
+                if (uses_mode<L, S>(4 * slot + 1)) g[4 * slot + 1] = g1;
+            }
+            if (p1) {
+                float g2, g3;
+                box_muller(x.z, x.w, g2, g3);
+                if (uses_mode<L, S>(4 * slot + 2)) g[4 * slot + 2] = g2;
+                if (uses_mode<L, S>(4 * slot + 3)) g[4 * slot + 3] = g3;
+            }
+        }
+    }
+}
+
+} // namespace flbm

@@ -1,0 +1,260 @@
+"""Python binding of the flbm C-ABI (include/flbm.h): argument marshalling only.
+
+Every step of the lattice update runs in the CUDA kernels of ``libflbm.so``;
+this module converts arguments, owns the PyTorch device buffers it attaches,
+and turns status codes into exceptions.  It never falls back to a CPU path:
+if the library is missing or no GPU is visible, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+D2Q9, D3Q19 = 0, 1
+STORE = {"f32": 0, "f16": 1, "bf16": 2}
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED, ESTATE = range(8)
+STATUS_NAMES = ["FLBM_OK", "FLBM_EINVAL", "FLBM_ENOMEM", "FLBM_ECUDA", "FLBM_ENONFINITE",
+                "FLBM_ETIMEOUT", "FLBM_EUNSUPPORTED", "FLBM_ESTATE"]
+
+OPT_STORAGE = 1
+OPT_LAMBDA_D = 2
+OPT_SDF = 3
+OPT_RHO0_A = 4
+OPT_RHO0_B = 5
+OPT_NOISE_RHO = 7
+OPT_FORCE_VELOCITY = 8
+OPT_SF_AXIS = 9
+OPT_KERNEL_TIMING = 10
+OPT_LAMBDA_MODE = 1000
+OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
+                "rho0_a": OPT_RHO0_A, "rho0_b": OPT_RHO0_B, "noise_rho": OPT_NOISE_RHO,
+                "force_velocity": OPT_FORCE_VELOCITY, "sf_axis": OPT_SF_AXIS,
+                "kernel_timing": OPT_KERNEL_TIMING}
+
+
+class FlbmError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libflbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, u64, dbl, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                      ctypes.c_double, ctypes.c_size_t)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        szp = ctypes.POINTER(ctypes.c_size_t)
+        sig = {
+            "flbm_create": (i32, [i32, i32, i32, i32, dbl, dbl, dbl, dbl, u64, ctypes.POINTER(vp)]),
+            "flbm_set_option": (i32, [vp, i32, dbl]),
+            "flbm_set_stream": (i32, [vp, vp]),
+            "flbm_buffer_bytes": (i32, [vp, szp, szp]),
+            "flbm_attach_buffers": (i32, [vp, vp, sz, vp, sz]),
+            "flbm_init": (i32, [vp, dp, dp]),
+            "flbm_step": (i32, [vp, i64]),
+            "flbm_sync": (i32, [vp]),
+            "flbm_get_step": (i32, [vp, i64p]),
+            "flbm_kernel_times": (i32, [vp, dp, i64p]),
+            "flbm_moments": (i32, [vp, dp, dp, dp, dp]),
+            "flbm_sf_sample": (i32, [vp]),
+            "flbm_structure_factor": (i32, [vp, i32, i32, dp, dp, dp, dp, i64p]),
+            "flbm_sf_reset": (i32, [vp]),
+            "flbm_get_populations": (i32, [vp, dp]),
+            "flbm_set_populations": (i32, [vp, dp, i64]),
+            "flbm_get_site_populations": (i32, [vp, i64p, i64, dp]),
+            "flbm_checkpoint": (i32, [vp, vp, szp]),
+            "flbm_restore": (i32, [vp, vp, sz]),
+            "flbm_last_error": (ctypes.c_char_p, [vp]),
+            "flbm_destroy": (None, [vp]),
+            "flbm_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def version() -> str:
+    return lib().flbm_version().decode()
+
+
+def check(handle, status):
+    if status != OK:
+        msg = lib().flbm_last_error(handle).decode(errors="replace") if handle else ""
+        raise FlbmError(status, msg)
+
+
+def flbm_create(lattice, nx, ny, nz, tau_a, tau_b, kT, G, seed):
+    h = ctypes.c_void_p()
+    st = lib().flbm_create(int(lattice), int(nx), int(ny), int(nz), float(tau_a), float(tau_b),
+                           float(kT), float(G), int(seed) & (2**64 - 1), ctypes.byref(h))
+    check(None, st)
+    return h
+
+
+class Lattice:
+    """One two-species periodic box on the GPU (a flbm_ctx).
+
+    Device memory for the populations and the density field comes from PyTorch
+    (``torch.empty`` on ``device``) and is attached to the context; the work
+    runs on ``stream`` (a ``torch.cuda.Stream``; a dedicated one by default).
+    """
+
+    def __init__(self, lattice, nx, ny, nz=1, tau_a=1.0, tau_b=1.0, kT=0.0, G=0.0, seed=1,
+                 storage="f32", device="cuda:0", stream=None, **options):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device visible: flbm runs on the GPU only")
+        self.lattice = int(lattice)
+        self.nx, self.ny = int(nx), int(ny)
+        self.nz = 1 if self.lattice == D2Q9 else int(nz)
+        self.D = 2 if self.lattice == D2Q9 else 3
+        self.Q = 9 if self.lattice == D2Q9 else 19
+        self.N = self.nx * self.ny * self.nz
+        self.device = torch.device(device)
+        self._h = None
+        self._h = flbm_create(self.lattice, self.nx, self.ny, self.nz, tau_a, tau_b, kT, G, seed)
+        self.set_option(OPT_STORAGE, STORE[storage] if isinstance(storage, str) else int(storage))
+        for k, v in options.items():
+            self.set_option(k, v)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        check(self._h, lib().flbm_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)))
+        pb, rb = ctypes.c_size_t(), ctypes.c_size_t()
+        check(self._h, lib().flbm_buffer_bytes(self._h, ctypes.byref(pb), ctypes.byref(rb)))
+        self.pop_buffer = torch.empty(pb.value, dtype=torch.uint8, device=self.device)
+        self.rho_buffer = torch.empty(rb.value, dtype=torch.uint8, device=self.device)
+        check(self._h, lib().flbm_attach_buffers(self._h, ctypes.c_void_p(self.pop_buffer.data_ptr()), pb.value,
+                                                 ctypes.c_void_p(self.rho_buffer.data_ptr()), rb.value))
+
+    # -- configuration ----------------------------------------------------
+    def set_option(self, key, value):
+        if isinstance(key, str):
+            key = OPTION_NAMES[key]
+        check(self._h, lib().flbm_set_option(self._h, int(key), float(value)))
+
+    def set_mode_rate(self, species, mode, lam):
+        self.set_option(OPT_LAMBDA_MODE + 100 * int(species) + int(mode), lam)
+
+    # -- state -------------------------------------------------------------
+    def init(self, rho_a=None, rho_b=None):
+        ra = None if rho_a is None else np.ascontiguousarray(rho_a, dtype=np.float64).ravel()
+        rb = None if rho_b is None else np.ascontiguousarray(rho_b, dtype=np.float64).ravel()
+        for a in (ra, rb):
+            if a is not None and a.size != self.N:
+                raise ValueError("density arrays need one value per site")
+        check(self._h, lib().flbm_init(self._h, _dp(ra), _dp(rb)))
+
+    def step(self, n=1):
+        check(self._h, lib().flbm_step(self._h, int(n)))
+
+    def sync(self):
+        check(self._h, lib().flbm_sync(self._h))
+
+    @property
+    def step_count(self):
+        v = ctypes.c_int64()
+        check(self._h, lib().flbm_get_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    def kernel_times(self):
+        """({'density': ms, 'collide': ms}, {'density': n, 'collide': n}) accumulated
+        while the kernel_timing option was on."""
+        ms = np.zeros(2)
+        n = np.zeros(2, dtype=np.int64)
+        check(self._h, lib().flbm_kernel_times(self._h, _dp(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return {"density": ms[0], "collide": ms[1]}, {"density": int(n[0]), "collide": int(n[1])}
+
+    def moments(self, fields=True):
+        """(rho_a, rho_b, u[D], cons[5]) as float64 arrays [z][y][x]."""
+        shp = (self.nz, self.ny, self.nx)
+        ra = np.empty(self.N) if fields else None
+        rb = np.empty(self.N) if fields else None
+        u = np.empty(self.D * self.N) if fields else None
+        cons = np.empty(5)
+        check(self._h, lib().flbm_moments(self._h, _dp(ra), _dp(rb), _dp(u), _dp(cons)))
+        if not fields:
+            return cons
+        return ra.reshape(shp), rb.reshape(shp), u.reshape((self.D,) + shp), cons
+
+    def sf_sample(self):
+        check(self._h, lib().flbm_sf_sample(self._h))
+
+    def structure_factor(self, axis=0, nk=None):
+        n_axis = (self.nx, self.ny, self.nz)[axis]
+        nk = n_axis // 2 if nk is None else nk
+        out = [np.empty(nk) for _ in range(4)]
+        n = ctypes.c_int64()
+        check(self._h, lib().flbm_structure_factor(self._h, axis, nk, *[_dp(o) for o in out], ctypes.byref(n)))
+        return (*out, n.value)
+
+    def sf_reset(self):
+        check(self._h, lib().flbm_sf_reset(self._h))
+
+    def get_populations(self):
+        f = np.empty(2 * self.Q * self.N)
+        check(self._h, lib().flbm_get_populations(self._h, _dp(f)))
+        return f.reshape(2, self.Q, self.nz, self.ny, self.nx)
+
+    def set_populations(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        if f.size != 2 * self.Q * self.N:
+            raise ValueError("populations need 2 * Q values per site")
+        check(self._h, lib().flbm_set_populations(self._h, _dp(f), int(step)))
+
+    def site_populations(self, sites):
+        s = np.ascontiguousarray(sites, dtype=np.int64).ravel()
+        out = np.empty(s.size * 2 * self.Q)
+        check(self._h, lib().flbm_get_site_populations(
+            self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), s.size, _dp(out)))
+        return out.reshape(s.size, 2, self.Q)
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t()
+        check(self._h, lib().flbm_checkpoint(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(self._h, lib().flbm_checkpoint(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def restore(self, image: bytes):
+        buf = ctypes.create_string_buffer(image, len(image))
+        check(self._h, lib().flbm_restore(self._h, buf, len(image)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().flbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

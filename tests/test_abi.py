@@ -1,0 +1,89 @@
+"""The C-ABI library loads and exports every entry point of include/flbm.h, and
+its argument checks work without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1410_5584_gb300 import _build
+from paper_1410_5584_gb300 import flbm as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(flbm_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return F.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            names += _declared(os.path.join(ROOT, "include", h))
+    assert "flbm_step" in names and "flbm_create" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_version(lib):
+    assert "sm_103a" in F.version()
+
+
+@pytest.mark.parametrize("args", [
+    (5, 16, 16, 1, 1.0, 1.0, 1e-4, 0.0),        # unknown lattice
+    (0, 16, 16, 2, 1.0, 1.0, 1e-4, 0.0),        # D2Q9 needs nz = 1
+    (1, 16, 16, 1, 1.0, 1.0, 1e-4, 0.0),        # D3Q19 needs nz >= 2
+    (0, 1, 16, 1, 1.0, 1.0, 1e-4, 0.0),         # dimension < 2
+    (0, 16, 16, 1, 0.5, 1.0, 1e-4, 0.0),        # tau <= 1/2 (2 lb - lb^2 <= 0)
+    (0, 16, 16, 1, 1.0, 0.4, 1e-4, 0.0),
+    (0, 16, 16, 1, 1.0, 1.0, -1e-4, 0.0),       # kT < 0
+    (0, 16, 70000, 1, 1.0, 1.0, 1e-4, 0.0),     # ny > 65535
+    (1, 2048, 2048, 512, 1.0, 1.0, 1e-4, 0.0),  # N >= 2^31
+    (0, 16, 16, 1, float("nan"), 1.0, 1e-4, 0.0),
+])
+def test_create_rejects_invalid_arguments(lib, args):
+    h = ctypes.c_void_p()
+    st = lib.flbm_create(*args, 1, ctypes.byref(h))
+    assert st == F.EINVAL
+    assert not h.value
+
+
+def test_options_are_validated(lib):
+    h = F.flbm_create(F.D2Q9, 8, 8, 1, 1.0, 1.0, 1e-4, 0.0, 1)
+    try:
+        assert lib.flbm_set_option(h, F.OPT_LAMBDA_D, 2.5) == F.EINVAL
+        assert b"lambda_d" in lib.flbm_last_error(h)
+        assert lib.flbm_set_option(h, 12345, 1.0) == F.EINVAL
+        assert lib.flbm_set_option(h, F.OPT_LAMBDA_MODE + 2, 1.0) == F.EINVAL  # a momentum mode
+        assert lib.flbm_set_option(h, F.OPT_LAMBDA_MODE + 100 + 8, 1.2) == F.OK
+        assert lib.flbm_set_option(h, F.OPT_STORAGE, 3) == F.EINVAL
+        assert lib.flbm_set_option(h, F.OPT_SF_AXIS, 2) == F.EINVAL  # no z axis in 2D
+        assert lib.flbm_set_option(h, F.OPT_RHO0_A, -1.0) == F.EINVAL
+        assert lib.flbm_step(h, 1) == F.ESTATE  # before init
+        assert lib.flbm_step(h, -1) == F.EINVAL
+        pb, rb = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.flbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(rb)) == F.OK
+        assert pb.value == 2 * 9 * 64 * 4 and rb.value == 2 * 64 * 4
+        assert lib.flbm_set_option(h, F.OPT_STORAGE, 2) == F.OK
+        assert lib.flbm_buffer_bytes(h, ctypes.byref(pb), None) == F.OK
+        assert pb.value == 2 * 9 * 64 * 2
+        need = ctypes.c_size_t()
+        assert lib.flbm_checkpoint(h, None, ctypes.byref(need)) == F.OK
+        assert need.value > pb.value
+    finally:
+        lib.flbm_destroy(h)
+
+
+def test_null_context_is_safe(lib):
+    assert lib.flbm_last_error(None) == b""
+    assert lib.flbm_step(None, 1) == F.EINVAL
+    lib.flbm_destroy(None)

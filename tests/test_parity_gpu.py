@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA library, called through its C-ABI, against the FP64
+oracle on the same seeded inputs and the same counter-based noise.
+
+Tolerances (element by element, relative to max |f|): 1e-6 per step and 1e-4
+after 1000 steps for float storage; the 16-bit formats are bounded by their
+rounding of the stored deviation (2^-11 relative for half, 2^-8 for bfloat16).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_5584_gb300 import D2Q9, D3Q19, FlbmError, Lattice
+from paper_1410_5584_gb300 import flbm as F
+from paper_1410_5584_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_THREADS = 8
+
+
+def _pair(lat, shape, tau=(1.0, 1.0), kT=1e-4, G=0.0, seed=1, storage="f32", **opts):
+    nz, ny, nx = shape
+    g = Lattice(lat, nx, ny, nz, tau[0], tau[1], kT, G, seed, storage=storage, **opts)
+    o = oracle.Oracle(lat, nx, ny, nz, tau[0], tau[1], kT, G, seed, **opts)
+    o.set_threads(ORACLE_THREADS)
+    return g, o
+
+
+def _random_state(lat, shape, rho=(1.0, 0.8), eps=0.02, seed=3):
+    c, w, T, N = oracle.tables(lat)
+    return inputs.random_populations(np.stack([w * rho[0], w * rho[1]]), shape, eps, seed=seed)
+
+
+def _rel(fg, fo):
+    return np.max(np.abs(fg - fo)) / np.max(np.abs(fo))
+
+
+SHAPES = [
+    (D2Q9, (1, 23, 37)),   # ragged: x not a multiple of the warp, odd y
+    (D2Q9, (1, 2, 2)),     # smallest box: every neighbour wraps
+    (D2Q9, (1, 64, 160)),  # several thread blocks along x plus a ragged tail
+    (D3Q19, (7, 6, 13)),
+    (D3Q19, (2, 2, 2)),
+    (D3Q19, (16, 12, 136)),
+]
+
+
+@pytest.mark.parametrize("lat,shape", SHAPES)
+@pytest.mark.parametrize("G,tau", [(0.0, (1.0, 1.0)), (0.9, (0.8, 1.0))])
+def test_single_steps_match_oracle(lat, shape, G, tau):
+    """Both in-place streaming parities (steps 1 and 2), G = 0 and G > 0,
+    tau_A != tau_B: <= 1e-6 relative per step."""
+    f0 = _random_state(lat, shape)
+    g, o = _pair(lat, shape, tau=tau, kT=1e-4, G=G, seed=77)
+    g.set_populations(f0, step=41)
+    o.set_f(f0, step=41)
+    for k in range(1, 3):
+        g.step(1)
+        o.step(1)
+        assert _rel(g.get_populations(), o.get_f()) <= 1e-6 * k
+    assert g.step_count == 43
+
+
+@pytest.mark.parametrize("lat,shape,tau,kT,G,rho", [
+    (D2Q9, (1, 64, 64), (1.0, 1.0), 1e-4, 0.0, (0.5, 0.5)),     # the 64^2 ideal-mixture workload
+    (D2Q9, (1, 48, 40), (0.8, 1.0), 1e-5, 0.9, (1.0, 1.0)),     # Shan-Chen mixture, G rho0 = 0.9
+    (D3Q19, (12, 10, 16), (1.0, 1.0), 1e-5, 0.9, (1.0, 1.0)),
+])
+def test_thousand_steps_match_oracle(lat, shape, tau, kT, G, rho):
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    ra = inputs.perturbed_density(shape, rho[0], 1e-3, seed=1, species=0)
+    rb = inputs.perturbed_density(shape, rho[1], 1e-3, seed=1, species=1)
+    g, o = _pair(lat, shape, tau=tau, kT=kT, G=G, seed=1)
+    g.init(ra, rb)
+    # the oracle starts from the same float-rounded rest state
+    o.set_f(g.get_populations(), step=0)
+    g.step(1000)
+    o.step(1000)
+    assert _rel(g.get_populations(), o.get_f()) <= 1e-4
+    assert n > 0
+
+
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 9, 11)), (D3Q19, (4, 5, 6))])
+@pytest.mark.parametrize("opts", [
+    dict(sdf=0),
+    dict(noise_rho=1, rho0_a=1.1, rho0_b=0.7),
+    dict(force_velocity=1),
+    dict(lambda_d=1.3),
+])
+def test_options_match_oracle(lat, shape, opts):
+    f0 = _random_state(lat, shape, rho=(1.1, 0.7))
+    g, o = _pair(lat, shape, tau=(0.9, 1.2), kT=3e-4, G=0.5, seed=5, **opts)
+    g.set_populations(f0, step=0)
+    o.set_f(f0, step=0)
+    g.step(2)
+    o.step(2)
+    assert _rel(g.get_populations(), o.get_f()) <= 2e-6
+
+
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 9, 11)), (D3Q19, (4, 5, 6))])
+def test_per_mode_rates_match_oracle(lat, shape):
+    Q = 9 if lat == D2Q9 else 19
+    D = 2 if lat == D2Q9 else 3
+    f0 = _random_state(lat, shape)
+    g, o = _pair(lat, shape, tau=(1.0, 1.0), kT=1e-4, G=0.4, seed=8)
+    for s in range(2):
+        for a in range(D + 1, Q):
+            lam = 0.6 + 0.05 * a + 0.3 * s
+            g.set_mode_rate(s, a, lam)
+            o.set_mode_rate(s, a, lam)
+    g.set_populations(f0)
+    o.set_f(f0)
+    g.step(2)
+    o.step(2)
+    assert _rel(g.get_populations(), o.get_f()) <= 2e-6
+
+
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 20, 24)), (D3Q19, (6, 7, 8))])
+def test_moments_and_totals_match_oracle(lat, shape):
+    f0 = _random_state(lat, shape)
+    g, o = _pair(lat, shape, tau=(0.8, 1.0), kT=1e-4, G=0.9, seed=4)
+    g.set_populations(f0)
+    o.set_f(f0)
+    g.step(3)
+    o.step(3)
+    ga, gb, gu, gc = g.moments()
+    oa, ob, ou, oc = o.moments()
+    assert np.max(np.abs(ga - oa)) <= 1e-6 * np.max(oa)
+    assert np.max(np.abs(gb - ob)) <= 1e-6 * np.max(ob)
+    assert np.max(np.abs(gu - ou)) <= 1e-6 * np.max(np.abs(ou)) + 1e-9
+    assert np.allclose(gc[:2], oc[:2], rtol=1e-7)
+    assert np.all(np.abs(gc[2:] - oc[2:]) <= 1e-6 * oc[0])
+
+
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 64, 64)), (D3Q19, (16, 16, 16))])
+def test_conservation_on_the_gpu(lat, shape):
+    """Mass of each species and total momentum over 1000 float steps (G = 0.9):
+    drift bounded by float rounding, ~1e-6 relative."""
+    nz, ny, nx = shape
+    g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-5, 0.9, 3)
+    g.init(inputs.perturbed_density(shape, 1.0, 1e-3, 3, 0), inputs.perturbed_density(shape, 1.0, 1e-3, 3, 1))
+    c0 = g.moments(fields=False)
+    g.step(1000)
+    c1 = g.moments(fields=False)
+    assert abs(c1[0] - c0[0]) <= 2e-6 * c0[0]
+    assert abs(c1[1] - c0[1]) <= 2e-6 * c0[1]
+    assert np.all(np.abs(c1[2:] - c0[2:]) <= 2e-6 * c0[0])
+
+
+@pytest.mark.parametrize("lat,shape,axis", [(D2Q9, (1, 16, 32), 0), (D2Q9, (1, 16, 32), 1),
+                                            (D3Q19, (8, 6, 10), 2)])
+def test_structure_factor_matches_oracle(lat, shape, axis):
+    f0 = _random_state(lat, shape, eps=0.01)
+    g, o = _pair(lat, shape, tau=(1.0, 1.0), kT=1e-4, G=0.3, seed=9)
+    g.set_option("sf_axis", axis)
+    g.set_populations(f0)
+    o.set_f(f0)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        g.sf_sample()
+        o.sf_sample(axis)
+    gs = g.structure_factor(axis)
+    os_ = o.structure_factor()
+    assert gs[4] == os_[4] == 3
+    for a, b in zip(gs[:4], os_[:4]):
+        assert np.allclose(a, b, rtol=2e-5, atol=1e-7 * np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("storage,bits", [("f16", 11), ("bf16", 8)])
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 16, 24)), (D3Q19, (6, 6, 8))])
+def test_sixteen_bit_storage_against_oracle(storage, bits, lat, shape):
+    """Populations stored as 16-bit deviations from w_i rho0: after one step
+    the error is the rounding of the stored deviation."""
+    c, w, T, N = oracle.tables(lat)
+    base = np.stack([w, w])[:, :, None, None, None]
+    f0 = _random_state(lat, shape, rho=(1.0, 1.0), eps=0.01)
+    g, o = _pair(lat, shape, tau=(1.0, 1.0), kT=1e-5, G=0.9, seed=2, storage=storage)
+    g.set_populations(f0)
+    start = g.get_populations()  # f0 with its deviations rounded to the format
+    assert np.max(np.abs(start - f0)) <= 2.0 ** -bits * np.max(np.abs(f0 - base))
+    o.set_f(start)
+    g.step(1)
+    o.step(1)
+    fo = o.get_f()
+    dev = np.max(np.abs(fo - base))
+    assert np.max(np.abs(g.get_populations() - fo)) <= 2.0 ** -bits * dev + 1e-6 * np.max(fo)
+
+
+@pytest.mark.parametrize("nsteps", [10, 11])
+def test_checkpoint_restore_is_bit_identical(nsteps):
+    shape = (5, 6, 7)
+    g = Lattice(D3Q19, 7, 6, 5, 0.8, 1.0, 1e-4, 0.9, 123)
+    g.init(inputs.perturbed_density(shape, 1.0, 1e-3, 1, 0), inputs.perturbed_density(shape, 1.0, 1e-3, 1, 1))
+    g.step(nsteps)
+    image = g.checkpoint()
+    g.step(7)
+    a = g.get_populations()
+    h = Lattice(D3Q19, 7, 6, 5, 1.0, 1.0, 0.0, 0.0, 999)  # parameters come from the image
+    h.restore(image)
+    assert h.step_count == nsteps
+    h.step(7)
+    assert np.array_equal(a, h.get_populations())
+    bad = bytearray(image)
+    bad[-1] ^= 0xFF
+    with pytest.raises(FlbmError) as e:
+        h.restore(bytes(bad))
+    assert e.value.status == F.EINVAL
+    wrong = Lattice(D3Q19, 8, 6, 5, 1.0, 1.0, 0.0, 0.0, 1)
+    with pytest.raises(FlbmError):
+        wrong.restore(image)
+
+
+def test_nonpositive_density_is_reported():
+    """A site whose density is driven negative is flagged on the device and
+    reported by the next synchronising call; re-initialising clears it."""
+    shape = (1, 8, 8)
+    g = Lattice(D2Q9, 8, 8, 1, 1.0, 1.0, 1e-4, 0.0, 1)
+    f0 = _random_state(D2Q9, shape)
+    f0[0, :, 0, 3, 3] = -0.05  # species A density -0.45 at one site
+    g.set_populations(f0)
+    g.step(1)
+    with pytest.raises(FlbmError) as e:
+        g.sync()
+    assert e.value.status == F.ENONFINITE
+    g.init()
+    g.step(2)
+    g.sync()
+
+
+def test_runtime_argument_errors():
+    g = Lattice(D2Q9, 8, 8, 1, 1.0, 1.0, 1e-4, 0.0, 1)
+    g.init()
+    with pytest.raises(FlbmError):
+        g.site_populations([64])
+    with pytest.raises(FlbmError):
+        g.structure_factor(0)  # no snapshot yet
+    with pytest.raises(FlbmError):
+        g.set_option("storage", 1)  # buffers exist
+    g.sf_sample()
+    with pytest.raises(FlbmError):
+        g.structure_factor(0, nk=5)  # nk > nx/2
+
+
+def _block_check(lat, shape, steps_before, nsample, seed):
+    """Sampled parity on a full-size box: for sampled sites r, the GPU's
+    post-collision values f_i(r + c_i, n+1) against the oracle's update of the
+    3^D block around r, drawn with r's global noise counters."""
+    nz, ny, nx = shape
+    D = 2 if lat == D2Q9 else 3
+    Q = 9 if lat == D2Q9 else 19
+    c, w, T, N = oracle.tables(lat)
+    g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-5, 0.9, seed)
+    g.init(inputs.perturbed_density(shape, 1.0, 1e-3, seed, 0), inputs.perturbed_density(shape, 1.0, 1e-3, seed, 1))
+    g.step(steps_before)
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz // 2, 0, nx - 1)]
+    pts += [tuple(int(rng.integers(0, m)) for m in (nz, ny, nx)) for _ in range(nsample)]
+    if D == 2:
+        pts = [(0, y, x) for (_, y, x) in pts]
+    offs = [(dz, dy, dx) for dz in ((-1, 0, 1) if D == 3 else (0,)) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    blocks = []
+    for (z, y, x) in pts:
+        ids = [(((z + dz) % nz) * ny + (y + dy) % ny) * nx + (x + dx) % nx for (dz, dy, dx) in offs]
+        blocks.append(ids)
+    before = g.site_populations(np.concatenate(blocks)).reshape(len(pts), len(offs), 2, Q)
+    g.step(1)
+    bz = 3 if D == 3 else 1
+    worst = 0.0
+    dst_ids = []
+    for (z, y, x) in pts:
+        dst_ids.append([(((z + c[i, 2]) % nz) * ny + (y + c[i, 1]) % ny) * nx + (x + c[i, 0]) % nx for i in range(Q)])
+    after = g.site_populations(np.concatenate(dst_ids)).reshape(len(pts), Q, 2, Q)
+    for k, (z, y, x) in enumerate(pts):
+        fb = np.zeros((2, Q, bz, 3, 3))
+        for j, (dz, dy, dx) in enumerate(offs):
+            fb[:, :, dz + 1 if D == 3 else 0, dy + 1, dx + 1] = before[k, j]
+        o = oracle.Oracle(lat, 3, 3, bz, 0.8, 1.0, 1e-5, 0.9, seed)
+        o.set_rng_origin((nz, ny, nx), ((z - 1) % nz if D == 3 else 0, (y - 1) % ny, (x - 1) % nx))
+        o.set_f(fb, step=steps_before)
+        o.step(1)
+        fo = o.get_f()
+        cz = 1 if D == 3 else 0
+        for i in range(Q):
+            ref = fo[:, i, (cz + c[i, 2]) % bz, 1 + c[i, 1], 1 + c[i, 0]]
+            got = after[k, i, :, i]
+            worst = max(worst, np.max(np.abs(got - ref)) / np.max(np.abs(fo)))
+        o.close()
+    return worst
+
+
+@pytest.mark.parametrize("steps_before", [2, 3])
+def test_full_size_d3q19_sampled_parity(steps_before):
+    """The 256^3 D3Q19 box the benchmark times, both streaming parities."""
+    assert _block_check(D3Q19, (256, 256, 256), steps_before, 40, seed=1) <= 1e-6
+
+
+def test_full_size_d2q9_sampled_parity():
+    """The 512^2 D2Q9 Shan-Chen box."""
+    assert _block_check(D2Q9, (1, 512, 512), 3, 60, seed=2) <= 1e-6
