@@ -37,6 +37,9 @@ WORKLOADS = {
     "d3q19-256-bf16": dict(lattice=1, nx=256, ny=256, nz=256, storage="bf16", tau=(1.0, 1.0), kT=1e-5, G=0.9,
                            rho0=1.0, desc="D3Q19 256^3 mixture, populations stored as BF16 deviations from "
                                           "w_i*rho0, FP32 collision"),
+    "d3q19-128": dict(lattice=1, nx=128, ny=128, nz=128, storage="f32", tau=(1.0, 1.0), kT=1e-5, G=0.9,
+                      rho0=1.0, desc="D3Q19 128^3 mixture, FP32 (profiling case: 319 MB of populations, "
+                                     "larger than L2)"),
     "d2q9-512": dict(lattice=0, nx=512, ny=512, nz=1, storage="f32", tau=(0.8, 1.0), kT=1e-5, G=0.9,
                      rho0=1.0, desc="D2Q9 512^2 periodic Shan-Chen mixture, FP32, G*rho0=0.9, tau=0.8/1.0, "
                                     "kT=1e-5 (fits in L2)"),

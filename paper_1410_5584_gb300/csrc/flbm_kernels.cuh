@@ -50,39 +50,40 @@ __device__ __forceinline__ Nbr make_nbr(const StepParams &p, int x, int y, int z
 }
 
 template <class L> __device__ __forceinline__ constexpr float wf(int i) { return (float)L::wd(i); }
-template <class L> __device__ __forceinline__ constexpr float invNf(int a) { return (float)(1.0 / L::Nd(a)); }
 
 // array index of the population f_i(site) that the current step reads
-template <class L, int PARITY>
-__device__ __forceinline__ size_t read_index(const Nbr &nb, size_t NN, int s, int i)
+template <class L, int PARITY, int I>
+__device__ __forceinline__ size_t read_index(const Nbr &nb, size_t NN, int s)
 {
-    if (PARITY == 0) return (size_t)(s * L::Q + i) * NN + nb.at(0, 0, 0);
-    return (size_t)(s * L::Q + L::opp(i)) * NN + nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+    if constexpr (PARITY == 0) return (size_t)(s * L::Q + I) * NN + nb.at(0, 0, 0);
+    else return (size_t)(s * L::Q + L::opp(I)) * NN + nb.at(-L::cx(I), -L::cy(I), -L::cz(I));
 }
 
 // array index where the post-collision f*_i(site) is written
-template <class L, int PARITY>
-__device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s, int i)
+template <class L, int PARITY, int I>
+__device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s)
 {
-    if (PARITY == 0) return (size_t)(s * L::Q + L::opp(i)) * NN + nb.at(0, 0, 0);
-    return (size_t)(s * L::Q + i) * NN + nb.at(L::cx(i), L::cy(i), L::cz(i));
+    if constexpr (PARITY == 0) return (size_t)(s * L::Q + L::opp(I)) * NN + nb.at(0, 0, 0);
+    else return (size_t)(s * L::Q + I) * NN + nb.at(L::cx(I), L::cy(I), L::cz(I));
 }
 
-// deviation moments m_a = sum_i T_ai delta_i (m_0 = rho - rho0)
+// deviation moments m_a = sum_i T_ai delta_i (m_0 = rho - rho0); the 0/+-1
+// entries of T become plain adds and subtracts
 template <class L>
-__device__ __forceinline__ void project(const float *d, float *m)
+__device__ __forceinline__ void project(const float (&d)[L::Q], float (&m)[L::Q])
 {
-#pragma unroll
-    for (int a = 0; a < L::Q; a++) {
+    static_for<L::Q>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
         float s = 0.0f;
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            if (L::T(a, i) == 1) s += d[i];
-            else if (L::T(a, i) == -1) s -= d[i];
-            else if (L::T(a, i) != 0) s += (float)L::T(a, i) * d[i];
-        }
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int t = L::T(a, i);
+            if constexpr (t == 1) s += d[i];
+            else if constexpr (t == -1) s -= d[i];
+            else if constexpr (t != 0) s += (float)t * d[i];
+        });
         m[a] = s;
-    }
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -96,14 +97,16 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
     if (x >= p.nx) return;
     const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
     const size_t NN = (size_t)p.N;
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
+    static_for<2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
         float sum = 0.0f;
-#pragma unroll
-        for (int i = 0; i < L::Q; i++)
-            sum += S::load_dev(pop, read_index<L, PARITY>(nb, NN, s, i), wf<L>(i) * p.rho0[s]);
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            sum += S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+        });
         rho[(size_t)s * NN + nb.at(0, 0, 0)] = p.rho0[s] + sum;
-    }
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -122,42 +125,49 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
 
     // 1. moments of both species (Eq. modes-discrete), density rho = rhobar
     float m[2][Q], rs[2];
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
+    static_for<2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
         float d[Q];
-#pragma unroll
-        for (int i = 0; i < Q; i++) d[i] = S::load_dev(pop, read_index<L, PARITY>(nb, NN, s, i), wf<L>(i) * p.rho0[s]);
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            d[i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+        });
         project<L>(d, m[s]);
         rs[s] = p.rho0[s] + m[s][0];
-    }
+    });
 
     // 2. Shan-Chen force from the other species' neighbour densities (Eq. FORCESTRUCTURE)
     float acc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-#pragma unroll
-    for (int i = 1; i < Q; i++) {
+    static_for<Q - 1>([&](auto kc) {
+        constexpr int i = decltype(kc)::value + 1;
+        constexpr float wi = (float)L::wd(i);
         const int ns = nb.at(L::cx(i), L::cy(i), L::cz(i));
         const float ra = __ldg(rho + ns), rb = __ldg(rho + NN + ns);
-        const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
-#pragma unroll
-        for (int d = 0; d < D; d++) {
-            if (c[d] != 0) {
-                acc[0][d] += (float)c[d] * wf<L>(i) * rb;
-                acc[1][d] += (float)c[d] * wf<L>(i) * ra;
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int cd = comp<L>(i, d);
+            if constexpr (cd != 0) {
+                constexpr float cw = (float)cd * wi;
+                acc[0][d] += cw * rb;
+                acc[1][d] += cw * ra;
             }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < 2; s++)
-#pragma unroll
-        for (int d = 0; d < D; d++) acc[s][d] *= -p.G;
+        });
+    });
+    static_for<D>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        acc[0][d] *= -p.G;
+        acc[1][d] *= -p.G;
+    });
 
     // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
     const float rt = rs[0] + rs[1];
     const float irt = 1.0f / rt;
     float u[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int d = 0; d < D; d++)
+    static_for<D>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
         u[d] = (m[0][1 + d] + m[1][1 + d] + 0.5f * (rs[0] * acc[0][d] + rs[1] * acc[1][d])) * irt;
+    });
     if (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt)) atomicOr(status, kStatusNonFinite);
 
     // 4. noise amplitudes of Eq. new-noise (local or reference densities)
@@ -171,38 +181,43 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
 
     // 5. momentum modes: common rate, opposite noise; species velocity for Phi
     float v[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
+    static_for<2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
         const float irs = 1.0f / rs[s];
-#pragma unroll
-        for (int d = 0; d < D; d++) {
-            const int a = 1 + d;
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int a = 1 + d;
             const float xi = (s == 0 ? amp_j : -amp_j) * g[0][a];
             const float R = p.lam[s][a] * (rs[s] * u[d] - m[s][a]) + p.hlam[s][a] * rs[s] * acc[s][d] + xi;
             v[s][d] = p.force_velocity ? m[s][a] * irs + 0.5f * acc[s][d] : (m[s][a] + 0.5f * R) * irs;
             m[s][a] += R;
-        }
-    }
+        });
+    });
 
     // 6. transport and ghost modes, then back-projection and streaming
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
+    static_for<2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
         float meq[Q], phi[Q];
         Closure<L>::eq_force(rs[s], u, acc[s], v[s], meq, phi);
-#pragma unroll
-        for (int a = D + 1; a < Q; a++)
-            m[s][a] += p.lam[s][a] * (meq[a] - m[s][a]) + p.hlam[s][a] * phi[a] +
-                       p.noise_amp[s][a] * sq[s] * g[s][a];
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            float acc_i = 0.0f;
-#pragma unroll
-            for (int a = 0; a < Q; a++) {
-                if (L::T(a, i) != 0) acc_i += (float)L::T(a, i) * invNf<L>(a) * m[s][a];
-            }
-            S::store_dev(pop, write_index<L, PARITY>(nb, NN, s, i), wf<L>(i) * acc_i, wf<L>(i) * p.rho0[s]);
-        }
-    }
+        static_for<Q - D - 1>([&](auto kc) {
+            constexpr int a = decltype(kc)::value + D + 1;
+            m[s][a] += p.lam[s][a] * (meq[a] - m[s][a]) + p.hlam[s][a] * phi[a] + p.noise_amp[s][a] * sq[s] * g[s][a];
+        });
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            float fi = 0.0f;
+            static_for<Q>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                constexpr int t = L::T(a, i);
+                if constexpr (t != 0) {
+                    constexpr float coef = (float)t * (float)(1.0 / L::Nd(a));
+                    fi += coef * m[s][a];
+                }
+            });
+            S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), wi * fi, wi * p.rho0[s]);
+        });
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -213,13 +228,15 @@ __global__ void k_init_rest(const StepParams p, const float *__restrict__ rho_in
 {
     const size_t NN = (size_t)p.N;
     for (size_t site = blockIdx.x * (size_t)blockDim.x + threadIdx.x; site < NN; site += (size_t)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
             const float r = rho_in[(size_t)s * NN + site];
-#pragma unroll
-            for (int i = 0; i < L::Q; i++)
-                S::store_dev(pop, (size_t)(s * L::Q + i) * NN + site, wf<L>(i) * (r - p.rho0[s]), wf<L>(i) * p.rho0[s]);
-        }
+            static_for<L::Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr float wi = (float)L::wd(i);
+                S::store_dev(pop, (size_t)(s * L::Q + i) * NN + site, wi * (r - p.rho0[s]), wi * p.rho0[s]);
+            });
+        });
     }
 }
 
@@ -232,14 +249,16 @@ __global__ void k_gather_sites(const StepParams p, const typename S::T *__restri
         const int site = (int)sites[k];
         const int x = site % p.nx, y = (site / p.nx) % p.ny, z = site / (p.nx * p.ny);
         const Nbr nb = make_nbr(p, x, y, z);
-#pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int i = 0; i < L::Q; i++) {
-                const float base = wf<L>(i) * p.rho0[s];
-                const float dev = S::load_dev(pop, read_index<L, PARITY>(nb, NN, s, i), base);
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<L::Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr float wi = (float)L::wd(i);
+                const float base = wi * p.rho0[s];
+                const float dev = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), base);
                 out[(k * 2 + s) * L::Q + i] = (double)base + (double)dev;
-            }
+            });
+        });
     }
 }
 
@@ -262,8 +281,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV])
     for (int k = 0; k < NV; k++) v[k] = sh[0][k];
 }
 
-template <class L> __device__ __forceinline__ constexpr double wdd(int i) { return L::wd(i); }
-
 template <class L, class S, int PARITY>
 __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, const typename S::T *__restrict__ pop,
                                                            const float *__restrict__ rho, double *__restrict__ rho_a,
@@ -283,34 +300,38 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
         const size_t NN = (size_t)p.N;
         const int site = at(0, 0, 0);
         double r[2], j[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, a[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
             double sum = 0.0;
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const size_t idx = PARITY == 0
-                                       ? (size_t)(s * Q + i) * NN + site
-                                       : (size_t)(s * Q + L::opp(i)) * NN + at(-L::cx(i), -L::cy(i), -L::cz(i));
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                const size_t idx = PARITY == 0 ? (size_t)(s * Q + i) * NN + site
+                                               : (size_t)(s * Q + L::opp(i)) * NN + at(-L::cx(i), -L::cy(i), -L::cz(i));
                 const double dv = (double)S::load_dev(pop, idx, (float)L::wd(i) * p.rho0[s]);
                 sum += dv;
-                j[s][0] += L::cx(i) * dv;
-                j[s][1] += L::cy(i) * dv;
-                j[s][2] += L::cz(i) * dv;
-            }
+                static_for<3>([&](auto dc) {
+                    constexpr int d = decltype(dc)::value;
+                    constexpr int cd = comp<L>(i, d);
+                    if constexpr (cd != 0) j[s][d] += cd * dv;
+                });
+            });
             r[s] = (double)p.rho0[s] + sum;
-        }
+        });
         // force with the density field (the same values the step kernel uses)
-#pragma unroll
-        for (int i = 1; i < Q; i++) {
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
             const int ns = at(L::cx(i), L::cy(i), L::cz(i));
             const double ra = rho[ns], rb = rho[NN + ns];
-            a[0][0] += wdd<L>(i) * L::cx(i) * rb;
-            a[0][1] += wdd<L>(i) * L::cy(i) * rb;
-            a[0][2] += wdd<L>(i) * L::cz(i) * rb;
-            a[1][0] += wdd<L>(i) * L::cx(i) * ra;
-            a[1][1] += wdd<L>(i) * L::cy(i) * ra;
-            a[1][2] += wdd<L>(i) * L::cz(i) * ra;
-        }
+            static_for<3>([&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                constexpr int cd = comp<L>(i, d);
+                if constexpr (cd != 0) {
+                    constexpr double cw = L::wd(i) * cd;
+                    a[0][d] += cw * rb;
+                    a[1][d] += cw * ra;
+                }
+            });
+        });
         const double ra0 = rho[site], rb0 = rho[NN + site];
         const double rt = r[0] + r[1];
         if (rho_a) rho_a[site] = r[0];

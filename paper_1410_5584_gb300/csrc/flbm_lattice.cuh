@@ -9,8 +9,21 @@
 // Everything here is constexpr so that, inside fully unrolled loops, the
 // 0/+-1/+-2 structure of T folds into straight-line adds.
 #pragma once
+#include <utility>
 
 namespace flbm {
+
+// Compile-time loop: f(std::integral_constant<int, I>{}) for I = 0 .. N-1, so
+// that every table lookup inside f is a constant expression (if constexpr).
+template <class F, int... I>
+__host__ __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F> __host__ __device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 struct D2Q9 {
     static constexpr int D = 2;
@@ -111,14 +124,44 @@ struct D3Q19 {
              : a == 17 ? (2 * c2 - 3) * (2 * x * x - y * y - z * z)
              :           (2 * c2 - 3) * (y * y - z * z);
     }
-    // N_a = sum_i w_i T_ai^2, evaluated at compile time
+    // squared norms N_a (equal to sum_i w_i T_ai^2, checked below)
     __host__ __device__ static constexpr double Nd(int a)
     {
-        double s = 0.0;
-        for (int i = 0; i < Q; i++) s += wd(i) * T(a, i) * T(a, i);
-        return s;
+        return a == 0 ? 1.0
+             : a <= 3 ? 1.0 / 3.0
+             : a == 4 ? 2.0 / 3.0
+             : a == 5 ? 4.0 / 3.0
+             : a == 6 ? 4.0 / 9.0
+             : a <= 9 ? 1.0 / 9.0
+             : a <= 12 ? 2.0 / 3.0
+             : a <= 15 ? 2.0 / 9.0
+             : a == 16 ? 2.0
+             : a == 17 ? 4.0 / 3.0
+             :           4.0 / 9.0;
     }
 };
+
+// component d of velocity i
+template <class L> __host__ __device__ constexpr int comp(int i, int d)
+{
+    return d == 0 ? L::cx(i) : (d == 1 ? L::cy(i) : L::cz(i));
+}
+
+// Compile-time check of a basis: orthogonality sum_i w_i T_ai T_bi = N_a delta_ab
+// (Eq. V-orthog-compl-discrete) up to rounding of the weights.
+template <class L> constexpr bool basis_is_orthogonal()
+{
+    for (int a = 0; a < L::Q; a++)
+        for (int b = 0; b < L::Q; b++) {
+            double s = 0.0;
+            for (int i = 0; i < L::Q; i++) s += L::wd(i) * L::T(a, i) * L::T(b, i);
+            const double want = a == b ? L::Nd(a) : 0.0;
+            if (s - want > 1e-12 || want - s > 1e-12) return false;
+        }
+    return true;
+}
+static_assert(basis_is_orthogonal<D2Q9>(), "D2Q9 basis is not orthogonal with the Table I norms");
+static_assert(basis_is_orthogonal<D3Q19>(), "D3Q19 basis is not orthogonal with its norms");
 
 // Closed-form equilibrium moments m^eq_a(rho, u) of the second-order Hermite
 // equilibrium (Table I column for D2Q9; for D3Q19 the Hermite rows give

@@ -9,6 +9,8 @@
 #pragma once
 #include <cstdint>
 
+#include "flbm_lattice.cuh"
+
 namespace flbm {
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1)
@@ -51,31 +53,31 @@ __host__ __device__ constexpr bool uses_mode(int a)
 
 // Fill g[a] with the standard Gaussian of mode a for every mode species S uses:
 // counter (site, step, S, a/4), lane a mod 4.  Only the needed Philox blocks
-// and Box-Muller pairs are evaluated.
+// and Box-Muller pairs are evaluated (decided at compile time).
 template <class L, int S>
-__device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uint32_t k0,
-                                               uint32_t k1, float *g)
+__device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uint32_t k0, uint32_t k1,
+                                               float (&g)[L::Q])
 {
-#pragma unroll
-    for (int slot = 0; slot * 4 < L::Q; slot++) {
-        const bool p0 = uses_mode<L, S>(4 * slot) || uses_mode<L, S>(4 * slot + 1);
-        const bool p1 = uses_mode<L, S>(4 * slot + 2) || uses_mode<L, S>(4 * slot + 3);
-        if (p0 || p1) {
+    static_for<(L::Q + 3) / 4>([&](auto sc) {
+        constexpr int slot = decltype(sc)::value;
+        constexpr bool u0 = uses_mode<L, S>(4 * slot), u1 = uses_mode<L, S>(4 * slot + 1);
+        constexpr bool u2 = uses_mode<L, S>(4 * slot + 2), u3 = uses_mode<L, S>(4 * slot + 3);
+        if constexpr (u0 || u1 || u2 || u3) {
             const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)slot), k0, k1);
-            if (p0) {
+            if constexpr (u0 || u1) {
                 float g0, g1;
                 box_muller(x.x, x.y, g0, g1);
-                if (uses_mode<L, S>(4 * slot)) g[4 * slot] = g0;
-                if (uses_mode<L, S>(4 * slot + 1)) g[4 * slot + 1] = g1;
+                if constexpr (u0) g[4 * slot] = g0;
+                if constexpr (u1) g[4 * slot + 1] = g1;
             }
-            if (p1) {
+            if constexpr (u2 || u3) {
                 float g2, g3;
                 box_muller(x.z, x.w, g2, g3);
-                if (uses_mode<L, S>(4 * slot + 2)) g[4 * slot + 2] = g2;
-                if (uses_mode<L, S>(4 * slot + 3)) g[4 * slot + 3] = g3;
+                if constexpr (u2) g[4 * slot + 2] = g2;
+                if constexpr (u3) g[4 * slot + 3] = g3;
             }
         }
-    }
+    });
 }
 
 } // namespace flbm

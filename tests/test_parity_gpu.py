@@ -164,8 +164,12 @@ def test_structure_factor_matches_oracle(lat, shape, axis):
     gs = g.structure_factor(axis)
     os_ = o.structure_factor()
     assert gs[4] == os_[4] == 3
-    for a, b in zip(gs[:4], os_[:4]):
-        assert np.allclose(a, b, rtol=2e-5, atol=1e-7 * np.max(np.abs(b)))
+    # The two states differ by float rounding of the populations (~1e-7), so each
+    # Fourier amplitude carries a relative error ~1e-5 after the large mean
+    # cancels; S_ab's error therefore scales with sqrt(S_aa S_bb).
+    for k in (0, 2, 3):
+        assert np.allclose(gs[k], os_[k], rtol=2e-5, atol=0)
+    assert np.all(np.abs(gs[1] - os_[1]) <= 2e-5 * np.sqrt(os_[0] * os_[2]))
 
 
 @pytest.mark.parametrize("storage,bits", [("f16", 11), ("bf16", 8)])
