@@ -15,6 +15,7 @@
 #include "flbm_lattice.cuh"
 #include "flbm_launch.h"
 #include "flbm_noise.cuh"
+#include "flbm_transform.cuh"
 
 namespace flbm {
 namespace kern {
@@ -67,25 +68,6 @@ __device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s)
     else return (size_t)(s * L::Q + I) * NN + nb.at(L::cx(I), L::cy(I), L::cz(I));
 }
 
-// deviation moments m_a = sum_i T_ai delta_i (m_0 = rho - rho0); the 0/+-1
-// entries of T become plain adds and subtracts
-template <class L>
-__device__ __forceinline__ void project(const float (&d)[L::Q], float (&m)[L::Q])
-{
-    static_for<L::Q>([&](auto ac) {
-        constexpr int a = decltype(ac)::value;
-        float s = 0.0f;
-        static_for<L::Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            constexpr int t = L::T(a, i);
-            if constexpr (t == 1) s += d[i];
-            else if constexpr (t == -1) s -= d[i];
-            else if constexpr (t != 0) s += (float)t * d[i];
-        });
-        m[a] = s;
-    });
-}
-
 // ---------------------------------------------------------------------------
 // density pass
 // ---------------------------------------------------------------------------
@@ -99,13 +81,15 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
     const size_t NN = (size_t)p.N;
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        float sum = 0.0f;
+        float d[L::Q], m[L::Q];
         static_for<L::Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr float wi = (float)L::wd(i);
-            sum += S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+            d[i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
         });
-        rho[(size_t)s * NN + nb.at(0, 0, 0)] = p.rho0[s] + sum;
+        // the collide kernel computes its own density with this same expression
+        Transform<L>::forward(d, m);
+        rho[(size_t)s * NN + nb.at(0, 0, 0)] = p.rho0[s] + m[0];
     });
 }
 
@@ -133,7 +117,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
             constexpr float wi = (float)L::wd(i);
             d[i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
         });
-        project<L>(d, m[s]);
+        Transform<L>::forward(d, m[s]);
         rs[s] = p.rho0[s] + m[s][0];
     });
 
@@ -203,19 +187,19 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
             constexpr int a = decltype(kc)::value + D + 1;
             m[s][a] += p.lam[s][a] * (meq[a] - m[s][a]) + p.hlam[s][a] * phi[a] + p.noise_amp[s][a] * sq[s] * g[s][a];
         });
+        // back to populations: delta*_i = w_i sum_a T_ai m*_a / N_a (Eq. algorithm)
+        float mu[Q], fo[Q];
+        static_for<Q>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            constexpr float invN = (float)(1.0 / L::Nd(a));
+            if constexpr (a == 0) mu[a] = m[s][a];
+            else mu[a] = invN * m[s][a];
+        });
+        Transform<L>::backward(mu, fo);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr float wi = (float)L::wd(i);
-            float fi = 0.0f;
-            static_for<Q>([&](auto ac) {
-                constexpr int a = decltype(ac)::value;
-                constexpr int t = L::T(a, i);
-                if constexpr (t != 0) {
-                    constexpr float coef = (float)t * (float)(1.0 / L::Nd(a));
-                    fi += coef * m[s][a];
-                }
-            });
-            S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), wi * fi, wi * p.rho0[s]);
+            S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), fo[i], wi * p.rho0[s]);
         });
     });
 }

@@ -19,9 +19,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
     constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; r++) {
-        const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
-        const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
-        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+        // one 32x32 -> 64-bit product gives both halves
+        const uint64_t p0 = (uint64_t)M0 * x.x;
+        const uint64_t p1 = (uint64_t)M1 * x.z;
+        x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ k1, (uint32_t)p0);
         k0 += W0;
         k1 += W1;
     }
@@ -31,13 +32,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
 // Box-Muller on one pair of words: u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and
 // u2 = (b >> 8) 2^-24 in [0, 1) are exact in float; g0 = r cos(2 pi u2),
 // g1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
+// The angle is folded exactly into [-pi, pi) (u2 - 1 for u2 >= 1/2, the same
+// sine and cosine), where the hardware sine/cosine have an absolute error of
+// about 2^-21; r = x rsqrt(x) (x = 0 when u1 = 1 gives r = 0).  The logarithm
+// keeps full single precision, so small radii stay accurate.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
 {
     const float u1 = (float)((a >> 8) + 1u) * 0x1.0p-24f;
     const float u2 = (float)(b >> 8) * 0x1.0p-24f;
-    const float r = sqrtf(-2.0f * logf(u1));
+    const float r2 = -2.0f * logf(u1);
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float t = u2 < 0.5f ? u2 : u2 - 1.0f;
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    __sincosf(6.28318530717958647692f * t, &s, &c);
     g0 = r * c;
     g1 = r * s;
 }
