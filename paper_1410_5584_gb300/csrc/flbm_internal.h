@@ -80,8 +80,9 @@ inline size_t storage_bytes(int storage) { return storage == FLBM_STORE_F32 ? 4 
 // return the launch error.
 // ---------------------------------------------------------------------------
 
-// Density pass: rho[s * N + site] = rho0^s + sum_i delta_i^s(site), reading the
-// populations according to the in-place streaming parity.
+// Density pass: (rho_A, rho_B) of each site as interleaved float pairs,
+// rho[2 * site + s] = rho0^s + sum_i delta_i^s(site), reading the populations
+// according to the in-place streaming parity.
 cudaError_t launch_density(int lat, int storage, int parity, const StepParams &p, const void *pop,
                            float *rho, cudaStream_t stream);
 
@@ -106,7 +107,8 @@ cudaError_t launch_sum_partials(const double *partials, int nblocks, double *out
 cudaError_t launch_sf_accumulate(int D, int nx, int ny, int nz, int axis, const double *obs,
                                  double *profile, double *acc, cudaStream_t stream);
 
-// Rest-state populations from a float density field (two planes of N).
+// Rest-state populations from a float density field (two planes of N: all of
+// species A, then all of species B).
 cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in,
                              void *pop, cudaStream_t stream);
 

@@ -73,12 +73,13 @@ __device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s)
 // ---------------------------------------------------------------------------
 template <class L, class S, int PARITY>
 __global__ void __launch_bounds__(128) k_density(const StepParams p, const typename S::T *__restrict__ pop,
-                                                 float *__restrict__ rho)
+                                                 float2 *__restrict__ rho)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
     const size_t NN = (size_t)p.N;
+    float r[2];
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         float d[L::Q], m[L::Q];
@@ -89,8 +90,9 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
         });
         // the collide kernel computes its own density with this same expression
         Transform<L>::forward(d, m);
-        rho[(size_t)s * NN + nb.at(0, 0, 0)] = p.rho0[s] + m[0];
+        r[s] = p.rho0[s] + m[0];
     });
+    rho[nb.at(0, 0, 0)] = make_float2(r[0], r[1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
 // ---------------------------------------------------------------------------
 template <class L, class S, int PARITY>
 __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S::T *__restrict__ pop,
-                                                 const float *__restrict__ rho, unsigned *__restrict__ status)
+                                                 const float2 *__restrict__ rho, unsigned *__restrict__ status)
 {
     constexpr int Q = L::Q, D = L::D;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,8 +128,8 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
     static_for<Q - 1>([&](auto kc) {
         constexpr int i = decltype(kc)::value + 1;
         constexpr float wi = (float)L::wd(i);
-        const int ns = nb.at(L::cx(i), L::cy(i), L::cz(i));
-        const float ra = __ldg(rho + ns), rb = __ldg(rho + NN + ns);
+        const float2 rn = __ldg(rho + nb.at(L::cx(i), L::cy(i), L::cz(i)));
+        const float ra = rn.x, rb = rn.y;
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             constexpr int cd = comp<L>(i, d);
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
 
     // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
     const float rt = rs[0] + rs[1];
-    const float irt = 1.0f / rt;
+    const float irt = __frcp_rn(rt);
     float u[3] = {0.0f, 0.0f, 0.0f};
     static_for<D>([&](auto dc) {
         constexpr int d = decltype(dc)::value;
@@ -160,14 +162,17 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
     float g[2][Q];
     draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, g[0]);
     draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, g[1]);
-    const float amp_j = p.noise_amp_j * sqrtf(n0 * n1 / (n0 + n1));
-    const float sq[2] = {sqrtf(n0), sqrtf(n1)};
+    // square roots as x rsqrt(x): the densities are positive on every valid state
+    // (a non-positive one has already raised the status flag)
+    const float hm = n0 * n1 * __frcp_rn(n0 + n1);
+    const float amp_j = p.noise_amp_j * (hm * rsqrtf(hm));
+    const float sq[2] = {n0 * rsqrtf(n0), n1 * rsqrtf(n1)};
 
     // 5. momentum modes: common rate, opposite noise; species velocity for Phi
     float v[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        const float irs = 1.0f / rs[s];
+        const float irs = __frcp_rn(rs[s]);
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             constexpr int a = 1 + d;
@@ -267,7 +272,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV])
 
 template <class L, class S, int PARITY>
 __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, const typename S::T *__restrict__ pop,
-                                                           const float *__restrict__ rho, double *__restrict__ rho_a,
+                                                           const float2 *__restrict__ rho, double *__restrict__ rho_a,
                                                            double *__restrict__ rho_b, double *__restrict__ u,
                                                            double *__restrict__ partials)
 {
@@ -304,8 +309,8 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
         // force with the density field (the same values the step kernel uses)
         static_for<Q - 1>([&](auto kc) {
             constexpr int i = decltype(kc)::value + 1;
-            const int ns = at(L::cx(i), L::cy(i), L::cz(i));
-            const double ra = rho[ns], rb = rho[NN + ns];
+            const float2 rn = rho[at(L::cx(i), L::cy(i), L::cz(i))];
+            const double ra = rn.x, rb = rn.y;
             static_for<3>([&](auto dc) {
                 constexpr int d = decltype(dc)::value;
                 constexpr int cd = comp<L>(i, d);
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
                 }
             });
         });
-        const double ra0 = rho[site], rb0 = rho[NN + site];
+        const double ra0 = rho[site].x, rb0 = rho[site].y;
         const double rt = r[0] + r[1];
         if (rho_a) rho_a[site] = r[0];
         if (rho_b) rho_b[site] = r[1];
@@ -349,8 +354,9 @@ cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *p
 {
     const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
     auto *ptr = static_cast<const typename S::T *>(pop);
-    if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, ptr, rho);
-    else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, ptr, rho);
+    auto *r2 = reinterpret_cast<float2 *>(rho);
+    if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, ptr, r2);
+    else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, ptr, r2);
     return cudaGetLastError();
 }
 
@@ -360,8 +366,9 @@ cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, co
 {
     const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
     auto *ptr = static_cast<typename S::T *>(pop);
-    if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, ptr, rho, status);
-    else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, ptr, rho, status);
+    auto *r2 = reinterpret_cast<const float2 *>(rho);
+    if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, ptr, r2, status);
+    else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, ptr, r2, status);
     return cudaGetLastError();
 }
 
@@ -390,8 +397,9 @@ cudaError_t Launch<L, S>::observables(int parity, const StepParams &p, const voi
     const dim3 b(kern::kObsBlock), g((p.nx + kern::kObsBlock - 1) / kern::kObsBlock, p.ny, p.nz);
     *nblocks = (int)(g.x * g.y * g.z);
     auto *ptr = static_cast<const typename S::T *>(pop);
-    if (parity == 0) kern::k_observables<L, S, 0><<<g, b, 0, st>>>(p, ptr, rho, ra, rb, u, partials);
-    else kern::k_observables<L, S, 1><<<g, b, 0, st>>>(p, ptr, rho, ra, rb, u, partials);
+    auto *r2 = reinterpret_cast<const float2 *>(rho);
+    if (parity == 0) kern::k_observables<L, S, 0><<<g, b, 0, st>>>(p, ptr, r2, ra, rb, u, partials);
+    else kern::k_observables<L, S, 1><<<g, b, 0, st>>>(p, ptr, r2, ra, rb, u, partials);
     return cudaGetLastError();
 }
 
