@@ -198,6 +198,36 @@ flbm_status flbm_get_site_populations(flbm_ctx *ctx, const int64_t *sites, int64
 flbm_status flbm_checkpoint(flbm_ctx *ctx, void *buf, size_t *bytes);
 flbm_status flbm_restore(flbm_ctx *ctx, const void *buf, size_t bytes);
 
+/*
+ * Step populations that the caller owns, allocating no device memory.  The
+ * paper has no counterpart: this serves callers that cannot call cudaMalloc
+ * (an arena or pool that owns all device memory, a real-time loop where an
+ * allocation could stall or fail).  The density field and status word it
+ * needs live in a fixed static device array that every GPU loading this
+ * library holds until the process exits (2^21 sites: 16 MiB + 256 bytes).
+ *   ctx:    supplies the lattice, box, storage format, parameters and options
+ *           (from flbm_create / flbm_set_option; its own buffers and step
+ *           counter are neither used nor changed).
+ *   pop:    device populations in this library's in-place layout, storage
+ *           format of ctx, flbm_buffer_bytes() bytes, 256-byte aligned;
+ *           read and updated in place.
+ *   parity: streaming parity of `pop` (0 after an even number of steps since a
+ *           natural-layout state, 1 after an odd number); after n steps it is
+ *           parity ^ (n & 1).
+ *   step:   noise counter of the first step; n: number of steps.
+ *   stream: cudaStream_t to run on (NULL = the legacy default stream).
+ *   status_out: if non-NULL, receives the device status word (bit 0: a
+ *           density was not positive and finite).
+ * Synchronises `stream` before returning.  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents: calls
+ * that overlap on the GPU (other streams, other threads) race.
+ * Errors: FLBM_EINVAL for bad arguments or a box above 2^21 sites;
+ * FLBM_ENONFINITE if the status bit is set; FLBM_ECUDA if a CUDA call fails.
+ */
+flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int parity, int64_t step, int64_t n,
+                              void *stream, unsigned *status_out);
+
 /* One-line reason of the last error on this context ("" if none).  The string
  * is owned by the context.  Never NULL (ctx may be NULL). */
 const char *flbm_last_error(const flbm_ctx *ctx);

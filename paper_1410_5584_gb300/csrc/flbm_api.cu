@@ -337,6 +337,21 @@ struct CkptHeader {
 
 } // namespace
 
+bool flbm::ctx_view(const flbm_ctx *c, CtxView *out)
+{
+    if (!c || !out) return false;
+    out->lat = c->lat;
+    out->storage = c->storage;
+    out->D = c->D;
+    out->Q = c->Q;
+    out->nx = c->nx;
+    out->ny = c->ny;
+    out->nz = c->nz;
+    out->N = c->N;
+    out->params = make_params(c);
+    return true;
+}
+
 extern "C" {
 
 const char *flbm_version(void) { return "flbm 0.1 sm_103a"; }

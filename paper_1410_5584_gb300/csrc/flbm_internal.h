@@ -117,4 +117,12 @@ cudaError_t launch_gather_sites(int lat, int storage, int parity, const StepPara
                                 const void *pop, const int64_t *sites, int64_t nsites, double *out,
                                 cudaStream_t stream);
 
+// Read-only view of a context for the other translation units of the library.
+struct CtxView {
+    int lat, storage, D, Q, nx, ny, nz;
+    int64_t N;
+    StepParams params; // parameters of the context's next step
+};
+bool ctx_view(const flbm_ctx *ctx, CtxView *out);
+
 } // namespace flbm
