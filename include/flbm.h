@@ -50,7 +50,7 @@ typedef enum {
     FLBM_ENOMEM = 2,       /* a host or device allocation failed */
     FLBM_ECUDA = 3,        /* a CUDA runtime call failed (reason in flbm_last_error) */
     FLBM_ENONFINITE = 4,   /* a density became non-positive or non-finite on the device */
-    FLBM_ETIMEOUT = 5,     /* a bounded device wait gave up */
+    FLBM_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the state is not valid */
     FLBM_EUNSUPPORTED = 6, /* valid request that this build does not support */
     FLBM_ESTATE = 7        /* call out of order (e.g. step before init) */
 } flbm_status;
@@ -63,6 +63,15 @@ typedef enum {
     FLBM_STORE_F16 = 1,  /* stored as half deviations from w_i * rho0^s; collided in float */
     FLBM_STORE_BF16 = 2  /* stored as bfloat16 deviations from w_i * rho0^s; collided in float */
 } flbm_storage;
+
+/* How flbm_step runs one update (option FLBM_OPT_SCHEDULE).  Both give the same
+ * populations bit for bit. */
+typedef enum {
+    FLBM_SCHEDULE_FUSED = 0,      /* default: one persistent launch per step; density and collision
+                                     work items ordered so the populations read for the densities are
+                                     reused from L2 by the collision (one HBM pass each way) */
+    FLBM_SCHEDULE_TWO_KERNELS = 1 /* a density kernel, then the collide kernel */
+} flbm_schedule;
 
 /* Option keys for flbm_set_option. */
 enum {
@@ -85,6 +94,13 @@ enum {
     FLBM_OPT_KERNEL_TIMING = 10, /* 1: flbm_step records CUDA events around each kernel on the
                                     context's stream (see flbm_kernel_times); 0 (default): off.
                                     Switching it clears the accumulated times */
+    FLBM_OPT_SCHEDULE = 11,      /* flbm_schedule: how flbm_step runs one step (same results) */
+    FLBM_OPT_WAIT_LIMIT_MS = 12, /* fused schedule: time after which a device-side dependency wait
+                                    gives up and sets the timeout status (FLBM_ETIMEOUT at the next
+                                    synchronising call); 1 .. 60000, default 2000 */
+    FLBM_OPT_TEST_STALL = 13,    /* failure-detection test hook: 1 makes every dependency wait of the
+                                    fused step wait for work that never comes, so it runs out after
+                                    the wait limit; 0 (default) off */
     FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
 };
@@ -143,10 +159,11 @@ flbm_status flbm_step(flbm_ctx *ctx, int64_t n);
  * (FLBM_ENONFINITE once a density was not positive and finite). */
 flbm_status flbm_sync(flbm_ctx *ctx);
 
-/* Accumulated device time of the kernels launched by flbm_step while
- * FLBM_OPT_KERNEL_TIMING was on, in milliseconds, per kernel kind:
- * ms[0] density pass, ms[1] fused collide-and-stream; launches[k] the number of
- * launches timed.  Either array may be NULL.  Synchronising. */
+/* Accumulated device time of the work flbm_step launched while
+ * FLBM_OPT_KERNEL_TIMING was on, in milliseconds: ms[0] the density kernel
+ * (two-kernel schedule) or the counter reset (fused schedule), ms[1] the
+ * collide kernel or the fused step kernel; launches[k] the number of steps
+ * timed.  Either array may be NULL.  Synchronising. */
 flbm_status flbm_kernel_times(flbm_ctx *ctx, double ms[2], int64_t launches[2]);
 
 /* Steps taken since flbm_init (or the restored checkpoint's count). */

@@ -23,12 +23,16 @@ struct flbm_ctx {
     // options
     double lam[2][kMaxQ] = {};
     int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
+    int schedule = FLBM_SCHEDULE_FUSED;
+    double wait_limit_ms = 2000.0;
+    int test_stall = 0;
     double rho0[2] = {1.0, 1.0};
     // state
     int64_t step = 0;
     int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
     bool initialised = false;
     bool faulted = false;
+    bool timed_out = false;
     // device buffers
     void *pop = nullptr;
     size_t pop_bytes = 0;
@@ -36,6 +40,7 @@ struct flbm_ctx {
     size_t rho_bytes = 0;
     bool own_buffers = false;
     unsigned *d_status = nullptr;
+    unsigned *d_pipe = nullptr;   // fused-step counters: next item + one per slice
     double *d_obs = nullptr;      // (2 + D) * N doubles: rho_a, rho_b, u
     double *d_partials = nullptr; // per-block totals
     size_t partials_cap = 0;
@@ -172,6 +177,15 @@ flbm_status ensure_buffers(flbm_ctx *c)
     return ensure_status(c);
 }
 
+flbm_status ensure_pipe(flbm_ctx *c)
+{
+    if (!c->d_pipe) {
+        const size_t n = 1 + (size_t)pipeline_slices(c->lat, c->ny, c->nz);
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_pipe, n * sizeof(unsigned)), "cudaMalloc(pipeline counters)");
+    }
+    return FLBM_OK;
+}
+
 flbm_status ensure_stage(flbm_ctx *c)
 {
     if (!c->h_stage) {
@@ -235,7 +249,10 @@ flbm_status sync_and_check(flbm_ctx *c)
         unsigned h = 0;
         FLBM_CUDA(c, cudaMemcpy(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost), "status read");
         if (h & kStatusNonFinite) c->faulted = true;
+        if (h & kStatusTimeout) c->timed_out = true;
     }
+    if (c->timed_out)
+        return fail(c, FLBM_ETIMEOUT, "a device-side wait of the fused step gave up (state is not valid)");
     if (c->faulted)
         return fail(c, FLBM_ENONFINITE, "a density became non-positive or non-finite on the device (step <= %lld)",
                     (long long)c->step);
@@ -417,6 +434,15 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
             free_sf(c);
             c->sf_axis = (int)v;
         }
+    } else if (key == FLBM_OPT_SCHEDULE) {
+        if (v != (double)FLBM_SCHEDULE_FUSED && v != (double)FLBM_SCHEDULE_TWO_KERNELS)
+            return fail(c, FLBM_EINVAL, "schedule must be 0 (fused) or 1 (two kernels)");
+        c->schedule = (int)v;
+    } else if (key == FLBM_OPT_WAIT_LIMIT_MS) {
+        if (!(v >= 1.0 && v <= 60000.0)) return fail(c, FLBM_EINVAL, "wait limit must lie in [1, 60000] ms");
+        c->wait_limit_ms = v;
+    } else if (key == FLBM_OPT_TEST_STALL) {
+        c->test_stall = v != 0.0;
     } else if (key == FLBM_OPT_KERNEL_TIMING) {
         if (c->stream) {
             flbm_status st = drain_timing(c);
@@ -507,6 +533,7 @@ flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
     c->step = 0;
     c->parity = 0;
     c->faulted = false;
+    c->timed_out = false;
     c->initialised = true;
     return FLBM_OK;
 }
@@ -515,6 +542,10 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
+    if (c->schedule == FLBM_SCHEDULE_FUSED) {
+        flbm_status st = ensure_pipe(c);
+        if (st != FLBM_OK) return st;
+    }
     StepParams p = make_params(c);
     for (int64_t t = 0; t < n; t++) {
         p.step = (uint32_t)c->step;
@@ -531,11 +562,18 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
             }
             FLBM_CUDA(c, cudaEventRecord(ev[0], c->stream), "cudaEventRecord");
         }
-        cudaError_t e = launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
-        if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
-        e = launch_collide(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
+        if (c->schedule == FLBM_SCHEDULE_FUSED) {
+            if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
+            cudaError_t e = launch_step_fused(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status,
+                                              c->d_pipe, c->wait_limit_ms, c->test_stall, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "fused step kernel launch");
+        } else {
+            cudaError_t e = launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
+            if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
+            e = launch_collide(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
+        }
         if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[2], c->stream), "cudaEventRecord");
         c->step++;
         c->parity ^= 1;
@@ -691,6 +729,7 @@ flbm_status flbm_set_populations(flbm_ctx *c, const double *f, int64_t step)
     c->step = step;
     c->parity = 0;
     c->faulted = false;
+    c->timed_out = false;
     c->initialised = true;
     return FLBM_OK;
 }
@@ -799,6 +838,7 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
         c->sf_axis = h.sf_axis;
     }
     c->faulted = false;
+    c->timed_out = false;
     c->initialised = true;
     return FLBM_OK;
 }
@@ -812,6 +852,7 @@ void flbm_destroy(flbm_ctx *c)
         if (c->rho) cudaFree(c->rho);
     }
     if (c->d_status) cudaFree(c->d_status);
+    if (c->d_pipe) cudaFree(c->d_pipe);
     if (c->d_obs) cudaFree(c->d_obs);
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_cons) cudaFree(c->d_cons);

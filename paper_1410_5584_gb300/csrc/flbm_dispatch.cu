@@ -25,6 +25,9 @@ template <class L, class S> struct DensityF {
 template <class L, class S> struct CollideF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::collide(a...); }
 };
+template <class L, class S> struct FusedF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::step_fused(a...); }
+};
 template <class L, class S> struct InitF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::init_rest(a...); }
 };
@@ -47,6 +50,12 @@ cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p
                            unsigned *status, cudaStream_t stream)
 {
     return dispatch<CollideF>(lat, storage, parity, p, pop, rho, status, stream);
+}
+
+cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams &p, void *pop, float *rho,
+                              unsigned *status, unsigned *counters, double wait_ms, int stall, cudaStream_t stream)
+{
+    return dispatch<FusedF>(lat, storage, parity, p, pop, rho, status, counters, wait_ms, stall, stream);
 }
 
 cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in, void *pop,

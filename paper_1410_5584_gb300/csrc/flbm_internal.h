@@ -30,6 +30,7 @@ struct StepParams {
 
 // Device status bits (ORed by kernels, read by the host at sync points).
 constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;   // a bounded device-side wait gave up
 
 // ---------------------------------------------------------------------------
 // Population storage.  Kernels work with deviations delta_i = f_i - w_i rho0^s:
@@ -89,6 +90,15 @@ cudaError_t launch_density(int lat, int storage, int parity, const StepParams &p
 // Fused force + moment collision + noise + in-place streaming of one step.
 cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop,
                            const float *rho, unsigned *status, cudaStream_t stream);
+
+// One whole step (densities and collision) as one persistent launch whose
+// work items are ordered so the densities' population reads are reused from
+// L2 by the collision.  counters: 1 + (number of slices) unsigned words of
+// scratch, reset by the launcher.  wait_ms bounds each dependency wait; stall
+// (test hook) makes every wait run out.
+cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams &p, void *pop, float *rho,
+                              unsigned *status, unsigned *counters, double wait_ms, int stall, cudaStream_t stream);
+inline int pipeline_slices(int lat, int ny, int nz) { return lat == FLBM_D2Q9 ? ny : nz; }
 
 // Per-site observables in double: rho_a, rho_b, u (D planes), any may be NULL,
 // plus per-block FP64 partial totals [nblocks][5] into `partials`; returns the

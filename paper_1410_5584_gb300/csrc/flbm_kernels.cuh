@@ -71,13 +71,10 @@ __device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s)
 // ---------------------------------------------------------------------------
 // density pass
 // ---------------------------------------------------------------------------
+// densities (rho_A, rho_B) of one site from its pre-collision populations
 template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(128) k_density(const StepParams p, const typename S::T *__restrict__ pop,
-                                                 float2 *__restrict__ rho)
+__device__ __forceinline__ float2 site_density(const StepParams &p, const typename S::T *__restrict__ pop, const Nbr &nb)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
     const size_t NN = (size_t)p.N;
     float r[2];
     static_for<2>([&](auto sc) {
@@ -88,24 +85,35 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
             constexpr float wi = (float)L::wd(i);
             d[i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
         });
-        // the collide kernel computes its own density with this same expression
+        // the collide step computes its own density with this same expression
         Transform<L>::forward(d, m);
         r[s] = p.rho0[s] + m[0];
     });
-    rho[nb.at(0, 0, 0)] = make_float2(r[0], r[1]);
+    return make_float2(r[0], r[1]);
+}
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_density(const StepParams p, const typename S::T *__restrict__ pop,
+                                                 float2 *__restrict__ rho)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+    rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
 }
 
 // ---------------------------------------------------------------------------
 // fused force + moment collision + noise + streaming
 // ---------------------------------------------------------------------------
-template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S::T *__restrict__ pop,
-                                                 const float2 *__restrict__ rho, unsigned *__restrict__ status)
+// Force + moment collision + noise + streaming of one site.  COHERENT_RHO: read
+// the density field through L2 only (ld.global.cg), for a density field written
+// earlier in the same kernel launch by other thread blocks.
+template <class L, class S, int PARITY, bool COHERENT_RHO>
+__device__ __forceinline__ void site_collide(const StepParams &p, typename S::T *__restrict__ pop,
+                                             const float2 *__restrict__ rho, unsigned *__restrict__ status,
+                                             const Nbr &nb)
 {
     constexpr int Q = L::Q, D = L::D;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
     const size_t NN = (size_t)p.N;
     const int site = nb.at(0, 0, 0);
 
@@ -128,7 +136,8 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
     static_for<Q - 1>([&](auto kc) {
         constexpr int i = decltype(kc)::value + 1;
         constexpr float wi = (float)L::wd(i);
-        const float2 rn = __ldg(rho + nb.at(L::cx(i), L::cy(i), L::cz(i)));
+        const float2 *rp = rho + nb.at(L::cx(i), L::cy(i), L::cz(i));
+        const float2 rn = COHERENT_RHO ? __ldcg(rp) : __ldg(rp);
         const float ra = rn.x, rb = rn.y;
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
@@ -207,6 +216,147 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
             S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), fo[i], wi * p.rho0[s]);
         });
     });
+}
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S::T *__restrict__ pop,
+                                                 const float2 *__restrict__ rho, unsigned *__restrict__ status)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+    site_collide<L, S, PARITY, false>(p, pop, rho, status, nb);
+}
+
+// ---------------------------------------------------------------------------
+// One whole step in one persistent launch.  The lattice is cut into slices
+// along its outermost axis (z in 3D, y in 2D), each slice into tiles of 128
+// sites along x.  Work items, taken in order from an atomic counter:
+//   D(j): densities of the tiles of slice j;   C(j): collide the tiles of slice j.
+// C(j) needs the densities of slices j-1, j, j+1; the order
+//   D(S-1) D(0) D(1) C(0) D(2) C(1) D(3) ... D(S-2) C(S-3) C(S-2) C(S-1)
+// places D(j+1) just before C(j), so the populations a D item pulls from HBM
+// are still in L2 when the C item of the same slice reads them again: each
+// population crosses HBM once each way per step.  A C item waits on per-slice
+// completion counters (bounded by a time limit; a timeout sets a status bit).
+// In-place streaming is safe: the slots a site's C item reads and writes are
+// touched by no other C item, and a D item only reads slots of its own slice
+// before that slice's C item runs.  Items are handed out in order, so an item
+// only ever waits on items already taken by running blocks.
+// ---------------------------------------------------------------------------
+struct PipeArgs {
+    unsigned *next_item;  // item counter (zero at launch)
+    unsigned *done;       // completed D tiles per slice (zero at launch)
+    int slices, tiles_per_slice, segs_per_row;
+    int total_items;
+    unsigned target;            // D tiles a slice needs before its neighbours' C items may run
+    unsigned long long wait_ns; // give-up time of one dependency wait
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// item q of the step -> (is_collide, slice)
+__device__ __forceinline__ void decode_item(int q, int S, bool &collide, int &slice)
+{
+    if (S < 4) {
+        collide = q >= S;
+        slice = collide ? q - S : q;
+        return;
+    }
+    if (q < 3) {
+        collide = false;
+        slice = q == 0 ? S - 1 : q - 1;
+        return;
+    }
+    if (q >= 2 * S - 3) {
+        collide = true;
+        slice = q - S;
+        return;
+    }
+    const int r = q - 3;
+    collide = (r & 1) == 0;
+    slice = collide ? r >> 1 : (r >> 1) + 2;
+}
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename S::T *__restrict__ pop,
+                                                    float2 *__restrict__ rho, unsigned *__restrict__ status,
+                                                    const PipeArgs a)
+{
+    __shared__ int s_item;
+    __shared__ int s_ok;
+    const int tpb = a.tiles_per_slice;
+    const int items_total = a.total_items;
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.next_item, 1u);
+    __syncthreads();
+    int item = s_item;
+    while (item < items_total) {
+        const int q = item / tpb, tile = item - q * tpb;
+        bool collide;
+        int slice;
+        decode_item(q, a.slices, collide, slice);
+        // take the next item early so its latency overlaps this one
+        int next = 0;
+        if (threadIdx.x == 0) next = (int)atomicAdd(a.next_item, 1u);
+        if (collide) {
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                const unsigned long long t0 = global_ns();
+                const int S = a.slices;
+                const int nbrs[3] = {slice == 0 ? S - 1 : slice - 1, slice, slice == S - 1 ? 0 : slice + 1};
+                for (int k = 0; k < 3 && ok; k++) {
+                    while (load_acquire(a.done + nbrs[k]) < a.target) {
+                        if (global_ns() - t0 > a.wait_ns) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+                if (!ok) atomicOr(status, kStatusTimeout);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return; // a dependency never completed: give up, the host sees the status bit
+        }
+        // tile -> site coordinates
+        int y, z;
+        if (L::D == 3) {
+            z = slice;
+            y = tile / a.segs_per_row;
+        } else {
+            z = 0;
+            y = slice;
+        }
+        const int x = (tile - (L::D == 3 ? y * a.segs_per_row : 0)) * 128 + threadIdx.x;
+        if (x < p.nx) {
+            const Nbr nb = make_nbr(p, x, y, z);
+            if (collide) site_collide<L, S, PARITY, true>(p, pop, rho, status, nb);
+            else rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (!collide) {
+                __threadfence();
+                atomicAdd(a.done + slice, 1u);
+            }
+            s_item = next;
+        }
+        __syncthreads();
+        item = s_item;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -369,6 +519,42 @@ cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, co
     auto *r2 = reinterpret_cast<const float2 *>(rho);
     if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, ptr, r2, status);
     else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, ptr, r2, status);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::step_fused(int parity, const StepParams &p, void *pop, float *rho, unsigned *status,
+                                     unsigned *counters, double wait_ms, int stall, cudaStream_t st)
+{
+    kern::PipeArgs a;
+    const int segs = (p.nx + 127) / 128;
+    a.slices = L::D == 3 ? p.nz : p.ny;
+    a.segs_per_row = segs;
+    a.tiles_per_slice = L::D == 3 ? p.ny * segs : segs;
+    a.total_items = 2 * a.slices * a.tiles_per_slice;
+    a.next_item = counters;
+    a.done = counters + 1;
+    a.target = (unsigned)a.tiles_per_slice + (stall ? 1u : 0u);
+    a.wait_ns = (unsigned long long)(wait_ms * 1e6);
+    // one resident wave of persistent blocks
+    static int blocks[2] = {0, 0};
+    if (!blocks[parity]) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = parity == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern::k_step_fused<L, S, 0>, 128, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern::k_step_fused<L, S, 1>, 128, 0);
+        if (e != cudaSuccess) return e;
+        blocks[parity] = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int grid = blocks[parity] < a.total_items ? blocks[parity] : a.total_items;
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + a.slices), st);
+    if (e != cudaSuccess) return e;
+    auto *ptr = static_cast<typename S::T *>(pop);
+    auto *r2 = reinterpret_cast<float2 *>(rho);
+    if (parity == 0) kern::k_step_fused<L, S, 0><<<grid, 128, 0, st>>>(p, ptr, r2, status, a);
+    else kern::k_step_fused<L, S, 1><<<grid, 128, 0, st>>>(p, ptr, r2, status, a);
     return cudaGetLastError();
 }
 

@@ -30,11 +30,16 @@ OPT_NOISE_RHO = 7
 OPT_FORCE_VELOCITY = 8
 OPT_SF_AXIS = 9
 OPT_KERNEL_TIMING = 10
+OPT_SCHEDULE = 11
+OPT_WAIT_LIMIT_MS = 12
+OPT_TEST_STALL = 13
+SCHEDULE = {"fused": 0, "two_kernels": 1}
 OPT_LAMBDA_MODE = 1000
 OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
                 "rho0_a": OPT_RHO0_A, "rho0_b": OPT_RHO0_B, "noise_rho": OPT_NOISE_RHO,
                 "force_velocity": OPT_FORCE_VELOCITY, "sf_axis": OPT_SF_AXIS,
-                "kernel_timing": OPT_KERNEL_TIMING}
+                "kernel_timing": OPT_KERNEL_TIMING, "schedule": OPT_SCHEDULE,
+                "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL}
 
 
 class FlbmError(RuntimeError):
@@ -187,7 +192,8 @@ class Lattice:
 
     def kernel_times(self):
         """({'density': ms, 'collide': ms}, {'density': n, 'collide': n}) accumulated
-        while the kernel_timing option was on."""
+        while the kernel_timing option was on.  With the fused schedule 'density'
+        is the counter reset and 'collide' the fused step kernel."""
         ms = np.zeros(2)
         n = np.zeros(2, dtype=np.int64)
         check(self._h, lib().flbm_kernel_times(self._h, _dp(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))

@@ -303,3 +303,40 @@ def test_full_size_d3q19_sampled_parity(steps_before):
 def test_full_size_d2q9_sampled_parity():
     """The 512^2 D2Q9 Shan-Chen box."""
     assert _block_check(D2Q9, (1, 512, 512), 3, 60, seed=2) <= 1e-6
+
+
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 2, 37)), (D2Q9, (1, 3, 130)), (D2Q9, (1, 64, 64)),
+                                       (D3Q19, (2, 5, 7)), (D3Q19, (3, 4, 9)), (D3Q19, (9, 6, 140))])
+def test_fused_and_two_kernel_schedules_agree_bitwise(lat, shape):
+    """The fused single-launch step (densities reused from L2) and the
+    density-then-collide kernels give identical populations, both parities,
+    including boxes with fewer than four slices."""
+    nz, ny, nx = shape
+    f0 = _random_state(lat, shape)
+    out = []
+    for sched in ("fused", "two_kernels"):
+        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
+        g.set_option("schedule", F.SCHEDULE[sched])
+        g.set_populations(f0, step=3)
+        g.step(5)
+        out.append(g.get_populations())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_fused_step_wait_timeout_is_reported():
+    """Failure detection without a GPU fault: a dependency wait that can never
+    be satisfied gives up after its time limit, the kernel returns, the host
+    reads FLBM_ETIMEOUT, and re-initialising restores a usable context."""
+    g = Lattice(D3Q19, 16, 8, 6, 1.0, 1.0, 1e-4, 0.5, 1)
+    g.init()
+    g.set_option("wait_limit_ms", 50)
+    g.set_option("test_stall", 1)
+    g.step(1)
+    with pytest.raises(FlbmError) as e:
+        g.sync()
+    assert e.value.status == F.ETIMEOUT
+    g.set_option("test_stall", 0)
+    g.init()
+    g.step(3)
+    g.sync()
+    assert g.moments(fields=False)[0] == pytest.approx(16 * 8 * 6, rel=1e-6)
