@@ -64,8 +64,8 @@ typedef enum {
     FLBM_STORE_BF16 = 2  /* stored as bfloat16 deviations from w_i * rho0^s; collided in float */
 } flbm_storage;
 
-/* How flbm_step runs one update (option FLBM_OPT_SCHEDULE).  Both give the same
- * populations bit for bit. */
+/* How flbm_step runs one update (option FLBM_OPT_SCHEDULE).  Both compute the
+ * same update; results agree to rounding (each schedule is deterministic). */
 typedef enum {
     FLBM_SCHEDULE_FUSED = 0,      /* default: one persistent launch per step; density and collision
                                      work items ordered so the populations read for the densities are

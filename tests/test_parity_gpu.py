@@ -307,20 +307,22 @@ def test_full_size_d2q9_sampled_parity():
 
 @pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 2, 37)), (D2Q9, (1, 3, 130)), (D2Q9, (1, 64, 64)),
                                        (D3Q19, (2, 5, 7)), (D3Q19, (3, 4, 9)), (D3Q19, (9, 6, 140))])
-def test_fused_and_two_kernel_schedules_agree_bitwise(lat, shape):
-    """The fused single-launch step (densities reused from L2) and the
-    density-then-collide kernels give identical populations, both parities,
-    including boxes with fewer than four slices."""
+def test_fused_and_two_kernel_schedules_agree(lat, shape):
+    """The fused single-launch step (densities reused from L2) is deterministic
+    run to run (bitwise), and agrees with the density-then-collide kernels to
+    rounding (the two instantiations may contract multiply-adds differently),
+    both parities, including boxes with fewer than four slices."""
     nz, ny, nx = shape
     f0 = _random_state(lat, shape)
     out = []
-    for sched in ("fused", "two_kernels"):
+    for sched in ("fused", "fused", "two_kernels"):
         g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
         g.set_option("schedule", F.SCHEDULE[sched])
         g.set_populations(f0, step=3)
         g.step(5)
         out.append(g.get_populations())
     assert np.array_equal(out[0], out[1])
+    assert _rel(out[0], out[2]) <= 5e-7
 
 
 def test_fused_step_wait_timeout_is_reported():
