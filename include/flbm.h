@@ -101,6 +101,9 @@ enum {
     FLBM_OPT_TEST_STALL = 13,    /* failure-detection test hook: 1 makes every dependency wait of the
                                     fused step wait for work that never comes, so it runs out after
                                     the wait limit; 0 (default) off */
+    FLBM_OPT_PIPE_LAG = 14,      /* fused schedule: how many slices the density work runs ahead of the
+                                    collisions; 0 (default) = the smallest lag that keeps it ahead of
+                                    the work in flight; else an integer >= 2 (results are identical) */
     FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
 };

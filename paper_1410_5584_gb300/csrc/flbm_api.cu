@@ -25,6 +25,7 @@ struct flbm_ctx {
     int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
     int schedule = FLBM_SCHEDULE_FUSED;
     double wait_limit_ms = 2000.0;
+    int pipe_lag = 0;
     int test_stall = 0;
     double rho0[2] = {1.0, 1.0};
     // state
@@ -441,6 +442,10 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
     } else if (key == FLBM_OPT_WAIT_LIMIT_MS) {
         if (!(v >= 1.0 && v <= 60000.0)) return fail(c, FLBM_EINVAL, "wait limit must lie in [1, 60000] ms");
         c->wait_limit_ms = v;
+    } else if (key == FLBM_OPT_PIPE_LAG) {
+        if (!(v == 0.0 || (v >= 2.0 && v <= 4096.0)) || v != (double)(int)v)
+            return fail(c, FLBM_EINVAL, "pipeline lag must be 0 (automatic) or an integer in [2, 4096]");
+        c->pipe_lag = (int)v;
     } else if (key == FLBM_OPT_TEST_STALL) {
         c->test_stall = v != 0.0;
     } else if (key == FLBM_OPT_KERNEL_TIMING) {
@@ -565,7 +570,7 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
         if (c->schedule == FLBM_SCHEDULE_FUSED) {
             if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
             cudaError_t e = launch_step_fused(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status,
-                                              c->d_pipe, c->wait_limit_ms, c->test_stall, c->stream);
+                                              c->d_pipe, c->wait_limit_ms, c->test_stall, c->pipe_lag, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "fused step kernel launch");
         } else {
             cudaError_t e = launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream);

@@ -53,9 +53,10 @@ cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p
 }
 
 cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams &p, void *pop, float *rho,
-                              unsigned *status, unsigned *counters, double wait_ms, int stall, cudaStream_t stream)
+                              unsigned *status, unsigned *counters, double wait_ms, int stall, int lag,
+                              cudaStream_t stream)
 {
-    return dispatch<FusedF>(lat, storage, parity, p, pop, rho, status, counters, wait_ms, stall, stream);
+    return dispatch<FusedF>(lat, storage, parity, p, pop, rho, status, counters, wait_ms, stall, lag, stream);
 }
 
 cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in, void *pop,

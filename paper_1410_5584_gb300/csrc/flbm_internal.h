@@ -93,11 +93,12 @@ cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p
 
 // One whole step (densities and collision) as one persistent launch whose
 // work items are ordered so the densities' population reads are reused from
-// L2 by the collision.  counters: 1 + (number of slices) unsigned words of
+// L2 by the collision.  counters: (number of slices) unsigned words of
 // scratch, reset by the launcher.  wait_ms bounds each dependency wait; stall
 // (test hook) makes every wait run out.
 cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams &p, void *pop, float *rho,
-                              unsigned *status, unsigned *counters, double wait_ms, int stall, cudaStream_t stream);
+                              unsigned *status, unsigned *counters, double wait_ms, int stall, int lag,
+                              cudaStream_t stream);
 inline int pipeline_slices(int lat, int ny, int nz) { return lat == FLBM_D2Q9 ? ny : nz; }
 
 // Per-site observables in double: rho_a, rho_b, u (D planes), any may be NULL,

@@ -107,29 +107,38 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
 // ---------------------------------------------------------------------------
 // Force + moment collision + noise + streaming of one site.  COHERENT_RHO: read
 // the density field through L2 only (ld.global.cg), for a density field written
-// earlier in the same kernel launch by other thread blocks.
-template <class L, class S, int PARITY, bool COHERENT_RHO>
+// earlier in the same kernel launch by other thread blocks.  STORE = false
+// computes without writing (an idle lane of a partial warp).  after_loads()
+// runs once the population loads are issued; returning false abandons the site.
+template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, class Hook = bool (*)()>
 __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T *__restrict__ pop,
                                              const float2 *__restrict__ rho, unsigned *__restrict__ status,
-                                             const Nbr &nb)
+                                             const Nbr &nb, Hook &&after_loads)
 {
     constexpr int Q = L::Q, D = L::D;
     const size_t NN = (size_t)p.N;
     const int site = nb.at(0, 0, 0);
 
-    // 1. moments of both species (Eq. modes-discrete), density rho = rhobar
+    // 1. moments of both species (Eq. modes-discrete), density rho = rhobar.
+    // All loads are issued first; `after_loads` runs while they are in flight.
     float m[2][Q], rs[2];
-    static_for<2>([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        float d[Q];
-        static_for<Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            constexpr float wi = (float)L::wd(i);
-            d[i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+    {
+        float d[2][Q];
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr float wi = (float)L::wd(i);
+                d[s][i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+            });
         });
-        Transform<L>::forward(d, m[s]);
-        rs[s] = p.rho0[s] + m[s][0];
-    });
+        if (!after_loads()) return;
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            Transform<L>::forward(d[s], m[s]);
+            rs[s] = p.rho0[s] + m[s][0];
+        });
+    }
 
     // 2. Shan-Chen force from the other species' neighbour densities (Eq. FORCESTRUCTURE)
     float acc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
@@ -163,7 +172,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
         constexpr int d = decltype(dc)::value;
         u[d] = (m[0][1 + d] + m[1][1 + d] + 0.5f * (rs[0] * acc[0][d] + rs[1] * acc[1][d])) * irt;
     });
-    if (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt)) atomicOr(status, kStatusNonFinite);
+    if (STORE && (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt))) atomicOr(status, kStatusNonFinite);
 
     // 4. noise amplitudes of Eq. new-noise (local or reference densities)
     const float n0 = p.noise_ref ? p.rho0[0] : rs[0];
@@ -213,7 +222,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr float wi = (float)L::wd(i);
-            S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), fo[i], wi * p.rho0[s]);
+            if (STORE) S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), fo[i], wi * p.rho0[s]);
         });
     });
 }
@@ -225,31 +234,36 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
-    site_collide<L, S, PARITY, false>(p, pop, rho, status, nb);
+    site_collide<L, S, PARITY, false>(p, pop, rho, status, nb, [] { return true; });
 }
 
 // ---------------------------------------------------------------------------
 // One whole step in one persistent launch.  The lattice is cut into slices
-// along its outermost axis (z in 3D, y in 2D), each slice into tiles of 128
-// sites along x.  Work items, taken in order from an atomic counter:
-//   D(j): densities of the tiles of slice j;   C(j): collide the tiles of slice j.
-// C(j) needs the densities of slices j-1, j, j+1; the order
-//   D(S-1) D(0) D(1) C(0) D(2) C(1) D(3) ... D(S-2) C(S-3) C(S-2) C(S-1)
-// places D(j+1) just before C(j), so the populations a D item pulls from HBM
-// are still in L2 when the C item of the same slice reads them again: each
-// population crosses HBM once each way per step.  A C item waits on per-slice
-// completion counters (bounded by a time limit; a timeout sets a status bit).
-// In-place streaming is safe: the slots a site's C item reads and writes are
-// touched by no other C item, and a D item only reads slots of its own slice
-// before that slice's C item runs.  Items are handed out in order, so an item
-// only ever waits on items already taken by running blocks.
+// along its outermost axis (z in 3D, y in 2D) and each slice into warp tiles of
+// 32 sites along x (T tiles per slice).  Two kinds of work:
+//   D(k, t): densities of tile t of slice k;  C(j, t): collide tile t of slice j,
+//   which needs the densities of slices j-1, j, j+1.
+// Work items, in order:
+//   prologue: D(k, t) for k in {S-1, 0, 1, ..., L}   ((L+2) T items)
+//   main    : item (j, t) = D(j+L+1, t) (when j+L+1 <= S-2) then C(j, t)   (S T items)
+// so the densities run L slices ahead of the collisions.  L is the smallest lag
+// that keeps the density work of a slice ahead of the window of items in flight
+// (one per warp of the grid); the populations a D item pulls from HBM are then
+// re-read from L2 by the C item of the same slice L+1 slices later, so each
+// population crosses HBM once each way per step.
+// Warp w takes items w, w + W, w + 2W, ...  (W warps, all resident: cooperative
+// launch).  A C part checks per-slice counters of finished D tiles; an item only
+// waits on items of smaller index, which resident warps already own, so the
+// waits always end (and are bounded in time anyway: a timeout sets a status bit
+// and the warp returns).  In-place streaming stays race-free: the slots a site's
+// C part reads and writes are touched by no other C part, and a D part reads
+// them only before the C part of that site runs.
 // ---------------------------------------------------------------------------
 struct PipeArgs {
-    unsigned *next_item;  // item counter (zero at launch)
-    unsigned *done;       // completed D tiles per slice (zero at launch)
-    int slices, tiles_per_slice, segs_per_row;
-    int total_items;
-    unsigned target;            // D tiles a slice needs before its neighbours' C items may run
+    unsigned *done;   // finished D tiles per slice (zero at launch)
+    int slices, tiles_per_slice, tiles_per_row, lag;
+    int prologue, total;
+    unsigned target;            // D tiles a slice needs before its neighbours' C parts may run
     unsigned long long wait_ns; // give-up time of one dependency wait
 };
 
@@ -267,27 +281,43 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned *p)
     return v;
 }
 
-// item q of the step -> (is_collide, slice)
-__device__ __forceinline__ void decode_item(int q, int S, bool &collide, int &slice)
+__device__ __forceinline__ unsigned load_relaxed(const unsigned *p)
 {
-    if (S < 4) {
-        collide = q >= S;
-        slice = collide ? q - S : q;
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void red_add_relaxed(unsigned *p, unsigned v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// item -> (D slice or -1, C slice or -1, tile)
+__device__ __forceinline__ void decode_item(const PipeArgs &a, int item, int &dslice, int &cslice, int &tile)
+{
+    const int S = a.slices, T = a.tiles_per_slice;
+    if (a.lag < 0) { // few slices: all densities, then all collisions
+        const int q = item / T;
+        tile = item - q * T;
+        dslice = q < S ? q : -1;
+        cslice = q < S ? -1 : q - S;
         return;
     }
-    if (q < 3) {
-        collide = false;
-        slice = q == 0 ? S - 1 : q - 1;
+    if (item < a.prologue) {
+        const int q = item / T;
+        tile = item - q * T;
+        dslice = q == 0 ? S - 1 : q - 1;
+        cslice = -1;
         return;
     }
-    if (q >= 2 * S - 3) {
-        collide = true;
-        slice = q - S;
-        return;
-    }
-    const int r = q - 3;
-    collide = (r & 1) == 0;
-    slice = collide ? r >> 1 : (r >> 1) + 2;
+    const int r = item - a.prologue;
+    const int j = r / T;
+    tile = r - j * T;
+    cslice = j;
+    dslice = j + a.lag + 1 <= S - 2 ? j + a.lag + 1 : -1;
 }
 
 template <class L, class S, int PARITY>
@@ -295,67 +325,90 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
                                                     float2 *__restrict__ rho, unsigned *__restrict__ status,
                                                     const PipeArgs a)
 {
-    __shared__ int s_item;
-    __shared__ int s_ok;
-    const int tpb = a.tiles_per_slice;
-    const int items_total = a.total_items;
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.next_item, 1u);
-    __syncthreads();
-    int item = s_item;
-    while (item < items_total) {
-        const int q = item / tpb, tile = item - q * tpb;
-        bool collide;
-        int slice;
-        decode_item(q, a.slices, collide, slice);
-        // take the next item early so its latency overlaps this one
-        int next = 0;
-        if (threadIdx.x == 0) next = (int)atomicAdd(a.next_item, 1u);
-        if (collide) {
-            if (threadIdx.x == 0) {
+    const int lane = threadIdx.x & 31;
+    const int W = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < a.total; item += W) {
+        int dslice, cslice, tile;
+        decode_item(a, item, dslice, cslice, tile);
+        // dependency counters of the C part, read early (relaxed); the fence
+        // issued after the population loads gives them acquire semantics
+        unsigned c0 = 0, c1 = 0, c2 = 0;
+        int nb3[3] = {0, 0, 0};
+        if (cslice >= 0) {
+            const int Sl = a.slices;
+            nb3[0] = cslice == 0 ? Sl - 1 : cslice - 1;
+            nb3[1] = cslice;
+            nb3[2] = cslice == Sl - 1 ? 0 : cslice + 1;
+            if (lane == 0) {
+                c0 = load_relaxed(a.done + nb3[0]);
+                c1 = load_relaxed(a.done + nb3[1]);
+                c2 = load_relaxed(a.done + nb3[2]);
+            }
+        }
+        // ---- D part
+        if (dslice >= 0) {
+            int y, z;
+            if (L::D == 3) {
+                z = dslice;
+                y = tile / a.tiles_per_row;
+            } else {
+                z = 0;
+                y = dslice;
+            }
+            const int x = (tile - (L::D == 3 ? y * a.tiles_per_row : 0)) * 32 + lane;
+            if (x < p.nx) {
+                const Nbr nb = make_nbr(p, x, y, z);
+                rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
+            }
+            __syncwarp();
+            if (cslice < 0 && lane == 0) { // no C part to carry the signal: publish now
+                fence_acq_rel();
+                red_add_relaxed(a.done + dslice, 1u);
+            }
+        }
+        // ---- C part
+        if (cslice >= 0) {
+            int y, z;
+            if (L::D == 3) {
+                z = cslice;
+                y = tile / a.tiles_per_row;
+            } else {
+                z = 0;
+                y = cslice;
+            }
+            const int x0 = (tile - (L::D == 3 ? y * a.tiles_per_row : 0)) * 32;
+            const bool active = x0 + lane < p.nx;
+            const int x = active ? x0 + lane : p.nx - 1; // idle lanes compute a real site without storing
+            const Nbr nb = make_nbr(p, x, y, z);
+            auto after_loads = [&]() -> bool {
                 int ok = 1;
-                const unsigned long long t0 = global_ns();
-                const int S = a.slices;
-                const int nbrs[3] = {slice == 0 ? S - 1 : slice - 1, slice, slice == S - 1 ? 0 : slice + 1};
-                for (int k = 0; k < 3 && ok; k++) {
-                    while (load_acquire(a.done + nbrs[k]) < a.target) {
-                        if (global_ns() - t0 > a.wait_ns) {
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(100);
+                if (lane == 0) {
+                    // release this item's densities; acquire the counters read above
+                    fence_acq_rel();
+                    if (dslice >= 0) red_add_relaxed(a.done + dslice, 1u);
+                    if (c0 < a.target || c1 < a.target || c2 < a.target) {
+                        const unsigned long long t0 = global_ns();
+                        for (int k = 0; k < 3 && ok; k++)
+                            while (load_acquire(a.done + nb3[k]) < a.target) {
+                                if (global_ns() - t0 > a.wait_ns) {
+                                    ok = 0;
+                                    break;
+                                }
+                                __nanosleep(64);
+                            }
+                        if (!ok) atomicOr(status, kStatusTimeout);
                     }
                 }
-                if (!ok) atomicOr(status, kStatusTimeout);
-                s_ok = ok;
+                return __shfl_sync(0xffffffffu, ok, 0) != 0;
+            };
+            bool alive = true;
+            if (active) {
+                site_collide<L, S, PARITY, true, true>(p, pop, rho, status, nb, [&] { return alive = after_loads(); });
+            } else {
+                site_collide<L, S, PARITY, true, false>(p, pop, rho, status, nb, [&] { return alive = after_loads(); });
             }
-            __syncthreads();
-            if (!s_ok) return; // a dependency never completed: give up, the host sees the status bit
+            if (!__shfl_sync(0xffffffffu, alive ? 1 : 0, 0)) return; // a wait gave up: the host sees the status bit
         }
-        // tile -> site coordinates
-        int y, z;
-        if (L::D == 3) {
-            z = slice;
-            y = tile / a.segs_per_row;
-        } else {
-            z = 0;
-            y = slice;
-        }
-        const int x = (tile - (L::D == 3 ? y * a.segs_per_row : 0)) * 128 + threadIdx.x;
-        if (x < p.nx) {
-            const Nbr nb = make_nbr(p, x, y, z);
-            if (collide) site_collide<L, S, PARITY, true>(p, pop, rho, status, nb);
-            else rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (!collide) {
-                __threadfence();
-                atomicAdd(a.done + slice, 1u);
-            }
-            s_item = next;
-        }
-        __syncthreads();
-        item = s_item;
     }
 }
 
@@ -524,19 +577,9 @@ cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, co
 
 template <class L, class S>
 cudaError_t Launch<L, S>::step_fused(int parity, const StepParams &p, void *pop, float *rho, unsigned *status,
-                                     unsigned *counters, double wait_ms, int stall, cudaStream_t st)
+                                     unsigned *counters, double wait_ms, int stall, int lag_opt, cudaStream_t st)
 {
-    kern::PipeArgs a;
-    const int segs = (p.nx + 127) / 128;
-    a.slices = L::D == 3 ? p.nz : p.ny;
-    a.segs_per_row = segs;
-    a.tiles_per_slice = L::D == 3 ? p.ny * segs : segs;
-    a.total_items = 2 * a.slices * a.tiles_per_slice;
-    a.next_item = counters;
-    a.done = counters + 1;
-    a.target = (unsigned)a.tiles_per_slice + (stall ? 1u : 0u);
-    a.wait_ns = (unsigned long long)(wait_ms * 1e6);
-    // one resident wave of persistent blocks
+    // one resident wave of persistent blocks (queried once per parity instance)
     static int blocks[2] = {0, 0};
     if (!blocks[parity]) {
         int dev = 0, sms = 0, per_sm = 0;
@@ -548,14 +591,38 @@ cudaError_t Launch<L, S>::step_fused(int parity, const StepParams &p, void *pop,
         if (e != cudaSuccess) return e;
         blocks[parity] = sms * (per_sm > 0 ? per_sm : 1);
     }
-    const int grid = blocks[parity] < a.total_items ? blocks[parity] : a.total_items;
-    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * (1 + a.slices), st);
+    kern::PipeArgs a;
+    a.done = counters;
+    a.tiles_per_row = (p.nx + 31) / 32;
+    a.slices = L::D == 3 ? p.nz : p.ny;
+    a.tiles_per_slice = L::D == 3 ? p.ny * a.tiles_per_row : a.tiles_per_row;
+    const int nT = a.tiles_per_slice, nS = a.slices;
+    // smallest lag whose density lead exceeds the warps in flight, unless set
+    const int warps = blocks[parity] * 4;
+    int lag = 2;
+    while (lag * nT < warps) lag++;
+    if (lag_opt >= 2) lag = lag_opt;
+    if (nS >= lag + 3) {
+        a.lag = lag;
+        a.prologue = (lag + 2) * nT;
+    } else {
+        a.lag = -1;
+        a.prologue = 0;
+    }
+    a.total = a.lag < 0 ? 2 * nS * nT : a.prologue + nS * nT;
+    a.target = (unsigned)nT + (stall ? 1u : 0u);
+    a.wait_ns = (unsigned long long)(wait_ms * 1e6);
+    const int need_warps = a.total;
+    int grid = blocks[parity];
+    if (grid * 4 > need_warps) grid = (need_warps + 3) / 4;
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * nS, st);
     if (e != cudaSuccess) return e;
     auto *ptr = static_cast<typename S::T *>(pop);
     auto *r2 = reinterpret_cast<float2 *>(rho);
-    if (parity == 0) kern::k_step_fused<L, S, 0><<<grid, 128, 0, st>>>(p, ptr, r2, status, a);
-    else kern::k_step_fused<L, S, 1><<<grid, 128, 0, st>>>(p, ptr, r2, status, a);
-    return cudaGetLastError();
+    StepParams pc = p;
+    void *args[] = {(void *)&pc, (void *)&ptr, (void *)&r2, (void *)&status, (void *)&a};
+    const void *fn = parity == 0 ? (const void *)kern::k_step_fused<L, S, 0> : (const void *)kern::k_step_fused<L, S, 1>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, st);
 }
 
 template <class L, class S>

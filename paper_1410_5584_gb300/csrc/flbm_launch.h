@@ -11,7 +11,7 @@ template <class L, class S> struct Launch {
     static cudaError_t collide(int parity, const StepParams &p, void *pop, const float *rho, unsigned *status,
                                cudaStream_t st);
     static cudaError_t step_fused(int parity, const StepParams &p, void *pop, float *rho, unsigned *status,
-                                  unsigned *counters, double wait_ms, int stall, cudaStream_t st);
+                                  unsigned *counters, double wait_ms, int stall, int lag, cudaStream_t st);
     static cudaError_t init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st);
     static cudaError_t gather(int parity, const StepParams &p, const void *pop, const int64_t *sites, int64_t n,
                               double *out, cudaStream_t st);
