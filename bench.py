@@ -88,7 +88,7 @@ def sources_digest():
 
 
 def recorded_traffic(workload, sites):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was
+    """DRAM bytes per collide launch from the committed ncu summary, if it was
     taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -325,12 +325,12 @@ def run_ours(args, wl):
         "config": {"workload": wl["desc"], "lattice": "D3Q19" if wl["lattice"] == 1 else "D2Q9",
                    "nx": nx, "ny": ny, "nz": nz, "storage": wl["storage"], "replicas": world,
                    "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2"},
-        "roofline": {"bound": "hbm", "kernel": "k_step_fused", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},
         "step_hbm_frac": alg_bytes / (t_max / args.steps) / 1e9 / peak,
-        "kernel_ms": {"counter_reset": kms["density"] / max(kn["density"], 1), "step": coll_ms},
-        "gpu_launches": kn["collide"],
+        "kernel_ms": {"density": kms["density"] / max(kn["density"], 1), "collide": coll_ms},
+        "gpu_launches": kn["density"] + kn["collide"],
         "clocks": clk.summary(),
         "e2e": e2e,
     }

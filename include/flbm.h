@@ -67,10 +67,11 @@ typedef enum {
 /* How flbm_step runs one update (option FLBM_OPT_SCHEDULE).  Both compute the
  * same update; results agree to rounding (each schedule is deterministic). */
 typedef enum {
-    FLBM_SCHEDULE_FUSED = 0,      /* default: one persistent launch per step; density and collision
-                                     work items ordered so the populations read for the densities are
-                                     reused from L2 by the collision (one HBM pass each way) */
-    FLBM_SCHEDULE_TWO_KERNELS = 1 /* a density kernel, then the collide kernel */
+    FLBM_SCHEDULE_FUSED = 0,      /* one persistent launch per step; density and collision work items
+                                     ordered so the populations read for the densities are reused from
+                                     L2 by the collision (one HBM pass each way).  Slower on GB300 while
+                                     the collision is instruction-bound */
+    FLBM_SCHEDULE_TWO_KERNELS = 1 /* default: a density kernel, then the collide kernel */
 } flbm_schedule;
 
 /* Option keys for flbm_set_option. */

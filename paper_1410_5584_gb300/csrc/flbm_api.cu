@@ -23,7 +23,7 @@ struct flbm_ctx {
     // options
     double lam[2][kMaxQ] = {};
     int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
-    int schedule = FLBM_SCHEDULE_FUSED;
+    int schedule = FLBM_SCHEDULE_TWO_KERNELS;
     double wait_limit_ms = 2000.0;
     int pipe_lag = 0;
     int test_stall = 0;
