@@ -34,26 +34,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
 // g1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
 // The angle is folded exactly into [-pi, pi) (u2 - 1 for u2 >= 1/2, the same
 // sine and cosine), where the hardware sine/cosine have an absolute error of
-// about 2^-21; r = x rsqrt(x) (x = 0 when u1 = 1 gives r = 0).
+// about 2^-21; r = x rsqrt(x).
 //
-// ln u1: for u1 <= 15/16 the hardware log2 (absolute error <= 2^-22 on
-// [1/2, 2], 2 ulp below) is accurate to ~3e-6 relative since |ln u1| >= 0.064;
+// ln u1: for u1 <= 31/32 the hardware log2 (absolute error <= 2^-22 on
+// [1/2, 2], 2 ulp below) is accurate to ~5e-6 relative since |ln u1| >= 0.0317;
 // nearer 1, where an absolute error would swamp the small radius, the Mercator
-// series ln(1 - v) = -(v + v^2/2 + ... + v^8/8) with v = 1 - u1 <= 1/16 (exact
-// by Sterbenz's lemma) is used, truncation error below 3e-11 relative.
+// series ln(1 - v) = -(v + v^2/2 + ... + v^5/5) with v = 1 - u1 <= 1/32 (exact by
+// Sterbenz's lemma) is used, truncation error below 1e-8 relative.
 __device__ __forceinline__ float log_unit_interval(float u1)
 {
     const float v = 1.0f - u1;
-    float ps = fmaf(v, 0.125f, 0.142857142857142857f);
-    ps = fmaf(v, ps, 0.166666666666666667f);
-    ps = fmaf(v, ps, 0.2f);
-    ps = fmaf(v, ps, 0.25f);
+    float ps = fmaf(v, 0.2f, 0.25f);
     ps = fmaf(v, ps, 0.333333333333333333f);
     ps = fmaf(v, ps, 0.5f);
     ps = fmaf(v, ps, 1.0f);
     const float near1 = -v * ps;
     const float far = __log2f(u1) * 0.693147180559945309f;
-    return u1 > 0.9375f ? near1 : far;
+    return u1 > 0.96875f ? near1 : far;
 }
 
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
@@ -61,7 +58,9 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, fl
     const float u1 = fmaf((float)(a >> 8), 0x1.0p-24f, 0x1.0p-24f); // ((a >> 8) + 1) 2^-24, exact
     const float u2 = (float)(b >> 8) * 0x1.0p-24f;
     const float r2 = -2.0f * log_unit_interval(u1);
-    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    // r = sqrt(r2); the tiny offset makes r2 = 0 (u1 = 1) give 0 instead of 0 * inf
+    // and is far below the rounding of the smallest nonzero r2 (~1.2e-7)
+    const float r = r2 * rsqrtf(r2 + 1e-30f);
     const float t = u2 < 0.5f ? u2 : u2 - 1.0f;
     float s, c;
     __sincosf(6.28318530717958647692f * t, &s, &c);

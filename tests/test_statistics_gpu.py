@@ -1,0 +1,100 @@
+"""Statistical checks of the GPU update against the paper's predictions
+(Sec. VI A): long runs on the GPU, snapshots of the axis structure factors,
+standard errors by batch means over time-correlated snapshots.  The
+predictions are the closed forms of Eqs. str-bin-hom and str-bin-hom-vel and
+the exact linearised-lattice covariance of tests/theory.py."""
+import numpy as np
+import pytest
+
+import oracle
+import theory
+from paper_1410_5584_gb300 import D2Q9, D3Q19, Lattice
+from paper_1410_5584_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _snapshots(g, burn, nsnap, every, axis=0):
+    g.step(burn)
+    snaps = []
+    for _ in range(nsnap):
+        g.step(every)
+        g.sf_reset()
+        g.sf_sample()
+        snaps.append(np.stack(g.structure_factor(axis)[:4]))
+    return np.array(snaps)
+
+
+def test_ideal_mixture_64x64_flat_structure_factor():
+    """The 64^2 ideal-mixture workload (rho_A = rho_B = 0.5, tau = 1, kT = 1e-4,
+    G = 0, seed 1): S_rho,rho = 3 kT rho0 at every k, S_rho,rho' = 0,
+    <u_b^2> = kT / rho_t0 per component (Sec. VI A, Fig. 1)."""
+    kT, rho0 = 1e-4, 0.5
+    g = Lattice(D2Q9, 64, 64, 1, 1.0, 1.0, kT, 0.0, 1)
+    g.init(np.full(64 * 64, rho0), np.full(64 * 64, rho0))
+    snaps = _snapshots(g, 2000, 2000, 20)
+    m, se = theory.batch_means(snaps)
+    keep = slice(0, 31)  # the k = pi Nyquist mode excluded
+    for idx in (0, 2):
+        er = m[idx, keep] / (3 * kT * rho0)
+        ese = se[idx, keep] / (3 * kT * rho0)
+        assert abs(er.mean() - 1) < 3 * np.sqrt((ese ** 2).sum()) / er.size + 0.005
+        assert np.all(np.abs(er - 1) < 5 * ese + 0.02)
+    assert np.all(np.abs(m[1, keep]) / kT < 5 * se[1, keep] / kT + 0.02)
+    eru = m[3, keep] / (kT / (2 * rho0))
+    eru_se = se[3, keep] / (kT / (2 * rho0))
+    assert abs(eru.mean() - 1) < 3 * np.sqrt((eru_se ** 2).sum()) / eru.size + 0.005
+    # mass of each species is conserved to float rounding over the run
+    cons = g.moments(fields=False)
+    assert cons[0] == pytest.approx(64 * 64 * rho0, rel=2e-6)
+    assert cons[1] == pytest.approx(64 * 64 * rho0, rel=2e-6)
+
+
+def test_no_sdf_is_detected_on_the_gpu():
+    """Without the species-momentum noise the densities are under-thermalised
+    and S_rho,rho' > 0 at small k (Sec. VI A, Fig. 1, "no-sdf")."""
+    kT, rho0 = 1e-4, 0.5
+    g = Lattice(D2Q9, 64, 2, 1, 1.0, 1.0, kT, 0.0, 3, sdf=0)
+    g.init(np.full(128, rho0), np.full(128, rho0))
+    snaps = _snapshots(g, 2000, 2000, 10)
+    m, se = theory.batch_means(snaps)
+    k = 2 * np.pi * np.arange(1, 33) / 64
+    low = k < 1.0
+    assert np.all(m[1, low] / kT > 0.3)
+    assert np.all(m[0, low] / (3 * kT * rho0) < 0.8)
+
+
+def test_shan_chen_mixture_512_against_lattice_theory():
+    """The 512^2 Shan-Chen mixture (G rho0 = 0.9, tau_A = 0.8, tau_B = 1.0,
+    kT = 1e-5, rho = 1 + 1e-3 g): after burn-in, S(k) at wavenumbers that relax
+    within the run follows the exact linearised-lattice prediction (which
+    includes the unequal rates and the common momentum rate 2/(tau_A+tau_B))."""
+    n, G, kT = 512, 0.9, 1e-5
+    shape = (1, n, n)
+    g = Lattice(D2Q9, n, n, 1, 0.8, 1.0, kT, G, 7)
+    g.init(inputs.perturbed_density(shape, 1.0, 1e-3, 7, 0), inputs.perturbed_density(shape, 1.0, 1e-3, 7, 1))
+    snaps = _snapshots(g, 6000, 2000, 20)
+    m, se = theory.batch_means(snaps)
+    c, w, T, N = oracle.tables(oracle.D2Q9)
+    lam = (1 / 0.8, 1 / 1.0)
+    lam_d = 2 / 1.8
+    for mi in (40, 80, 128, 180, 230):  # k = 0.49 ... 2.82
+        k = 2 * np.pi * (mi + 1) / n
+        pred = theory.lattice_linear_sk(c, w, T, N, [k], G, rho=(1.0, 1.0), lam=lam, lam_d=lam_d, kT=kT)
+        assert abs(m[0, mi] - pred[0]) < 4 * se[0, mi] + 0.03 * pred[0], (mi, m[0, mi], pred[0])
+        assert abs(m[2, mi] - pred[2]) < 4 * se[2, mi] + 0.03 * pred[2], (mi, m[2, mi], pred[2])
+        assert abs(m[1, mi] - pred[1]) < 4 * se[1, mi] + 0.03 * pred[0], (mi, m[1, mi], pred[1])
+
+
+def test_d3q19_ideal_mixture_flat_structure_factor():
+    """D3Q19, G = 0: S_rho,rho = 3 kT rho0 and S_rho,rho' = 0 along x."""
+    kT, rho0 = 1e-4, 1.0
+    g = Lattice(D3Q19, 32, 4, 4, 1.0, 1.0, kT, 0.0, 5)
+    g.init()
+    snaps = _snapshots(g, 2000, 2000, 10)
+    m, se = theory.batch_means(snaps)
+    keep = slice(0, 15)
+    er = m[0, keep] / (3 * kT * rho0)
+    ese = se[0, keep] / (3 * kT * rho0)
+    assert abs(er.mean() - 1) < 3 * np.sqrt((ese ** 2).sum()) / er.size + 0.01
+    assert np.all(np.abs(m[1, keep]) / kT < 5 * se[1, keep] / kT + 0.03)
