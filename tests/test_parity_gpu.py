@@ -330,6 +330,7 @@ def test_fused_step_wait_timeout_is_reported():
     be satisfied gives up after its time limit, the kernel returns, the host
     reads FLBM_ETIMEOUT, and re-initialising restores a usable context."""
     g = Lattice(D3Q19, 16, 8, 6, 1.0, 1.0, 1e-4, 0.5, 1)
+    g.set_option("schedule", F.SCHEDULE["fused"])
     g.init()
     g.set_option("wait_limit_ms", 50)
     g.set_option("test_stall", 1)
