@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage forms")
     return ap.parse_args()
 
 
@@ -157,6 +158,64 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def storage_forms(wl, seed, steps, device):
+    """The FP16 / BF16 deviation-storage forms beside the float run: MLUPS on the
+    bench box, and their errors against the float-storage GPU run on a 32^3
+    sub-case (densities, velocities, axis S(k) sampled along the same noise
+    history, mass drift).  Errors against the FP64 oracle are measured by the
+    test suite (tests/test_precision_gpu.py)."""
+    import numpy as np
+    import torch
+
+    from paper_1410_5584_gb300 import Lattice
+    from paper_1410_5584_gb300 import inputs
+
+    out = {}
+    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
+    for st in ("f16", "bf16"):
+        lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
+                      storage=st, device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"])
+        lat.init()
+        lat.step(10)
+        lat.sync()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(lat.stream)
+        lat.step(steps)
+        s1.record(lat.stream)
+        lat.sync()
+        out[st] = {"value": nx * ny * nz * steps / (s0.elapsed_time(s1) / 1e3) / 1e6, "unit": "MLUPS",
+                   "steps": steps, "bytes_per_site": 2 * (19 if wl["lattice"] == 1 else 9) * 2 * 2}
+        lat.close()
+    # accuracy on a small box of the same lattice and parameters
+    n3 = 32
+    shape = (n3, n3, n3) if wl["lattice"] == 1 else (1, 256, 256)
+    runs = {}
+    for st in ("f32", "f16", "bf16"):
+        lat = Lattice(wl["lattice"], shape[2], shape[1], shape[0], wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"],
+                      seed, storage=st, device=device)
+        lat.init(inputs.perturbed_density(shape, wl["rho0"], 1e-3, seed, 0),
+                 inputs.perturbed_density(shape, wl["rho0"], 1e-3, seed, 1))
+        c0 = lat.moments(fields=False)
+        for _ in range(20):
+            lat.step(10)
+            lat.sf_sample()
+        ra, rb, u, c1 = lat.moments()
+        runs[st] = dict(ra=ra, rb=rb, u=u, drift=max(abs(c1[k] - c0[k]) / c0[k] for k in (0, 1)),
+                        sk=np.stack(lat.structure_factor(0)[:3]))
+        lat.close()
+    ref = runs["f32"]
+    for st in ("f16", "bf16"):
+        r = runs[st]
+        s_ref = ref["sk"][0] + ref["sk"][2]
+        out[st]["error_vs_f32"] = {
+            "case": f"{'x'.join(str(v) for v in shape[::-1])}, 200 steps, S(k) every 10",
+            "rho_abs": float(max(np.max(np.abs(r["ra"] - ref["ra"])), np.max(np.abs(r["rb"] - ref["rb"])))),
+            "u_rel": float(np.max(np.abs(r["u"] - ref["u"])) / np.max(np.abs(ref["u"]))),
+            "sk_rel": float(np.max(np.abs(r["sk"][0] + r["sk"][2] - s_ref) / s_ref)),
+            "mass_drift": float(r["drift"]), "mass_drift_f32": float(ref["drift"])}
+    return out
 
 
 def cpu_baseline(wl, seed, budget_s=15.0):
@@ -334,6 +393,8 @@ def run_ours(args, wl):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    if not args.no_forms and wl["storage"] == "f32":
+        line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
     print(json.dumps(line), flush=True)

@@ -219,6 +219,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
             else mu[a] = invN * m[s][a];
         });
         Transform<L>::backward(mu, fo);
+        fo[0] = Transform<L>::rest_closing_mass(fo, m[s][0]);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr float wi = (float)L::wd(i);

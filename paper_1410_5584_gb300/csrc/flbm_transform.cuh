@@ -60,6 +60,15 @@ template <> struct Transform<D2Q9> {
         f[6] = wd * (E4 + O4);
         f[8] = wd * (E4 - O4);
     }
+    // Rest population that makes the density expression of forward() return m0:
+    // the float weights do not sum to 1 exactly, so w_i m0 spread over the
+    // directions would leak mass at a rate proportional to rho - rho0.
+    template <class R> __host__ __device__ __forceinline__ static constexpr R rest_closing_mass(const R (&f)[9], R m0)
+    {
+        const R A = (f[1] + f[3]) + (f[2] + f[4]);
+        const R E = (f[5] + f[7]) + (f[6] + f[8]);
+        return (m0 - E) - A;
+    }
 };
 
 // D3Q19 with the basis of flbm_lattice.cuh.  Pairs: P1 (1,2) x; P2 (3,4) y;
@@ -155,6 +164,15 @@ template <> struct Transform<D3Q19> {
         f[16] = we * (E8 - O8);
         f[17] = we * (E9 + O9);
         f[18] = we * (E9 - O9);
+    }
+    // Rest population that makes the density expression of forward() return m0
+    // (see the D2Q9 version).
+    template <class R> __host__ __device__ __forceinline__ static constexpr R rest_closing_mass(const R (&f)[19], R m0)
+    {
+        const R A = ((f[1] + f[2]) + (f[3] + f[4])) + (f[5] + f[6]);
+        const R E = (((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14]))) +
+                    ((f[15] + f[16]) + (f[17] + f[18]));
+        return (m0 - E) - A;
     }
 };
 
