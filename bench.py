@@ -218,6 +218,52 @@ def storage_forms(wl, seed, steps, device):
     return out
 
 
+def batched_form(seed, steps, device, nrep=64):
+    """The batching form: nrep independent D2Q9 replicas, n_x and n_y drawn from
+    {64, 128, 256, 512}, kT log-uniform in [1e-6, 1e-4], G rho0 uniform in
+    [0, 0.9], distinct Philox keys, rho = 1, tau = 1; one density and one
+    collide launch per step for all replicas, replayed from CUDA graphs.
+    Compared with the same replicas stepped as separate contexts."""
+    import torch
+
+    from paper_1410_5584_gb300 import Batch, Lattice
+    from paper_1410_5584_gb300 import inputs
+
+    cfg = inputs.batch_replica_configs(nrep, seed)
+    reps = [dict(nx=c["nx"], ny=c["ny"], tau_a=1.0, tau_b=1.0, kT=c["kT"], G=c["G"], seed=c["seed"]) for c in cfg]
+    sites = sum(c["nx"] * c["ny"] for c in cfg)
+
+    def timed(run, stream):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        s0.record(stream)
+        run()
+        s1.record(stream)
+        torch.cuda.synchronize(device)
+        return s0.elapsed_time(s1) / 1e3
+
+    b = Batch(0, reps, device=device, graph_steps=16)
+    b.init()
+    b.step(32)
+    b.sync()
+    t_batch = timed(lambda: b.step(steps), b.stream)
+    b.sync()
+    b.close()
+    stream = torch.cuda.Stream(device=device)
+    lats = [Lattice(0, r["nx"], r["ny"], 1, 1.0, 1.0, r["kT"], r["G"], r["seed"], device=device, stream=stream)
+            for r in reps]
+    for g in lats:
+        g.init()
+        g.step(2)
+    t_sep = timed(lambda: [g.step(steps) for g in lats], stream)
+    for g in lats:
+        g.sync()
+        g.close()
+    return {"value": sites * steps / t_batch / 1e6, "unit": "MLUPS", "replicas": nrep, "sites": sites,
+            "steps": steps, "graph_steps": 16, "per_replica_launches_mlups": sites * steps / t_sep / 1e6,
+            "speedup_vs_per_replica_launches": t_sep / t_batch}
+
+
 def cpu_baseline(wl, seed, budget_s=15.0):
     """The FP64 oracle, single-threaded as it stands, on a bounded sample: the
     same lattice and parameters on a smaller periodic box."""
@@ -395,6 +441,7 @@ def run_ours(args, wl):
     }
     if not args.no_forms and wl["storage"] == "f32":
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
+        line["forms"]["batched"] = batched_form(args.seed, max(200, args.steps // 2), device)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
     print(json.dumps(line), flush=True)

@@ -105,6 +105,8 @@ enum {
     FLBM_OPT_PIPE_LAG = 14,      /* fused schedule: how many slices the density work runs ahead of the
                                     collisions; 0 (default) = the smallest lag that keeps it ahead of
                                     the work in flight; else an integer >= 2 (results are identical) */
+    FLBM_OPT_GRAPH_STEPS = 15,   /* batches: steps per CUDA graph replayed by flbm_step (0 = launch each
+                                    step directly); default 16 */
     FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
 };
@@ -248,6 +250,47 @@ flbm_status flbm_restore(flbm_ctx *ctx, const void *buf, size_t bytes);
  */
 flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int parity, int64_t step, int64_t n,
                               void *stream, unsigned *status_out);
+
+/*
+ * Batches of independent replicas (many boxes of uneven size, parameters and
+ * noise keys advanced together; SURVEY: the batching form).  Each replica is the
+ * same problem as a lone context created with its parameters -- its site index
+ * and therefore its noise are replica-local -- so a replica of a batch and a
+ * lone context with the same parameters and state give the same populations.
+ * A step of the batch is one density launch and one collide launch over a work
+ * list of 128-site tiles spanning every replica; flbm_step replays CUDA graphs of
+ * FLBM_OPT_GRAPH_STEPS steps.
+ * On a batch context: flbm_set_option (applied to every replica),
+ * flbm_set_stream, flbm_buffer_bytes, flbm_attach_buffers, flbm_init (host
+ * densities concatenated replica by replica, or NULL), flbm_step, flbm_sync,
+ * flbm_moments (fields concatenated replica by replica, u as [replica][d][site];
+ * cons summed over replicas), flbm_sf_sample (every replica), flbm_sf_reset,
+ * flbm_get/set_populations (concatenated [replica][species][i][site]),
+ * flbm_checkpoint/restore, flbm_destroy.  Per-replica structure factors, site
+ * populations and moments come from the replica views.
+ */
+typedef struct {
+    int nx, ny, nz;             /* box of this replica (nz = 1 for D2Q9) */
+    double tau_a, tau_b, kT, G; /* as in flbm_create */
+    uint64_t seed;              /* Philox key of this replica */
+    double rho0_a, rho0_b;      /* reference densities (uniform init, 16-bit deviation base) */
+} flbm_rep_params;
+
+/* Create a batch of nrep replicas with parameters p[0..nrep-1].  No device
+ * memory is allocated here.  FLBM_EINVAL if a replica's parameters are invalid
+ * (same rules as flbm_create) or the total site count reaches 2^31. */
+flbm_status flbm_batch_create(flbm_lattice lat, int nrep, const flbm_rep_params *p, flbm_ctx **out);
+
+/* Replica `rep` of a batch as a context of its own (owned by the batch, valid
+ * until the batch is destroyed).  It supports the observation calls --
+ * flbm_moments, flbm_sf_sample, flbm_structure_factor, flbm_sf_reset,
+ * flbm_get_populations, flbm_get_site_populations, flbm_get_step,
+ * flbm_set_option(FLBM_OPT_SF_AXIS) -- and answers FLBM_ESTATE to calls that
+ * would change it alone (step, init, set_populations, restore, other options). */
+flbm_status flbm_batch_replica(flbm_ctx *batch, int rep, flbm_ctx **view);
+
+/* Number of replicas and total sites of a batch (either pointer may be NULL). */
+flbm_status flbm_batch_size(const flbm_ctx *batch, int *nrep, int64_t *sites);
 
 /* One-line reason of the last error on this context ("" if none).  The string
  * is owned by the context.  Never NULL (ctx may be NULL). */

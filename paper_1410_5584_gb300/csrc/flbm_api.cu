@@ -8,61 +8,15 @@
 #include <new>
 #include <vector>
 
-#include "flbm_internal.h"
+#include "flbm_ctx.h"
 #include "flbm_lattice.cuh"
 
 using namespace flbm;
 
-struct flbm_ctx {
-    // problem
-    int lat = 0, D = 2, Q = 9;
-    int nx = 0, ny = 0, nz = 1;
-    int64_t N = 0;
-    double tau[2] = {1.0, 1.0}, kT = 0.0, G = 0.0;
-    uint64_t seed = 0;
-    // options
-    double lam[2][kMaxQ] = {};
-    int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
-    int schedule = FLBM_SCHEDULE_TWO_KERNELS;
-    double wait_limit_ms = 2000.0;
-    int pipe_lag = 0;
-    int test_stall = 0;
-    double rho0[2] = {1.0, 1.0};
-    // state
-    int64_t step = 0;
-    int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
-    bool initialised = false;
-    bool faulted = false;
-    bool timed_out = false;
-    // device buffers
-    void *pop = nullptr;
-    size_t pop_bytes = 0;
-    float *rho = nullptr;
-    size_t rho_bytes = 0;
-    bool own_buffers = false;
-    unsigned *d_status = nullptr;
-    unsigned *d_pipe = nullptr;   // fused-step counters: next item + one per slice
-    double *d_obs = nullptr;      // (2 + D) * N doubles: rho_a, rho_b, u
-    double *d_partials = nullptr; // per-block totals
-    size_t partials_cap = 0;
-    double *d_cons = nullptr;     // 5 doubles
-    double *d_sf = nullptr;       // 4 * n_axis/2 accumulators
-    double *d_profile = nullptr;  // (2 + D) * n_axis
-    int64_t sf_count = 0;
-    float *h_stage = nullptr;     // pinned staging, 2 * N floats
-    // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;      // recorded in order: start, after density, after collide, ...
-    size_t ev_used = 0;
-    double kernel_ms[2] = {0.0, 0.0};
-    int64_t kernel_launches[2] = {0, 0};
-    // stream
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    char err[512] = {0};
-};
 
-namespace {
+
+namespace flbm {
+namespace host {
 
 const char *kNoError = "";
 
@@ -82,11 +36,6 @@ flbm_status cuda_fail(flbm_ctx *c, cudaError_t e, const char *what)
     return fail(c, FLBM_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-#define FLBM_CUDA(ctx, call, what)                                \
-    do {                                                          \
-        cudaError_t e_ = (call);                                  \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, what); \
-    } while (0)
 
 double lat_w(int lat, int i) { return lat == FLBM_D2Q9 ? D2Q9::wd(i) : D3Q19::wd(i); }
 double lat_N(int lat, int a) { return lat == FLBM_D2Q9 ? D2Q9::Nd(a) : D3Q19::Nd(a); }
@@ -353,7 +302,10 @@ struct CkptHeader {
     uint64_t payload_hash;
 };
 
-} // namespace
+} // namespace host
+} // namespace flbm
+
+using namespace flbm::host;
 
 bool flbm::ctx_view(const flbm_ctx *c, CtxView *out)
 {
@@ -409,6 +361,9 @@ flbm_status flbm_create(flbm_lattice lat, int nx, int ny, int nz, double tau_a, 
 flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
 {
     if (!c) return FLBM_EINVAL;
+    if (is_batch(c)) return batch_set_option(c, key, v);
+    if (c->is_view && key != FLBM_OPT_SF_AXIS && !view_call_allowed(c))
+        return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
     if (key == FLBM_OPT_STORAGE) {
         if (c->pop) return fail(c, FLBM_ESTATE, "the storage format is fixed once the buffers exist");
         if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, FLBM_EINVAL, "storage must be 0 (f32), 1 (f16) or 2 (bf16)");
@@ -470,13 +425,18 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
 flbm_status flbm_set_stream(flbm_ctx *c, void *stream)
 {
     if (!c) return FLBM_EINVAL;
+    if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
     if (c->own_stream && c->stream) {
         cudaStreamSynchronize(c->stream);
         cudaStreamDestroy(c->stream);
     }
     c->stream = static_cast<cudaStream_t>(stream);
     c->own_stream = false;
-    if (!stream) return ensure_stream(c);
+    if (!stream) {
+        flbm_status st = ensure_stream(c);
+        if (st != FLBM_OK) return st;
+    }
+    if (is_batch(c)) return batch_set_stream(c, stream);
     return FLBM_OK;
 }
 
@@ -491,6 +451,7 @@ flbm_status flbm_buffer_bytes(const flbm_ctx *c, size_t *pop_bytes, size_t *rho_
 flbm_status flbm_attach_buffers(flbm_ctx *c, void *pop, size_t pop_bytes, void *rho, size_t rho_bytes)
 {
     if (!c) return FLBM_EINVAL;
+    if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
     if (c->pop) return fail(c, FLBM_ESTATE, "buffers already exist");
     if (!pop || !rho) return fail(c, FLBM_EINVAL, "NULL buffer");
     if (pop_bytes < pop_bytes_of(c) || rho_bytes < rho_bytes_of(c))
@@ -513,12 +474,16 @@ flbm_status flbm_attach_buffers(flbm_ctx *c, void *pop, size_t pop_bytes, void *
     c->own_buffers = false;
     flbm_status st = ensure_stream(c);
     if (st != FLBM_OK) return st;
-    return ensure_status(c);
+    if ((st = ensure_status(c)) != FLBM_OK) return st;
+    if (is_batch(c)) return batch_attach_buffers(c, pop, pop_bytes, rho, rho_bytes);
+    return FLBM_OK;
 }
 
 flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
 {
     if (!c) return FLBM_EINVAL;
+    if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
+    if (is_batch(c)) return batch_init(c, rho_a, rho_b);
     flbm_status st = ensure_buffers(c);
     if (st != FLBM_OK) return st;
     if ((st = ensure_stage(c)) != FLBM_OK) return st;
@@ -546,6 +511,8 @@ flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
 flbm_status flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
+    if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
+    if (is_batch(c)) return batch_step(c, n);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
     if (c->schedule == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
@@ -617,6 +584,7 @@ flbm_status flbm_get_step(const flbm_ctx *c, int64_t *step)
 flbm_status flbm_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, double *cons)
 {
     if (!c) return FLBM_EINVAL;
+    if (is_batch(c)) return batch_moments(c, rho_a, rho_b, u, cons);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_moments before flbm_init");
     flbm_status st = ensure_obs(c);
     if (st != FLBM_OK) return st;
@@ -639,6 +607,7 @@ flbm_status flbm_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, d
 flbm_status flbm_sf_sample(flbm_ctx *c)
 {
     if (!c) return FLBM_EINVAL;
+    if (is_batch(c)) return batch_sf_sample(c);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_sf_sample before flbm_init");
     flbm_status st = ensure_obs(c);
     if (st != FLBM_OK) return st;
@@ -660,6 +629,7 @@ flbm_status flbm_structure_factor(flbm_ctx *c, int axis, int nk, double *S_aa, d
                                   double *S_uu, int64_t *nsamples)
 {
     if (!c) return FLBM_EINVAL;
+    if (is_batch(c)) return fail(c, FLBM_EINVAL, "a batch has one structure factor per replica: use flbm_batch_replica");
     if (axis != c->sf_axis) return fail(c, FLBM_EINVAL, "axis %d differs from the sampled axis %d", axis, c->sf_axis);
     const int half = axis_len(c, axis) / 2;
     if (nk < 1 || nk > half) return fail(c, FLBM_EINVAL, "nk must lie in [1, %d]", half);
@@ -679,6 +649,14 @@ flbm_status flbm_structure_factor(flbm_ctx *c, int axis, int nk, double *S_aa, d
 flbm_status flbm_sf_reset(flbm_ctx *c)
 {
     if (!c) return FLBM_EINVAL;
+    if (is_batch(c)) {
+        for (int r = 0;; r++) {
+            flbm_ctx *v = nullptr;
+            if (flbm_batch_replica(c, r, &v) != FLBM_OK) break;
+            flbm_sf_reset(v);
+        }
+        return FLBM_OK;
+    }
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_sf(c);
     return FLBM_OK;
@@ -687,6 +665,7 @@ flbm_status flbm_sf_reset(flbm_ctx *c)
 flbm_status flbm_get_populations(flbm_ctx *c, double *f)
 {
     if (!c || !f) return FLBM_EINVAL;
+    if (is_batch(c)) return batch_get_populations(c, f);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "no populations before flbm_init");
     flbm_status st = sync_and_check(c);
     if (st != FLBM_OK) return st;
@@ -703,6 +682,8 @@ flbm_status flbm_get_populations(flbm_ctx *c, double *f)
 flbm_status flbm_set_populations(flbm_ctx *c, const double *f, int64_t step)
 {
     if (!c || !f || step < 0) return FLBM_EINVAL;
+    if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
+    if (is_batch(c)) return batch_set_populations(c, f, step);
     flbm_status st = ensure_buffers(c);
     if (st != FLBM_OK) return st;
     FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -742,6 +723,7 @@ flbm_status flbm_set_populations(flbm_ctx *c, const double *f, int64_t step)
 flbm_status flbm_get_site_populations(flbm_ctx *c, const int64_t *sites, int64_t nsites, double *out)
 {
     if (!c || (!sites && nsites) || (!out && nsites) || nsites < 0) return FLBM_EINVAL;
+    if (is_batch(c)) return fail(c, FLBM_EINVAL, "site indices are per replica: use flbm_batch_replica");
     if (!c->initialised) return fail(c, FLBM_ESTATE, "no populations before flbm_init");
     for (int64_t k = 0; k < nsites; k++)
         if (sites[k] < 0 || sites[k] >= c->N) return fail(c, FLBM_EINVAL, "site index %lld out of range", (long long)sites[k]);
@@ -765,6 +747,7 @@ flbm_status flbm_get_site_populations(flbm_ctx *c, const int64_t *sites, int64_t
 flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
 {
     if (!c || !bytes) return FLBM_EINVAL;
+    if (is_batch(c)) return batch_checkpoint(c, buf, bytes);
     const size_t payload = pop_bytes_of(c);
     const size_t need = sizeof(CkptHeader) + payload;
     if (!buf) {
@@ -808,6 +791,8 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
 flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
 {
     if (!c || !buf) return FLBM_EINVAL;
+    if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
+    if (is_batch(c)) return batch_restore(c, buf, bytes);
     if (bytes < sizeof(CkptHeader)) return fail(c, FLBM_EINVAL, "checkpoint image too small");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
@@ -851,6 +836,8 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
 void flbm_destroy(flbm_ctx *c)
 {
     if (!c) return;
+    if (c->is_view && c->batch) return; // replica views belong to their batch
+    if (c->batch) batch_destroy(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->own_buffers) {
         if (c->pop) cudaFree(c->pop);

@@ -1,0 +1,100 @@
+// flbm_ctx.h -- the context behind the opaque flbm_ctx handle, and the host
+// helpers the C-ABI translation units share (not installed).
+#pragma once
+#include <cstdarg>
+#include <vector>
+
+#include "flbm_internal.h"
+
+namespace flbm {
+struct BatchState; // flbm_batch.cu
+}
+
+struct flbm_ctx {
+    // problem
+    int lat = 0, D = 2, Q = 9;
+    int nx = 0, ny = 0, nz = 1;
+    int64_t N = 0;
+    double tau[2] = {1.0, 1.0}, kT = 0.0, G = 0.0;
+    uint64_t seed = 0;
+    // options
+    double lam[2][flbm::kMaxQ] = {};
+    int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
+    int schedule = FLBM_SCHEDULE_TWO_KERNELS;
+    double wait_limit_ms = 2000.0;
+    int pipe_lag = 0;
+    int test_stall = 0;
+    double rho0[2] = {1.0, 1.0};
+    // state
+    int64_t step = 0;
+    int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
+    bool initialised = false;
+    bool faulted = false;
+    bool timed_out = false;
+    // device buffers
+    void *pop = nullptr;
+    size_t pop_bytes = 0;
+    float *rho = nullptr;
+    size_t rho_bytes = 0;
+    bool own_buffers = false;
+    unsigned *d_status = nullptr;
+    unsigned *d_pipe = nullptr;   // fused-step counters: next item + one per slice
+    double *d_obs = nullptr;      // (2 + D) * N doubles: rho_a, rho_b, u
+    double *d_partials = nullptr; // per-block totals
+    size_t partials_cap = 0;
+    double *d_cons = nullptr;     // 5 doubles
+    double *d_sf = nullptr;       // 4 * n_axis/2 accumulators
+    double *d_profile = nullptr;  // (2 + D) * n_axis
+    int64_t sf_count = 0;
+    float *h_stage = nullptr;     // pinned staging, 2 * N floats
+    // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;      // recorded in order: start, after density, after collide, ...
+    size_t ev_used = 0;
+    double kernel_ms[2] = {0.0, 0.0};
+    int64_t kernel_launches[2] = {0, 0};
+    // stream
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char err[512] = {0};
+    // batch of independent replicas (flbm_batch_create), or a view of one replica
+    flbm::BatchState *batch = nullptr;
+    bool is_view = false;
+};
+
+#define FLBM_CUDA(ctx, call, what)                                               \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) return flbm::host::cuda_fail((ctx), e_, what);   \
+    } while (0)
+
+namespace flbm {
+namespace host {
+flbm_status fail(flbm_ctx *c, flbm_status st, const char *fmt, ...);
+flbm_status cuda_fail(flbm_ctx *c, cudaError_t e, const char *what);
+StepParams make_params(const flbm_ctx *c);
+flbm_status ensure_stream(flbm_ctx *c);
+flbm_status ensure_status(flbm_ctx *c);
+flbm_status ensure_stage(flbm_ctx *c);
+flbm_status sync_and_check(flbm_ctx *c);
+size_t pop_bytes_of(const flbm_ctx *c);
+size_t rho_bytes_of(const flbm_ctx *c);
+uint64_t fnv1a(const unsigned char *p, size_t n);
+} // namespace host
+
+// batch entry points used by the C-ABI functions when ctx->batch is set
+flbm_status batch_set_option(flbm_ctx *c, int key, double v);
+flbm_status batch_set_stream(flbm_ctx *c, void *stream);
+flbm_status batch_attach_buffers(flbm_ctx *c, void *pop, size_t pop_bytes, void *rho, size_t rho_bytes);
+flbm_status batch_init(flbm_ctx *c, const double *rho_a, const double *rho_b);
+flbm_status batch_step(flbm_ctx *c, int64_t n);
+flbm_status batch_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, double *cons);
+flbm_status batch_sf_sample(flbm_ctx *c);
+flbm_status batch_get_populations(flbm_ctx *c, double *f);
+flbm_status batch_set_populations(flbm_ctx *c, const double *f, int64_t step);
+flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes);
+flbm_status batch_restore(flbm_ctx *c, const void *buf, size_t bytes);
+void batch_destroy(flbm_ctx *c);
+bool view_call_allowed(const flbm_ctx *c); // false for mutating calls on a replica view
+inline bool is_batch(const flbm_ctx *c) { return c->batch && !c->is_view; }
+} // namespace flbm

@@ -28,6 +28,9 @@ template <class L, class S> struct CollideF {
 template <class L, class S> struct FusedF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::step_fused(a...); }
 };
+template <class L, class S> struct BatchF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::batch_step(a...); }
+};
 template <class L, class S> struct InitF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::init_rest(a...); }
 };
@@ -57,6 +60,13 @@ cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams
                               cudaStream_t stream)
 {
     return dispatch<FusedF>(lat, storage, parity, p, pop, rho, status, counters, wait_ms, stall, lag, stream);
+}
+
+cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,
+                              void *pop, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                              cudaStream_t stream)
+{
+    return dispatch<BatchF>(lat, storage, parity, reps, tiles, ntiles, pop, rho, status, step_base, k, stream);
 }
 
 cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in, void *pop,

@@ -28,6 +28,14 @@ struct StepParams {
     uint32_t step;             // noise counter word for this step
 };
 
+// One replica of a batch: its step parameters and the offsets of its slices of
+// the shared population array (elements) and density field (sites).
+struct RepInfo {
+    StepParams p;
+    unsigned long long pop_off;
+    unsigned long long rho_off;
+};
+
 // Device status bits (ORed by kernels, read by the host at sync points).
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;   // a bounded device-side wait gave up
@@ -100,6 +108,16 @@ cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams
                               unsigned *status, unsigned *counters, double wait_ms, int stall, int lag,
                               cudaStream_t stream);
 inline int pipeline_slices(int lat, int ny, int nz) { return lat == FLBM_D2Q9 ? ny : nz; }
+
+// One step of every replica of a batch (density then collide over the tile
+// work list: tiles[t] = (replica, first site of 128)); the noise counter of the
+// step is *step_base + k.
+cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,
+                              void *pop, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                              cudaStream_t stream);
+// *p += v and *p = v on the device (one thread), for the batch step counter.
+cudaError_t launch_add_u32(unsigned *p, unsigned v, cudaStream_t stream);
+cudaError_t launch_set_u32(unsigned *p, unsigned v, cudaStream_t stream);
 
 // Per-site observables in double: rho_a, rho_b, u (D planes), any may be NULL,
 // plus per-block FP64 partial totals [nblocks][5] into `partials`; returns the

@@ -414,6 +414,65 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
 }
 
 // ---------------------------------------------------------------------------
+// Batched step: many independent boxes of uneven size in one launch.  The
+// work list holds one entry per 128 consecutive sites of a replica; a block
+// stages its replica's parameters in shared memory and runs the same per-site
+// code as the single-box kernels on that replica's slice of the shared buffers.
+// The step's noise counter is read from device memory (base + k), so a CUDA
+// graph of several steps can be replayed without changing its parameters.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stage_params(const RepInfo *__restrict__ reps, int r, StepParams &sp,
+                                             unsigned long long &pop_off, unsigned long long &rho_off,
+                                             const unsigned *__restrict__ step_base, unsigned k)
+{
+    constexpr int words = (int)(sizeof(StepParams) / sizeof(unsigned));
+    static_assert(sizeof(StepParams) % sizeof(unsigned) == 0, "StepParams must be a whole number of words");
+    const unsigned *src = reinterpret_cast<const unsigned *>(&reps[r].p);
+    unsigned *dst = reinterpret_cast<unsigned *>(&sp);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldg(src + w);
+    if (threadIdx.x == 0) {
+        pop_off = reps[r].pop_off;
+        rho_off = reps[r].rho_off;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sp.step = *step_base + k;
+    __syncthreads();
+}
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_density_batch(const RepInfo *__restrict__ reps, const int2 *__restrict__ tiles,
+                                                       typename S::T *__restrict__ pop, float2 *__restrict__ rho,
+                                                       const unsigned *__restrict__ step_base, unsigned k)
+{
+    __shared__ StepParams sp;
+    __shared__ unsigned long long pop_off, rho_off;
+    const int2 t = tiles[blockIdx.x];
+    stage_params(reps, t.x, sp, pop_off, rho_off, step_base, k);
+    const int site = t.y + (int)threadIdx.x;
+    if (site >= sp.N) return;
+    const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
+    const Nbr nb = make_nbr(sp, x, y, z);
+    rho[rho_off + site] = site_density<L, S, PARITY>(sp, pop + pop_off, nb);
+}
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict__ reps, const int2 *__restrict__ tiles,
+                                                       typename S::T *__restrict__ pop, const float2 *__restrict__ rho,
+                                                       unsigned *__restrict__ status, const unsigned *__restrict__ step_base,
+                                                       unsigned k)
+{
+    __shared__ StepParams sp;
+    __shared__ unsigned long long pop_off, rho_off;
+    const int2 t = tiles[blockIdx.x];
+    stage_params(reps, t.x, sp, pop_off, rho_off, step_base, k);
+    const int site = t.y + (int)threadIdx.x;
+    if (site >= sp.N) return;
+    const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
+    const Nbr nb = make_nbr(sp, x, y, z);
+    site_collide<L, S, PARITY, false>(sp, pop + pop_off, rho + rho_off, status, nb, [] { return true; });
+}
+
+// ---------------------------------------------------------------------------
 // rest-state initialisation and site gather
 // ---------------------------------------------------------------------------
 template <class L, class S>
@@ -624,6 +683,23 @@ cudaError_t Launch<L, S>::step_fused(int parity, const StepParams &p, void *pop,
     void *args[] = {(void *)&pc, (void *)&ptr, (void *)&r2, (void *)&status, (void *)&a};
     const void *fn = parity == 0 ? (const void *)kern::k_step_fused<L, S, 0> : (const void *)kern::k_step_fused<L, S, 1>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, st);
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,
+                                     float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                                     cudaStream_t st)
+{
+    auto *ptr = static_cast<typename S::T *>(pop);
+    auto *r2 = reinterpret_cast<float2 *>(rho);
+    if (parity == 0) {
+        kern::k_density_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+        kern::k_collide_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+    } else {
+        kern::k_density_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+        kern::k_collide_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+    }
+    return cudaGetLastError();
 }
 
 template <class L, class S>

@@ -94,7 +94,22 @@ __global__ void __launch_bounds__(256) k_dft_accumulate(int D, int n_axis, doubl
     }
 }
 
+__global__ void k_add_u32(unsigned *p, unsigned v) { *p += v; }
+__global__ void k_set_u32(unsigned *p, unsigned v) { *p = v; }
+
 } // namespace
+
+cudaError_t launch_add_u32(unsigned *p, unsigned v, cudaStream_t stream)
+{
+    k_add_u32<<<1, 1, 0, stream>>>(p, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_u32(unsigned *p, unsigned v, cudaStream_t stream)
+{
+    k_set_u32<<<1, 1, 0, stream>>>(p, v);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sum_partials(const double *partials, int nblocks, double *out, cudaStream_t stream)
 {

@@ -34,6 +34,7 @@ OPT_SCHEDULE = 11
 OPT_WAIT_LIMIT_MS = 12
 OPT_TEST_STALL = 13
 OPT_PIPE_LAG = 14
+OPT_GRAPH_STEPS = 15
 SCHEDULE = {"fused": 0, "two_kernels": 1}
 OPT_LAMBDA_MODE = 1000
 OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
@@ -41,7 +42,15 @@ OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF
                 "force_velocity": OPT_FORCE_VELOCITY, "sf_axis": OPT_SF_AXIS,
                 "kernel_timing": OPT_KERNEL_TIMING, "schedule": OPT_SCHEDULE,
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
-                "pipe_lag": OPT_PIPE_LAG}
+                "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS}
+
+
+class RepParams(ctypes.Structure):
+    """flbm_rep_params: one replica of a batch."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("tau_a", ctypes.c_double), ("tau_b", ctypes.c_double), ("kT", ctypes.c_double),
+                ("G", ctypes.c_double), ("seed", ctypes.c_uint64), ("rho0_a", ctypes.c_double),
+                ("rho0_b", ctypes.c_double)]
 
 
 class FlbmError(RuntimeError):
@@ -95,6 +104,9 @@ def lib():
             "flbm_last_error": (ctypes.c_char_p, [vp]),
             "flbm_destroy": (None, [vp]),
             "flbm_version": (ctypes.c_char_p, []),
+            "flbm_batch_create": (i32, [i32, i32, ctypes.POINTER(RepParams), ctypes.POINTER(vp)]),
+            "flbm_batch_replica": (i32, [vp, i32, ctypes.POINTER(vp)]),
+            "flbm_batch_size": (i32, [vp, ctypes.POINTER(ctypes.c_int), i64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -126,7 +138,180 @@ def flbm_create(lattice, nx, ny, nz, tau_a, tau_b, kT, G, seed):
     return h
 
 
-class Lattice:
+class _Context:
+    """Observation and state calls shared by single boxes, batches and replica views."""
+
+    def sync(self):
+        check(self._h, lib().flbm_sync(self._h))
+
+    @property
+    def step_count(self):
+        v = ctypes.c_int64()
+        check(self._h, lib().flbm_get_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_option(self, key, value):
+        if isinstance(key, str):
+            key = OPTION_NAMES[key]
+        check(self._h, lib().flbm_set_option(self._h, int(key), float(value)))
+
+    def sf_sample(self):
+        check(self._h, lib().flbm_sf_sample(self._h))
+
+    def sf_reset(self):
+        check(self._h, lib().flbm_sf_reset(self._h))
+
+    def moments(self, fields=True):
+        """(rho_a, rho_b, u[D], cons[5]) as float64 arrays [z][y][x]."""
+        shp = (self.nz, self.ny, self.nx)
+        ra = np.empty(self.N) if fields else None
+        rb = np.empty(self.N) if fields else None
+        u = np.empty(self.D * self.N) if fields else None
+        cons = np.empty(5)
+        check(self._h, lib().flbm_moments(self._h, _dp(ra), _dp(rb), _dp(u), _dp(cons)))
+        if not fields:
+            return cons
+        return ra.reshape(shp), rb.reshape(shp), u.reshape((self.D,) + shp), cons
+
+    def structure_factor(self, axis=0, nk=None):
+        n_axis = (self.nx, self.ny, self.nz)[axis]
+        nk = n_axis // 2 if nk is None else nk
+        out = [np.empty(nk) for _ in range(4)]
+        n = ctypes.c_int64()
+        check(self._h, lib().flbm_structure_factor(self._h, axis, nk, *[_dp(o) for o in out], ctypes.byref(n)))
+        return (*out, n.value)
+
+    def get_populations(self):
+        f = np.empty(2 * self.Q * self.N)
+        check(self._h, lib().flbm_get_populations(self._h, _dp(f)))
+        return f.reshape(2, self.Q, self.nz, self.ny, self.nx)
+
+    def set_populations(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        if f.size != 2 * self.Q * self.N:
+            raise ValueError("populations need 2 * Q values per site")
+        check(self._h, lib().flbm_set_populations(self._h, _dp(f), int(step)))
+
+    def site_populations(self, sites):
+        s = np.ascontiguousarray(sites, dtype=np.int64).ravel()
+        out = np.empty(s.size * 2 * self.Q)
+        check(self._h, lib().flbm_get_site_populations(
+            self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), s.size, _dp(out)))
+        return out.reshape(s.size, 2, self.Q)
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t()
+        check(self._h, lib().flbm_checkpoint(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(self._h, lib().flbm_checkpoint(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def restore(self, image: bytes):
+        buf = ctypes.create_string_buffer(image, len(image))
+        check(self._h, lib().flbm_restore(self._h, buf, len(image)))
+
+
+class ReplicaView(_Context):
+    """One replica of a Batch, for observation (moments, structure factors,
+    populations).  Owned by its batch."""
+
+    def __init__(self, batch, rep, params):
+        self._batch = batch
+        h = ctypes.c_void_p()
+        check(batch._h, lib().flbm_batch_replica(batch._h, int(rep), ctypes.byref(h)))
+        self._h = h
+        self.lattice = batch.lattice
+        self.nx, self.ny = params.nx, params.ny
+        self.nz = 1 if self.lattice == D2Q9 else params.nz
+        self.D, self.Q = batch.D, batch.Q
+        self.N = self.nx * self.ny * self.nz
+
+
+
+class Batch(_Context):
+    """Many independent two-species boxes of uneven size advanced together
+    (flbm_batch_create).  ``replicas`` is a list of dicts with nx, ny[, nz],
+    tau_a, tau_b, kT, G, seed[, rho0_a, rho0_b]."""
+
+    def __init__(self, lattice, replicas, storage="f32", device="cuda:0", stream=None, **options):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device visible: flbm runs on the GPU only")
+        self.lattice = int(lattice)
+        self.D = 2 if self.lattice == D2Q9 else 3
+        self.Q = 9 if self.lattice == D2Q9 else 19
+        arr = (RepParams * len(replicas))()
+        for k, r in enumerate(replicas):
+            arr[k] = RepParams(int(r["nx"]), int(r["ny"]), int(r.get("nz", 1)), float(r.get("tau_a", 1.0)),
+                               float(r.get("tau_b", 1.0)), float(r.get("kT", 0.0)), float(r.get("G", 0.0)),
+                               int(r.get("seed", 1)) & (2**64 - 1), float(r.get("rho0_a", 1.0)),
+                               float(r.get("rho0_b", 1.0)))
+        self._params = arr
+        self._h = None
+        h = ctypes.c_void_p()
+        check(None, lib().flbm_batch_create(self.lattice, len(replicas), arr, ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int()
+        sites = ctypes.c_int64()
+        check(self._h, lib().flbm_batch_size(self._h, ctypes.byref(n), ctypes.byref(sites)))
+        self.nrep, self.N = n.value, sites.value
+        self.sizes = [arr[k].nx * arr[k].ny * (arr[k].nz if self.lattice == D3Q19 else 1) for k in range(self.nrep)]
+        self.set_option(OPT_STORAGE, STORE[storage] if isinstance(storage, str) else int(storage))
+        for k, v in options.items():
+            self.set_option(k, v)
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        check(self._h, lib().flbm_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)))
+        pb, rb = ctypes.c_size_t(), ctypes.c_size_t()
+        check(self._h, lib().flbm_buffer_bytes(self._h, ctypes.byref(pb), ctypes.byref(rb)))
+        self.pop_buffer = torch.empty(pb.value, dtype=torch.uint8, device=self.device)
+        self.rho_buffer = torch.empty(rb.value, dtype=torch.uint8, device=self.device)
+        check(self._h, lib().flbm_attach_buffers(self._h, ctypes.c_void_p(self.pop_buffer.data_ptr()), pb.value,
+                                                 ctypes.c_void_p(self.rho_buffer.data_ptr()), rb.value))
+        self.replicas = [ReplicaView(self, k, arr[k]) for k in range(self.nrep)]
+
+    def init(self, rho_a=None, rho_b=None):
+        ra = None if rho_a is None else np.ascontiguousarray(rho_a, dtype=np.float64).ravel()
+        rb = None if rho_b is None else np.ascontiguousarray(rho_b, dtype=np.float64).ravel()
+        check(self._h, lib().flbm_init(self._h, _dp(ra), _dp(rb)))
+
+    def step(self, n=1):
+        check(self._h, lib().flbm_step(self._h, int(n)))
+
+    def moments(self):
+        """(rho_a, rho_b, u, cons): per-replica fields concatenated, u as
+        [replica][d][site] flattened, cons summed over replicas."""
+        ra, rb = np.empty(self.N), np.empty(self.N)
+        u = np.empty(self.D * self.N)
+        cons = np.empty(5)
+        check(self._h, lib().flbm_moments(self._h, _dp(ra), _dp(rb), _dp(u), _dp(cons)))
+        return ra, rb, u, cons
+
+    def get_populations(self):
+        f = np.empty(2 * self.Q * self.N)
+        check(self._h, lib().flbm_get_populations(self._h, _dp(f)))
+        return f
+
+    def set_populations(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        check(self._h, lib().flbm_set_populations(self._h, _dp(f), int(step)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.replicas = []
+            lib().flbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice(_Context):
     """One two-species periodic box on the GPU (a flbm_ctx).
 
     Device memory for the populations and the density field comes from PyTorch
@@ -163,11 +348,6 @@ class Lattice:
                                                  ctypes.c_void_p(self.rho_buffer.data_ptr()), rb.value))
 
     # -- configuration ----------------------------------------------------
-    def set_option(self, key, value):
-        if isinstance(key, str):
-            key = OPTION_NAMES[key]
-        check(self._h, lib().flbm_set_option(self._h, int(key), float(value)))
-
     def set_mode_rate(self, species, mode, lam):
         self.set_option(OPT_LAMBDA_MODE + 100 * int(species) + int(mode), lam)
 
@@ -183,15 +363,6 @@ class Lattice:
     def step(self, n=1):
         check(self._h, lib().flbm_step(self._h, int(n)))
 
-    def sync(self):
-        check(self._h, lib().flbm_sync(self._h))
-
-    @property
-    def step_count(self):
-        v = ctypes.c_int64()
-        check(self._h, lib().flbm_get_step(self._h, ctypes.byref(v)))
-        return v.value
-
     def kernel_times(self):
         """({'density': ms, 'collide': ms}, {'density': n, 'collide': n}) accumulated
         while the kernel_timing option was on.  With the fused schedule 'density'
@@ -200,61 +371,6 @@ class Lattice:
         n = np.zeros(2, dtype=np.int64)
         check(self._h, lib().flbm_kernel_times(self._h, _dp(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return {"density": ms[0], "collide": ms[1]}, {"density": int(n[0]), "collide": int(n[1])}
-
-    def moments(self, fields=True):
-        """(rho_a, rho_b, u[D], cons[5]) as float64 arrays [z][y][x]."""
-        shp = (self.nz, self.ny, self.nx)
-        ra = np.empty(self.N) if fields else None
-        rb = np.empty(self.N) if fields else None
-        u = np.empty(self.D * self.N) if fields else None
-        cons = np.empty(5)
-        check(self._h, lib().flbm_moments(self._h, _dp(ra), _dp(rb), _dp(u), _dp(cons)))
-        if not fields:
-            return cons
-        return ra.reshape(shp), rb.reshape(shp), u.reshape((self.D,) + shp), cons
-
-    def sf_sample(self):
-        check(self._h, lib().flbm_sf_sample(self._h))
-
-    def structure_factor(self, axis=0, nk=None):
-        n_axis = (self.nx, self.ny, self.nz)[axis]
-        nk = n_axis // 2 if nk is None else nk
-        out = [np.empty(nk) for _ in range(4)]
-        n = ctypes.c_int64()
-        check(self._h, lib().flbm_structure_factor(self._h, axis, nk, *[_dp(o) for o in out], ctypes.byref(n)))
-        return (*out, n.value)
-
-    def sf_reset(self):
-        check(self._h, lib().flbm_sf_reset(self._h))
-
-    def get_populations(self):
-        f = np.empty(2 * self.Q * self.N)
-        check(self._h, lib().flbm_get_populations(self._h, _dp(f)))
-        return f.reshape(2, self.Q, self.nz, self.ny, self.nx)
-
-    def set_populations(self, f, step=0):
-        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
-        if f.size != 2 * self.Q * self.N:
-            raise ValueError("populations need 2 * Q values per site")
-        check(self._h, lib().flbm_set_populations(self._h, _dp(f), int(step)))
-
-    def site_populations(self, sites):
-        s = np.ascontiguousarray(sites, dtype=np.int64).ravel()
-        out = np.empty(s.size * 2 * self.Q)
-        check(self._h, lib().flbm_get_site_populations(
-            self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), s.size, _dp(out)))
-        return out.reshape(s.size, 2, self.Q)
-
-    def checkpoint(self) -> bytes:
-        n = ctypes.c_size_t()
-        check(self._h, lib().flbm_checkpoint(self._h, None, ctypes.byref(n)))
-        buf = ctypes.create_string_buffer(n.value)
-        check(self._h, lib().flbm_checkpoint(self._h, buf, ctypes.byref(n)))
-        return buf.raw[:n.value]
-
-    def restore(self, image: bytes):
-        buf = ctypes.create_string_buffer(image, len(image))
-        check(self._h, lib().flbm_restore(self._h, buf, len(image)))
 
     def close(self):
         if getattr(self, "_h", None):

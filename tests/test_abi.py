@@ -87,3 +87,29 @@ def test_null_context_is_safe(lib):
     assert lib.flbm_last_error(None) == b""
     assert lib.flbm_step(None, 1) == F.EINVAL
     lib.flbm_destroy(None)
+
+
+def test_batch_create_validates_replicas(lib):
+    good = F.RepParams(8, 6, 1, 1.0, 1.0, 1e-4, 0.1, 3, 1.0, 1.0)
+    bad_tau = F.RepParams(8, 6, 1, 0.5, 1.0, 1e-4, 0.1, 3, 1.0, 1.0)
+    bad_rho = F.RepParams(8, 6, 1, 1.0, 1.0, 1e-4, 0.1, 3, 0.0, 1.0)
+    for arr in [(F.RepParams * 2)(good, bad_tau), (F.RepParams * 1)(bad_rho)]:
+        h = ctypes.c_void_p()
+        assert lib.flbm_batch_create(0, len(arr), arr, ctypes.byref(h)) == F.EINVAL
+        assert not h.value
+    arr = (F.RepParams * 2)(good, F.RepParams(5, 7, 1, 0.9, 1.1, 1e-5, 0.2, 4, 1.0, 0.8))
+    h = ctypes.c_void_p()
+    assert lib.flbm_batch_create(0, 2, arr, ctypes.byref(h)) == F.OK
+    try:
+        n, sites = ctypes.c_int(), ctypes.c_int64()
+        assert lib.flbm_batch_size(h, ctypes.byref(n), ctypes.byref(sites)) == F.OK
+        assert (n.value, sites.value) == (2, 48 + 35)
+        v = ctypes.c_void_p()
+        assert lib.flbm_batch_replica(h, 1, ctypes.byref(v)) == F.OK
+        assert lib.flbm_step(v, 1) == F.ESTATE          # views are read-only
+        assert lib.flbm_set_option(v, F.OPT_SF_AXIS, 1) == F.OK
+        assert lib.flbm_batch_replica(h, 2, ctypes.byref(v)) == F.EINVAL
+        assert lib.flbm_set_option(h, F.OPT_GRAPH_STEPS, -1) == F.EINVAL
+        lib.flbm_destroy(v)                             # a view is not destroyed on its own
+    finally:
+        lib.flbm_destroy(h)
