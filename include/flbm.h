@@ -82,8 +82,15 @@ enum {
                                     else 2/(tau_A + tau_B) */
     FLBM_OPT_SDF = 3,            /* 1 (default): noise on the species momenta ("sdf");
                                     0: switched off ("no-sdf" control of Sec. VI A) */
-    FLBM_OPT_RHO0_A = 4,         /* reference density of A: uniform init and 16-bit deviation base;
-                                    default 1 */
+    FLBM_OPT_RHO0_A = 4,         /* reference density of A, default 1: the uniform init value and
+                                    the base of the stored deviations f_i - w_i rho0 (all storage
+                                    formats).  Set it near the mean density: then the deviations
+                                    are small, float subtraction of the base is exact and the
+                                    total mass only random-walks at the rounding of one
+                                    population per site and step.  Far from it (for instance
+                                    rho = rho0 / 2) the deviations are as large as the
+                                    populations and the mass drifts slowly at their rounding
+                                    (about 1e-10 relative per step). */
     FLBM_OPT_RHO0_B = 5,         /* same for B */
     FLBM_OPT_NOISE_RHO = 7,      /* 0 (default): local densities in the noise amplitudes
                                     (Sec. VII); 1: the reference densities rho0 (Eq. new-noise,

@@ -63,14 +63,17 @@ StepParams make_params(const flbm_ctx *c)
     p.N = (int)c->N;
     p.G = (float)c->G;
     const double mu = 3.0 * c->kT; // k_B T / c_s^2
-    for (int s = 0; s < 2; s++)
-        for (int a = 0; a < c->Q; a++) {
-            const double lb = c->lam[s][a];
-            p.lam[s][a] = (float)lb;
-            p.hlam[s][a] = (float)(1.0 - 0.5 * lb);
-            p.noise_amp[s][a] = a > c->D ? (float)std::sqrt((2.0 * lb - lb * lb) * lat_N(c->lat, a) * mu) : 0.0f;
-        }
     const double lb_d = c->lam[0][1];
+    p.lam_d = (float)lb_d;
+    p.hlam_d = (float)(1.0 - 0.5 * lb_d);
+    for (int s = 0; s < 2; s++)
+        for (int a = c->D + 1; a < c->Q; a++) {
+            const double lb = c->lam[s][a], Na = lat_N(c->lat, a);
+            p.cm[s][a] = (float)((1.0 - lb) / Na);
+            p.ceq[s][a] = (float)(lb / Na);
+            p.cphi[s][a] = (float)((1.0 - 0.5 * lb) / Na);
+            p.cxi[s][a] = (float)(std::sqrt((2.0 * lb - lb * lb) * Na * mu) / Na);
+        }
     p.noise_amp_j = c->sdf ? (float)std::sqrt((2.0 * lb_d - lb_d * lb_d) * c->kT) : 0.0f;
     p.rho0[0] = (float)c->rho0[0];
     p.rho0[1] = (float)c->rho0[1];

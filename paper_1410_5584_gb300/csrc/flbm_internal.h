@@ -17,9 +17,14 @@ struct StepParams {
     int nx, ny, nz;
     int N;                     // nx * ny * nz  (< 2^31)
     float G;                   // inter-species coupling, Eq. FORCESTRUCTURE
-    float lam[2][kMaxQ];       // lambdabar_a per species (lam[s][1..D] = lambdabar_d)
-    float hlam[2][kMaxQ];      // 1 - lambdabar_a / 2  (Eq. forcerenorm)
-    float noise_amp[2][kMaxQ]; // a > D: sqrt((2 lb_a - lb_a^2) N_a kT / c_s^2); times sqrt(rho^s)
+    float lam_d;               // common momentum rate lambdabar_d of both species
+    float hlam_d;              // 1 - lambdabar_d / 2  (Eq. forcerenorm)
+    // Non-conserved modes a > D of species s, relaxed as in Eq. algorithm with
+    // 1/N_a folded in: m*_a / N_a = cm m_a + ceq m^eq_a + cphi Phi_a + cxi sqrt(rho^s) g_a
+    float cm[2][kMaxQ];        // (1 - lambdabar_a) / N_a
+    float ceq[2][kMaxQ];       // lambdabar_a / N_a
+    float cphi[2][kMaxQ];      // (1 - lambdabar_a / 2) / N_a
+    float cxi[2][kMaxQ];       // sqrt((2 lb_a - lb_a^2) N_a kT / c_s^2) / N_a  (Eq. new-noise)
     float noise_amp_j;         // sqrt((2 lb_d - lb_d^2) kT); times sqrt(rho rho'/rho_t); 0 = no-sdf
     float rho0[2];             // reference densities: 16-bit deviation base, noise reference
     int noise_ref;             // 1: noise amplitudes from rho0 instead of the local densities
@@ -46,39 +51,48 @@ constexpr unsigned kStatusTimeout = 2u;   // a bounded device-side wait gave up
 // small non-conserved moments free of cancellation; the 16-bit formats store
 // the deviation itself.
 // ---------------------------------------------------------------------------
+// encode() forms the stored word of a deviation and decode() the deviation a
+// load of that word gives; both round once, without contraction, so a kernel
+// can know exactly what the next step will load.
 struct StoreF32 {
     using T = float;
+    __device__ __forceinline__ static T encode(float dev, float base) { return __fadd_rn(base, dev); }
+    __device__ __forceinline__ static float decode(T v, float base) { return __fsub_rn(v, base); }
     __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
     {
-        return __ldg(p + idx) - base;
+        return decode(__ldg(p + idx), base);
     }
     __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float base)
     {
-        p[idx] = base + dev;
+        p[idx] = encode(dev, base);
     }
 };
 
 struct StoreF16 {
     using T = __half;
-    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float)
+    __device__ __forceinline__ static T encode(float dev, float) { return __float2half_rn(dev); }
+    __device__ __forceinline__ static float decode(T v, float) { return __half2float(v); }
+    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
     {
-        return __half2float(p[idx]);
+        return decode(p[idx], base);
     }
-    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float)
+    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float base)
     {
-        p[idx] = __float2half_rn(dev);
+        p[idx] = encode(dev, base);
     }
 };
 
 struct StoreBF16 {
     using T = __nv_bfloat16;
-    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float)
+    __device__ __forceinline__ static T encode(float dev, float) { return __float2bfloat16_rn(dev); }
+    __device__ __forceinline__ static float decode(T v, float) { return __bfloat162float(v); }
+    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
     {
-        return __bfloat162float(p[idx]);
+        return decode(p[idx], base);
     }
-    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float)
+    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float base)
     {
-        p[idx] = __float2bfloat16_rn(dev);
+        p[idx] = encode(dev, base);
     }
 };
 

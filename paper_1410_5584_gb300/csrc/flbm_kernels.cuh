@@ -174,17 +174,18 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
     });
     if (STORE && (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt))) atomicOr(status, kStatusNonFinite);
 
-    // 4. noise amplitudes of Eq. new-noise (local or reference densities)
+    // 4. Gaussians scaled by the amplitudes of Eq. new-noise (local or reference
+    // densities): sqrt(rho rho'/rho_t) for the shared momentum noise, sqrt(rho^s)
+    // for the other modes of species s (their per-mode factors are in cxi).
+    // Square roots as x rsqrt(x): the densities are positive on every valid state
+    // (a non-positive one has already raised the status flag).
     const float n0 = p.noise_ref ? p.rho0[0] : rs[0];
     const float n1 = p.noise_ref ? p.rho0[1] : rs[1];
-    float g[2][Q];
-    draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, g[0]);
-    draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, g[1]);
-    // square roots as x rsqrt(x): the densities are positive on every valid state
-    // (a non-positive one has already raised the status flag)
     const float hm = n0 * n1 * __frcp_rn(n0 + n1);
     const float amp_j = p.noise_amp_j * (hm * rsqrtf(hm));
-    const float sq[2] = {n0 * rsqrtf(n0), n1 * rsqrtf(n1)};
+    float g[2][Q];
+    draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g[0]);
+    draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g[1]);
 
     // 5. momentum modes: common rate, opposite noise; species velocity for Phi
     float v[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
@@ -194,36 +195,52 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             constexpr int a = 1 + d;
-            const float xi = (s == 0 ? amp_j : -amp_j) * g[0][a];
-            const float R = p.lam[s][a] * (rs[s] * u[d] - m[s][a]) + p.hlam[s][a] * rs[s] * acc[s][d] + xi;
+            const float xi = s == 0 ? g[0][a] : -g[0][a];
+            const float R = p.lam_d * (rs[s] * u[d] - m[s][a]) + p.hlam_d * rs[s] * acc[s][d] + xi;
             v[s][d] = p.force_velocity ? m[s][a] * irs + 0.5f * acc[s][d] : (m[s][a] + 0.5f * R) * irs;
             m[s][a] += R;
         });
     });
 
-    // 6. transport and ghost modes, then back-projection and streaming
+    // 6. transport and ghost modes, then back-projection and streaming.  With
+    // mu_a = m*_a / N_a: m*_a = m_a + lambdabar_a (m^eq_a - m_a) + (1 - lambdabar_a/2)
+    // Phi_a + xi_a, i.e. mu_a = cm m_a + rho (ceq X_a + cphi Y_a) + cxi g_a, and for
+    // the ghost modes (m^eq = Phi = 0) mu_a = cm m_a + cxi g_a.
+    float X[Q];
+    Closure<L>::eq(u, X);
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        float meq[Q], phi[Q];
-        Closure<L>::eq_force(rs[s], u, acc[s], v[s], meq, phi);
+        float Y[Q];
+        Closure<L>::force(acc[s], v[s], Y);
+        float mu[Q], fo[Q];
+        mu[0] = m[s][0];
+        static_for<D>([&](auto dc) {
+            constexpr int a = decltype(dc)::value + 1;
+            constexpr float invN = (float)(1.0 / L::Nd(a));
+            mu[a] = invN * m[s][a];
+        });
         static_for<Q - D - 1>([&](auto kc) {
             constexpr int a = decltype(kc)::value + D + 1;
-            m[s][a] += p.lam[s][a] * (meq[a] - m[s][a]) + p.hlam[s][a] * phi[a] + p.noise_amp[s][a] * sq[s] * g[s][a];
-        });
-        // back to populations: delta*_i = w_i sum_a T_ai m*_a / N_a (Eq. algorithm)
-        float mu[Q], fo[Q];
-        static_for<Q>([&](auto ac) {
-            constexpr int a = decltype(ac)::value;
-            constexpr float invN = (float)(1.0 / L::Nd(a));
-            if constexpr (a == 0) mu[a] = m[s][a];
-            else mu[a] = invN * m[s][a];
+            float t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * g[s][a]);
+            if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
+            mu[a] = t;
         });
         Transform<L>::backward(mu, fo);
-        fo[0] = Transform<L>::rest_closing_mass(fo, m[s][0]);
+        // Mass balance: the moving populations are encoded first and replaced by
+        // the deviations their stored words will load as; the rest population
+        // then takes m0 minus what they hold, so the rounding of their stores
+        // cannot leak mass.
+        typename S::T word[Q];
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
+            const float base = (float)L::wd(i) * p.rho0[s];
+            word[i] = S::encode(fo[i], base);
+            fo[i] = S::decode(word[i], base);
+        });
+        word[0] = S::encode(Transform<L>::rest_closing_mass(fo, m[s][0]), (float)L::wd(0) * p.rho0[s]);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            constexpr float wi = (float)L::wd(i);
-            if (STORE) S::store_dev(pop, write_index<L, PARITY, i>(nb, NN, s), fo[i], wi * p.rho0[s]);
+            if (STORE) pop[write_index<L, PARITY, i>(nb, NN, s)] = word[i];
         });
     });
 }

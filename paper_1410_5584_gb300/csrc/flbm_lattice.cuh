@@ -163,51 +163,55 @@ template <class L> constexpr bool basis_is_orthogonal()
 static_assert(basis_is_orthogonal<D2Q9>(), "D2Q9 basis is not orthogonal with the Table I norms");
 static_assert(basis_is_orthogonal<D3Q19>(), "D3Q19 basis is not orthogonal with its norms");
 
-// Closed-form equilibrium moments m^eq_a(rho, u) of the second-order Hermite
-// equilibrium (Table I column for D2Q9; for D3Q19 the Hermite rows give
-// rho, rho u, rho |u|^2, rho (2ux^2 - uy^2 - uz^2), rho (uy^2 - uz^2), rho u_a u_b),
-// and forcing moments Phi_a(rho, a, v) of Eq. hermite-for truncated at second
-// order: Phi_ab = rho (a_a v_b + v_a a_b) projected on the same rows; ghosts 0.
-// Only rows a > D are produced (the momentum rows are handled separately).
+// Closed-form equilibrium and forcing moments of the non-conserved transport
+// modes a = D+1 .. kGhost-1.  The second-order Hermite equilibrium gives
+// m^eq_a = rho X_a(u) (the Table I column for D2Q9; for D3Q19 the rows
+// |u|^2, 2ux^2 - uy^2 - uz^2, uy^2 - uz^2, u_a u_b), X depending on the
+// baricentric velocity alone and so common to both species.  The forcing
+// moments of Eq. hermite-for truncated at second order, Phi_ab = rho (a_a v_b +
+// v_a a_b), projected on the same rows give Phi_a = rho Y_a(a, v).  The ghost
+// modes a >= kGhost have m^eq = Phi = 0; the momentum rows are handled apart.
 template <class L> struct Closure;
 
 template <> struct Closure<D2Q9> {
-    __device__ __forceinline__ static void eq_force(float rho, const float *u, const float *a,
-                                                    const float *v, float *meq, float *phi)
+    static constexpr int kGhost = 6;
+    __device__ __forceinline__ static void eq(const float *u, float *X)
     {
         const float uxx = u[0] * u[0], uyy = u[1] * u[1];
-        meq[3] = 3.0f * rho * (uxx + uyy);
-        meq[4] = rho * (uxx - uyy);
-        meq[5] = rho * u[0] * u[1];
-        meq[6] = meq[7] = meq[8] = 0.0f;
+        X[3] = 3.0f * (uxx + uyy);
+        X[4] = uxx - uyy;
+        X[5] = u[0] * u[1];
+    }
+    __device__ __forceinline__ static void force(const float *a, const float *v, float *Y)
+    {
         const float axvx = a[0] * v[0], ayvy = a[1] * v[1];
-        phi[3] = 6.0f * rho * (axvx + ayvy);
-        phi[4] = 2.0f * rho * (axvx - ayvy);
-        phi[5] = rho * (a[0] * v[1] + a[1] * v[0]);
-        phi[6] = phi[7] = phi[8] = 0.0f;
+        Y[3] = 6.0f * (axvx + ayvy);
+        Y[4] = 2.0f * (axvx - ayvy);
+        Y[5] = a[0] * v[1] + a[1] * v[0];
     }
 };
 
 template <> struct Closure<D3Q19> {
-    __device__ __forceinline__ static void eq_force(float rho, const float *u, const float *a,
-                                                    const float *v, float *meq, float *phi)
+    static constexpr int kGhost = 10;
+    __device__ __forceinline__ static void eq(const float *u, float *X)
     {
         const float uxx = u[0] * u[0], uyy = u[1] * u[1], uzz = u[2] * u[2];
-        meq[4] = rho * (uxx + uyy + uzz);
-        meq[5] = rho * (2.0f * uxx - uyy - uzz);
-        meq[6] = rho * (uyy - uzz);
-        meq[7] = rho * u[0] * u[1];
-        meq[8] = rho * u[1] * u[2];
-        meq[9] = rho * u[0] * u[2];
+        X[4] = uxx + uyy + uzz;
+        X[5] = 2.0f * uxx - uyy - uzz;
+        X[6] = uyy - uzz;
+        X[7] = u[0] * u[1];
+        X[8] = u[1] * u[2];
+        X[9] = u[0] * u[2];
+    }
+    __device__ __forceinline__ static void force(const float *a, const float *v, float *Y)
+    {
         const float pxx = 2.0f * a[0] * v[0], pyy = 2.0f * a[1] * v[1], pzz = 2.0f * a[2] * v[2];
-        phi[4] = rho * (pxx + pyy + pzz);
-        phi[5] = rho * (2.0f * pxx - pyy - pzz);
-        phi[6] = rho * (pyy - pzz);
-        phi[7] = rho * (a[0] * v[1] + a[1] * v[0]);
-        phi[8] = rho * (a[1] * v[2] + a[2] * v[1]);
-        phi[9] = rho * (a[0] * v[2] + a[2] * v[0]);
-#pragma unroll
-        for (int k = 10; k < 19; k++) meq[k] = phi[k] = 0.0f;
+        Y[4] = pxx + pyy + pzz;
+        Y[5] = 2.0f * pxx - pyy - pzz;
+        Y[6] = pyy - pzz;
+        Y[7] = a[0] * v[1] + a[1] * v[0];
+        Y[8] = a[1] * v[2] + a[2] * v[1];
+        Y[9] = a[0] * v[2] + a[2] * v[0];
     }
 };
 

@@ -29,41 +29,63 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
     return x;
 }
 
-// Box-Muller on one pair of words: u1 = ((a >> 8) + 1) 2^-24 in (0, 1] and
-// u2 = (b >> 8) 2^-24 in [0, 1) are exact in float; g0 = r cos(2 pi u2),
-// g1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
-// The angle is folded exactly into [-pi, pi) (u2 - 1 for u2 >= 1/2, the same
-// sine and cosine), where the hardware sine/cosine have an absolute error of
-// about 2^-21; r = x rsqrt(x).
-//
-// ln u1: for u1 <= 31/32 the hardware log2 (absolute error <= 2^-22 on
-// [1/2, 2], 2 ulp below) is accurate to ~5e-6 relative since |ln u1| >= 0.0317;
-// nearer 1, where an absolute error would swamp the small radius, the Mercator
-// series ln(1 - v) = -(v + v^2/2 + ... + v^5/5) with v = 1 - u1 <= 1/32 (exact by
-// Sterbenz's lemma) is used, truncation error below 1e-8 relative.
-__device__ __forceinline__ float log_unit_interval(float u1)
+// Hardware approximations (PTX lg2/rsqrt/sin/cos .approx.ftz).  Every argument
+// they get below is zero or a normal number, so flushing subnormals changes no
+// result and spares the subnormal handling of the non-ftz forms.
+__device__ __forceinline__ float lg2_hw(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_hw(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_hw(float x, float &s, float &c)
+{
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
+}
+
+// -2 ln u1 for u1 in (0, 1].  For u1 <= 31/32 the hardware log2 (absolute error
+// <= 2^-22 on [1/2, 2], 2 ulp below) is accurate to ~5e-6 relative since
+// |ln u1| >= 0.0317; nearer 1, where an absolute error would swamp the small
+// radius, the Mercator series -2 ln(1 - v) = 2 (v + v^2/2 + ... + v^5/5) with
+// v = 1 - u1 <= 1/32 (exact by Sterbenz's lemma) is used, truncation error
+// below 1e-8 relative.
+__device__ __forceinline__ float minus_two_log_unit_interval(float u1)
 {
     const float v = 1.0f - u1;
-    float ps = fmaf(v, 0.2f, 0.25f);
-    ps = fmaf(v, ps, 0.333333333333333333f);
-    ps = fmaf(v, ps, 0.5f);
+    float ps = fmaf(v, 0.4f, 0.5f);
+    ps = fmaf(v, ps, 0.666666667f);
     ps = fmaf(v, ps, 1.0f);
-    const float near1 = -v * ps;
-    const float far = __log2f(u1) * 0.693147180559945309f;
+    ps = fmaf(v, ps, 2.0f);
+    const float near1 = v * ps;
+    const float far = lg2_hw(u1) * -1.38629436111989061883f; // -2 ln 2
     return u1 > 0.96875f ? near1 : far;
 }
 
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
+// Box-Muller on one pair of words, scaled: g0 = scale r cos(2 pi u2),
+// g1 = scale r sin(2 pi u2), r = sqrt(-2 ln u1), with u1 = ((a >> 8) + 1) 2^-24
+// in (0, 1] and u2 = (b >> 8) 2^-24 in [0, 1), both exact in float.  The angle
+// is taken in [-pi, pi), where the hardware sine and cosine have an absolute
+// error of about 2^-21: reading b as signed and shifting arithmetically gives
+// u2 for u2 < 1/2 and u2 - 1 above (the same sine and cosine).  r = x rsqrt(x).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float scale, float &g0, float &g1)
 {
     const float u1 = fmaf((float)(a >> 8), 0x1.0p-24f, 0x1.0p-24f); // ((a >> 8) + 1) 2^-24, exact
-    const float u2 = (float)(b >> 8) * 0x1.0p-24f;
-    const float r2 = -2.0f * log_unit_interval(u1);
-    // r = sqrt(r2); the tiny offset makes r2 = 0 (u1 = 1) give 0 instead of 0 * inf
-    // and is far below the rounding of the smallest nonzero r2 (~1.2e-7)
-    const float r = r2 * rsqrtf(r2 + 1e-30f);
-    const float t = u2 < 0.5f ? u2 : u2 - 1.0f;
+    const float r2 = minus_two_log_unit_interval(u1);
+    // the tiny offset makes r2 = 0 (u1 = 1) give 0 instead of 0 * inf and is far
+    // below the rounding of the smallest nonzero r2 (~1.2e-7)
+    const float r = scale * (r2 * rsqrt_hw(r2 + 1e-30f));
+    // 2 pi t with t = (signed b >> 8) 2^-24: one rounding, as 2 pi 2^-24 is the
+    // float 2 pi times a power of two
+    const float ang = (float)((int32_t)b >> 8) * (6.28318530717958647692f * 0x1.0p-24f);
     float s, c;
-    __sincosf(6.28318530717958647692f * t, &s, &c);
+    sincos_hw(ang, s, c);
     g0 = r * c;
     g1 = r * s;
 }
@@ -77,31 +99,50 @@ __host__ __device__ constexpr bool uses_mode(int a)
     return a < L::Q && (a > L::D || (S == 0 && a >= 1 && a <= L::D));
 }
 
-// Fill g[a] with the standard Gaussian of mode a for every mode species S uses:
-// counter (site, step, S, a/4), lane a mod 4.  Only the needed Philox blocks
-// and Box-Muller pairs are evaluated (decided at compile time).
+// Scale kind of mode a: 1 for a momentum mode (scaled by scale_j), 0 otherwise.
+template <class L> __host__ __device__ constexpr int scale_kind(int a) { return a >= 1 && a <= L::D ? 1 : 0; }
+
+// One Box-Muller pair for modes (a0, a0 + 1) of species S.  When both modes are
+// used with different scales (D2Q9: momentum mode 2 beside mode 3) the radius
+// stays unscaled and each output takes its own scale.
+template <class L, int S, int a0>
+__device__ __forceinline__ void gaussian_pair(uint32_t wa, uint32_t wb, float scale_j, float scale, float (&g)[L::Q])
+{
+    constexpr bool use0 = uses_mode<L, S>(a0), use1 = uses_mode<L, S>(a0 + 1);
+    if constexpr (use0 || use1) {
+        constexpr int k0 = scale_kind<L>(a0), k1 = scale_kind<L>(a0 + 1);
+        constexpr bool mixed = use0 && use1 && k0 != k1;
+        constexpr int kind = use0 ? k0 : k1;
+        float g0, g1;
+        if constexpr (mixed) {
+            box_muller(wa, wb, 1.0f, g0, g1);
+            g0 *= k0 ? scale_j : scale;
+            g1 *= k1 ? scale_j : scale;
+        } else {
+            box_muller(wa, wb, kind ? scale_j : scale, g0, g1);
+        }
+        if constexpr (use0) g[a0] = g0;
+        if constexpr (use1) g[a0 + 1] = g1;
+    }
+}
+
+// Fill g[a] with the Gaussian of mode a, times its scale, for every mode
+// species S uses: counter (site, step, S, a/4), lane a mod 4.  The momentum
+// modes (species 0 only) are scaled by scale_j, the others by scale.  Only the
+// needed Philox blocks and Box-Muller pairs are evaluated (decided at compile
+// time).
 template <class L, int S>
 __device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uint32_t k0, uint32_t k1,
-                                               float (&g)[L::Q])
+                                               float scale_j, float scale, float (&g)[L::Q])
 {
     static_for<(L::Q + 3) / 4>([&](auto sc) {
         constexpr int slot = decltype(sc)::value;
-        constexpr bool u0 = uses_mode<L, S>(4 * slot), u1 = uses_mode<L, S>(4 * slot + 1);
-        constexpr bool u2 = uses_mode<L, S>(4 * slot + 2), u3 = uses_mode<L, S>(4 * slot + 3);
-        if constexpr (u0 || u1 || u2 || u3) {
+        constexpr bool any = uses_mode<L, S>(4 * slot) || uses_mode<L, S>(4 * slot + 1) ||
+                             uses_mode<L, S>(4 * slot + 2) || uses_mode<L, S>(4 * slot + 3);
+        if constexpr (any) {
             const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)slot), k0, k1);
-            if constexpr (u0 || u1) {
-                float g0, g1;
-                box_muller(x.x, x.y, g0, g1);
-                if constexpr (u0) g[4 * slot] = g0;
-                if constexpr (u1) g[4 * slot + 1] = g1;
-            }
-            if constexpr (u2 || u3) {
-                float g2, g3;
-                box_muller(x.z, x.w, g2, g3);
-                if constexpr (u2) g[4 * slot + 2] = g2;
-                if constexpr (u3) g[4 * slot + 3] = g3;
-            }
+            gaussian_pair<L, S, 4 * slot>(x.x, x.y, scale_j, scale, g);
+            gaussian_pair<L, S, 4 * slot + 2>(x.z, x.w, scale_j, scale, g);
         }
     });
 }
