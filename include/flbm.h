@@ -64,14 +64,22 @@ typedef enum {
     FLBM_STORE_BF16 = 2  /* stored as bfloat16 deviations from w_i * rho0^s; collided in float */
 } flbm_storage;
 
-/* How flbm_step runs one update (option FLBM_OPT_SCHEDULE).  Both compute the
- * same update; results agree to rounding (each schedule is deterministic). */
+/* How flbm_step runs one update (option FLBM_OPT_SCHEDULE).  All compute the
+ * same update and each is deterministic; the two-kernel and overlap schedules
+ * give bitwise identical results, the fused one agrees to rounding. */
 typedef enum {
-    FLBM_SCHEDULE_FUSED = 0,      /* one persistent launch per step; density and collision work items
-                                     ordered so the populations read for the densities are reused from
-                                     L2 by the collision (one HBM pass each way).  Slower on GB300 while
-                                     the collision is instruction-bound */
-    FLBM_SCHEDULE_TWO_KERNELS = 1 /* default: a density kernel, then the collide kernel */
+    FLBM_SCHEDULE_FUSED = 0,       /* one persistent launch per step; density and collision work items
+                                      ordered so the populations read for the densities are reused from
+                                      L2 by the collision (one HBM pass each way).  Slower on GB300 while
+                                      the collision is instruction-bound */
+    FLBM_SCHEDULE_TWO_KERNELS = 1, /* a density kernel over the box, then the collide kernel */
+    FLBM_SCHEDULE_OVERLAP = 2      /* the box cut into FLBM_OPT_SLABS slabs along its last axis (z;
+                                      y for D2Q9): the collide kernel runs slab by slab on the
+                                      context's stream while the next step's density kernel runs, on a
+                                      second stream of higher priority, on every slab whose neighbours
+                                      have been collided, so the memory-bound density pass overlaps the
+                                      instruction-bound collision.  Ordered by CUDA events only.  Boxes
+                                      with fewer than 3 planes (rows) run the two-kernel schedule */
 } flbm_schedule;
 
 /* Option keys for flbm_set_option. */
@@ -114,6 +122,8 @@ enum {
                                     the work in flight; else an integer >= 2 (results are identical) */
     FLBM_OPT_GRAPH_STEPS = 15,   /* batches: steps per CUDA graph replayed by flbm_step (0 = launch each
                                     step directly); default 16 */
+    FLBM_OPT_SLABS = 16,         /* overlap schedule: number of slabs, 3 .. 256 (at most the number of
+                                    planes, or rows for D2Q9); default 8 */
     FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
 };
@@ -175,8 +185,10 @@ flbm_status flbm_sync(flbm_ctx *ctx);
 /* Accumulated device time of the work flbm_step launched while
  * FLBM_OPT_KERNEL_TIMING was on, in milliseconds: ms[0] the density kernel
  * (two-kernel schedule) or the counter reset (fused schedule), ms[1] the
- * collide kernel or the fused step kernel; launches[k] the number of steps
- * timed.  Either array may be NULL.  Synchronising. */
+ * collide kernel or the fused step kernel; under the overlap schedule the sums
+ * of the density and of the collide slab launches (which overlap in time).
+ * launches[k] is the number of steps timed.  Either array may be NULL.
+ * Synchronising. */
 flbm_status flbm_kernel_times(flbm_ctx *ctx, double ms[2], int64_t launches[2]);
 
 /* Steps taken since flbm_init (or the restored checkpoint's count). */

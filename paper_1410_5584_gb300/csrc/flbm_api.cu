@@ -1,6 +1,7 @@
 // flbm_api.cu -- the C-ABI of include/flbm.h: context, argument checks, buffer
 // ownership, the step loop, observables, checkpoints and error reporting.
 // Every entry point catches its own failures and returns an flbm_status.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -61,6 +62,9 @@ StepParams make_params(const flbm_ctx *c)
     p.ny = c->ny;
     p.nz = c->nz;
     p.N = (int)c->N;
+    p.y0 = p.z0 = 0;
+    p.yn = c->ny;
+    p.zn = c->nz;
     p.G = (float)c->G;
     const double mu = 3.0 * c->kT; // k_B T / c_s^2
     const double lb_d = c->lam[0][1];
@@ -217,16 +221,13 @@ flbm_status drain_timing(flbm_ctx *c)
 {
     if (c->ev_used == 0) return FLBM_OK;
     FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    // events come in triples: before density, between the kernels, after collide
-    for (size_t k = 0; k + 2 < c->ev_used; k += 3) {
-        float a = 0.0f, b = 0.0f;
-        FLBM_CUDA(c, cudaEventElapsedTime(&a, c->ev_pool[k], c->ev_pool[k + 1]), "cudaEventElapsedTime");
-        FLBM_CUDA(c, cudaEventElapsedTime(&b, c->ev_pool[k + 1], c->ev_pool[k + 2]), "cudaEventElapsedTime");
-        c->kernel_ms[0] += a;
-        c->kernel_ms[1] += b;
-        c->kernel_launches[0]++;
-        c->kernel_launches[1]++;
+    if (c->stream_d) FLBM_CUDA(c, cudaStreamSynchronize(c->stream_d), "cudaStreamSynchronize");
+    for (const auto &m : c->marks) {
+        float ms = 0.0f;
+        FLBM_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[m.start], c->ev_pool[m.end]), "cudaEventElapsedTime");
+        c->kernel_ms[m.kernel] += ms;
     }
+    c->marks.clear();
     c->ev_used = 0;
     return FLBM_OK;
 }
@@ -241,6 +242,40 @@ flbm_status next_event(flbm_ctx *c, cudaEvent_t *ev)
     *ev = c->ev_pool[c->ev_used++];
     return FLBM_OK;
 }
+
+// Event-timing bracket around one launch on stream st (a no-op unless the
+// kernel_timing option is on): begin() records the start event, end() the end
+// event and the mark that drain_timing() turns into milliseconds.
+struct TimedLaunch {
+    flbm_ctx *c;
+    cudaStream_t st;
+    int kernel;
+    size_t start = 0;
+    flbm_status begin()
+    {
+        if (!c->timing) return FLBM_OK;
+        if (c->ev_used + 2 > 3 * 4096) {
+            flbm_status s = drain_timing(c);
+            if (s != FLBM_OK) return s;
+        }
+        cudaEvent_t e;
+        flbm_status s = next_event(c, &e);
+        if (s != FLBM_OK) return s;
+        start = c->ev_used - 1;
+        FLBM_CUDA(c, cudaEventRecord(e, st), "cudaEventRecord");
+        return FLBM_OK;
+    }
+    flbm_status end()
+    {
+        if (!c->timing) return FLBM_OK;
+        cudaEvent_t e;
+        flbm_status s = next_event(c, &e);
+        if (s != FLBM_OK) return s;
+        FLBM_CUDA(c, cudaEventRecord(e, st), "cudaEventRecord");
+        c->marks.push_back({start, c->ev_used - 1, kernel});
+        return FLBM_OK;
+    }
+};
 
 flbm_status density_now(flbm_ctx *c, const StepParams &p)
 {
@@ -394,9 +429,14 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
             c->sf_axis = (int)v;
         }
     } else if (key == FLBM_OPT_SCHEDULE) {
-        if (v != (double)FLBM_SCHEDULE_FUSED && v != (double)FLBM_SCHEDULE_TWO_KERNELS)
-            return fail(c, FLBM_EINVAL, "schedule must be 0 (fused) or 1 (two kernels)");
+        if (v != (double)FLBM_SCHEDULE_FUSED && v != (double)FLBM_SCHEDULE_TWO_KERNELS &&
+            v != (double)FLBM_SCHEDULE_OVERLAP)
+            return fail(c, FLBM_EINVAL, "schedule must be 0 (fused), 1 (two kernels) or 2 (overlap)");
         c->schedule = (int)v;
+    } else if (key == FLBM_OPT_SLABS) {
+        if (!(v >= 3.0 && v <= 256.0) || v != (double)(int)v)
+            return fail(c, FLBM_EINVAL, "slabs must be an integer in [3, 256]");
+        c->slabs = (int)v;
     } else if (key == FLBM_OPT_WAIT_LIMIT_MS) {
         if (!(v >= 1.0 && v <= 60000.0)) return fail(c, FLBM_EINVAL, "wait limit must lie in [1, 60000] ms");
         c->wait_limit_ms = v;
@@ -511,45 +551,153 @@ flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
     return FLBM_OK;
 }
 
+// One slab of the overlap schedule: planes (rows for D2Q9) [j n / K, (j + 1) n / K).
+StepParams slab_params(const flbm_ctx *c, StepParams p, int j, int K)
+{
+    const int n = c->lat == FLBM_D2Q9 ? c->ny : c->nz;
+    const int lo = (int)((int64_t)j * n / K), hi = (int)((int64_t)(j + 1) * n / K);
+    if (c->lat == FLBM_D2Q9) {
+        p.y0 = lo;
+        p.yn = hi - lo;
+    } else {
+        p.z0 = lo;
+        p.zn = hi - lo;
+    }
+    return p;
+}
+
+int overlap_slabs(const flbm_ctx *c)
+{
+    const int n = c->lat == FLBM_D2Q9 ? c->ny : c->nz;
+    return std::min(c->slabs, n);
+}
+
+flbm_status ensure_overlap(flbm_ctx *c, int K)
+{
+    if (!c->stream_d) {
+        int least = 0, greatest = 0;
+        FLBM_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+        FLBM_CUDA(c, cudaStreamCreateWithPriority(&c->stream_d, cudaStreamNonBlocking, greatest),
+                  "cudaStreamCreateWithPriority");
+    }
+    while ((int)c->ev_dep.size() < 2 * K) {
+        cudaEvent_t e;
+        FLBM_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        c->ev_dep.push_back(e);
+    }
+    return FLBM_OK;
+}
+
+// n steps of the overlap schedule.  With the AA layout every array slot belongs
+// to the read/write set of exactly one site, so launches over disjoint slabs
+// never touch the same slot, and the orderings that matter are:
+//  - the density of slab j for step t+1 reads the sets of slab j's sites, which
+//    the collisions of slabs j-1, j, j+1 at step t filled (streaming moves one
+//    plane at most);
+//  - the collision of slab j at step t+1 reads the densities of slabs j-1, j,
+//    j+1 (the force stencil) and overwrites slab j's sets, after their density
+//    pass read them;
+//  - a density launch overwrites rho of its slab only after the step-t
+//    collisions that read it (slabs j-1, j, j+1) are done.
+// The collisions run in slab order on the context's stream, starting at slab 0
+// or K/2 on alternate steps so that the two density slabs that wait for the
+// last collision of a step are far from the first collisions of the next; the
+// densities run on the second stream, each after the collision that completes
+// its inputs.  The first step's densities are one launch over the box.
+flbm_status step_overlap(flbm_ctx *c, int64_t n, StepParams p)
+{
+    const int K = overlap_slabs(c);
+    flbm_status st = ensure_overlap(c, K);
+    if (st != FLBM_OK) return st;
+    cudaEvent_t *evC = c->ev_dep.data(), *evD = c->ev_dep.data() + K;
+    auto density = [&](cudaStream_t s, const StepParams &q, int parity) -> flbm_status {
+        TimedLaunch tl{c, s, 0};
+        if ((st = tl.begin()) != FLBM_OK) return st;
+        cudaError_t e = launch_density(c->lat, c->storage, parity, q, c->pop, c->rho, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
+        return tl.end();
+    };
+    auto collide = [&](const StepParams &q) -> flbm_status {
+        TimedLaunch tl{c, c->stream, 1};
+        if ((st = tl.begin()) != FLBM_OK) return st;
+        cudaError_t e = launch_collide(c->lat, c->storage, c->parity, q, c->pop, c->rho, c->d_status, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
+        return tl.end();
+    };
+    if ((st = density(c->stream, p, c->parity)) != FLBM_OK) return st;
+    for (int64_t t = 0; t < n; t++) {
+        p.step = (uint32_t)c->step;
+        const int s0 = (c->step & 1) ? K / 2 : 0;
+        const bool more = t + 1 < n;
+        for (int q = 0; q < K; q++) {
+            const int j = (s0 + q) % K;
+            if (t > 0)
+                for (int d = -1; d <= 1; d++)
+                    FLBM_CUDA(c, cudaStreamWaitEvent(c->stream, evD[(j + d + K) % K], 0), "cudaStreamWaitEvent");
+            if ((st = collide(slab_params(c, p, j, K))) != FLBM_OK) return st;
+            FLBM_CUDA(c, cudaEventRecord(evC[j], c->stream), "cudaEventRecord");
+            if (!more) continue;
+            // densities of step t+1 whose three input slabs are now collided
+            int ready[3], nready = 0;
+            if (q >= 2) ready[nready++] = (s0 + q - 1) % K;
+            if (q == K - 1) {
+                ready[nready++] = (s0 + K - 1) % K;
+                ready[nready++] = s0;
+            }
+            if (nready == 0) continue;
+            FLBM_CUDA(c, cudaStreamWaitEvent(c->stream_d, evC[j], 0), "cudaStreamWaitEvent");
+            for (int r = 0; r < nready; r++) {
+                if ((st = density(c->stream_d, slab_params(c, p, ready[r], K), c->parity ^ 1)) != FLBM_OK) return st;
+                FLBM_CUDA(c, cudaEventRecord(evD[ready[r]], c->stream_d), "cudaEventRecord");
+            }
+        }
+        if (c->timing) {
+            c->kernel_launches[0]++;
+            c->kernel_launches[1]++;
+        }
+        c->step++;
+        c->parity ^= 1;
+    }
+    return FLBM_OK;
+}
+
 flbm_status flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
     if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
     if (is_batch(c)) return batch_step(c, n);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
+    if (n == 0) return FLBM_OK;
+    StepParams p = make_params(c);
+    if (c->schedule == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
     if (c->schedule == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
         if (st != FLBM_OK) return st;
     }
-    StepParams p = make_params(c);
     for (int64_t t = 0; t < n; t++) {
         p.step = (uint32_t)c->step;
-        cudaEvent_t ev[3];
-        if (c->timing) {
-            // bound the number of outstanding events
-            if (c->ev_used + 3 > 3 * 4096) {
-                flbm_status st = drain_timing(c);
-                if (st != FLBM_OK) return st;
-            }
-            for (int k = 0; k < 3; k++) {
-                flbm_status st = next_event(c, &ev[k]);
-                if (st != FLBM_OK) return st;
-            }
-            FLBM_CUDA(c, cudaEventRecord(ev[0], c->stream), "cudaEventRecord");
-        }
+        flbm_status st;
+        TimedLaunch t0{c, c->stream, 0}, t1{c, c->stream, 1};
+        if ((st = t0.begin()) != FLBM_OK) return st;
         if (c->schedule == FLBM_SCHEDULE_FUSED) {
-            if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
+            if ((st = t0.end()) != FLBM_OK) return st;
+            if ((st = t1.begin()) != FLBM_OK) return st;
             cudaError_t e = launch_step_fused(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status,
                                               c->d_pipe, c->wait_limit_ms, c->test_stall, c->pipe_lag, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "fused step kernel launch");
         } else {
             cudaError_t e = launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
-            if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[1], c->stream), "cudaEventRecord");
+            if ((st = t0.end()) != FLBM_OK) return st;
+            if ((st = t1.begin()) != FLBM_OK) return st;
             e = launch_collide(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
         }
-        if (c->timing) FLBM_CUDA(c, cudaEventRecord(ev[2], c->stream), "cudaEventRecord");
+        if ((st = t1.end()) != FLBM_OK) return st;
+        if (c->timing) {
+            c->kernel_launches[0]++;
+            c->kernel_launches[1]++;
+        }
         c->step++;
         c->parity ^= 1;
     }
@@ -854,6 +1002,8 @@ void flbm_destroy(flbm_ctx *c)
     free_sf(c);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_dep) cudaEventDestroy(e);
+    if (c->stream_d) cudaStreamDestroy(c->stream_d);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -48,9 +48,18 @@ struct flbm_ctx {
     int64_t sf_count = 0;
     float *h_stage = nullptr;     // pinned staging, 2 * N floats
     // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
+    struct TimingMark {
+        size_t start, end; // ev_pool indices
+        int kernel;        // 0 density (or counter reset), 1 collide (or fused step)
+    };
     bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;      // recorded in order: start, after density, after collide, ...
+    std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
+    std::vector<TimingMark> marks;
+    // overlap schedule
+    int slabs = 8;
+    cudaStream_t stream_d = nullptr;  // density stream, higher priority than the context's
+    std::vector<cudaEvent_t> ev_dep;  // [0, K): after collide slab j; [K, 2K): after density slab j
     double kernel_ms[2] = {0.0, 0.0};
     int64_t kernel_launches[2] = {0, 0};
     // stream

@@ -16,6 +16,8 @@ constexpr int kMaxQ = 19;
 struct StepParams {
     int nx, ny, nz;
     int N;                     // nx * ny * nz  (< 2^31)
+    int y0, z0, yn, zn;        // rows [y0, y0 + yn) and planes [z0, z0 + zn) a density or collide
+                               // launch covers (one slab of the overlap schedule); 0, 0, ny, nz = all
     float G;                   // inter-species coupling, Eq. FORCESTRUCTURE
     float lam_d;               // common momentum rate lambdabar_d of both species
     float hlam_d;              // 1 - lambdabar_d / 2  (Eq. forcerenorm)

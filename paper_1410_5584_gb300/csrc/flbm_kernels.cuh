@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
-    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+    const Nbr nb = make_nbr(p, x, blockIdx.y + p.y0, blockIdx.z + p.z0);
     rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
 }
 
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S:
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
-    const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+    const Nbr nb = make_nbr(p, x, blockIdx.y + p.y0, blockIdx.z + p.z0);
     site_collide<L, S, PARITY, false>(p, pop, rho, status, nb, [] { return true; });
 }
 
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
 
 
 inline dim3 site_block(int nx) { return dim3(nx >= 128 ? 128 : ((nx + 31) / 32) * 32); }
-inline dim3 site_grid(const StepParams &p, dim3 blk) { return dim3((p.nx + blk.x - 1) / blk.x, p.ny, p.nz); }
+inline dim3 site_grid(const StepParams &p, dim3 blk) { return dim3((p.nx + blk.x - 1) / blk.x, p.yn, p.zn); }
 
 } // namespace kern
 

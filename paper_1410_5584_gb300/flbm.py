@@ -35,14 +35,15 @@ OPT_WAIT_LIMIT_MS = 12
 OPT_TEST_STALL = 13
 OPT_PIPE_LAG = 14
 OPT_GRAPH_STEPS = 15
-SCHEDULE = {"fused": 0, "two_kernels": 1}
+OPT_SLABS = 16
+SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
 OPT_LAMBDA_MODE = 1000
 OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
                 "rho0_a": OPT_RHO0_A, "rho0_b": OPT_RHO0_B, "noise_rho": OPT_NOISE_RHO,
                 "force_velocity": OPT_FORCE_VELOCITY, "sf_axis": OPT_SF_AXIS,
                 "kernel_timing": OPT_KERNEL_TIMING, "schedule": OPT_SCHEDULE,
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
-                "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS}
+                "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS}
 
 
 class RepParams(ctypes.Structure):

@@ -325,6 +325,37 @@ def test_fused_and_two_kernel_schedules_agree(lat, shape):
     assert _rel(out[0], out[2]) <= 5e-7
 
 
+@pytest.mark.parametrize("lat,shape,slabs", [(D2Q9, (1, 2, 37), 8), (D2Q9, (1, 3, 130), 8), (D2Q9, (1, 17, 33), 8),
+                                             (D2Q9, (1, 64, 64), 5), (D3Q19, (2, 5, 7), 8), (D3Q19, (3, 4, 9), 3),
+                                             (D3Q19, (9, 6, 140), 8), (D3Q19, (16, 8, 8), 16)])
+def test_overlap_schedule_matches_two_kernels_bitwise(lat, shape, slabs):
+    """The slab-overlapped schedule runs the same per-site arithmetic as the
+    two-kernel schedule, so after any number of steps, split into any calls
+    (both streaming parities, both starting slabs of the alternation), the
+    states agree bit for bit; boxes with fewer than 3 planes fall back to the
+    two-kernel schedule.  Kernel timing does not change the result."""
+    nz, ny, nx = shape
+    f0 = _random_state(lat, shape)
+    ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
+    ref.set_option("schedule", F.SCHEDULE["two_kernels"])
+    ref.set_populations(f0, step=3)
+    ref.step(8)
+    want = ref.get_populations()
+    for timing in (0, 1):
+        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
+        g.set_option("schedule", F.SCHEDULE["overlap"])
+        g.set_option("slabs", slabs)
+        g.set_option("kernel_timing", timing)
+        g.set_populations(f0, step=3)
+        for n in (1, 2, 5):
+            g.step(n)
+        assert g.step_count == 11
+        assert np.array_equal(g.get_populations(), want)
+        if timing:
+            ms, cnt = g.kernel_times()
+            assert cnt["collide"] == 8 and ms["collide"] > 0 and ms["density"] > 0
+
+
 def test_fused_step_wait_timeout_is_reported():
     """Failure detection without a GPU fault: a dependency wait that can never
     be satisfied gives up after its time limit, the kernel returns, the host
