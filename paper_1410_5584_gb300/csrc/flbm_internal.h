@@ -53,12 +53,14 @@ constexpr unsigned kStatusTimeout = 2u;   // a bounded device-side wait gave up
 // small non-conserved moments free of cancellation; the 16-bit formats store
 // the deviation itself.
 // ---------------------------------------------------------------------------
-// encode() forms the stored word of a deviation and decode() the deviation a
-// load of that word gives; both round once, without contraction, so a kernel
-// can know exactly what the next step will load.
+// encode() forms the stored word of a deviation, encode_w() that of the
+// deviation w y, and decode() the deviation a load of a word gives; each is a
+// fixed sequence of roundings without contraction, so a kernel can know
+// exactly what the next step will load.
 struct StoreF32 {
     using T = float;
     __device__ __forceinline__ static T encode(float dev, float base) { return __fadd_rn(base, dev); }
+    __device__ __forceinline__ static T encode_w(float w, float y, float base) { return __fmaf_rn(w, y, base); }
     __device__ __forceinline__ static float decode(T v, float base) { return __fsub_rn(v, base); }
     __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
     {
@@ -73,6 +75,7 @@ struct StoreF32 {
 struct StoreF16 {
     using T = __half;
     __device__ __forceinline__ static T encode(float dev, float) { return __float2half_rn(dev); }
+    __device__ __forceinline__ static T encode_w(float w, float y, float) { return __float2half_rn(__fmul_rn(w, y)); }
     __device__ __forceinline__ static float decode(T v, float) { return __half2float(v); }
     __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
     {
@@ -87,6 +90,10 @@ struct StoreF16 {
 struct StoreBF16 {
     using T = __nv_bfloat16;
     __device__ __forceinline__ static T encode(float dev, float) { return __float2bfloat16_rn(dev); }
+    __device__ __forceinline__ static T encode_w(float w, float y, float)
+    {
+        return __float2bfloat16_rn(__fmul_rn(w, y));
+    }
     __device__ __forceinline__ static float decode(T v, float) { return __bfloat162float(v); }
     __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
     {

@@ -225,7 +225,9 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
             if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
             mu[a] = t;
         });
-        Transform<L>::backward(mu, fo);
+        // delta*_i = w_i y_i with y_i = sum_a T_ai mu_a, the weight folded into the store
+        float y[Q];
+        Transform<L>::backward(mu, y);
         // Mass balance: the moving populations are encoded first and replaced by
         // the deviations their stored words will load as; the rest population
         // then takes m0 minus what they hold, so the rounding of their stores
@@ -233,8 +235,9 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
         typename S::T word[Q];
         static_for<Q - 1>([&](auto kc) {
             constexpr int i = decltype(kc)::value + 1;
-            const float base = (float)L::wd(i) * p.rho0[s];
-            word[i] = S::encode(fo[i], base);
+            constexpr float wi = (float)L::wd(i);
+            const float base = wi * p.rho0[s];
+            word[i] = S::encode_w(wi, y[i], base);
             fo[i] = S::decode(word[i], base);
         });
         word[0] = S::encode(Transform<L>::rest_closing_mass(fo, m[s][0]), (float)L::wd(0) * p.rho0[s]);

@@ -29,7 +29,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
     return x;
 }
 
-// Hardware approximations (PTX lg2/rsqrt/sin/cos .approx.ftz).  Every argument
+// Hardware approximations (PTX lg2/sqrt/sin/cos .approx.ftz).  Every argument
 // they get below is zero or a normal number, so flushing subnormals changes no
 // result and spares the subnormal handling of the non-ftz forms.
 __device__ __forceinline__ float lg2_hw(float x)
@@ -38,10 +38,10 @@ __device__ __forceinline__ float lg2_hw(float x)
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float rsqrt_hw(float x)
+__device__ __forceinline__ float sqrt_hw(float x)
 {
     float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ void sincos_hw(float x, float &s, float &c)
@@ -73,14 +73,11 @@ __device__ __forceinline__ float minus_two_log_unit_interval(float u1)
 // in (0, 1] and u2 = (b >> 8) 2^-24 in [0, 1), both exact in float.  The angle
 // is taken in [-pi, pi), where the hardware sine and cosine have an absolute
 // error of about 2^-21: reading b as signed and shifting arithmetically gives
-// u2 for u2 < 1/2 and u2 - 1 above (the same sine and cosine).  r = x rsqrt(x).
+// u2 for u2 < 1/2 and u2 - 1 above (the same sine and cosine).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float scale, float &g0, float &g1)
 {
     const float u1 = fmaf((float)(a >> 8), 0x1.0p-24f, 0x1.0p-24f); // ((a >> 8) + 1) 2^-24, exact
-    const float r2 = minus_two_log_unit_interval(u1);
-    // the tiny offset makes r2 = 0 (u1 = 1) give 0 instead of 0 * inf and is far
-    // below the rounding of the smallest nonzero r2 (~1.2e-7)
-    const float r = scale * (r2 * rsqrt_hw(r2 + 1e-30f));
+    const float r = scale * sqrt_hw(minus_two_log_unit_interval(u1)); // u1 = 1 gives r = 0
     // 2 pi t with t = (signed b >> 8) 2^-24: one rounding, as 2 pi 2^-24 is the
     // float 2 pi times a power of two
     const float ang = (float)((int32_t)b >> 8) * (6.28318530717958647692f * 0x1.0p-24f);

@@ -1,6 +1,7 @@
 // flbm_transform.cuh -- moment transforms m_a = sum_i T_ai f_i and
-// f_i = w_i sum_a T_ai mu_a (mu_a = m_a / N_a, Eq. modes-discrete) factored over
-// opposite-velocity pairs.
+// y_i = sum_a T_ai mu_a (mu_a = m_a / N_a, so that f_i = w_i y_i, Eq.
+// modes-discrete) factored over opposite-velocity pairs.  The weights w_i are
+// left to the caller, which folds them into the store.
 //
 // Rows of T are either even or odd in c, so with S_p = f_i + f_opp(i) and
 // D_p = f_i - f_opp(i) the even moments need only the pair sums and the odd
@@ -36,7 +37,7 @@ template <> struct Transform<D2Q9> {
         m[7] = (R)-1 * D2 + (R)2 * (D3 + D4);      // (3|c|^2 - 4) c_y
         m[8] = (R)2 * f[0] + (R)-4 * A + (R)8 * E; // 9|c|^4 - 15|c|^2 + 2
     }
-    // f_i = w_i sum_a T_ai mu_a
+    // y_i = sum_a T_ai mu_a
     template <class R>
     __host__ __device__ __forceinline__ static constexpr void backward(const R (&u)[9], R (&f)[9])
     {
@@ -49,16 +50,15 @@ template <> struct Transform<D2Q9> {
         const R O1 = u[1] - u[6], O2 = u[2] - u[7];
         const R px = u[1] + (R)2 * u[6], py = u[2] + (R)2 * u[7];
         const R O3 = px + py, O4 = py - px;
-        constexpr R w0 = (R)(4.0 / 9.0), wa = (R)(1.0 / 9.0), wd = (R)(1.0 / 36.0);
-        f[0] = w0 * (u[0] + (R)-2 * u[3] + (R)2 * u[8]);
-        f[1] = wa * (E1 + O1);
-        f[3] = wa * (E1 - O1);
-        f[2] = wa * (E2 + O2);
-        f[4] = wa * (E2 - O2);
-        f[5] = wd * (E3 + O3);
-        f[7] = wd * (E3 - O3);
-        f[6] = wd * (E4 + O4);
-        f[8] = wd * (E4 - O4);
+        f[0] = u[0] + (R)-2 * u[3] + (R)2 * u[8];
+        f[1] = E1 + O1;
+        f[3] = E1 - O1;
+        f[2] = E2 + O2;
+        f[4] = E2 - O2;
+        f[5] = E3 + O3;
+        f[7] = E3 - O3;
+        f[6] = E4 + O4;
+        f[8] = E4 - O4;
     }
     // Rest population that makes the density expression of forward() return m0:
     // the float weights do not sum to 1 exactly, so w_i m0 spread over the
@@ -144,26 +144,25 @@ template <> struct Transform<D3Q19> {
         const R O7 = Xe - Ze - (u[13] + u[15]);
         const R O8 = Ye + Ze + (u[14] - u[15]);
         const R O9 = Ye - Ze + (u[14] + u[15]);
-        constexpr R w0 = (R)(1.0 / 3.0), wa = (R)(1.0 / 18.0), we = (R)(1.0 / 36.0);
-        f[0] = w0 * (u[0] - u[4] + u[16]);
-        f[1] = wa * (E1 + O1);
-        f[2] = wa * (E1 - O1);
-        f[3] = wa * (E2 + O2);
-        f[4] = wa * (E2 - O2);
-        f[5] = wa * (E3 + O3);
-        f[6] = wa * (E3 - O3);
-        f[7] = we * (E4 + O4);
-        f[8] = we * (E4 - O4);
-        f[9] = we * (E5 + O5);
-        f[10] = we * (E5 - O5);
-        f[11] = we * (E6 + O6);
-        f[12] = we * (E6 - O6);
-        f[13] = we * (E7 + O7);
-        f[14] = we * (E7 - O7);
-        f[15] = we * (E8 + O8);
-        f[16] = we * (E8 - O8);
-        f[17] = we * (E9 + O9);
-        f[18] = we * (E9 - O9);
+        f[0] = u[0] - u[4] + u[16];
+        f[1] = E1 + O1;
+        f[2] = E1 - O1;
+        f[3] = E2 + O2;
+        f[4] = E2 - O2;
+        f[5] = E3 + O3;
+        f[6] = E3 - O3;
+        f[7] = E4 + O4;
+        f[8] = E4 - O4;
+        f[9] = E5 + O5;
+        f[10] = E5 - O5;
+        f[11] = E6 + O6;
+        f[12] = E6 - O6;
+        f[13] = E7 + O7;
+        f[14] = E7 - O7;
+        f[15] = E8 + O8;
+        f[16] = E8 - O8;
+        f[17] = E9 + O9;
+        f[18] = E9 - O9;
     }
     // Rest population that makes the density expression of forward() return m0
     // (see the D2Q9 version).
@@ -177,9 +176,8 @@ template <> struct Transform<D3Q19> {
 };
 
 // Compile-time proof: on every unit vector the factored forward transform
-// returns the column T_.i and the factored backward transform (with the weights
-// divided out) returns the row T_a. (all values are small integers, exact in
-// double).
+// returns the column T_.i and the factored backward transform the row T_a.
+// (all values are small integers, exact in double).
 template <class L> constexpr bool factored_transforms_match()
 {
     constexpr int Q = L::Q;
@@ -190,11 +188,8 @@ template <class L> constexpr bool factored_transforms_match()
         for (int a = 0; a < Q; a++)
             if (out[a] != (double)L::T(a, k)) return false;
         Transform<L>::backward(e, out);
-        for (int i = 0; i < Q; i++) {
-            const double want = L::wd(i) * L::T(k, i);
-            const double diff = out[i] - want;
-            if (diff > 1e-15 || diff < -1e-15) return false;
-        }
+        for (int i = 0; i < Q; i++)
+            if (out[i] != (double)L::T(k, i)) return false;
     }
     return true;
 }
