@@ -52,30 +52,54 @@ __device__ __forceinline__ Nbr make_nbr(const StepParams &p, int x, int y, int z
 
 template <class L> __device__ __forceinline__ constexpr float wf(int i) { return (float)L::wd(i); }
 
+// slot and site of the population f_i(site) that the current step reads
+template <class L, int PARITY, int I> __device__ __forceinline__ constexpr int read_slot()
+{
+    return PARITY == 0 ? I : L::opp(I);
+}
+template <class L, int PARITY, int I> __device__ __forceinline__ unsigned read_site(const Nbr &nb)
+{
+    if constexpr (PARITY == 0) return (unsigned)nb.at(0, 0, 0);
+    else return (unsigned)nb.at(-L::cx(I), -L::cy(I), -L::cz(I));
+}
+// slot and site where the post-collision f*_i(site) is written
+template <class L, int PARITY, int I> __device__ __forceinline__ constexpr int write_slot()
+{
+    return PARITY == 0 ? L::opp(I) : I;
+}
+template <class L, int PARITY, int I> __device__ __forceinline__ unsigned write_site(const Nbr &nb)
+{
+    if constexpr (PARITY == 0) return (unsigned)nb.at(0, 0, 0);
+    else return (unsigned)nb.at(L::cx(I), L::cy(I), L::cz(I));
+}
 // array index of the population f_i(site) that the current step reads
 template <class L, int PARITY, int I>
 __device__ __forceinline__ size_t read_index(const Nbr &nb, size_t NN, int s)
 {
-    if constexpr (PARITY == 0) return (size_t)(s * L::Q + I) * NN + nb.at(0, 0, 0);
-    else return (size_t)(s * L::Q + L::opp(I)) * NN + nb.at(-L::cx(I), -L::cy(I), -L::cz(I));
+    return (size_t)(s * L::Q + read_slot<L, PARITY, I>()) * NN + read_site<L, PARITY, I>(nb);
 }
 
-// array index where the post-collision f*_i(site) is written
-template <class L, int PARITY, int I>
-__device__ __forceinline__ size_t write_index(const Nbr &nb, size_t NN, int s)
-{
-    if constexpr (PARITY == 0) return (size_t)(s * L::Q + L::opp(I)) * NN + nb.at(0, 0, 0);
-    else return (size_t)(s * L::Q + I) * NN + nb.at(L::cx(I), L::cy(I), L::cz(I));
-}
+// Where the slot planes of the population array start: slot j of species s is
+// the plane pop + (s Q + j) N.  FlatPlanes computes it in the kernel;
+// PlaneTable carries the 2Q plane pointers in the kernel's parameter space, so
+// an access is a uniform pointer plus a 32-bit site offset.
+template <class T> struct FlatPlanes {
+    T *pop;
+    size_t N;
+    template <class L> __device__ __forceinline__ T *plane(int s, int j) const { return pop + (size_t)(s * L::Q + j) * N; }
+};
+template <class T> struct PlaneTable {
+    T *ptr[2 * kMaxQ];
+    template <class L> __device__ __forceinline__ T *plane(int s, int j) const { return ptr[s * L::Q + j]; }
+};
 
 // ---------------------------------------------------------------------------
 // density pass
 // ---------------------------------------------------------------------------
 // densities (rho_A, rho_B) of one site from its pre-collision populations
-template <class L, class S, int PARITY>
-__device__ __forceinline__ float2 site_density(const StepParams &p, const typename S::T *__restrict__ pop, const Nbr &nb)
+template <class L, class S, int PARITY, class P>
+__device__ __forceinline__ float2 site_density(const StepParams &p, const P &planes, const Nbr &nb)
 {
-    const size_t NN = (size_t)p.N;
     float r[2];
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
@@ -83,7 +107,8 @@ __device__ __forceinline__ float2 site_density(const StepParams &p, const typena
         static_for<L::Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr float wi = (float)L::wd(i);
-            d[i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+            d[i] = S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()), read_site<L, PARITY, i>(nb),
+                               wi * p.rho0[s]);
         });
         // the collide step computes its own density with this same expression
         Transform<L>::forward(d, m);
@@ -93,13 +118,13 @@ __device__ __forceinline__ float2 site_density(const StepParams &p, const typena
 }
 
 template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(128) k_density(const StepParams p, const typename S::T *__restrict__ pop,
+__global__ void __launch_bounds__(128) k_density(const StepParams p, const PlaneTable<const typename S::T> planes,
                                                  float2 *__restrict__ rho)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const Nbr nb = make_nbr(p, x, blockIdx.y + p.y0, blockIdx.z + p.z0);
-    rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
+    rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, planes, nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -110,13 +135,12 @@ __global__ void __launch_bounds__(128) k_density(const StepParams p, const typen
 // earlier in the same kernel launch by other thread blocks.  STORE = false
 // computes without writing (an idle lane of a partial warp).  after_loads()
 // runs once the population loads are issued; returning false abandons the site.
-template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, class Hook = bool (*)()>
-__device__ __forceinline__ void site_collide(const StepParams &p, typename S::T *__restrict__ pop,
+template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, class P, class Hook = bool (*)()>
+__device__ __forceinline__ void site_collide(const StepParams &p, const P &planes,
                                              const float2 *__restrict__ rho, unsigned *__restrict__ status,
                                              const Nbr &nb, Hook &&after_loads)
 {
     constexpr int Q = L::Q, D = L::D;
-    const size_t NN = (size_t)p.N;
     const int site = nb.at(0, 0, 0);
 
     // 1. moments of both species (Eq. modes-discrete), density rho = rhobar.
@@ -129,7 +153,8 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr float wi = (float)L::wd(i);
-                d[s][i] = S::load_dev(pop, read_index<L, PARITY, i>(nb, NN, s), wi * p.rho0[s]);
+                d[s][i] = S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()),
+                                      read_site<L, PARITY, i>(nb), wi * p.rho0[s]);
             });
         });
         if (!after_loads()) return;
@@ -243,19 +268,19 @@ __device__ __forceinline__ void site_collide(const StepParams &p, typename S::T 
         word[0] = S::encode(Transform<L>::rest_closing_mass(fo, m[s][0]), (float)L::wd(0) * p.rho0[s]);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            if (STORE) pop[write_index<L, PARITY, i>(nb, NN, s)] = word[i];
+            if (STORE) planes.template plane<L>(s, write_slot<L, PARITY, i>())[write_site<L, PARITY, i>(nb)] = word[i];
         });
     });
 }
 
 template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(128) k_collide(const StepParams p, typename S::T *__restrict__ pop,
+__global__ void __launch_bounds__(128) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
                                                  const float2 *__restrict__ rho, unsigned *__restrict__ status)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
     const Nbr nb = make_nbr(p, x, blockIdx.y + p.y0, blockIdx.z + p.z0);
-    site_collide<L, S, PARITY, false>(p, pop, rho, status, nb, [] { return true; });
+    site_collide<L, S, PARITY, false>(p, planes, rho, status, nb, [] { return true; });
 }
 
 // ---------------------------------------------------------------------------
@@ -346,6 +371,7 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
                                                     float2 *__restrict__ rho, unsigned *__restrict__ status,
                                                     const PipeArgs a)
 {
+    const FlatPlanes<typename S::T> planes{pop, (size_t)p.N};
     const int lane = threadIdx.x & 31;
     const int W = (int)((gridDim.x * blockDim.x) >> 5);
     for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < a.total; item += W) {
@@ -379,7 +405,7 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
             const int x = (tile - (L::D == 3 ? y * a.tiles_per_row : 0)) * 32 + lane;
             if (x < p.nx) {
                 const Nbr nb = make_nbr(p, x, y, z);
-                rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, pop, nb);
+                rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, planes, nb);
             }
             __syncwarp();
             if (cslice < 0 && lane == 0) { // no C part to carry the signal: publish now
@@ -424,9 +450,9 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
             };
             bool alive = true;
             if (active) {
-                site_collide<L, S, PARITY, true, true>(p, pop, rho, status, nb, [&] { return alive = after_loads(); });
+                site_collide<L, S, PARITY, true, true>(p, planes, rho, status, nb, [&] { return alive = after_loads(); });
             } else {
-                site_collide<L, S, PARITY, true, false>(p, pop, rho, status, nb, [&] { return alive = after_loads(); });
+                site_collide<L, S, PARITY, true, false>(p, planes, rho, status, nb, [&] { return alive = after_loads(); });
             }
             if (!__shfl_sync(0xffffffffu, alive ? 1 : 0, 0)) return; // a wait gave up: the host sees the status bit
         }
@@ -472,7 +498,7 @@ __global__ void __launch_bounds__(128) k_density_batch(const RepInfo *__restrict
     if (site >= sp.N) return;
     const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
     const Nbr nb = make_nbr(sp, x, y, z);
-    rho[rho_off + site] = site_density<L, S, PARITY>(sp, pop + pop_off, nb);
+    rho[rho_off + site] = site_density<L, S, PARITY>(sp, FlatPlanes<const typename S::T>{pop + pop_off, (size_t)sp.N}, nb);
 }
 
 template <class L, class S, int PARITY>
@@ -489,7 +515,8 @@ __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict
     if (site >= sp.N) return;
     const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
     const Nbr nb = make_nbr(sp, x, y, z);
-    site_collide<L, S, PARITY, false>(sp, pop + pop_off, rho + rho_off, status, nb, [] { return true; });
+    site_collide<L, S, PARITY, false>(sp, FlatPlanes<typename S::T>{pop + pop_off, (size_t)sp.N}, rho + rho_off, status, nb,
+                                      [] { return true; });
 }
 
 // ---------------------------------------------------------------------------
@@ -632,14 +659,23 @@ inline dim3 site_grid(const StepParams &p, dim3 blk) { return dim3((p.nx + blk.x
 
 } // namespace kern
 
+namespace kern {
+template <class T> PlaneTable<T> plane_table(T *pop, int Q, int N)
+{
+    PlaneTable<T> t{};
+    for (int k = 0; k < 2 * Q; k++) t.ptr[k] = pop + (size_t)k * (size_t)N;
+    return t;
+}
+} // namespace kern
+
 template <class L, class S>
 cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *pop, float *rho, cudaStream_t st)
 {
     const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
-    auto *ptr = static_cast<const typename S::T *>(pop);
+    const auto planes = kern::plane_table(static_cast<const typename S::T *>(pop), L::Q, p.N);
     auto *r2 = reinterpret_cast<float2 *>(rho);
-    if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, ptr, r2);
-    else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, ptr, r2);
+    if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
+    else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, planes, r2);
     return cudaGetLastError();
 }
 
@@ -648,10 +684,10 @@ cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, co
                                   cudaStream_t st)
 {
     const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
-    auto *ptr = static_cast<typename S::T *>(pop);
+    const auto planes = kern::plane_table(static_cast<typename S::T *>(pop), L::Q, p.N);
     auto *r2 = reinterpret_cast<const float2 *>(rho);
-    if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, ptr, r2, status);
-    else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, ptr, r2, status);
+    if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, planes, r2, status);
+    else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, planes, r2, status);
     return cudaGetLastError();
 }
 
