@@ -124,6 +124,11 @@ enum {
                                     step directly); default 16 */
     FLBM_OPT_SLABS = 16,         /* overlap schedule: number of slabs, 3 .. 256 (at most the number of
                                     planes, or rows for D2Q9); default 8 */
+    FLBM_OPT_BLOCK_X = 17,       /* thread block of the density and collide kernels: sites along x,
+                                    32, 64 or 128 (default; capped at nx rounded up to 32) */
+    FLBM_OPT_BLOCK_Y = 18,       /* ... and rows along y, 1 (default), 2 or 4; x * y <= 128.
+                                    The shape changes speed only, never results.  Set one of the
+                                    two first when the other would exceed the product limit */
     FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
 };
@@ -151,6 +156,12 @@ flbm_status flbm_create(flbm_lattice lat, int nx, int ny, int nz, double tau_a, 
 /* Set one option (keys above).  FLBM_EINVAL for an unknown key or a value out of
  * range; FLBM_ESTATE for FLBM_OPT_STORAGE after the buffers exist. */
 flbm_status flbm_set_option(flbm_ctx *ctx, int key, double value);
+
+/* Read one option's current value into *value (FLBM_OPT_GRAPH_STEPS on batches
+ * only; FLBM_OPT_LAMBDA_MODE + 100 s + a for the rate of one mode).
+ * FLBM_EINVAL for an unknown key, FLBM_EUNSUPPORTED for a key the context
+ * does not have. */
+flbm_status flbm_get_option(const flbm_ctx *ctx, int key, double *value);
 
 /* Run the context's work on `stream` (a cudaStream_t, NULL = the library's own
  * non-blocking stream).  The caller keeps ownership of the stream and must keep
@@ -310,6 +321,30 @@ flbm_status flbm_batch_replica(flbm_ctx *batch, int rep, flbm_ctx **view);
 
 /* Number of replicas and total sites of a batch (either pointer may be NULL). */
 flbm_status flbm_batch_size(const flbm_ctx *batch, int *nrep, int64_t *sites);
+
+/*
+ * Launch-settings autotuner (no counterpart in the paper, which gives no
+ * implementation).  Times candidate settings on this context's own state and
+ * keeps the fastest:
+ *   single box: the two-kernel schedule and the overlap schedule with 4 or 8
+ *               slabs, each with thread blocks of 128x1, 64x2 and 32x4 sites;
+ *   batch:      FLBM_OPT_GRAPH_STEPS of 0, 4, 16 and 64.
+ * Every candidate computes bitwise the same update, so tuning changes speed,
+ * never results.  Each candidate runs 2 untimed and `steps` timed steps
+ * (1 .. 100000) from the same saved state: the populations are copied aside on
+ * the device (one population-array of scratch, freed before returning; a batch
+ * uses a host checkpoint image), and the state, step counter and parity are
+ * put back after every candidate, so the call leaves the simulation where it
+ * was.  The three fastest are timed twice and the least time wins.
+ * cache_path: NULL, or a JSON file of earlier choices keyed by GPU name, SM
+ * count and problem (lattice, storage, box or batch size); a stored choice is
+ * applied without timing, a new one is added to the file (written to a
+ * temporary name, then renamed).  Read the result with flbm_get_option.
+ * Synchronising.  Errors: FLBM_EINVAL for steps out of range or an unreadable
+ * or unwritable cache, FLBM_ESTATE before flbm_init or on a replica view,
+ * FLBM_ENOMEM without room for the scratch copy, and any error of flbm_step.
+ */
+flbm_status flbm_autotune(flbm_ctx *ctx, int steps, const char *cache_path);
 
 /* One-line reason of the last error on this context ("" if none).  The string
  * is owned by the context.  Never NULL (ctx may be NULL). */

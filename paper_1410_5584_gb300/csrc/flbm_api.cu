@@ -65,6 +65,8 @@ StepParams make_params(const flbm_ctx *c)
     p.y0 = p.z0 = 0;
     p.yn = c->ny;
     p.zn = c->nz;
+    p.block_x = c->block_x;
+    p.block_y = c->block_y;
     p.G = (float)c->G;
     const double mu = 3.0 * c->kT; // k_B T / c_s^2
     const double lb_d = c->lam[0][1];
@@ -433,6 +435,15 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
             v != (double)FLBM_SCHEDULE_OVERLAP)
             return fail(c, FLBM_EINVAL, "schedule must be 0 (fused), 1 (two kernels) or 2 (overlap)");
         c->schedule = (int)v;
+    } else if (key == FLBM_OPT_BLOCK_X || key == FLBM_OPT_BLOCK_Y) {
+        const int bx = key == FLBM_OPT_BLOCK_X ? (int)v : c->block_x;
+        const int by = key == FLBM_OPT_BLOCK_Y ? (int)v : c->block_y;
+        if (v != (double)(int)v || (key == FLBM_OPT_BLOCK_X && bx != 32 && bx != 64 && bx != 128) ||
+            (key == FLBM_OPT_BLOCK_Y && by != 1 && by != 2 && by != 4) || bx * by > kSiteBlockMax)
+            return fail(c, FLBM_EINVAL, "block shape must be x in {32,64,128}, y in {1,2,4}, x*y <= %d",
+                        kSiteBlockMax);
+        c->block_x = bx;
+        c->block_y = by;
     } else if (key == FLBM_OPT_SLABS) {
         if (!(v >= 3.0 && v <= 256.0) || v != (double)(int)v)
             return fail(c, FLBM_EINVAL, "slabs must be an integer in [3, 256]");
@@ -461,6 +472,40 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
         c->lam[s][a] = v;
     } else {
         return fail(c, FLBM_EINVAL, "unknown option key %d", key);
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
+{
+    if (!c || !value) return FLBM_EINVAL;
+    switch (key) {
+    case FLBM_OPT_STORAGE: *value = c->storage; break;
+    case FLBM_OPT_LAMBDA_D: *value = c->lam[0][1]; break;
+    case FLBM_OPT_SDF: *value = c->sdf; break;
+    case FLBM_OPT_RHO0_A: *value = c->rho0[0]; break;
+    case FLBM_OPT_RHO0_B: *value = c->rho0[1]; break;
+    case FLBM_OPT_NOISE_RHO: *value = c->noise_ref; break;
+    case FLBM_OPT_FORCE_VELOCITY: *value = c->force_velocity; break;
+    case FLBM_OPT_SF_AXIS: *value = c->sf_axis; break;
+    case FLBM_OPT_KERNEL_TIMING: *value = c->timing ? 1.0 : 0.0; break;
+    case FLBM_OPT_SCHEDULE: *value = c->schedule; break;
+    case FLBM_OPT_WAIT_LIMIT_MS: *value = c->wait_limit_ms; break;
+    case FLBM_OPT_TEST_STALL: *value = c->test_stall; break;
+    case FLBM_OPT_PIPE_LAG: *value = c->pipe_lag; break;
+    case FLBM_OPT_GRAPH_STEPS:
+        if (!is_batch(c)) return FLBM_EUNSUPPORTED;
+        *value = batch_graph_steps(c);
+        break;
+    case FLBM_OPT_SLABS: *value = c->slabs; break;
+    case FLBM_OPT_BLOCK_X: *value = c->block_x; break;
+    case FLBM_OPT_BLOCK_Y: *value = c->block_y; break;
+    default: {
+        const int s = (key - FLBM_OPT_LAMBDA_MODE) / 100, a = (key - FLBM_OPT_LAMBDA_MODE) % 100;
+        if (key < FLBM_OPT_LAMBDA_MODE || key >= FLBM_OPT_LAMBDA_MODE + 200 || a <= c->D || a >= c->Q)
+            return FLBM_EINVAL;
+        *value = c->lam[s][a];
+    }
     }
     return FLBM_OK;
 }

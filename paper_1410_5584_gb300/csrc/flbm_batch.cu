@@ -180,7 +180,8 @@ flbm_status batch_set_option(flbm_ctx *c, int key, double v)
         return FLBM_OK;
     }
     if (key == FLBM_OPT_SF_AXIS || key == FLBM_OPT_KERNEL_TIMING || key == FLBM_OPT_SCHEDULE ||
-        key == FLBM_OPT_PIPE_LAG || key == FLBM_OPT_WAIT_LIMIT_MS || key == FLBM_OPT_TEST_STALL) {
+        key == FLBM_OPT_PIPE_LAG || key == FLBM_OPT_WAIT_LIMIT_MS || key == FLBM_OPT_TEST_STALL ||
+        key == FLBM_OPT_SLABS || key == FLBM_OPT_BLOCK_X || key == FLBM_OPT_BLOCK_Y) {
         if (key == FLBM_OPT_SF_AXIS) {
             for (flbm_ctx *vw : b->views) {
                 const flbm_status st = on_view(b, vw, [&](flbm_ctx *x) { return flbm_set_option(x, key, v); });
@@ -201,6 +202,8 @@ flbm_status batch_set_option(flbm_ctx *c, int key, double v)
     b->reps_dirty = true;
     return FLBM_OK;
 }
+
+int batch_graph_steps(const flbm_ctx *c) { return c->batch->graph_steps; }
 
 flbm_status batch_set_stream(flbm_ctx *c, void *stream)
 {

@@ -56,6 +56,8 @@ struct flbm_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<TimingMark> marks;
+    // launch shape of the density and collide kernels
+    int block_x = 128, block_y = 1;
     // overlap schedule
     int slabs = 8;
     cudaStream_t stream_d = nullptr;  // density stream, higher priority than the context's
@@ -104,6 +106,7 @@ flbm_status batch_set_populations(flbm_ctx *c, const double *f, int64_t step);
 flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes);
 flbm_status batch_restore(flbm_ctx *c, const void *buf, size_t bytes);
 void batch_destroy(flbm_ctx *c);
+int batch_graph_steps(const flbm_ctx *c);
 bool view_call_allowed(const flbm_ctx *c); // false for mutating calls on a replica view
 inline bool is_batch(const flbm_ctx *c) { return c->batch && !c->is_view; }
 } // namespace flbm

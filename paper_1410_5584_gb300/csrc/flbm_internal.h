@@ -11,6 +11,7 @@
 namespace flbm {
 
 constexpr int kMaxQ = 19;
+constexpr int kSiteBlockMax = 128; // largest thread block of the density and collide kernels
 
 // Everything one step kernel needs, passed by value (kernel parameter space).
 struct StepParams {
@@ -18,6 +19,7 @@ struct StepParams {
     int N;                     // nx * ny * nz  (< 2^31)
     int y0, z0, yn, zn;        // rows [y0, y0 + yn) and planes [z0, z0 + zn) a density or collide
                                // launch covers (one slab of the overlap schedule); 0, 0, ny, nz = all
+    int block_x, block_y;      // thread-block shape of the density and collide launches (x by y sites)
     float G;                   // inter-species coupling, Eq. FORCESTRUCTURE
     float lam_d;               // common momentum rate lambdabar_d of both species
     float hlam_d;              // 1 - lambdabar_d / 2  (Eq. forcerenorm)

@@ -118,12 +118,14 @@ __device__ __forceinline__ float2 site_density(const StepParams &p, const P &pla
 }
 
 template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(128) k_density(const StepParams p, const PlaneTable<const typename S::T> planes,
-                                                 float2 *__restrict__ rho)
+__global__ void __launch_bounds__(kSiteBlockMax) k_density(const StepParams p,
+                                                           const PlaneTable<const typename S::T> planes,
+                                                           float2 *__restrict__ rho)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const Nbr nb = make_nbr(p, x, blockIdx.y + p.y0, blockIdx.z + p.z0);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.yn) return;
+    const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
     rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, planes, nb);
 }
 
@@ -274,12 +276,14 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
 }
 
 template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(128) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
-                                                 const float2 *__restrict__ rho, unsigned *__restrict__ status)
+__global__ void __launch_bounds__(kSiteBlockMax) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
+                                                           const float2 *__restrict__ rho,
+                                                           unsigned *__restrict__ status)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const Nbr nb = make_nbr(p, x, blockIdx.y + p.y0, blockIdx.z + p.z0);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.yn) return;
+    const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
     site_collide<L, S, PARITY, false>(p, planes, rho, status, nb, [] { return true; });
 }
 
@@ -654,8 +658,17 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
 }
 
 
-inline dim3 site_block(int nx) { return dim3(nx >= 128 ? 128 : ((nx + 31) / 32) * 32); }
-inline dim3 site_grid(const StepParams &p, dim3 blk) { return dim3((p.nx + blk.x - 1) / blk.x, p.yn, p.zn); }
+// thread block of the density and collide launches: block_x sites along x (at
+// most nx rounded up to a warp) by block_y rows
+inline dim3 site_block(const StepParams &p)
+{
+    const int wx = ((p.nx + 31) / 32) * 32;
+    return dim3(p.block_x < wx ? p.block_x : wx, p.block_y);
+}
+inline dim3 site_grid(const StepParams &p, dim3 blk)
+{
+    return dim3((p.nx + blk.x - 1) / blk.x, (p.yn + blk.y - 1) / blk.y, p.zn);
+}
 
 } // namespace kern
 
@@ -671,7 +684,7 @@ template <class T> PlaneTable<T> plane_table(T *pop, int Q, int N)
 template <class L, class S>
 cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *pop, float *rho, cudaStream_t st)
 {
-    const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
+    const dim3 b = kern::site_block(p), g = kern::site_grid(p, b);
     const auto planes = kern::plane_table(static_cast<const typename S::T *>(pop), L::Q, p.N);
     auto *r2 = reinterpret_cast<float2 *>(rho);
     if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
@@ -683,7 +696,7 @@ template <class L, class S>
 cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, const float *rho, unsigned *status,
                                   cudaStream_t st)
 {
-    const dim3 b = kern::site_block(p.nx), g = kern::site_grid(p, b);
+    const dim3 b = kern::site_block(p), g = kern::site_grid(p, b);
     const auto planes = kern::plane_table(static_cast<typename S::T *>(pop), L::Q, p.N);
     auto *r2 = reinterpret_cast<const float2 *>(rho);
     if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, planes, r2, status);

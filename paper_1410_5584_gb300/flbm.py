@@ -36,6 +36,8 @@ OPT_TEST_STALL = 13
 OPT_PIPE_LAG = 14
 OPT_GRAPH_STEPS = 15
 OPT_SLABS = 16
+OPT_BLOCK_X = 17
+OPT_BLOCK_Y = 18
 SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
 OPT_LAMBDA_MODE = 1000
 OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
@@ -43,7 +45,8 @@ OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF
                 "force_velocity": OPT_FORCE_VELOCITY, "sf_axis": OPT_SF_AXIS,
                 "kernel_timing": OPT_KERNEL_TIMING, "schedule": OPT_SCHEDULE,
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
-                "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS}
+                "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS,
+                "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y}
 
 
 class RepParams(ctypes.Structure):
@@ -85,6 +88,8 @@ def lib():
         sig = {
             "flbm_create": (i32, [i32, i32, i32, i32, dbl, dbl, dbl, dbl, u64, ctypes.POINTER(vp)]),
             "flbm_set_option": (i32, [vp, i32, dbl]),
+            "flbm_get_option": (i32, [vp, i32, dp]),
+            "flbm_autotune": (i32, [vp, i32, ctypes.c_char_p]),
             "flbm_set_stream": (i32, [vp, vp]),
             "flbm_buffer_bytes": (i32, [vp, szp, szp]),
             "flbm_attach_buffers": (i32, [vp, vp, sz, vp, sz]),
@@ -155,6 +160,22 @@ class _Context:
         if isinstance(key, str):
             key = OPTION_NAMES[key]
         check(self._h, lib().flbm_set_option(self._h, int(key), float(value)))
+
+    def get_option(self, key):
+        if isinstance(key, str):
+            key = OPTION_NAMES[key]
+        v = ctypes.c_double()
+        check(self._h, lib().flbm_get_option(self._h, int(key), ctypes.byref(v)))
+        return v.value
+
+    def autotune(self, steps=20, cache=None):
+        """flbm_autotune: time the candidate launch settings on the current state
+        (left unchanged), keep the fastest, and return them; `cache` is an
+        optional JSON file of earlier choices."""
+        path = None if cache is None else os.fsencode(cache)
+        check(self._h, lib().flbm_autotune(self._h, int(steps), path))
+        keys = ("graph_steps",) if isinstance(self, Batch) else ("schedule", "slabs", "block_x", "block_y")
+        return {k: int(self.get_option(k)) for k in keys}
 
     def sf_sample(self):
         check(self._h, lib().flbm_sf_sample(self._h))

@@ -83,6 +83,31 @@ def test_options_are_validated(lib):
         lib.flbm_destroy(h)
 
 
+def test_launch_settings_are_validated_and_read_back(lib):
+    """Block shape, schedule and slab options (host logic only; no GPU)."""
+    h = F.flbm_create(F.D3Q19, 16, 16, 16, 1.0, 1.0, 1e-4, 0.0, 1)
+    v = ctypes.c_double()
+    try:
+        for key, bad in ((F.OPT_BLOCK_X, 48), (F.OPT_BLOCK_X, 256), (F.OPT_BLOCK_Y, 3), (F.OPT_BLOCK_Y, 8),
+                         (F.OPT_SCHEDULE, 3), (F.OPT_SLABS, 2), (F.OPT_SLABS, 4.5)):
+            assert lib.flbm_set_option(h, key, bad) == F.EINVAL, (key, bad)
+        assert lib.flbm_set_option(h, F.OPT_BLOCK_X, 32) == F.OK
+        assert lib.flbm_set_option(h, F.OPT_BLOCK_Y, 4) == F.OK
+        assert lib.flbm_set_option(h, F.OPT_BLOCK_X, 64) == F.EINVAL  # 64 x 4 > 128 sites
+        assert lib.flbm_set_option(h, F.OPT_SCHEDULE, F.SCHEDULE["overlap"]) == F.OK
+        assert lib.flbm_set_option(h, F.OPT_SLABS, 5) == F.OK
+        for key, want in ((F.OPT_BLOCK_X, 32), (F.OPT_BLOCK_Y, 4), (F.OPT_SCHEDULE, 2), (F.OPT_SLABS, 5),
+                          (F.OPT_LAMBDA_MODE + 100 + 7, 1.0)):
+            assert lib.flbm_get_option(h, key, ctypes.byref(v)) == F.OK and v.value == want, key
+        assert lib.flbm_get_option(h, F.OPT_GRAPH_STEPS, ctypes.byref(v)) == F.EUNSUPPORTED  # batches only
+        assert lib.flbm_get_option(h, 12345, ctypes.byref(v)) == F.EINVAL
+        # the autotuner checks its arguments and the state before touching the GPU
+        assert lib.flbm_autotune(h, 0, None) == F.EINVAL
+        assert lib.flbm_autotune(h, 5, None) == F.ESTATE  # before init
+    finally:
+        lib.flbm_destroy(h)
+
+
 def test_null_context_is_safe(lib):
     assert lib.flbm_last_error(None) == b""
     assert lib.flbm_step(None, 1) == F.EINVAL
