@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage and batching forms")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
     return ap.parse_args()
 
 
@@ -79,9 +80,18 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the files that define the step kernels (device code and the structures they
+# take); the host runtime around them can change without touching the kernels
+KERNEL_SOURCES = ("flbm_internal.h", "flbm_kernels.cuh", "flbm_lattice.cuh", "flbm_launch.h", "flbm_noise.cuh",
+                  "flbm_transform.cuh", "inst_*.cu")
+
+
 def sources_digest():
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1410_5584_gb300", "csrc", "*"))):
+    files = set()
+    for pat in KERNEL_SOURCES:
+        files.update(glob.glob(os.path.join(ROOT, "paper_1410_5584_gb300", "csrc", pat)))
+    for p in sorted(files):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())
@@ -222,8 +232,9 @@ def batched_form(seed, steps, device, nrep=64):
     """The batching form: nrep independent D2Q9 replicas, n_x and n_y drawn from
     {64, 128, 256, 512}, kT log-uniform in [1e-6, 1e-4], G rho0 uniform in
     [0, 0.9], distinct Philox keys, rho = 1, tau = 1; one density and one
-    collide launch per step for all replicas, replayed from CUDA graphs.
-    Compared with the same replicas stepped as separate contexts."""
+    collide launch per step for all replicas, replayed from CUDA graphs whose
+    length the autotuner picks.  Compared with the same replicas stepped as
+    separate contexts, 5000 steps each (the batching workload's length)."""
     import torch
 
     from paper_1410_5584_gb300 import Batch, Lattice
@@ -242,9 +253,10 @@ def batched_form(seed, steps, device, nrep=64):
         torch.cuda.synchronize(device)
         return s0.elapsed_time(s1) / 1e3
 
-    b = Batch(0, reps, device=device, graph_steps=16)
+    b = Batch(0, reps, device=device)
     b.init()
-    b.step(32)
+    graph_steps = b.autotune(steps=200)["graph_steps"]
+    b.step(2 * max(graph_steps, 1))
     b.sync()
     t_batch = timed(lambda: b.step(steps), b.stream)
     b.sync()
@@ -260,7 +272,7 @@ def batched_form(seed, steps, device, nrep=64):
         g.sync()
         g.close()
     return {"value": sites * steps / t_batch / 1e6, "unit": "MLUPS", "replicas": nrep, "sites": sites,
-            "steps": steps, "graph_steps": 16, "per_replica_launches_mlups": sites * steps / t_sep / 1e6,
+            "steps": steps, "graph_steps": graph_steps, "per_replica_launches_mlups": sites * steps / t_sep / 1e6,
             "speedup_vs_per_replica_launches": t_sep / t_batch}
 
 
@@ -362,6 +374,8 @@ def run_ours(args, wl):
     lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
                   storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"])
     lat.init()
+    # launch settings from the autotuner (untimed; the state is left as it was)
+    launch = None if args.no_autotune else lat.autotune(steps=20)
     lat.step(args.warmup)
     lat.sync()
 
@@ -429,7 +443,8 @@ def run_ours(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "lattice": "D3Q19" if wl["lattice"] == 1 else "D2Q9",
                    "nx": nx, "ny": ny, "nz": nz, "storage": wl["storage"], "replicas": world,
-                   "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2"},
+                   "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2",
+                   "launch": launch},
         "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},
@@ -441,7 +456,7 @@ def run_ours(args, wl):
     }
     if not args.no_forms and wl["storage"] == "f32":
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
-        line["forms"]["batched"] = batched_form(args.seed, max(200, args.steps // 2), device)
+        line["forms"]["batched"] = batched_form(args.seed, 5000, device)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
     print(json.dumps(line), flush=True)
