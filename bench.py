@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage and batching forms")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
+    ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap"], default=None,
+                    help="force one step schedule (implies --no-autotune)")
     return ap.parse_args()
 
 
@@ -375,7 +377,13 @@ def run_ours(args, wl):
                   storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"])
     lat.init()
     # launch settings from the autotuner (untimed; the state is left as it was)
-    launch = None if args.no_autotune else lat.autotune(steps=20)
+    launch = None
+    if args.schedule:
+        from paper_1410_5584_gb300 import flbm as F
+        lat.set_option("schedule", F.SCHEDULE[args.schedule])
+        launch = {"schedule": F.SCHEDULE[args.schedule]}
+    elif not args.no_autotune:
+        launch = lat.autotune(steps=20)
     lat.step(args.warmup)
     lat.sync()
 
