@@ -135,6 +135,34 @@ def gaussian(seed: int, site: int, step: int, species: int, mode: int) -> float:
     return lib().orc_gaussian(seed, site, step, species, mode)
 
 
+def structure_factor_full(rho_a, rho_b):
+    """Structure factors of one snapshot at every lattice wavevector (the
+    quantities of Eq. str-bin-hom, Sec. IV A, off the axes too).  With
+    rho_hat(k) = sum_r (rho(r) - <rho>) exp(-i k.r) and k_alpha = 2 pi m_alpha /
+    n_alpha: S_aa = |rho_hat_a|^2 / N, S_ab = Re(rho_hat_a conj rho_hat_b) / N,
+    S_bb = |rho_hat_b|^2 / N, arrays shaped like the fields ([z][y][x], m_alpha
+    in numpy FFT order; k = 0 is 0).  numpy's FFT is the library step of the
+    definition."""
+    a = np.asarray(rho_a, dtype=np.float64)
+    b = np.asarray(rho_b, dtype=np.float64)
+    n = a.size
+    fa = np.fft.fftn(a - a.mean())
+    fb = np.fft.fftn(b - b.mean())
+    return np.abs(fa) ** 2 / n, (fa * np.conj(fb)).real / n, np.abs(fb) ** 2 / n
+
+
+def structure_functions(s_aa, s_ab, s_bb, rho0_a, rho0_b):
+    """(S_tt, S_CC, S_tC) of Eq. structurefunctions from the density structure
+    factors: total density rho_t = rho + rho' and concentration C = rho / rho_t
+    linearised about (rho0_a, rho0_b), delta rho_t = delta rho + delta rho',
+    delta C = (rho0_b delta rho - rho0_a delta rho') / rho_t0^2."""
+    rt = rho0_a + rho0_b
+    s_tt = s_aa + 2.0 * s_ab + s_bb
+    s_cc = (rho0_b ** 2 * s_aa - 2.0 * rho0_a * rho0_b * s_ab + rho0_a ** 2 * s_bb) / rt ** 4
+    s_tc = (rho0_b * s_aa + (rho0_b - rho0_a) * s_ab - rho0_a * s_bb) / rt ** 2
+    return s_tt, s_cc, s_tc
+
+
 class Oracle:
     """Handle on one oracle lattice (two species, periodic box)."""
 
