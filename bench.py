@@ -462,6 +462,21 @@ def run_ours(args, wl):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    if not args.no_forms:
+        # one full-wavevector structure-factor snapshot on the bench box (observables,
+        # packing, three axes of line FFTs, FP64 accumulation), event-timed
+        lat.sfk_sample()
+        lat.sync()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(lat.stream)
+        for _ in range(5):
+            lat.sfk_sample()
+        s1.record(lat.stream)
+        lat.sync()
+        sfk_ms = s0.elapsed_time(s1) / 5
+        lat.sfk_reset()
+        line["sk_full"] = {"ms_per_snapshot": sfk_ms, "sites": sites,
+                           "note": "S_aa, S_ab, S_bb at every wavevector: observables, float line FFTs, FP64 sums"}
     if not args.no_forms and wl["storage"] == "f32":
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
         line["forms"]["batched"] = batched_form(args.seed, 5000, device)

@@ -232,6 +232,41 @@ flbm_status flbm_structure_factor(flbm_ctx *ctx, int axis, int nk, double *S_aa,
 /* Clear the structure-factor accumulators. */
 flbm_status flbm_sf_reset(flbm_ctx *ctx);
 
+/*
+ * Structure factors at every lattice wavevector (Sec. IV A: the quantities of
+ * Eq. str-bin-hom off the axes too) and the structure functions of Eq.
+ * structurefunctions.
+ *
+ * flbm_sfk_sample adds one snapshot: with delta rho^s = rho^s - <rho^s> and
+ * rho_hat^s(k) = sum_r delta rho^s(r) exp(-i k.r), k_a = 2 pi m_a / n_a, it
+ * accumulates |rho_hat_A|^2, Re(rho_hat_A conj rho_hat_B), |rho_hat_B|^2 in
+ * FP64.  The transform runs in float on the fluctuation fields (relative
+ * error ~1e-6, far below the statistical error of any estimate).  Device
+ * memory: N (3 doubles + 1 complex float), allocated on the first call.
+ * Axis lengths up to 4096 when a power of two, up to 3072 otherwise
+ * (FLBM_EUNSUPPORTED beyond).  Asynchronous on the context's stream.
+ *
+ * flbm_sfk copies the ensemble means S_aa, S_ab, S_bb = <...> / N into three
+ * caller-owned host arrays of N doubles each (any may be NULL), laid out
+ * [m_z][m_y][m_x] like the sites (m_a >= n_a / 2 stands for the negative
+ * wavevector m_a - n_a; k = 0 is 0 up to rounding).  *nsamples (may be NULL)
+ * receives the snapshot count.  Synchronising; FLBM_ESTATE before a sample.
+ *
+ * flbm_sfk_functions forms, from the same means, the structure factors of the
+ * total density rho_t = rho + rho' and the concentration C = rho / rho_t
+ * linearised about (rho0_a, rho0_b):  S_tt = S_aa + 2 S_ab + S_bb,
+ * S_CC = (rho0_b^2 S_aa - 2 rho0_a rho0_b S_ab + rho0_a^2 S_bb) / rho_t0^4,
+ * S_tC = (rho0_b S_aa + (rho0_b - rho0_a) S_ab - rho0_a S_bb) / rho_t0^2.
+ * Same layout and rules; FLBM_EINVAL for non-positive reference densities.
+ *
+ * flbm_sfk_reset clears the accumulators and frees their memory.
+ */
+flbm_status flbm_sfk_sample(flbm_ctx *ctx);
+flbm_status flbm_sfk(flbm_ctx *ctx, double *S_aa, double *S_ab, double *S_bb, int64_t *nsamples);
+flbm_status flbm_sfk_functions(flbm_ctx *ctx, double rho0_a, double rho0_b, double *S_tt, double *S_cc,
+                               double *S_tc);
+flbm_status flbm_sfk_reset(flbm_ctx *ctx);
+
 /* Copy the populations, natural layout [2][Q][N], to / from host doubles
  * (2 * Q * N values).  get: synchronising; set: converts to the storage format
  * and sets the step counter to `step`. */

@@ -46,6 +46,12 @@ struct flbm_ctx {
     double *d_sf = nullptr;       // 4 * n_axis/2 accumulators
     double *d_profile = nullptr;  // (2 + D) * n_axis
     int64_t sf_count = 0;
+    // full-wavevector structure factors (flbm_sfk_*)
+    float2 *d_sfk_z = nullptr;         // N complex: packed fluctuation field, transformed in place
+    double *d_sfk_acc = nullptr;       // 3 N: sums of |A|^2, Re(A conj B), |B|^2
+    float2 *d_sfk_tw[3] = {nullptr, nullptr, nullptr}; // twiddles per axis
+    int sfk_tw_n[3] = {0, 0, 0};
+    int64_t sfk_count = 0;
     float *h_stage = nullptr;     // pinned staging, 2 * N floats
     // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
     struct TimingMark {
@@ -88,6 +94,8 @@ flbm_status ensure_stream(flbm_ctx *c);
 flbm_status ensure_status(flbm_ctx *c);
 flbm_status ensure_stage(flbm_ctx *c);
 flbm_status sync_and_check(flbm_ctx *c);
+flbm_status ensure_obs(flbm_ctx *c);
+flbm_status density_now(flbm_ctx *c, const StepParams &p);
 size_t pop_bytes_of(const flbm_ctx *c);
 size_t rho_bytes_of(const flbm_ctx *c);
 uint64_t fnv1a(const unsigned char *p, size_t n);
@@ -107,6 +115,7 @@ flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes);
 flbm_status batch_restore(flbm_ctx *c, const void *buf, size_t bytes);
 void batch_destroy(flbm_ctx *c);
 int batch_graph_steps(const flbm_ctx *c);
+void free_sfk(flbm_ctx *c); // flbm_sfk.cu
 bool view_call_allowed(const flbm_ctx *c); // false for mutating calls on a replica view
 inline bool is_batch(const flbm_ctx *c) { return c->batch && !c->is_view; }
 } // namespace flbm

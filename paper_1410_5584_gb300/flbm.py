@@ -102,6 +102,10 @@ def lib():
             "flbm_sf_sample": (i32, [vp]),
             "flbm_structure_factor": (i32, [vp, i32, i32, dp, dp, dp, dp, i64p]),
             "flbm_sf_reset": (i32, [vp]),
+            "flbm_sfk_sample": (i32, [vp]),
+            "flbm_sfk": (i32, [vp, dp, dp, dp, i64p]),
+            "flbm_sfk_functions": (i32, [vp, dbl, dbl, dp, dp, dp]),
+            "flbm_sfk_reset": (i32, [vp]),
             "flbm_get_populations": (i32, [vp, dp]),
             "flbm_set_populations": (i32, [vp, dp, i64]),
             "flbm_get_site_populations": (i32, [vp, i64p, i64, dp]),
@@ -179,6 +183,30 @@ class _Context:
 
     def sf_sample(self):
         check(self._h, lib().flbm_sf_sample(self._h))
+
+    def sfk_sample(self):
+        """flbm_sfk_sample: one snapshot of the structure factors at every wavevector."""
+        check(self._h, lib().flbm_sfk_sample(self._h))
+
+    def sfk_reset(self):
+        check(self._h, lib().flbm_sfk_reset(self._h))
+
+    def _sfk_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def sfk(self):
+        """(S_aa, S_ab, S_bb, nsamples): ensemble means at every wavevector,
+        arrays [m_z][m_y][m_x] (numpy FFT order)."""
+        out = [np.empty(self._sfk_shape()) for _ in range(3)]
+        n = ctypes.c_int64()
+        check(self._h, lib().flbm_sfk(self._h, *[_dp(o) for o in out], ctypes.byref(n)))
+        return (*out, n.value)
+
+    def sfk_functions(self, rho0_a, rho0_b):
+        """(S_tt, S_CC, S_tC) of Eq. structurefunctions about (rho0_a, rho0_b)."""
+        out = [np.empty(self._sfk_shape()) for _ in range(3)]
+        check(self._h, lib().flbm_sfk_functions(self._h, float(rho0_a), float(rho0_b), *[_dp(o) for o in out]))
+        return tuple(out)
 
     def sf_reset(self):
         check(self._h, lib().flbm_sf_reset(self._h))
