@@ -476,7 +476,7 @@ def run_ours(args, wl):
         sfk_ms = s0.elapsed_time(s1) / 5
         lat.sfk_reset()
         line["sk_full"] = {"ms_per_snapshot": sfk_ms, "sites": sites,
-                           "note": "S_aa, S_ab, S_bb at every wavevector: observables, float line FFTs, FP64 sums"}
+                           "note": "S_aa, S_ab, S_bb at every wavevector: fluctuation fields, float line FFTs, FP64 sums"}
     if not args.no_forms and wl["storage"] == "f32":
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
         line["forms"]["batched"] = batched_form(args.seed, 5000, device)

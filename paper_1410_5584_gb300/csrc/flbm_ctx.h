@@ -49,6 +49,7 @@ struct flbm_ctx {
     // full-wavevector structure factors (flbm_sfk_*)
     float2 *d_sfk_z = nullptr;         // N complex: packed fluctuation field, transformed in place
     double *d_sfk_acc = nullptr;       // 3 N: sums of |A|^2, Re(A conj B), |B|^2
+    double *d_sfk_mean = nullptr;      // the two fields' means of the current snapshot
     float2 *d_sfk_tw[3] = {nullptr, nullptr, nullptr}; // twiddles per axis
     int sfk_tw_n[3] = {0, 0, 0};
     int64_t sfk_count = 0;

@@ -37,6 +37,9 @@ template <class L, class S> struct InitF {
 template <class L, class S> struct GatherF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::gather(a...); }
 };
+template <class L, class S> struct SfkF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::sfk_fields(a...); }
+};
 template <class L, class S> struct ObsF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::observables(a...); }
 };
@@ -79,6 +82,12 @@ cudaError_t launch_gather_sites(int lat, int storage, int parity, const StepPara
                                 const int64_t *sites, int64_t nsites, double *out, cudaStream_t stream)
 {
     return dispatch<GatherF>(lat, storage, parity, p, pop, sites, nsites, out, stream);
+}
+
+cudaError_t launch_sfk_fields(int lat, int storage, int parity, const StepParams &p, const void *pop, float2 *z,
+                              double *partials, int *nblocks, cudaStream_t stream)
+{
+    return dispatch<SfkF>(lat, storage, parity, p, pop, z, partials, nblocks, stream);
 }
 
 cudaError_t launch_observables(int lat, int storage, int parity, const StepParams &p, const void *pop,

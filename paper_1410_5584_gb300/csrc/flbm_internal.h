@@ -151,6 +151,12 @@ cudaError_t launch_observables(int lat, int storage, int parity, const StepParam
                                const void *pop, const float *rho, double *rho_a, double *rho_b,
                                double *u, double *partials, int *nblocks, cudaStream_t stream);
 
+// Density fluctuation fields for the full-wavevector structure factor:
+// z[site] = (rho_A - rho0_A, rho_B - rho0_B) in float, per-block FP64 partial
+// sums [nblocks][2] into `partials`; the block count goes to *nblocks.
+cudaError_t launch_sfk_fields(int lat, int storage, int parity, const StepParams &p, const void *pop, float2 *z,
+                              double *partials, int *nblocks, cudaStream_t stream);
+
 // Fixed-order sum of [nblocks][5] partials into out[5].
 cudaError_t launch_sum_partials(const double *partials, int nblocks, double *out,
                                 cudaStream_t stream);

@@ -584,6 +584,41 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[NV])
     for (int k = 0; k < NV; k++) v[k] = sh[0][k];
 }
 
+// Density fluctuation fields for the full-wavevector structure factor:
+// z(site) = (sum_i delta_i^A, sum_i delta_i^B), each species' density minus its
+// reference rho0, summed in float as in the step kernels, plus per-block FP64
+// partial sums (fixed order) from which the means follow.
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(kObsBlock) k_sfk_fields(const StepParams p,
+                                                          const PlaneTable<const typename S::T> planes,
+                                                          float2 *__restrict__ z, double *__restrict__ partials)
+{
+    __shared__ double sh[kObsBlock][2];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    double tot[2] = {0.0, 0.0};
+    if (x < p.nx) {
+        const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
+        float sum[2] = {0.0f, 0.0f};
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<L::Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                sum[s] += S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()), read_site<L, PARITY, i>(nb),
+                                      (float)L::wd(i) * p.rho0[s]);
+            });
+        });
+        z[nb.at(0, 0, 0)] = make_float2(sum[0], sum[1]);
+        tot[0] = sum[0];
+        tot[1] = sum[1];
+    }
+    block_sum<2, kObsBlock>(tot, sh);
+    if (threadIdx.x == 0) {
+        const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+        partials[2 * b] = tot[0];
+        partials[2 * b + 1] = tot[1];
+    }
+}
+
 template <class L, class S, int PARITY>
 __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, const typename S::T *__restrict__ pop,
                                                            const float2 *__restrict__ rho, double *__restrict__ rho_a,
@@ -602,51 +637,54 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
         auto at = [&](int dx, int dy, int dz) { return (zs[dz + 1] * p.ny + ys[dy + 1]) * p.nx + xs[dx + 1]; };
         const size_t NN = (size_t)p.N;
         const int site = at(0, 0, 0);
-        double r[2], j[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, a[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        // per-site sums in float, as in the step kernels: the deviations are
+        // small, so their float sums are accurate to ~1e-7 of themselves, and
+        // rho = rho0 + sum is formed in double (the totals keep FP64
+        // precision; this GPU's FP64 rate is a small fraction of its FP32 rate)
+        float sum[2] = {0.0f, 0.0f}, j[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+        float a[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
         static_for<2>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            double sum = 0.0;
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 const size_t idx = PARITY == 0 ? (size_t)(s * Q + i) * NN + site
                                                : (size_t)(s * Q + L::opp(i)) * NN + at(-L::cx(i), -L::cy(i), -L::cz(i));
-                const double dv = (double)S::load_dev(pop, idx, (float)L::wd(i) * p.rho0[s]);
-                sum += dv;
+                const float dv = S::load_dev(pop, idx, (float)L::wd(i) * p.rho0[s]);
+                sum[s] += dv;
                 static_for<3>([&](auto dc) {
                     constexpr int d = decltype(dc)::value;
                     constexpr int cd = comp<L>(i, d);
-                    if constexpr (cd != 0) j[s][d] += cd * dv;
+                    if constexpr (cd != 0) j[s][d] += (float)cd * dv;
                 });
             });
-            r[s] = (double)p.rho0[s] + sum;
         });
         // force with the density field (the same values the step kernel uses)
         static_for<Q - 1>([&](auto kc) {
             constexpr int i = decltype(kc)::value + 1;
             const float2 rn = rho[at(L::cx(i), L::cy(i), L::cz(i))];
-            const double ra = rn.x, rb = rn.y;
             static_for<3>([&](auto dc) {
                 constexpr int d = decltype(dc)::value;
                 constexpr int cd = comp<L>(i, d);
                 if constexpr (cd != 0) {
-                    constexpr double cw = L::wd(i) * cd;
-                    a[0][d] += cw * rb;
-                    a[1][d] += cw * ra;
+                    constexpr float cw = (float)(L::wd(i) * cd);
+                    a[0][d] += cw * rn.y;
+                    a[1][d] += cw * rn.x;
                 }
             });
         });
-        const double ra0 = rho[site].x, rb0 = rho[site].y;
-        const double rt = r[0] + r[1];
-        if (rho_a) rho_a[site] = r[0];
-        if (rho_b) rho_b[site] = r[1];
-        tot[0] = r[0];
-        tot[1] = r[1];
+        const float ra0 = rho[site].x, rb0 = rho[site].y;
+        const double r0 = (double)p.rho0[0] + (double)sum[0], r1 = (double)p.rho0[1] + (double)sum[1];
+        const float rt = (float)(r0 + r1);
+        if (rho_a) rho_a[site] = r0;
+        if (rho_b) rho_b[site] = r1;
+        tot[0] = r0;
+        tot[1] = r1;
 #pragma unroll
         for (int d = 0; d < D; d++) {
-            const double Ft = -(double)p.G * (ra0 * a[0][d] + rb0 * a[1][d]);
-            const double jt = j[0][d] + j[1][d] + 0.5 * Ft;
-            if (u) u[(size_t)d * NN + site] = jt / rt;
-            tot[2 + d] = jt;
+            const float Ft = -p.G * (ra0 * a[0][d] + rb0 * a[1][d]);
+            const float jt = j[0][d] + j[1][d] + 0.5f * Ft;
+            if (u) u[(size_t)d * NN + site] = (double)(jt / rt);
+            tot[2 + d] = (double)jt;
         }
     }
     block_sum<5, kObsBlock>(tot, sh);
@@ -786,6 +824,18 @@ cudaError_t Launch<L, S>::gather(int parity, const StepParams &p, const void *po
     const int blocks = (int)((n + 127) / 128);
     if (parity == 0) kern::k_gather_sites<L, S, 0><<<blocks, 128, 0, st>>>(p, ptr, sites, n, out);
     else kern::k_gather_sites<L, S, 1><<<blocks, 128, 0, st>>>(p, ptr, sites, n, out);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::sfk_fields(int parity, const StepParams &p, const void *pop, float2 *z, double *partials,
+                                     int *nblocks, cudaStream_t st)
+{
+    const dim3 b(kern::kObsBlock), g((p.nx + kern::kObsBlock - 1) / kern::kObsBlock, p.ny, p.nz);
+    *nblocks = (int)(g.x * g.y * g.z);
+    const auto planes = kern::plane_table(static_cast<const typename S::T *>(pop), L::Q, p.N);
+    if (parity == 0) kern::k_sfk_fields<L, S, 0><<<g, b, 0, st>>>(p, planes, z, partials);
+    else kern::k_sfk_fields<L, S, 1><<<g, b, 0, st>>>(p, planes, z, partials);
     return cudaGetLastError();
 }
 

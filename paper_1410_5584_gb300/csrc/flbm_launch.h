@@ -18,6 +18,8 @@ template <class L, class S> struct Launch {
     static cudaError_t init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st);
     static cudaError_t gather(int parity, const StepParams &p, const void *pop, const int64_t *sites, int64_t n,
                               double *out, cudaStream_t st);
+    static cudaError_t sfk_fields(int parity, const StepParams &p, const void *pop, float2 *z, double *partials,
+                                  int *nblocks, cudaStream_t st);
     static cudaError_t observables(int parity, const StepParams &p, const void *pop, const float *rho, double *ra,
                                    double *rb, double *u, double *partials, int *nblocks, cudaStream_t st);
 };

@@ -2,11 +2,13 @@
 // of Eq. str-bin-hom, Sec. IV A, over the whole Brillouin zone) and the
 // structure functions of Eq. structurefunctions, accumulated on the device.
 //
-// One snapshot: the density fluctuations delta rho^s = rho^s - <rho^s> (from
-// the FP64 per-site observables and the FP64 totals) are packed as one
-// complex field z = delta rho_A + i delta rho_B in float and transformed in
-// place along every axis by line FFTs in shared memory (radix 2 for
-// power-of-two lengths, a direct DFT otherwise).  The two real spectra follow
+// One snapshot: a fields kernel sums each site's population deviations into
+// z = (rho_A - rho0_A) + i (rho_B - rho0_B) in float, with FP64 block partials
+// from which the means follow (fixed order).  The first line-FFT pass
+// subtracts the means as it loads, so z becomes the fluctuation field
+// delta rho_A + i delta rho_B, and every axis is transformed in place by line
+// FFTs in shared memory (radix 2 for power-of-two lengths, a direct DFT
+// otherwise).  The two real spectra follow
 // from Hermitian symmetry, rho_hat_A(k) = (z(k) + conj z(-k)) / 2 and
 // rho_hat_B(k) = (z(k) - conj z(-k)) / (2i), and their products are added
 // into FP64 accumulators.  The transform is in float because this GPU's FP64
@@ -57,8 +59,20 @@ struct Lines {
     }
 };
 
+// the value a line transform loads: z minus the field means when `mean` is set
+// (the first pass), z otherwise
+__device__ __forceinline__ float2 load_point(const float2 *data, long idx, const double *mean)
+{
+    float2 v = data[idx];
+    if (mean) {
+        v.x -= (float)mean[0];
+        v.y -= (float)mean[1];
+    }
+    return v;
+}
+
 __global__ void __launch_bounds__(kFftThreads) k_fft_pow2(float2 *__restrict__ data, const Lines L,
-                                                          const float2 *__restrict__ tw)
+                                                          const float2 *__restrict__ tw, const double *mean)
 {
     extern __shared__ float2 sm[];
     const long l0 = (long)blockIdx.x * L.group;
@@ -67,7 +81,8 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pow2(float2 *__restrict__ d
     for (int e = threadIdx.x; e < tile; e += kFftThreads) {
         int g, j;
         L.split(e, g, j);
-        if (l0 + g < L.count) sm[g * n + (int)(__brev((unsigned)j) >> (32 - L.log2n))] = data[L.base(l0 + g) + j * L.stride];
+        if (l0 + g < L.count)
+            sm[g * n + (int)(__brev((unsigned)j) >> (32 - L.log2n))] = load_point(data, L.base(l0 + g) + j * L.stride, mean);
     }
     __syncthreads();
     for (int s = 1; s <= L.log2n; s++) {
@@ -91,7 +106,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pow2(float2 *__restrict__ d
 
 // direct DFT of lines of any length: out_k = sum_j in_j exp(-2 pi i j k / n)
 __global__ void __launch_bounds__(kFftThreads) k_dft_lines(float2 *__restrict__ data, const Lines L,
-                                                           const float2 *__restrict__ tw)
+                                                           const float2 *__restrict__ tw, const double *mean)
 {
     extern __shared__ float2 sm[];
     const long l0 = (long)blockIdx.x * L.group;
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(kFftThreads) k_dft_lines(float2 *__restrict__ 
     for (int e = threadIdx.x; e < tile; e += kFftThreads) {
         int g, j;
         L.split(e, g, j);
-        if (l0 + g < L.count) in[g * n + j] = data[L.base(l0 + g) + j * L.stride];
+        if (l0 + g < L.count) in[g * n + j] = load_point(data, L.base(l0 + g) + j * L.stride, mean);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < tile; e += kFftThreads) {
@@ -125,30 +140,50 @@ __global__ void __launch_bounds__(kFftThreads) k_dft_lines(float2 *__restrict__ 
     }
 }
 
-__global__ void k_sfk_pack(const double *__restrict__ ra, const double *__restrict__ rb,
-                           const double *__restrict__ cons, long N, float2 *__restrict__ z)
+// means of the two fields from the [nblocks][2] block partials (one block,
+// fixed order): mean[s] = sum / N
+__global__ void __launch_bounds__(256) k_sfk_means(const double *__restrict__ partials, int nblocks, long N,
+                                                   double *__restrict__ mean)
 {
-    const double ma = cons[0] / (double)N, mb = cons[1] / (double)N;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
-        z[i] = make_float2((float)(ra[i] - ma), (float)(rb[i] - mb));
+    __shared__ double sh[256][2];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += 256) {
+        a += partials[2 * k];
+        b += partials[2 * k + 1];
+    }
+    sh[threadIdx.x][0] = a;
+    sh[threadIdx.x][1] = b;
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride) {
+            sh[threadIdx.x][0] += sh[threadIdx.x + stride][0];
+            sh[threadIdx.x][1] += sh[threadIdx.x + stride][1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mean[0] = sh[0][0] / (double)N;
+        mean[1] = sh[0][1] / (double)N;
+    }
 }
 
 // acc[0..2][k] += |A|^2, Re(A conj B), |B|^2 with A, B the spectra of the real
-// and imaginary parts of z
-__global__ void k_sfk_accumulate(const float2 *__restrict__ z, int nx, int ny, int nz, double *__restrict__ acc)
+// and imaginary parts of z (products in float, sums in FP64); grid over
+// (x blocks, y, z)
+__global__ void __launch_bounds__(128) k_sfk_accumulate(const float2 *__restrict__ z, int nx, int ny, int nz,
+                                                        double *__restrict__ acc)
 {
-    const long N = (long)nx * ny * nz;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        const int mx = (int)(i % nx), my = (int)((i / nx) % ny), mz = (int)(i / ((long)nx * ny));
-        const long im = ((long)((nz - mz) % nz) * ny + (ny - my) % ny) * nx + (nx - mx) % nx;
-        const float2 a = z[i], b = z[im];
-        const double zr = a.x, zi = a.y, mr = b.x, mi = b.y;
-        const double Ar = 0.5 * (zr + mr), Ai = 0.5 * (zi - mi);
-        const double Br = 0.5 * (zi + mi), Bi = 0.5 * (mr - zr);
-        acc[i] += Ar * Ar + Ai * Ai;
-        acc[N + i] += Ar * Br + Ai * Bi;
-        acc[2 * N + i] += Br * Br + Bi * Bi;
-    }
+    const int mx = blockIdx.x * blockDim.x + threadIdx.x, my = blockIdx.y, mz = blockIdx.z;
+    if (mx >= nx) return;
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t i = ((size_t)mz * ny + my) * nx + mx;
+    const size_t im = ((size_t)(mz == 0 ? 0 : nz - mz) * ny + (my == 0 ? 0 : ny - my)) * nx + (mx == 0 ? 0 : nx - mx);
+    const float2 a = z[i], b = z[im];
+    const float Ar = 0.5f * (a.x + b.x), Ai = 0.5f * (a.y - b.y);
+    const float Br = 0.5f * (a.y + b.y), Bi = 0.5f * (b.x - a.x);
+    acc[i] += (double)(Ar * Ar + Ai * Ai);
+    acc[N + i] += (double)(Ar * Br + Ai * Bi);
+    acc[2 * N + i] += (double)(Br * Br + Bi * Bi);
 }
 
 // the structure factors (acc scaled) or the structure functions of Eq.
@@ -199,7 +234,7 @@ flbm_status ensure_twiddles(flbm_ctx *c, int axis, int n)
     return FLBM_OK;
 }
 
-flbm_status transform_axis(flbm_ctx *c, int axis)
+flbm_status transform_axis(flbm_ctx *c, int axis, const double *mean)
 {
     const int n = axis == 0 ? c->nx : (axis == 1 ? c->ny : c->nz);
     if (n == 1) return FLBM_OK;
@@ -217,8 +252,8 @@ flbm_status transform_axis(flbm_ctx *c, int axis)
     L.group = std::max(1, std::min(16, kSmemBudget / (buffers * n * (int)sizeof(float2))));
     const size_t smem = (size_t)buffers * L.group * n * sizeof(float2);
     const unsigned blocks = (unsigned)((L.count + L.group - 1) / L.group);
-    if (L.log2n >= 0) k_fft_pow2<<<blocks, kFftThreads, smem, c->stream>>>(c->d_sfk_z, L, c->d_sfk_tw[axis]);
-    else k_dft_lines<<<blocks, kFftThreads, smem, c->stream>>>(c->d_sfk_z, L, c->d_sfk_tw[axis]);
+    if (L.log2n >= 0) k_fft_pow2<<<blocks, kFftThreads, smem, c->stream>>>(c->d_sfk_z, L, c->d_sfk_tw[axis], mean);
+    else k_dft_lines<<<blocks, kFftThreads, smem, c->stream>>>(c->d_sfk_z, L, c->d_sfk_tw[axis], mean);
     FLBM_CUDA(c, cudaGetLastError(), "line transform launch");
     return FLBM_OK;
 }
@@ -244,6 +279,8 @@ void free_sfk(flbm_ctx *c)
 {
     if (c->d_sfk_z) cudaFree(c->d_sfk_z);
     if (c->d_sfk_acc) cudaFree(c->d_sfk_acc);
+    if (c->d_sfk_mean) cudaFree(c->d_sfk_mean);
+    c->d_sfk_mean = nullptr;
     for (int a = 0; a < 3; a++) {
         if (c->d_sfk_tw[a]) cudaFree(c->d_sfk_tw[a]);
         c->d_sfk_tw[a] = nullptr;
@@ -264,10 +301,11 @@ flbm_status flbm_sfk_sample(flbm_ctx *c)
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_sfk_sample before flbm_init");
     flbm_status st = sfk_supported(c);
     if (st != FLBM_OK) return st;
-    if ((st = ensure_obs(c)) != FLBM_OK) return st;
+    if ((st = ensure_obs(c)) != FLBM_OK) return st; // block partials buffer
     if (!c->d_sfk_acc) {
         if (cudaMalloc((void **)&c->d_sfk_acc, 3 * (size_t)c->N * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void **)&c->d_sfk_z, (size_t)c->N * sizeof(float2)) != cudaSuccess) {
+            cudaMalloc((void **)&c->d_sfk_z, (size_t)c->N * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_sfk_mean, 2 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             free_sfk(c);
             return fail(c, FLBM_ENOMEM, "full-k structure factor buffers (%zu bytes) do not fit",
@@ -277,17 +315,15 @@ flbm_status flbm_sfk_sample(flbm_ctx *c)
         c->sfk_count = 0;
     }
     const StepParams p = make_params(c);
-    if ((st = density_now(c, p)) != FLBM_OK) return st;
     int nb = 0;
-    double *ra = c->d_obs, *rb = c->d_obs + c->N;
-    FLBM_CUDA(c, launch_observables(c->lat, c->storage, c->parity, p, c->pop, c->rho, ra, rb, nullptr, c->d_partials,
-                                    &nb, c->stream), "observables kernel launch");
-    FLBM_CUDA(c, launch_sum_partials(c->d_partials, nb, c->d_cons, c->stream), "reduction kernel launch");
-    k_sfk_pack<<<grid_for(c->N), 256, 0, c->stream>>>(ra, rb, c->d_cons, (long)c->N, c->d_sfk_z);
-    FLBM_CUDA(c, cudaGetLastError(), "pack kernel launch");
+    FLBM_CUDA(c, launch_sfk_fields(c->lat, c->storage, c->parity, p, c->pop, c->d_sfk_z, c->d_partials, &nb, c->stream),
+              "fields kernel launch");
+    k_sfk_means<<<1, 256, 0, c->stream>>>(c->d_partials, nb, (long)c->N, c->d_sfk_mean);
+    FLBM_CUDA(c, cudaGetLastError(), "means kernel launch");
     for (int a = 0; a < 3; a++)
-        if ((st = transform_axis(c, a)) != FLBM_OK) return st;
-    k_sfk_accumulate<<<grid_for(c->N), 256, 0, c->stream>>>(c->d_sfk_z, c->nx, c->ny, c->nz, c->d_sfk_acc);
+        if ((st = transform_axis(c, a, a == 0 ? c->d_sfk_mean : nullptr)) != FLBM_OK) return st;
+    const dim3 blk(128), grd((c->nx + 127) / 128, c->ny, c->nz);
+    k_sfk_accumulate<<<grd, blk, 0, c->stream>>>(c->d_sfk_z, c->nx, c->ny, c->nz, c->d_sfk_acc);
     FLBM_CUDA(c, cudaGetLastError(), "accumulate kernel launch");
     c->sfk_count++;
     return FLBM_OK;
