@@ -163,6 +163,38 @@ def structure_functions(s_aa, s_ab, s_bb, rho0_a, rho0_b):
     return s_tt, s_cc, s_tc
 
 
+def interface_heights(rho_a, x_liquid, x_gas):
+    """Heights of the two interfaces of a stripe (Sec. VI B): rho_a[y][x] of a
+    D2Q9 box whose A-rich stripe contains column x_liquid and whose B-rich
+    region contains column x_gas.  The bulk values rho_l, rho_g are the means
+    of rho_a over y at those columns; in the window of columns from x_gas up
+    to x_liquid (periodic) and in the one from x_liquid up to x_gas, the
+    liquid fraction L(y) = sum_x (rho_a - rho_g) / (rho_l - rho_g) places the
+    dividing surface (Gibbs), column x covering [x - 1/2, x + 1/2):
+    h1(y) = x_liquid - 1/2 - L1(y), h2(y) = x_liquid - 1/2 + L2(y), in the
+    frame of x_liquid (h1 may be negative when the window wraps).  Returns
+    (h1, h2) as float arrays over y."""
+    r = np.asarray(rho_a, dtype=np.float64)
+    ny, nx = r.shape
+    rl, rg = r[:, x_liquid].mean(), r[:, x_gas].mean()
+    frac = (r - rg) / (rl - rg)
+    w1 = [(x_gas + k) % nx for k in range((x_liquid - x_gas) % nx)]
+    w2 = [(x_liquid + k) % nx for k in range((x_gas - x_liquid) % nx)]
+    h1 = x_liquid - 0.5 - frac[:, w1].sum(axis=1)
+    h2 = x_liquid - 0.5 + frac[:, w2].sum(axis=1)
+    return h1, h2
+
+
+def height_spectrum(h):
+    """S_h(k_m) = |sum_y (h(y) - <h>) exp(-i k_m y)|^2 / n_y, k_m = 2 pi m / n_y,
+    m = 1 .. n_y / 2 (the capillary spectrum of Eq. predictionspectrum per unit
+    length); numpy's FFT is the library step."""
+    h = np.asarray(h, dtype=np.float64)
+    ny = h.size
+    f = np.fft.fft(h - h.mean())
+    return np.abs(f[1:ny // 2 + 1]) ** 2 / ny
+
+
 class Oracle:
     """Handle on one oracle lattice (two species, periodic box)."""
 
