@@ -278,6 +278,52 @@ def batched_form(seed, steps, device, nrep=64):
             "speedup_vs_per_replica_launches": t_sep / t_batch}
 
 
+def capillary_form(seed, device, steps=20000):
+    """The capillary-fluctuation workload of Sec. VI B: a D2Q9 100 x 512 box
+    with an A-rich stripe 50 wide (G = 1.5, kT = 1e-5, all rates 1): MLUPS of a
+    lone context and of the same box as a one-replica batch replayed from CUDA
+    graphs (51,200 sites are too few to hide launch latency), and the time of
+    one tracked height-spectrum snapshot."""
+    import numpy as np
+    import torch
+
+    from paper_1410_5584_gb300 import Batch, Lattice
+
+    nx, ny = 100, 512
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    phi = 0.25 * (1 + np.tanh((x - 25) / 2.0)) * (1 - np.tanh((x - 75) / 2.0))
+    ra, rb = (0.06 + 2.24 * phi).ravel(), (0.06 + 2.24 * (1 - phi)).ravel()
+
+    def timed(run, stream):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        s0.record(stream)
+        run()
+        s1.record(stream)
+        torch.cuda.synchronize(device)
+        return s0.elapsed_time(s1) / 1e3
+
+    g = Lattice(0, nx, ny, 1, 1.0, 1.0, 1e-5, 1.5, seed, device=device, rho0_a=1.18, rho0_b=1.18)
+    g.init(ra, rb)
+    g.step(2000)
+    t_lone = timed(lambda: g.step(steps), g.stream)
+    g.cap_sample(-1, -1)
+    t_cap = timed(lambda: [g.cap_sample(-1, -1) for _ in range(100)], g.stream) / 100
+    g.sync()
+    b = Batch(0, [dict(nx=nx, ny=ny, tau_a=1.0, tau_b=1.0, kT=1e-5, G=1.5, seed=seed, rho0_a=1.18, rho0_b=1.18)],
+              device=device)
+    b.init(ra, rb)
+    graph_steps = b.autotune(steps=2000)["graph_steps"]
+    b.step(2000)
+    t_batch = timed(lambda: b.step(steps), b.stream)
+    b.sync()
+    b.close()
+    sites = nx * ny
+    return {"unit": "MLUPS", "sites": sites, "steps": steps, "lone_context": sites * steps / t_lone / 1e6,
+            "one_replica_batch": sites * steps / t_batch / 1e6, "graph_steps": graph_steps,
+            "ms_per_height_snapshot": t_cap * 1e3}
+
+
 def cpu_baseline(wl, seed, budget_s=15.0):
     """The FP64 oracle, single-threaded as it stands, on a bounded sample: the
     same lattice and parameters on a smaller periodic box."""
@@ -480,6 +526,7 @@ def run_ours(args, wl):
     if not args.no_forms and wl["storage"] == "f32":
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
         line["forms"]["batched"] = batched_form(args.seed, 5000, device)
+        line["forms"]["capillary"] = capillary_form(args.seed, device)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
     print(json.dumps(line), flush=True)

@@ -267,6 +267,38 @@ flbm_status flbm_sfk_functions(flbm_ctx *ctx, double rho0_a, double rho0_b, doub
                                double *S_tc);
 flbm_status flbm_sfk_reset(flbm_ctx *ctx);
 
+/*
+ * Capillary fluctuations of a flat interface (Sec. VI B, Eq.
+ * predictionspectrum: <|h_hat(k)|^2> = kT / (gamma k^2)).  D2Q9 boxes holding a
+ * stripe rich in species A that spans y and contains column x_liquid, with
+ * the B-rich phase at column x_gas (FLBM_EUNSUPPORTED for D3Q19).
+ *
+ * flbm_cap_sample adds one snapshot.  With x_liquid = x_gas = -1 the columns
+ * follow the stripe, which wanders over long runs: x_liquid is the middle of
+ * the window of n_x/2 columns holding the most A (summed over y) and x_gas
+ * the column half a box away, found on the device for each snapshot (the
+ * mean heights then refer to each snapshot's own frame).  The bulk values rho_l, rho_g are the
+ * means of rho_A over y at the two columns.  In the window of columns from
+ * x_gas up to x_liquid (periodic) and in the one from x_liquid up to x_gas,
+ * the liquid fraction L(y) = sum_x (rho_A - rho_g) / (rho_l - rho_g) places
+ * the dividing surface of each interface, column x covering
+ * [x - 1/2, x + 1/2): h1(y) = x_liquid - 1/2 - L1(y), h2(y) = x_liquid - 1/2 +
+ * L2(y) (frame of x_liquid).  Each interface's mean height is removed and
+ * |sum_y dh(y) exp(-i k_m y)|^2 / n_y, k_m = 2 pi m / n_y, averaged over the
+ * two interfaces, is accumulated in FP64.  Asynchronous; fixed columns must
+ * stay the same until flbm_cap_reset (else FLBM_EINVAL).  Device memory: N
+ * complex floats and (2.5 n_y + n_x) doubles.
+ *
+ * flbm_cap_spectrum writes S_h[m - 1] for m = 1 .. nk (nk <= n_y / 2), the
+ * means over snapshots, and h_mean[2], the mean heights of the two
+ * interfaces; either may be NULL.  Synchronising; FLBM_ESTATE before a sample.
+ *
+ * flbm_cap_reset clears the accumulators and frees their memory.
+ */
+flbm_status flbm_cap_sample(flbm_ctx *ctx, int x_liquid, int x_gas);
+flbm_status flbm_cap_spectrum(flbm_ctx *ctx, int nk, double *S_h, double *h_mean, int64_t *nsamples);
+flbm_status flbm_cap_reset(flbm_ctx *ctx);
+
 /* Copy the populations, natural layout [2][Q][N], to / from host doubles
  * (2 * Q * N values).  get: synchronising; set: converts to the storage format
  * and sets the step counter to `step`. */
@@ -318,7 +350,7 @@ flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int parity, int64_
 
 /*
  * Batches of independent replicas (many boxes of uneven size, parameters and
- * noise keys advanced together; SURVEY: the batching form).  Each replica is the
+ * noise keys advanced together, as for ensembles of Sec. VI runs).  Each replica is the
  * same problem as a lone context created with its parameters -- its site index
  * and therefore its noise are replica-local -- so a replica of a batch and a
  * lone context with the same parameters and state give the same populations.

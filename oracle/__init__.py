@@ -185,6 +185,21 @@ def interface_heights(rho_a, x_liquid, x_gas):
     return h1, h2
 
 
+def track_stripe(rho_a):
+    """Bulk columns of a stripe that may have moved: with C(x) the sum over y of
+    rho_a, the window of n_x/2 consecutive columns (periodic) with the largest
+    sum of C holds the stripe (ties: the lowest first column x0); returns
+    (x_liquid, x_gas) = (x0 + w/2, x0 + w/2 + n_x/2) mod n_x with w = n_x/2."""
+    r = np.asarray(rho_a, dtype=np.float64)
+    ny, nx = r.shape
+    c = r.sum(axis=0)
+    w = nx // 2
+    sums = np.array([sum(c[(x0 + k) % nx] for k in range(w)) for x0 in range(nx)])
+    x0 = int(np.argmax(sums))  # the first maximum
+    xl = (x0 + w // 2) % nx
+    return xl, (xl + nx // 2) % nx
+
+
 def height_spectrum(h):
     """S_h(k_m) = |sum_y (h(y) - <h>) exp(-i k_m y)|^2 / n_y, k_m = 2 pi m / n_y,
     m = 1 .. n_y / 2 (the capillary spectrum of Eq. predictionspectrum per unit

@@ -1046,6 +1046,7 @@ void flbm_destroy(flbm_ctx *c)
     if (c->d_cons) cudaFree(c->d_cons);
     free_sf(c);
     free_sfk(c);
+    free_cap(c);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_dep) cudaEventDestroy(e);

@@ -53,6 +53,12 @@ struct flbm_ctx {
     float2 *d_sfk_tw[3] = {nullptr, nullptr, nullptr}; // twiddles per axis
     int sfk_tw_n[3] = {0, 0, 0};
     int64_t sfk_count = 0;
+    // capillary spectrum of a stripe (flbm_cap_*)
+    float2 *d_cap_z = nullptr;   // N: rho_A - rho0_A (and rho_B) of the snapshot
+    double *d_cap_h = nullptr;   // heights [2][ny], spectrum sums [ny/2], mean-height sums [2], bulk [2]
+    double2 *d_cap_tw = nullptr; // (cos, -sin)(2 pi j / ny)
+    int64_t cap_count = 0;
+    int cap_xl = 0, cap_xg = 0;
     float *h_stage = nullptr;     // pinned staging, 2 * N floats
     // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
     struct TimingMark {
@@ -117,6 +123,7 @@ flbm_status batch_restore(flbm_ctx *c, const void *buf, size_t bytes);
 void batch_destroy(flbm_ctx *c);
 int batch_graph_steps(const flbm_ctx *c);
 void free_sfk(flbm_ctx *c); // flbm_sfk.cu
+void free_cap(flbm_ctx *c); // flbm_capillary.cu
 bool view_call_allowed(const flbm_ctx *c); // false for mutating calls on a replica view
 inline bool is_batch(const flbm_ctx *c) { return c->batch && !c->is_view; }
 } // namespace flbm

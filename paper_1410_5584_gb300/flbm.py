@@ -106,6 +106,9 @@ def lib():
             "flbm_sfk": (i32, [vp, dp, dp, dp, i64p]),
             "flbm_sfk_functions": (i32, [vp, dbl, dbl, dp, dp, dp]),
             "flbm_sfk_reset": (i32, [vp]),
+            "flbm_cap_sample": (i32, [vp, i32, i32]),
+            "flbm_cap_spectrum": (i32, [vp, i32, dp, dp, i64p]),
+            "flbm_cap_reset": (i32, [vp]),
             "flbm_get_populations": (i32, [vp, dp]),
             "flbm_set_populations": (i32, [vp, dp, i64]),
             "flbm_get_site_populations": (i32, [vp, i64p, i64, dp]),
@@ -207,6 +210,21 @@ class _Context:
         out = [np.empty(self._sfk_shape()) for _ in range(3)]
         check(self._h, lib().flbm_sfk_functions(self._h, float(rho0_a), float(rho0_b), *[_dp(o) for o in out]))
         return tuple(out)
+
+    def cap_sample(self, x_liquid, x_gas):
+        """flbm_cap_sample: one snapshot of the two interface heights' spectrum."""
+        check(self._h, lib().flbm_cap_sample(self._h, int(x_liquid), int(x_gas)))
+
+    def cap_spectrum(self, nk=None):
+        """(S_h[m = 1..nk], h_mean[2], nsamples) of the capillary snapshots."""
+        nk = self.ny // 2 if nk is None else int(nk)
+        s, hm = np.empty(nk), np.empty(2)
+        n = ctypes.c_int64()
+        check(self._h, lib().flbm_cap_spectrum(self._h, nk, _dp(s), _dp(hm), ctypes.byref(n)))
+        return s, hm, n.value
+
+    def cap_reset(self):
+        check(self._h, lib().flbm_cap_reset(self._h))
 
     def sf_reset(self):
         check(self._h, lib().flbm_sf_reset(self._h))

@@ -53,3 +53,17 @@ def test_spectrum_of_one_mode(m):
     # Nyquist mode only its cosine part survives on the integer sites
     want[m - 1] = ny * A ** 2 / 4 if m < ny // 2 else ny * (A * np.cos(phase)) ** 2
     assert np.allclose(s, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("center", [50.0, 13.0, 91.5])
+def test_tracking_finds_the_stripe(center):
+    """A stripe of half the box width centred anywhere (across the periodic
+    edge too): the liquid column is its middle, the gas column half a box away."""
+    ny, nx = 8, 100
+    x = np.arange(nx)
+    d = (x - center + nx / 2) % nx - nx / 2  # signed periodic distance to the centre
+    phi = 0.5 * (1 - np.tanh((np.abs(d) - 25.0) / 2.0))
+    r = np.tile(0.06 + 2.24 * phi, (ny, 1))
+    xl, xg = oracle.track_stripe(r)
+    assert abs(((xl - center + nx / 2) % nx) - nx / 2) <= 1.0
+    assert xg == (xl + 50) % nx

@@ -2,8 +2,9 @@
 bfloat16 deviations from w_i rho0, collided in float) against the FP64 oracle
 and the float-storage run, on a 32^3 D3Q19 Shan-Chen case: densities,
 velocities, the axis structure factors sampled along the same noise history,
-and mass drift.  Writes the measured errors to gpurun_out/precision.json when
-that folder exists (a record for the design notes)."""
+and mass drift.  Writes the measured errors to precision.json in the folder
+named by the FLBM_REPORT_DIR environment variable, when it is set (a record
+for the design notes)."""
 import json
 import os
 
@@ -63,8 +64,8 @@ def test_sixteen_bit_storage_accuracy_report():
     runs = {s: _run_gpu(s, f0) for s in ("f32", "f16", "bf16")}
     report = {s: {"vs_oracle": _errors(runs[s], ref), "vs_f32": _errors(runs[s], runs["f32"])} for s in runs}
     report["case"] = f"D3Q19 {N3}^3, tau={TAU}, kT={KT}, G={G}, {STEPS} steps, S(k) every {EVERY}"
-    if os.path.isdir("gpurun_out"):
-        with open(os.path.join("gpurun_out", "precision.json"), "w") as f:
+    if os.environ.get("FLBM_REPORT_DIR"):
+        with open(os.path.join(os.environ["FLBM_REPORT_DIR"], "precision.json"), "w") as f:
             json.dump(report, f, indent=1)
     print(json.dumps(report))
     # float storage: parity-level agreement
