@@ -82,6 +82,14 @@ def lib():
             L.orc_philox4x32_10.argtypes = [up, up, up]
             L.orc_gaussian.restype = dbl
             L.orc_gaussian.argtypes = [u64, u32, u32, u32, u32]
+            L.orcm_create.restype = vp
+            L.orcm_create.argtypes = [i32, i32, i32, i32, i32, dp, dbl, dp, u64]
+            L.orcm_destroy.argtypes = [vp]
+            L.orcm_init.argtypes = [vp, dp]
+            L.orcm_set_f.argtypes = [vp, dp, i64]
+            L.orcm_get_f.argtypes = [vp, dp]
+            L.orcm_step.argtypes = [vp, i64]
+            L.orcm_moments.argtypes = [vp, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -133,6 +141,65 @@ def philox4x32_10(ctr, key):
 
 def gaussian(seed: int, site: int, step: int, species: int, mode: int) -> float:
     return lib().orc_gaussian(seed, site, step, species, mode)
+
+
+class MultiOracle:
+    """The N-species update (App. C-D) in FP64: rates 1/tau_s per species, the
+    common momentum rate N / sum tau_s, mean-field forces G[s][t] between
+    different species (diagonal ignored), projected momentum noise."""
+
+    def __init__(self, lattice, nspecies, nx, ny, nz, tau, kT, G, seed):
+        self.lattice, self.ns = int(lattice), int(nspecies)
+        c, w, T, N = tables(lattice)
+        self.Q, self.D = len(w), 2 if lattice == D2Q9 else 3
+        self.nx, self.ny = int(nx), int(ny)
+        self.nz = 1 if lattice == D2Q9 else int(nz)
+        self.N = self.nx * self.ny * self.nz
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        G = np.ascontiguousarray(G, dtype=np.float64).reshape(self.ns, self.ns)
+        assert tau.size == self.ns
+        self._h = lib().orcm_create(self.lattice, self.ns, self.nx, self.ny, self.nz, _dp(tau), float(kT),
+                                    _dp(G), int(seed) & (2 ** 64 - 1))
+        if not self._h:
+            raise ValueError("bad multi-species oracle parameters")
+
+    def init(self, rho=None):
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).ravel()
+        lib().orcm_init(self._h, _dp(r))
+
+    def set_f(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        assert f.size == self.ns * self.Q * self.N
+        lib().orcm_set_f(self._h, _dp(f), int(step))
+
+    def get_f(self):
+        f = np.zeros(self.ns * self.Q * self.N)
+        lib().orcm_get_f(self._h, _dp(f))
+        return f.reshape(self.ns, self.Q, self.nz, self.ny, self.nx)
+
+    def step(self, n=1):
+        if lib().orcm_step(self._h, int(n)) != 0:
+            raise FloatingPointError("a density became non-positive")
+
+    def moments(self):
+        """(rho [ns][z][y][x], u [D][z][y][x], cons [ns + 3])"""
+        rho = np.zeros(self.ns * self.N)
+        u = np.zeros(self.D * self.N)
+        cons = np.zeros(self.ns + 3)
+        lib().orcm_moments(self._h, _dp(rho), _dp(u), _dp(cons))
+        shp = (self.nz, self.ny, self.nx)
+        return rho.reshape((self.ns,) + shp), u.reshape((self.D,) + shp), cons
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orcm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def structure_factor_full(rho_a, rho_b):

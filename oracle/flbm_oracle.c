@@ -37,6 +37,10 @@
  *     counter (site, step, species, a/4), Gaussian = lane a mod 4 of a
  *     Box-Muller pair (the paper only says "Box-Muller", Sec. VI A).
  *   - D3Q19 basis: not in the paper; rows given in d3q19_tables() below.
+ *
+ * The orcm_* functions at the end hold the N-species update of App. C-D (more
+ * than two species, forces between different species only, projected momentum
+ * noise); their readings are listed beside them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -772,3 +776,253 @@ int orc_structure_factor(const orc_t *o, double *s_aa, double *s_ab, double *s_b
 }
 
 void orc_sf_reset(orc_t *o) { sf_free(o); }
+
+/* ======================================================================== */
+/* N species (App. C-D: the multicomponent generalisation), N = 2 .. 8       */
+/* ======================================================================== */
+/*
+ * The update of Sec. V for N species sigma, each with its own rate
+ * lambdabar_sigma = 1/tau_sigma for every non-conserved mode, a common
+ * momentum rate lambdabar_d (total momentum conservation needs one; by default
+ * N / sum_sigma tau_sigma, i.e. 2/(tau_A + tau_B) for two species) and
+ * mean-field forces between different species only (App. D: the species are
+ * not self-interacting; G symmetric, G_ss = 0):
+ *   a^s(r) = -sum_{s' != s} G_{s s'} sum_i w_i rho^{s'}(r + c_i) c_i
+ *   u = sum_s (jbar^s + rho^s a^s / 2) / rho_t
+ * Noise (App. D, homogeneous form with the local densities): the momentum
+ * noises have the covariance (2 lb_d - lb_d^2) k_B T (rho^s delta_{s s'} -
+ * rho^s rho^{s'} / rho_t); drawn as xi^s = A (eta^s - C^s sum_{s'} eta^{s'}) with
+ * eta^s = sqrt(rho^s) g^s, C^s = rho^s / rho_t, A = sqrt((2 lb_d - lb_d^2) k_B T),
+ * which has exactly that covariance and zero total.  The other modes have the
+ * variances of Eq. new-noise per species, independent.  g^s of mode a comes
+ * from orc_gaussian(seed, site, step, s, a) for every mode a >= 1.
+ */
+#define ORCM_MAXS 8
+
+typedef struct {
+    int lat;
+    orc_lattice L;
+    int ns, nx, ny, nz;
+    long N;
+    double tau[ORCM_MAXS], kT, G[ORCM_MAXS][ORCM_MAXS], lam_d;
+    uint64_t seed;
+    double *f[ORCM_MAXS], *fn[ORCM_MAXS], *rho[ORCM_MAXS];
+    long step;
+} orcm_t;
+
+orcm_t *orcm_create(int lat, int ns, int nx, int ny, int nz, const double *tau, double kT, const double *G,
+                    uint64_t seed)
+{
+    if (ns < 2 || ns > ORCM_MAXS) return NULL;
+    orcm_t *o = (orcm_t *)calloc(1, sizeof(orcm_t));
+    if (!o) return NULL;
+    if (build_lattice(lat, &o->L)) {
+        free(o);
+        return NULL;
+    }
+    o->lat = lat;
+    o->ns = ns;
+    o->nx = nx;
+    o->ny = ny;
+    o->nz = o->L.D == 2 ? 1 : nz;
+    o->N = (long)o->nx * o->ny * o->nz;
+    o->kT = kT;
+    o->seed = seed;
+    double tsum = 0.0;
+    for (int s = 0; s < ns; s++) {
+        o->tau[s] = tau[s];
+        tsum += tau[s];
+        for (int t = 0; t < ns; t++) o->G[s][t] = s == t ? 0.0 : G[s * ns + t];
+    }
+    o->lam_d = ns / tsum;
+    for (int s = 0; s < ns; s++) {
+        o->f[s] = (double *)calloc((size_t)o->L.Q * o->N, sizeof(double));
+        o->fn[s] = (double *)calloc((size_t)o->L.Q * o->N, sizeof(double));
+        o->rho[s] = (double *)calloc((size_t)o->N, sizeof(double));
+        if (!o->f[s] || !o->fn[s] || !o->rho[s]) return NULL;
+    }
+    return o;
+}
+
+void orcm_destroy(orcm_t *o)
+{
+    if (!o) return;
+    for (int s = 0; s < o->ns; s++) {
+        free(o->f[s]);
+        free(o->fn[s]);
+        free(o->rho[s]);
+    }
+    free(o);
+}
+
+/* rest state f_i = w_i rho^s (rho: ns planes of N, or NULL for rho = 1) */
+void orcm_init(orcm_t *o, const double *rho)
+{
+    for (int s = 0; s < o->ns; s++)
+        for (int i = 0; i < o->L.Q; i++)
+            for (long site = 0; site < o->N; site++)
+                o->f[s][i * o->N + site] = o->L.w[i] * (rho ? rho[s * o->N + site] : 1.0);
+    o->step = 0;
+}
+
+void orcm_set_f(orcm_t *o, const double *f, long step)
+{
+    for (int s = 0; s < o->ns; s++) memcpy(o->f[s], f + (size_t)s * o->L.Q * o->N, sizeof(double) * o->L.Q * o->N);
+    o->step = step;
+}
+
+void orcm_get_f(const orcm_t *o, double *f)
+{
+    for (int s = 0; s < o->ns; s++) memcpy(f + (size_t)s * o->L.Q * o->N, o->f[s], sizeof(double) * o->L.Q * o->N);
+}
+
+static long neighbour_m(const orcm_t *o, long site, const int c[3])
+{
+    long x = site % o->nx, y = (site / o->nx) % o->ny, z = site / ((long)o->nx * o->ny);
+    x = (x + c[0] + o->nx) % o->nx;
+    y = (y + c[1] + o->ny) % o->ny;
+    z = (z + c[2] + o->nz) % o->nz;
+    return (z * o->ny + y) * o->nx + x;
+}
+
+static void density_pass_m(orcm_t *o)
+{
+    for (int s = 0; s < o->ns; s++)
+        for (long site = 0; site < o->N; site++) {
+            double r = 0.0;
+            for (int i = 0; i < o->L.Q; i++) r += o->f[s][i * o->N + site];
+            o->rho[s][site] = r;
+        }
+}
+
+/* a^s(r) = -sum_{s'} G_{s s'} sum_i w_i rho^{s'}(r + c_i) c_i */
+static void acceleration_m(const orcm_t *o, long site, int s, double acc[3])
+{
+    acc[0] = acc[1] = acc[2] = 0.0;
+    for (int t = 0; t < o->ns; t++) {
+        if (o->G[s][t] == 0.0) continue;
+        for (int i = 0; i < o->L.Q; i++) {
+            double r = o->rho[t][neighbour_m(o, site, o->L.c[i])];
+            for (int d = 0; d < 3; d++) acc[d] += -o->G[s][t] * o->L.w[i] * r * o->L.c[i][d];
+        }
+    }
+}
+
+/* R[s][a] for every species at one site; nonzero if a density is not positive */
+static int collide_site_m(const orcm_t *o, long site, double R[ORCM_MAXS][ORC_MAXQ])
+{
+    const orc_lattice *L = &o->L;
+    const int D = L->D, Q = L->Q, ns = o->ns;
+    double rho[ORCM_MAXS], m[ORCM_MAXS][ORC_MAXQ], acc[ORCM_MAXS][3];
+    double rho_t = 0.0;
+    for (int s = 0; s < ns; s++) {
+        double pop[ORC_MAXQ];
+        for (int i = 0; i < Q; i++) pop[i] = o->f[s][i * o->N + site];
+        project(L, pop, m[s]);
+        rho[s] = o->rho[s][site];
+        if (!(rho[s] > 0.0) || !isfinite(rho[s])) return 1;
+        acceleration_m(o, site, s, acc[s]);
+        rho_t += rho[s];
+    }
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < D; d++) {
+        double jt = 0.0;
+        for (int s = 0; s < ns; s++) jt += m[s][1 + d] + 0.5 * rho[s] * acc[s][d];
+        u[d] = jt / rho_t;
+    }
+    const double mu = 3.0 * o->kT;
+    const double lam_d = o->lam_d;
+    const double amp_d = sqrt((2.0 * lam_d - lam_d * lam_d) * o->kT);
+    double xi[ORCM_MAXS][ORC_MAXQ];
+    for (int d = 0; d < D; d++) {
+        double eta[ORCM_MAXS], sum = 0.0;
+        for (int s = 0; s < ns; s++) {
+            eta[s] = sqrt(rho[s]) * orc_gaussian(o->seed, (uint32_t)site, (uint32_t)o->step, (uint32_t)s, (uint32_t)(1 + d));
+            sum += eta[s];
+        }
+        for (int s = 0; s < ns; s++) xi[s][1 + d] = amp_d * (eta[s] - rho[s] / rho_t * sum);
+    }
+    for (int s = 0; s < ns; s++) {
+        const double lam = 1.0 / o->tau[s];
+        for (int a = D + 1; a < Q; a++) {
+            double var = (2.0 * lam - lam * lam) * L->N[a] * mu * rho[s];
+            xi[s][a] = sqrt(var) * orc_gaussian(o->seed, (uint32_t)site, (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
+        }
+    }
+    for (int s = 0; s < ns; s++) {
+        double pfeq[ORC_MAXQ], meq[ORC_MAXQ], pphi[ORC_MAXQ], phi0[ORC_MAXQ], mphi[ORC_MAXQ], v[3] = {0, 0, 0};
+        const double zero[3] = {0.0, 0.0, 0.0};
+        feq_pop(L, rho[s], u, pfeq);
+        project(L, pfeq, meq);
+        phi_pop(L, rho[s], acc[s], zero, pphi); /* momentum rows: rho a whatever v is */
+        project(L, pphi, phi0);
+        R[s][0] = 0.0;
+        for (int d = 0; d < D; d++) {
+            int a = 1 + d;
+            R[s][a] = lam_d * (meq[a] - m[s][a]) + (1.0 - 0.5 * lam_d) * phi0[a] + xi[s][a];
+            v[d] = (m[s][a] + 0.5 * R[s][a]) / rho[s]; /* m = mbar + R/2, Eq. alg-mom */
+        }
+        phi_pop(L, rho[s], acc[s], v, pphi);
+        project(L, pphi, mphi);
+        const double lam = 1.0 / o->tau[s];
+        for (int a = D + 1; a < Q; a++) R[s][a] = lam * (meq[a] - m[s][a]) + (1.0 - 0.5 * lam) * mphi[a] + xi[s][a];
+    }
+    return 0;
+}
+
+int orcm_step(orcm_t *o, long n)
+{
+    const orc_lattice *L = &o->L;
+    for (long t = 0; t < n; t++) {
+        density_pass_m(o);
+        for (long site = 0; site < o->N; site++) {
+            double R[ORCM_MAXS][ORC_MAXQ];
+            if (collide_site_m(o, site, R)) return 4;
+            for (int s = 0; s < o->ns; s++)
+                for (int i = 0; i < L->Q; i++) {
+                    double dr = 0.0;
+                    for (int a = 0; a < L->Q; a++) dr += L->T[a][i] * R[s][a] / L->N[a];
+                    o->fn[s][i * o->N + neighbour_m(o, site, L->c[i])] = o->f[s][i * o->N + site] + L->w[i] * dr;
+                }
+        }
+        for (int s = 0; s < o->ns; s++) {
+            double *t2 = o->f[s];
+            o->f[s] = o->fn[s];
+            o->fn[s] = t2;
+        }
+        o->step++;
+    }
+    return 0;
+}
+
+/* rho (ns planes), u = sum_s (jbar^s + rho^s a^s / 2) / rho_t (D planes), and
+ * cons = [sum rho^0 .. sum rho^{ns-1}, total momentum with the half force x3] */
+int orcm_moments(orcm_t *o, double *rho, double *u, double *cons)
+{
+    const orc_lattice *L = &o->L;
+    const int ns = o->ns;
+    density_pass_m(o);
+    double tot[ORCM_MAXS + 3] = {0};
+    for (long site = 0; site < o->N; site++) {
+        double rt = 0.0, jt[3] = {0, 0, 0};
+        for (int s = 0; s < ns; s++) {
+            double r = o->rho[s][site], acc[3];
+            acceleration_m(o, site, s, acc);
+            if (rho) rho[s * o->N + site] = r;
+            tot[s] += r;
+            rt += r;
+            for (int d = 0; d < 3; d++) {
+                double j = 0.0;
+                for (int i = 0; i < L->Q; i++) j += L->c[i][d] * o->f[s][i * o->N + site];
+                jt[d] += j + 0.5 * r * acc[d];
+            }
+        }
+        for (int d = 0; d < L->D; d++) {
+            if (u) u[(long)d * o->N + site] = jt[d] / rt;
+            tot[ns + d] += jt[d];
+        }
+    }
+    if (cons)
+        for (int k = 0; k < ns + 3; k++) cons[k] = tot[k];
+    return 0;
+}

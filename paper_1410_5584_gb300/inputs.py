@@ -22,12 +22,13 @@ def perturbed_density(shape, rho0: float, amplitude: float, seed: int, species: 
 
 
 def random_populations(base: np.ndarray, shape, rel_eps: float, seed: int) -> np.ndarray:
-    """Populations base[s, i] * (1 + rel_eps * g) per site; base has shape [2, Q].
+    """Populations base[s, i] * (1 + rel_eps * g) per site; base has shape
+    [species, Q] (two species for the binary mixture, more for the N-species one).
 
-    Returns float64 [2][Q][z][y][x] rounded to float32 values, so the same state
-    is exactly representable on both sides of a parity comparison."""
+    Returns float64 [species][Q][z][y][x] rounded to float32 values, so the same
+    state is exactly representable on both sides of a parity comparison."""
     base = np.asarray(base, dtype=np.float64)
-    g = _rng(seed, 200).standard_normal(size=(2, base.shape[1]) + tuple(shape))
+    g = _rng(seed, 200).standard_normal(size=base.shape + tuple(shape))
     f = base[:, :, None, None, None] * (1.0 + rel_eps * g)
     return f.astype(np.float32).astype(np.float64)
 

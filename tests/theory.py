@@ -151,3 +151,75 @@ def lattice_linear_sk(c, w, T, N, k_vec, G, rho=(1.0, 1.0), lam=(1.0, 1.0), lam_
         e += 0.5 * (rho[0] * acc[0][d] + rho[1] * acc[1][d]) / rt
         suu += (e.conj() @ P @ e).real / D
     return (eA @ P @ eA).real, (eA @ P @ eB).real, (eB @ P @ eB).real, suu
+
+
+def multi_sk(kT, rho, G, alpha):
+    """S_{s s'}(k) of an N-species mixture (App. D): the self-consistency
+    condition mu alpha^{st} + sum_k rho^k gamma^{sk} alpha^{tk} + gamma^{st} = 0
+    with alpha^{st} = G_{st} alpha(k) gives gamma = -mu A (1 + R A)^-1 and
+    S = mu R + R gamma R = mu R (1 + A R)^-1, R = diag(rho), A = alpha G."""
+    R = np.diag(np.asarray(rho, dtype=float))
+    A = alpha * np.asarray(G, dtype=float)
+    return kT / CS2 * R @ np.linalg.inv(np.eye(len(rho)) + A @ R)
+
+
+def multi_lattice_linear_sk(c, w, T, N, k_vec, G, rho, tau, kT):
+    """Exact stationary structure factors S_{s s'}(k) of the N-species lattice
+    update (App. C-D) linearised about a uniform rest state: the same Fourier
+    state-space model as lattice_linear_sk with ns species, per-species rates
+    1/tau_s on the non-conserved modes, the common momentum rate
+    ns / sum tau_s, forces between different species only and the projected
+    momentum noise (2 lb_d - lb_d^2) kT (rho^s delta - rho^s rho^t / rho_t)."""
+    import scipy.linalg as sl
+
+    c = np.asarray(c, dtype=float)
+    rho = np.asarray(rho, dtype=float)
+    G = np.asarray(G, dtype=float) * (1 - np.eye(len(rho)))
+    ns, Q = len(rho), len(w)
+    D = int(np.count_nonzero(np.abs(c).sum(axis=0)))
+    lam = 1.0 / np.asarray(tau, dtype=float)
+    lam_d = ns / np.sum(tau)
+    kv = np.zeros(3)
+    kv[:len(k_vec)] = k_vec
+    ph = np.exp(1j * (c @ kv))
+    n = ns * Q
+    rt = rho.sum()
+    # acc[s][d]: the acceleration of species s as a linear form of f
+    acc = np.zeros((ns, D, n), complex)
+    for s in range(ns):
+        for t in range(ns):
+            for d in range(D):
+                acc[s, d, t * Q:(t + 1) * Q] += -G[s, t] * np.sum(w * c[:, d] * ph)
+    ub = np.zeros((D, n), complex)
+    for d in range(D):
+        for s in range(ns):
+            ub[d, s * Q:(s + 1) * Q] += c[:, d] / rt
+            ub[d] += 0.5 * rho[s] * acc[s, d] / rt
+    Rm = np.zeros((n, n), complex)
+    for s in range(ns):
+        for d in range(D):
+            j = np.zeros(n, complex)
+            j[s * Q:(s + 1) * Q] = c[:, d]
+            Rm[s * Q + 1 + d] = lam_d * (rho[s] * ub[d] - j) + (1 - lam_d / 2) * rho[s] * acc[s, d]
+        for a in range(D + 1, Q):
+            Rm[s * Q + a, s * Q:(s + 1) * Q] = -lam[s] * T[a]
+    Bm = np.zeros((n, n))
+    for s in range(ns):
+        Bm[s * Q:(s + 1) * Q, s * Q:(s + 1) * Q] = (np.asarray(w)[:, None] * np.asarray(T).T) / np.asarray(N)[None, :]
+    S = np.diag(np.concatenate([np.exp(-1j * (c @ kv))] * ns))
+    A = S @ (np.eye(n) + Bm @ Rm)
+    Xi = np.zeros((n, n))
+    cov_d = (2 * lam_d - lam_d ** 2) * kT * (np.diag(rho) - np.outer(rho, rho) / rt)
+    for d in range(D):
+        a = 1 + d
+        for s in range(ns):
+            for t in range(ns):
+                Xi[s * Q + a, t * Q + a] = cov_d[s, t]
+    for s in range(ns):
+        for a in range(D + 1, Q):
+            Xi[s * Q + a, s * Q + a] = (2 * lam[s] - lam[s] ** 2) * N[a] * 3 * kT * rho[s]
+    P = sl.solve_discrete_lyapunov(A, S @ Bm @ Xi @ Bm.T @ S.conj().T, method="direct")
+    E = np.zeros((ns, n))
+    for s in range(ns):
+        E[s, s * Q:(s + 1) * Q] = 1
+    return (E @ P @ E.T).real
