@@ -85,7 +85,7 @@ def measured_peaks():
 # the files that define the step kernels (device code and the structures they
 # take); the host runtime around them can change without touching the kernels
 KERNEL_SOURCES = ("flbm_internal.h", "flbm_kernels.cuh", "flbm_lattice.cuh", "flbm_launch.h", "flbm_noise.cuh",
-                  "flbm_transform.cuh", "inst_*.cu")
+                  "flbm_transform.cuh", "inst_d*.cu")
 
 
 def sources_digest():
@@ -324,6 +324,48 @@ def capillary_form(seed, device, steps=20000):
             "ms_per_height_snapshot": t_cap * 1e3}
 
 
+def multi_form(seed, device, steps=100, n=256, ns=3):
+    """The N-species form (App. C-D): a D3Q19 n^3 box of three species, rho =
+    (1, 0.8, 0.6), tau = (1, 0.8, 1.25), G = 0.3 between every pair, kT = 1e-5:
+    GLUPS of the whole step, and the collide kernel's achieved bandwidth on its
+    algorithmic bytes (every population read and written once, the site's
+    float4 density read once) against the measured HBM copy rate."""
+    import numpy as np
+    import torch
+
+    from paper_1410_5584_gb300 import MultiLattice
+    from paper_1410_5584_gb300 import flbm as F
+
+    rhos, taus = [1.0, 0.8, 0.6, 0.9][:ns], [1.0, 0.8, 1.25, 0.9][:ns]
+    G = 0.3 * (1 - np.eye(ns))
+    g = MultiLattice(1, ns, n, n, n, taus, 1e-5, G, seed, rho0=rhos, device=device)
+    g.init()
+    g.step(5)
+    g.sync()
+    g.set_option(F.OPT_KERNEL_TIMING, 1)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(g.stream)
+    g.step(steps)
+    s1.record(g.stream)
+    g.sync()
+    t = s0.elapsed_time(s1) / 1e3
+    ms, launches = g.kernel_times()
+    g.close()
+    sites = n ** 3
+    q = 19
+    collide_bytes = sites * (ns * q * 4 * 2 + 16)
+    density_bytes = sites * (ns * q * 4 + 16)
+    peak, kind = measured_peaks()
+    t_col = ms["collide"] / 1e3 / launches["collide"]
+    t_den = ms["density"] / 1e3 / launches["density"]
+    return {"value": sites * steps / t / 1e9, "unit": "GLUPS", "species": ns, "box": f"{n}^3 D3Q19",
+            "steps": steps, "ms_density": t_den * 1e3, "ms_collide": t_col * 1e3,
+            "roofline_collide": {"bound": "hbm", "achieved": collide_bytes / t_col / 1e9, "peak": peak,
+                                 "unit": "GB/s", "frac": collide_bytes / t_col / 1e9 / peak, "peak_kind": kind,
+                                 "bytes_per_site": collide_bytes // sites},
+            "density_gbs": density_bytes / t_den / 1e9}
+
+
 def cpu_baseline(wl, seed, budget_s=15.0):
     """The FP64 oracle, single-threaded as it stands, on a bounded sample: the
     same lattice and parameters on a smaller periodic box."""
@@ -527,6 +569,7 @@ def run_ours(args, wl):
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
         line["forms"]["batched"] = batched_form(args.seed, 5000, device)
         line["forms"]["capillary"] = capillary_form(args.seed, device)
+        line["forms"]["species3"] = multi_form(args.seed, device)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
     print(json.dumps(line), flush=True)

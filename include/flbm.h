@@ -129,8 +129,11 @@ enum {
     FLBM_OPT_BLOCK_Y = 18,       /* ... and rows along y, 1 (default), 2 or 4; x * y <= 128.
                                     The shape changes speed only, never results.  Set one of the
                                     two first when the other would exceed the product limit */
-    FLBM_OPT_LAMBDA_MODE = 1000  /* + 100 * species + a, a > D: rate lambdabar_a of one
+    FLBM_OPT_LAMBDA_MODE = 1000, /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
+    FLBM_OPT_RHO0_SPECIES = 2000 /* N-species contexts only: + s, reference density of species s
+                                    (default 1): the uniform init value and the base of the
+                                    stored deviations; only before flbm_minit */
 };
 
 /*
@@ -423,6 +426,88 @@ void flbm_destroy(flbm_ctx *ctx);
 
 /* Library version string, e.g. "flbm 0.1 sm_103a". */
 const char *flbm_version(void);
+
+/*
+ * N-species mixtures (App. C-D): the update above for 2 <= N <= 4 species on
+ * their own context type.  Per site r and step n, for every species sigma:
+ *   - rho^sigma = sum_i fbar_i^sigma;
+ *   - a^sigma(r) = -sum_{s != sigma} G_{sigma s} sum_i w_i rho^s(r + c_i) c_i
+ *     (forces between different species only; G symmetric, diagonal ignored);
+ *   - u = sum_sigma (jbar^sigma + rho^sigma a^sigma / 2) / rho_t;
+ *   - non-conserved modes of species sigma relax with lambdabar = 1/tau_sigma,
+ *     the momenta with the common rate lambdabar_d = N / sum_sigma tau_sigma;
+ *   - momentum noise with covariance (2 lb_d - lb_d^2) kT (rho^sigma delta -
+ *     rho^sigma rho^s / rho_t) (local densities), drawn as
+ *     xi^sigma = A (eta^sigma - C^sigma sum_s eta^s), eta^s = sqrt(rho^s) g^s,
+ *     C = rho / rho_t, A = sqrt((2 lb_d - lb_d^2) kT); it sums to zero over the
+ *     species, so the total momentum is conserved;
+ *   - the other modes' noise with the variances of Eq. new-noise per species.
+ * g of mode a of species s at (site, n) is lane a mod 4 of Box-Muller on
+ * Philox4x32-10 with counter (site, n, s, a/4), as for two species; every
+ * species draws its own momentum Gaussians.  Populations are stored as float
+ * in the natural layout [s][i][z][y][x] where exposed.  Conventions (errors,
+ * asynchrony, site order, lattice units) are those of the two-species calls.
+ */
+typedef struct flbm_mctx flbm_mctx; /* opaque; created and freed by the library */
+
+/* Create an N-species context (no device memory yet).  tau: nspecies
+ * relaxation times (> 0.5); G: nspecies x nspecies row-major couplings,
+ * symmetric and finite (the diagonal is ignored).  Errors: FLBM_EINVAL for
+ * nspecies outside 2..4, an unknown lattice, a box outside the limits of
+ * flbm_create, tau <= 0.5, kT < 0, an asymmetric or non-finite G, or NULL
+ * pointers. */
+flbm_status flbm_mcreate(flbm_lattice lat, int nspecies, int nx, int ny, int nz, const double *tau,
+                         double kT, const double *G, uint64_t seed, flbm_mctx **out);
+
+/* Options: FLBM_OPT_KERNEL_TIMING, FLBM_OPT_BLOCK_X, FLBM_OPT_BLOCK_Y (as for
+ * two species) and FLBM_OPT_RHO0_SPECIES + s.  FLBM_EINVAL otherwise. */
+flbm_status flbm_mset_option(flbm_mctx *ctx, int key, double value);
+
+/* Run on a caller-owned cudaStream_t (NULL: a stream the context creates). */
+flbm_status flbm_mset_stream(flbm_mctx *ctx, void *stream);
+
+/* Rest state f_i = w_i rho^s: rho = host [nspecies][N] doubles (positive,
+ * finite) or NULL for rho^s = the reference densities.  Allocates the
+ * populations (nspecies Q N floats) and the density field (16 bytes a site).
+ * Resets the step counter.  Synchronising. */
+flbm_status flbm_minit(flbm_mctx *ctx, const double *rho);
+
+/* Advance n >= 0 steps (asynchronous): per step a density kernel, then the
+ * collide kernel.  Step n uses noise counter n.  FLBM_ESTATE before init. */
+flbm_status flbm_mstep(flbm_mctx *ctx, int64_t n);
+
+/* Wait for the stream; FLBM_ENONFINITE once a density was not positive and finite. */
+flbm_status flbm_msync(flbm_mctx *ctx);
+
+/* Device time of the density (ms[0]) and collide (ms[1]) kernels of the steps
+ * taken while FLBM_OPT_KERNEL_TIMING was on; either array may be NULL.
+ * Synchronising. */
+flbm_status flbm_mkernel_times(flbm_mctx *ctx, double ms[2], int64_t launches[2]);
+
+flbm_status flbm_mget_step(const flbm_mctx *ctx, int64_t *step);
+
+/* Observables of the current state: rho = host [nspecies][N] doubles, u = host
+ * [D][N] doubles (the u above), cons = nspecies + 3 FP64 totals [sum rho^0 ..
+ * sum rho^{N-1}, total momentum sum (jbar_t + F_t / 2) x, y, z].  Any pointer
+ * may be NULL.  Synchronising. */
+flbm_status flbm_mmoments(flbm_mctx *ctx, double *rho, double *u, double *cons);
+
+/* Populations, natural layout [nspecies][Q][N], to / from host doubles.  get:
+ * synchronising; set: rounds to float, sets the step counter to `step` and
+ * makes the context ready to step. */
+flbm_status flbm_mget_populations(flbm_mctx *ctx, double *f);
+flbm_status flbm_mset_populations(flbm_mctx *ctx, const double *f, int64_t step);
+
+/* Natural-layout populations of `nsites` sites (indices in [0, N)), out = host
+ * [nsites][nspecies][Q] doubles.  For sampled checks on large boxes.
+ * Synchronising.  FLBM_EINVAL for an index out of range. */
+flbm_status flbm_mget_site_populations(flbm_mctx *ctx, const int64_t *sites, int64_t nsites, double *out);
+
+/* One-line reason of the last error ("" if none); never NULL. */
+const char *flbm_mlast_error(const flbm_mctx *ctx);
+
+/* Free the context and its device memory.  NULL is a no-op. */
+void flbm_mdestroy(flbm_mctx *ctx);
 
 #ifdef __cplusplus
 }

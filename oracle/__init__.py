@@ -90,6 +90,7 @@ def lib():
             L.orcm_get_f.argtypes = [vp, dp]
             L.orcm_step.argtypes = [vp, i64]
             L.orcm_moments.argtypes = [vp, dp, dp, dp]
+            L.orcm_set_rng_origin.argtypes = [vp, i64, i64, i64, i64, i64, i64]
             _lib = L
     return _lib
 
@@ -176,6 +177,13 @@ class MultiOracle:
         f = np.zeros(self.ns * self.Q * self.N)
         lib().orcm_get_f(self._h, _dp(f))
         return f.reshape(self.ns, self.Q, self.nz, self.ny, self.nx)
+
+    def set_rng_origin(self, global_shape, origin):
+        """Draw the noise of local site (x, y, z) with the index of site
+        (x, y, z) + origin of a periodic box of shape (nz, ny, nx)."""
+        gnz, gny, gnx = global_shape
+        oz, oy, ox = origin
+        lib().orcm_set_rng_origin(self._h, gnx, gny, gnz, ox, oy, oz)
 
     def step(self, n=1):
         if lib().orcm_step(self._h, int(n)) != 0:

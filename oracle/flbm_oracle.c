@@ -808,6 +808,8 @@ typedef struct {
     uint64_t seed;
     double *f[ORCM_MAXS], *fn[ORCM_MAXS], *rho[ORCM_MAXS];
     long step;
+    int rng_global;           /* noise drawn with site indices of a larger box */
+    long gnx, gny, gnz, ox, oy, oz;
 } orcm_t;
 
 orcm_t *orcm_create(int lat, int ns, int nx, int ny, int nz, const double *tau, double kT, const double *G,
@@ -876,6 +878,27 @@ void orcm_get_f(const orcm_t *o, double *f)
     for (int s = 0; s < o->ns; s++) memcpy(f + (size_t)s * o->L.Q * o->N, o->f[s], sizeof(double) * o->L.Q * o->N);
 }
 
+/* Treat this box as the block of a periodic gnx * gny * gnz box whose local
+ * site (0,0,0) sits at (ox, oy, oz) (as orc_set_rng_origin). */
+void orcm_set_rng_origin(orcm_t *o, long gnx, long gny, long gnz, long ox, long oy, long oz)
+{
+    o->rng_global = 1;
+    o->gnx = gnx;
+    o->gny = gny;
+    o->gnz = gnz;
+    o->ox = ox;
+    o->oy = oy;
+    o->oz = oz;
+}
+
+static uint32_t rng_site_m(const orcm_t *o, long site)
+{
+    if (!o->rng_global) return (uint32_t)site;
+    long x = site % o->nx, y = (site / o->nx) % o->ny, z = site / ((long)o->nx * o->ny);
+    long gx = (x + o->ox) % o->gnx, gy = (y + o->oy) % o->gny, gz = (z + o->oz) % o->gnz;
+    return (uint32_t)((gz * o->gny + gy) * o->gnx + gx);
+}
+
 static long neighbour_m(const orcm_t *o, long site, const int c[3])
 {
     long x = site % o->nx, y = (site / o->nx) % o->ny, z = site / ((long)o->nx * o->ny);
@@ -937,7 +960,7 @@ static int collide_site_m(const orcm_t *o, long site, double R[ORCM_MAXS][ORC_MA
     for (int d = 0; d < D; d++) {
         double eta[ORCM_MAXS], sum = 0.0;
         for (int s = 0; s < ns; s++) {
-            eta[s] = sqrt(rho[s]) * orc_gaussian(o->seed, (uint32_t)site, (uint32_t)o->step, (uint32_t)s, (uint32_t)(1 + d));
+            eta[s] = sqrt(rho[s]) * orc_gaussian(o->seed, rng_site_m(o, site), (uint32_t)o->step, (uint32_t)s, (uint32_t)(1 + d));
             sum += eta[s];
         }
         for (int s = 0; s < ns; s++) xi[s][1 + d] = amp_d * (eta[s] - rho[s] / rho_t * sum);
@@ -946,7 +969,7 @@ static int collide_site_m(const orcm_t *o, long site, double R[ORCM_MAXS][ORC_MA
         const double lam = 1.0 / o->tau[s];
         for (int a = D + 1; a < Q; a++) {
             double var = (2.0 * lam - lam * lam) * L->N[a] * mu * rho[s];
-            xi[s][a] = sqrt(var) * orc_gaussian(o->seed, (uint32_t)site, (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
+            xi[s][a] = sqrt(var) * orc_gaussian(o->seed, rng_site_m(o, site), (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
         }
     }
     for (int s = 0; s < ns; s++) {

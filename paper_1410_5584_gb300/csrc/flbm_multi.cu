@@ -1,0 +1,507 @@
+// flbm_multi.cu -- the flbm_m* C-ABI: N-species mixtures (arXiv 1410.5584,
+// App. C-D) on one GPU.  Kernels in flbm_multi.cuh.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "flbm_multi.cuh"
+
+struct flbm_mctx {
+    int lat = 0, D = 2, Q = 9, ns = 0;
+    int nx = 0, ny = 0, nz = 1;
+    int64_t N = 0;
+    double tau[flbm::kMaxSpecies] = {}, kT = 0.0, G[flbm::kMaxSpecies][flbm::kMaxSpecies] = {};
+    double rho0[flbm::kMaxSpecies] = {1.0, 1.0, 1.0, 1.0};
+    double lam_d = 1.0;
+    uint64_t seed = 0;
+    int block_x = 128, block_y = 1;
+    // state
+    int64_t step = 0;
+    int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
+    bool initialised = false, faulted = false;
+    // device buffers
+    float *pop = nullptr;
+    float4 *drho = nullptr;
+    unsigned *d_status = nullptr;
+    double *d_obs = nullptr;      // ns * N + D * N doubles
+    double *d_partials = nullptr; // per-block totals
+    size_t partials_cap = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // per-kernel event timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs (start, end), kernel = (index / 2) % 2
+    size_t ev_used = 0;
+    double kernel_ms[2] = {0.0, 0.0};
+    int64_t kernel_launches[2] = {0, 0};
+    char err[512] = {0};
+};
+
+namespace {
+
+using flbm::MStepParams;
+
+const char kNoError[] = "";
+
+flbm_status mfail(flbm_mctx *c, flbm_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        std::vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define MCUDA(ctx, call, what)                                                                            \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return mfail((ctx), FLBM_ECUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+double lat_N(int lat, int a) { return lat == FLBM_D2Q9 ? flbm::D2Q9::Nd(a) : flbm::D3Q19::Nd(a); }
+
+MStepParams make_mparams(const flbm_mctx *c)
+{
+    MStepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nz = c->nz;
+    p.N = (int)c->N;
+    p.block_x = c->block_x;
+    p.block_y = c->block_y;
+    for (int s = 0; s < c->ns; s++)
+        for (int t = 0; t < c->ns; t++) p.G[s][t] = s == t ? 0.0f : (float)c->G[s][t];
+    p.lam_d = (float)c->lam_d;
+    p.hlam_d = (float)(1.0 - 0.5 * c->lam_d);
+    p.amp_d = (float)std::sqrt((2.0 * c->lam_d - c->lam_d * c->lam_d) * c->kT);
+    const double mu = 3.0 * c->kT; // k_B T / c_s^2
+    for (int s = 0; s < c->ns; s++) {
+        const double lb = 1.0 / c->tau[s];
+        for (int a = c->D + 1; a < c->Q; a++) {
+            const double Na = lat_N(c->lat, a);
+            p.cm[s][a] = (float)((1.0 - lb) / Na);
+            p.ceq[s][a] = (float)(lb / Na);
+            p.cphi[s][a] = (float)((1.0 - 0.5 * lb) / Na);
+            p.cxi[s][a] = (float)(std::sqrt((2.0 * lb - lb * lb) * Na * mu) / Na);
+        }
+        p.rho0[s] = (float)c->rho0[s];
+    }
+    p.key0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
+    p.key1 = (uint32_t)(c->seed >> 32);
+    p.step = (uint32_t)c->step;
+    return p;
+}
+
+// Dispatch over (lattice, species count).
+template <class F> cudaError_t dispatch(const flbm_mctx *c, F &&f)
+{
+    using namespace flbm;
+    if (c->lat == FLBM_D2Q9) {
+        switch (c->ns) {
+        case 2: return f(MLaunch<D2Q9, 2>{});
+        case 3: return f(MLaunch<D2Q9, 3>{});
+        case 4: return f(MLaunch<D2Q9, 4>{});
+        }
+    } else {
+        switch (c->ns) {
+        case 2: return f(MLaunch<D3Q19, 2>{});
+        case 3: return f(MLaunch<D3Q19, 3>{});
+        case 4: return f(MLaunch<D3Q19, 4>{});
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t pop_elems(const flbm_mctx *c) { return (size_t)c->ns * c->Q * (size_t)c->N; }
+
+flbm_status ensure_buffers(flbm_mctx *c)
+{
+    if (!c->stream) {
+        MCUDA(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    if (!c->pop) {
+        cudaError_t e = cudaMalloc((void **)&c->pop, pop_elems(c) * sizeof(float));
+        if (e != cudaSuccess) {
+            c->pop = nullptr;
+            return mfail(c, FLBM_ENOMEM, "cudaMalloc of %zu population bytes failed: %s", pop_elems(c) * sizeof(float),
+                         cudaGetErrorString(e));
+        }
+        e = cudaMalloc((void **)&c->drho, (size_t)c->N * sizeof(float4));
+        if (e != cudaSuccess) {
+            c->drho = nullptr;
+            return mfail(c, FLBM_ENOMEM, "cudaMalloc of the density field failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!c->d_status) {
+        MCUDA(c, cudaMalloc((void **)&c->d_status, sizeof(unsigned)), "cudaMalloc(status)");
+        MCUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "cudaMemset(status)");
+    }
+    return FLBM_OK;
+}
+
+flbm_status sync_and_check(flbm_mctx *c)
+{
+    MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    unsigned st = 0;
+    MCUDA(c, cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost), "status read");
+    if (st & flbm::kStatusNonFinite) {
+        c->faulted = true;
+        return mfail(c, FLBM_ENONFINITE, "a density became non-positive or non-finite on the device");
+    }
+    return FLBM_OK;
+}
+
+flbm_status check_ready(flbm_mctx *c)
+{
+    if (!c) return FLBM_EINVAL;
+    if (!c->initialised) return mfail(c, FLBM_ESTATE, "call flbm_minit or flbm_mset_populations first");
+    return FLBM_OK;
+}
+
+cudaEvent_t timing_event(flbm_mctx *c)
+{
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev.push_back(e);
+    }
+    return c->ev[c->ev_used++];
+}
+
+flbm_status drain_timing(flbm_mctx *c)
+{
+    if (c->ev_used == 0) return FLBM_OK;
+    MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float ms = 0.0f;
+        MCUDA(c, cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]), "cudaEventElapsedTime");
+        const int kernel = (int)((k / 2) % 2);
+        c->kernel_ms[kernel] += ms;
+        c->kernel_launches[kernel] += 1;
+    }
+    c->ev_used = 0;
+    return FLBM_OK;
+}
+
+// The density field of the current state.
+flbm_status density_now(flbm_mctx *c, const MStepParams &p)
+{
+    cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::density(c->parity, p, c->pop, c->drho, c->stream); });
+    MCUDA(c, e, "density kernel launch");
+    return FLBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+flbm_status flbm_mcreate(flbm_lattice lat, int nspecies, int nx, int ny, int nz, const double *tau, double kT,
+                         const double *G, uint64_t seed, flbm_mctx **out)
+{
+    if (!out) return FLBM_EINVAL;
+    *out = nullptr;
+    if (lat != FLBM_D2Q9 && lat != FLBM_D3Q19) return FLBM_EINVAL;
+    if (nspecies < 2 || nspecies > flbm::kMaxSpecies || !tau || !G) return FLBM_EINVAL;
+    if (nx < 2 || ny < 2 || ny > 65535) return FLBM_EINVAL;
+    if (lat == FLBM_D2Q9 ? nz != 1 : (nz < 2 || nz > 65535)) return FLBM_EINVAL;
+    if ((int64_t)nx * ny * nz >= (int64_t(1) << 31)) return FLBM_EINVAL;
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return FLBM_EINVAL;
+    double tsum = 0.0;
+    for (int s = 0; s < nspecies; s++) {
+        if (!(tau[s] > 0.5) || !std::isfinite(tau[s])) return FLBM_EINVAL;
+        tsum += tau[s];
+    }
+    for (int s = 0; s < nspecies; s++)
+        for (int t = 0; t < nspecies; t++)
+            if (!std::isfinite(G[s * nspecies + t]) || G[s * nspecies + t] != G[t * nspecies + s]) return FLBM_EINVAL;
+    flbm_mctx *c = new (std::nothrow) flbm_mctx();
+    if (!c) return FLBM_ENOMEM;
+    c->lat = lat;
+    c->D = lat == FLBM_D2Q9 ? 2 : 3;
+    c->Q = lat == FLBM_D2Q9 ? 9 : 19;
+    c->ns = nspecies;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = (int64_t)nx * ny * nz;
+    c->kT = kT;
+    c->seed = seed;
+    for (int s = 0; s < nspecies; s++) {
+        c->tau[s] = tau[s];
+        for (int t = 0; t < nspecies; t++) c->G[s][t] = s == t ? 0.0 : G[s * nspecies + t];
+    }
+    c->lam_d = nspecies / tsum;
+    *out = c;
+    return FLBM_OK;
+}
+
+flbm_status flbm_mset_option(flbm_mctx *c, int key, double v)
+{
+    if (!c) return FLBM_EINVAL;
+    if (key == FLBM_OPT_KERNEL_TIMING) {
+        if (v != 0.0 && v != 1.0) return mfail(c, FLBM_EINVAL, "kernel timing is 0 or 1");
+        if (c->stream) {
+            flbm_status st = drain_timing(c);
+            if (st != FLBM_OK) return st;
+        }
+        c->timing = v != 0.0;
+        c->kernel_ms[0] = c->kernel_ms[1] = 0.0;
+        c->kernel_launches[0] = c->kernel_launches[1] = 0;
+        return FLBM_OK;
+    }
+    if (key == FLBM_OPT_BLOCK_X || key == FLBM_OPT_BLOCK_Y) {
+        const int b = (int)v;
+        if ((double)b != v) return mfail(c, FLBM_EINVAL, "the block shape is an integer");
+        const int bx = key == FLBM_OPT_BLOCK_X ? b : c->block_x, by = key == FLBM_OPT_BLOCK_Y ? b : c->block_y;
+        if ((bx != 32 && bx != 64 && bx != 128) || (by != 1 && by != 2 && by != 4) || bx * by > flbm::kSiteBlockMax)
+            return mfail(c, FLBM_EINVAL, "block shape %d x %d: x in {32, 64, 128}, y in {1, 2, 4}, x y <= 128", bx, by);
+        c->block_x = bx;
+        c->block_y = by;
+        return FLBM_OK;
+    }
+    if (key >= FLBM_OPT_RHO0_SPECIES && key < FLBM_OPT_RHO0_SPECIES + c->ns) {
+        if (c->initialised) return mfail(c, FLBM_ESTATE, "the reference densities are fixed once the state exists");
+        if (!(v > 0.0) || !std::isfinite(v)) return mfail(c, FLBM_EINVAL, "a reference density is positive");
+        c->rho0[key - FLBM_OPT_RHO0_SPECIES] = v;
+        return FLBM_OK;
+    }
+    return mfail(c, FLBM_EINVAL, "unknown option %d for an N-species context", key);
+}
+
+flbm_status flbm_mset_stream(flbm_mctx *c, void *stream)
+{
+    if (!c) return FLBM_EINVAL;
+    if (c->initialised) {
+        MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    }
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    c->stream = (cudaStream_t)stream;
+    c->own_stream = false;
+    if (!c->stream) {
+        MCUDA(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_minit(flbm_mctx *c, const double *rho)
+{
+    if (!c) return FLBM_EINVAL;
+    flbm_status st = ensure_buffers(c);
+    if (st != FLBM_OK) return st;
+    const size_t n = (size_t)c->ns * c->N;
+    std::vector<float> h(n);
+    for (int s = 0; s < c->ns; s++)
+        for (int64_t k = 0; k < c->N; k++) {
+            const double r = rho ? rho[(size_t)s * c->N + k] : c->rho0[s];
+            if (!(r > 0.0) || !std::isfinite(r)) return mfail(c, FLBM_EINVAL, "densities must be positive and finite");
+            h[(size_t)s * c->N + k] = (float)r;
+        }
+    float *d = nullptr;
+    MCUDA(c, cudaMallocAsync((void **)&d, n * sizeof(float), c->stream), "cudaMallocAsync");
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    const MStepParams p = make_mparams(c);
+    if (e == cudaSuccess) e = dispatch(c, [&](auto l) { return decltype(l)::init_rest(p, d, c->pop, c->stream); });
+    cudaFreeAsync(d, c->stream);
+    MCUDA(c, e, "rest-state initialisation");
+    MCUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "cudaMemset(status)");
+    MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    c->step = 0;
+    c->parity = 0;
+    c->faulted = false;
+    c->initialised = true;
+    return FLBM_OK;
+}
+
+flbm_status flbm_mstep(flbm_mctx *c, int64_t n)
+{
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    if (n < 0) return mfail(c, FLBM_EINVAL, "negative step count");
+    for (int64_t k = 0; k < n; k++) {
+        const MStepParams p = make_mparams(c);
+        const int parity = c->parity;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+        if (c->timing) {
+            if (c->ev_used + 4 > 4096) {
+                st = drain_timing(c);
+                if (st != FLBM_OK) return st;
+            }
+            e0 = timing_event(c);
+            e1 = timing_event(c);
+            e2 = timing_event(c);
+            e3 = timing_event(c);
+            if (!e0 || !e1 || !e2 || !e3) return mfail(c, FLBM_ECUDA, "cudaEventCreate failed");
+            MCUDA(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
+        }
+        cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::density(parity, p, c->pop, c->drho, c->stream); });
+        MCUDA(c, e, "density kernel launch");
+        if (c->timing) {
+            MCUDA(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
+            MCUDA(c, cudaEventRecord(e2, c->stream), "cudaEventRecord");
+        }
+        e = dispatch(c, [&](auto l) {
+            return decltype(l)::collide(parity, p, c->pop, c->drho, c->d_status, c->stream);
+        });
+        MCUDA(c, e, "collide kernel launch");
+        if (c->timing) MCUDA(c, cudaEventRecord(e3, c->stream), "cudaEventRecord");
+        c->parity ^= 1;
+        c->step++;
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_msync(flbm_mctx *c)
+{
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    return sync_and_check(c);
+}
+
+flbm_status flbm_mkernel_times(flbm_mctx *c, double ms[2], int64_t launches[2])
+{
+    if (!c) return FLBM_EINVAL;
+    if (c->stream) {
+        flbm_status st = drain_timing(c);
+        if (st != FLBM_OK) return st;
+    }
+    for (int k = 0; k < 2; k++) {
+        if (ms) ms[k] = c->kernel_ms[k];
+        if (launches) launches[k] = c->kernel_launches[k];
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_mget_step(const flbm_mctx *c, int64_t *step)
+{
+    if (!c || !step) return FLBM_EINVAL;
+    *step = c->step;
+    return FLBM_OK;
+}
+
+flbm_status flbm_mmoments(flbm_mctx *c, double *rho, double *u, double *cons)
+{
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    const MStepParams p = make_mparams(c);
+    const int nblk = (int)((c->N + flbm::mkern::kObsBlock - 1) / flbm::mkern::kObsBlock);
+    const size_t ncol = (size_t)c->ns + 3;
+    if (!c->d_obs) MCUDA(c, cudaMalloc((void **)&c->d_obs, (size_t)(c->ns + c->D) * c->N * sizeof(double)), "cudaMalloc(obs)");
+    if (c->partials_cap < (size_t)nblk * ncol) {
+        if (c->d_partials) cudaFree(c->d_partials);
+        c->d_partials = nullptr;
+        MCUDA(c, cudaMalloc((void **)&c->d_partials, (size_t)nblk * ncol * sizeof(double)), "cudaMalloc(partials)");
+        c->partials_cap = (size_t)nblk * ncol;
+    }
+    st = density_now(c, p);
+    if (st != FLBM_OK) return st;
+    double *d_rho = c->d_obs, *d_u = c->d_obs + (size_t)c->ns * c->N;
+    int nb = 0;
+    cudaError_t e = dispatch(c, [&](auto l) {
+        return decltype(l)::observables(c->parity, p, c->pop, c->drho, rho ? d_rho : nullptr, u ? d_u : nullptr,
+                                        c->d_partials, &nb, c->stream);
+    });
+    MCUDA(c, e, "observables kernel launch");
+    st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    if (rho) MCUDA(c, cudaMemcpy(rho, d_rho, (size_t)c->ns * c->N * sizeof(double), cudaMemcpyDeviceToHost), "copy rho");
+    if (u) MCUDA(c, cudaMemcpy(u, d_u, (size_t)c->D * c->N * sizeof(double), cudaMemcpyDeviceToHost), "copy u");
+    if (cons) {
+        // the per-block totals, summed in block order
+        std::vector<double> h((size_t)nb * ncol);
+        MCUDA(c, cudaMemcpy(h.data(), c->d_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "copy totals");
+        for (size_t k = 0; k < ncol; k++) cons[k] = 0.0;
+        for (int b = 0; b < nb; b++)
+            for (size_t k = 0; k < ncol; k++) cons[k] += h[(size_t)b * ncol + k];
+    }
+    return FLBM_OK;
+}
+
+flbm_status flbm_mget_populations(flbm_mctx *c, double *f)
+{
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    if (!f) return mfail(c, FLBM_EINVAL, "null output");
+    const MStepParams p = make_mparams(c);
+    const size_t n = pop_elems(c);
+    float *d = nullptr;
+    MCUDA(c, cudaMallocAsync((void **)&d, n * sizeof(float), c->stream), "cudaMallocAsync");
+    cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::natural(c->parity, p, c->pop, d, c->stream); });
+    std::vector<float> h(n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d, c->stream);
+    MCUDA(c, e, "natural-layout copy");
+    st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    for (size_t k = 0; k < n; k++) f[k] = h[k];
+    return FLBM_OK;
+}
+
+flbm_status flbm_mget_site_populations(flbm_mctx *c, const int64_t *sites, int64_t nsites, double *out)
+{
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    if (nsites < 0 || (nsites > 0 && (!sites || !out))) return mfail(c, FLBM_EINVAL, "bad site list");
+    for (int64_t k = 0; k < nsites; k++)
+        if (sites[k] < 0 || sites[k] >= c->N) return mfail(c, FLBM_EINVAL, "site %lld out of range", (long long)sites[k]);
+    if (nsites == 0) return FLBM_OK;
+    const MStepParams p = make_mparams(c);
+    const size_t nout = (size_t)nsites * c->ns * c->Q;
+    int64_t *d_sites = nullptr;
+    double *d_out = nullptr;
+    MCUDA(c, cudaMallocAsync((void **)&d_sites, (size_t)nsites * sizeof(int64_t), c->stream), "cudaMallocAsync");
+    cudaError_t e = cudaMallocAsync((void **)&d_out, nout * sizeof(double), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_sites, sites, (size_t)nsites * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = dispatch(c, [&](auto l) { return decltype(l)::gather(c->parity, p, c->pop, d_sites, nsites, d_out, c->stream); });
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d_sites, c->stream);
+    if (d_out) cudaFreeAsync(d_out, c->stream);
+    MCUDA(c, e, "site gather");
+    return sync_and_check(c);
+}
+
+flbm_status flbm_mset_populations(flbm_mctx *c, const double *f, int64_t step)
+{
+    if (!c) return FLBM_EINVAL;
+    if (!f || step < 0) return mfail(c, FLBM_EINVAL, "null input or negative step");
+    flbm_status st = ensure_buffers(c);
+    if (st != FLBM_OK) return st;
+    const size_t n = pop_elems(c);
+    std::vector<float> h(n);
+    for (size_t k = 0; k < n; k++) h[k] = (float)f[k];
+    MCUDA(c, cudaMemcpyAsync(c->pop, h.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy populations");
+    MCUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "cudaMemset(status)");
+    MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    c->step = step;
+    c->parity = 0;
+    c->faulted = false;
+    c->initialised = true;
+    return FLBM_OK;
+}
+
+const char *flbm_mlast_error(const flbm_mctx *c) { return c ? c->err : kNoError; }
+
+void flbm_mdestroy(flbm_mctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaFree(c->pop);
+    cudaFree(c->drho);
+    cudaFree(c->d_status);
+    cudaFree(c->d_obs);
+    cudaFree(c->d_partials);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+} // extern "C"

@@ -1,0 +1,540 @@
+// flbm_multi.cuh -- kernels of the N-species update (arXiv 1410.5584, App. C-D),
+// instantiated per (lattice, species count) in the inst_multi_*.cu units.
+//
+// The update is the lattice algorithm of Sec. V B (Eqs. algorithm and lattice
+// finalstep) for NS = 2 .. 4 species sigma, with
+//   - rates lambdabar_a^sigma on the non-conserved modes of each species and one
+//     common momentum rate lambdabar_d (total momentum is conserved only if the
+//     momentum relaxation matrix d^{sigma s} = lambdabar_d (delta - C^s) of
+//     App. C has equal rates),
+//   - mean-field forces between different species only (App. D):
+//     a^sigma(r) = -sum_{s != sigma} G_{sigma s} sum_i w_i rho^s(r + c_i) c_i,
+//   - u = sum_sigma (jbar^sigma + rho^sigma a^sigma / 2) / rho_t,
+//   - momentum noise with covariance (2 lb_d - lb_d^2) kT (rho^sigma delta -
+//     rho^sigma rho^s / rho_t) (the N-species form of Eq. new-noise, local
+//     densities): xi^sigma = A (eta^sigma - C^sigma sum_s eta^s), eta^s =
+//     sqrt(rho^s) g^s, C = rho / rho_t, A = sqrt((2 lb_d - lb_d^2) kT), which
+//     has exactly that covariance and sums to zero over the species,
+//   - the other modes' noise with the per-species variances of Eq. new-noise.
+// Unit Gaussian g of mode a of species s at (site, step): lane a mod 4 of
+// Box-Muller on Philox4x32-10 with counter (site, step, s, a/4), as in the
+// two-species kernels.
+//
+// Storage: float populations, the same in-place "AA" streaming and plane
+// layout [s][i][site] as the two-species kernels (flbm_kernels.cuh); the
+// kernels work on deviations f_i - w_i rho0^s.  The density field holds one
+// float4 per site: the deviations rho^s - rho0^s of up to four species.
+#pragma once
+#include "flbm_internal.h"
+#include "flbm_kernels.cuh"
+#include "flbm_lattice.cuh"
+#include "flbm_noise.cuh"
+#include "flbm_transform.cuh"
+
+namespace flbm {
+
+constexpr int kMaxSpecies = 4;
+
+// Everything one step of an N-species box needs (kernel parameter space).
+struct MStepParams {
+    int nx, ny, nz, N;
+    int block_x, block_y;
+    float G[kMaxSpecies][kMaxSpecies]; // couplings between different species (zero diagonal)
+    float lam_d, hlam_d;               // common momentum rate and 1 - lam_d / 2 (Eq. forcerenorm)
+    float amp_d;                       // sqrt((2 lam_d - lam_d^2) kT)
+    // non-conserved modes a > D of species s with 1/N_a folded in:
+    // m*_a / N_a = cm m_a + ceq m^eq_a + cphi Phi_a + cxi sqrt(rho^s) g_a
+    float cm[kMaxSpecies][kMaxQ], ceq[kMaxSpecies][kMaxQ], cphi[kMaxSpecies][kMaxQ], cxi[kMaxSpecies][kMaxQ];
+    float rho0[kMaxSpecies];           // reference densities (base of the stored deviations)
+    uint32_t key0, key1, step;
+};
+
+template <class T> struct MPlanes {
+    T *ptr[kMaxSpecies * kMaxQ];
+    template <class L> __device__ __forceinline__ T *plane(int s, int j) const { return ptr[s * L::Q + j]; }
+};
+
+// Launchers of one (lattice, species count) pair; asynchronous on `st`, return
+// the launch error.
+template <class L, int NS> struct MLaunch {
+    // density deviations of every site (float4 per site)
+    static cudaError_t density(int parity, const MStepParams &p, const float *pop, float4 *drho, cudaStream_t st);
+    // force + moment collision + noise + in-place streaming of one step
+    static cudaError_t collide(int parity, const MStepParams &p, float *pop, const float4 *drho, unsigned *status,
+                               cudaStream_t st);
+    // per-site rho^s and u (either may be NULL) in double, per-block FP64 partial
+    // totals [nblocks][NS + 3] of (rho^s, jbar_t + F_t / 2); needs drho of the state
+    static cudaError_t observables(int parity, const MStepParams &p, const float *pop, const float4 *drho,
+                                   double *rho, double *u, double *partials, int *nblocks, cudaStream_t st);
+    // natural-layout copy [NS][Q][N] of the populations
+    static cudaError_t natural(int parity, const MStepParams &p, const float *pop, float *out, cudaStream_t st);
+    // natural-layout populations of selected sites: out[k][s][i] (doubles)
+    static cudaError_t gather(int parity, const MStepParams &p, const float *pop, const int64_t *sites, int64_t n,
+                              double *out, cudaStream_t st);
+    // rest state f_i = w_i rho^s from float densities [NS][N]
+    static cudaError_t init_rest(const MStepParams &p, const float *rho, float *pop, cudaStream_t st);
+};
+
+namespace mkern {
+
+constexpr int kObsBlock = 128;
+
+__device__ __forceinline__ kern::Nbr make_nbr(const MStepParams &p, int x, int y, int z)
+{
+    kern::Nbr n;
+    n.nx = p.nx;
+    n.ny = p.ny;
+    n.xs[0] = x == 0 ? p.nx - 1 : x - 1;
+    n.xs[1] = x;
+    n.xs[2] = x == p.nx - 1 ? 0 : x + 1;
+    n.ys[0] = y == 0 ? p.ny - 1 : y - 1;
+    n.ys[1] = y;
+    n.ys[2] = y == p.ny - 1 ? 0 : y + 1;
+    n.zs[0] = z == 0 ? p.nz - 1 : z - 1;
+    n.zs[1] = z;
+    n.zs[2] = z == p.nz - 1 ? 0 : z + 1;
+    return n;
+}
+
+__device__ __forceinline__ float get4(const float4 &v, int t)
+{
+    return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
+}
+
+// Unit Gaussians of the lanes of one Philox block (counter (site, step, s,
+// slot)) that MASK selects (bit l = lane l); lanes (0, 1) and (2, 3) are the
+// cosine and sine outputs of one Box-Muller pair each.
+template <int MASK>
+__device__ __forceinline__ void slot_gaussians(uint32_t site, uint32_t step, uint32_t s, uint32_t slot, uint32_t k0,
+                                               uint32_t k1, float (&g)[4])
+{
+    const uint4 x = philox4x32_10(make_uint4(site, step, s, slot), k0, k1);
+    if constexpr ((MASK & 3) != 0) box_muller(x.x, x.y, 1.0f, g[0], g[1]);
+    if constexpr ((MASK & 12) != 0) box_muller(x.z, x.w, 1.0f, g[2], g[3]);
+}
+
+// Loads of the NS Q pre-collision deviations of a site.
+template <class L, int NS, int PARITY, class P>
+__device__ __forceinline__ void load_site(const MStepParams &p, const P &planes, const kern::Nbr &nb,
+                                          float (&d)[NS][L::Q])
+{
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            const float v = __ldg(planes.template plane<L>(s, kern::read_slot<L, PARITY, i>()) +
+                                  kern::read_site<L, PARITY, i>(nb));
+            d[s][i] = __fsub_rn(v, wi * p.rho0[s]);
+        });
+    });
+}
+
+template <class L, int NS, int PARITY>
+__global__ void __launch_bounds__(kSiteBlockMax) k_mdensity(const MStepParams p, const MPlanes<const float> planes,
+                                                            float4 *__restrict__ drho)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const kern::Nbr nb = make_nbr(p, x, y, blockIdx.z);
+    float d[NS][L::Q];
+    load_site<L, NS, PARITY>(p, planes, nb, d);
+    float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        float m[L::Q];
+        // the collide kernel computes its own densities with this same expression
+        Transform<L>::forward(d[s], m);
+        r[s] = m[0];
+    });
+    drho[nb.at(0, 0, 0)] = make_float4(r[0], r[1], r[2], r[3]);
+}
+
+template <class L, int NS, int PARITY>
+__global__ void __launch_bounds__(kSiteBlockMax) k_mcollide(const MStepParams p, const MPlanes<float> planes,
+                                                            const float4 *__restrict__ drho,
+                                                            unsigned *__restrict__ status)
+{
+    constexpr int Q = L::Q, D = L::D;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const kern::Nbr nb = make_nbr(p, x, y, blockIdx.z);
+    const int site = nb.at(0, 0, 0);
+
+    // 1. moments of every species (Eq. modes-discrete); rho^s = rhobar^s
+    float m[NS][Q], rs[NS];
+    {
+        float d[NS][Q];
+        load_site<L, NS, PARITY>(p, planes, nb, d);
+        static_for<NS>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            Transform<L>::forward(d[s], m[s]);
+            rs[s] = p.rho0[s] + m[s][0];
+        });
+    }
+
+    // 2. mean-field forces between different species (App. D, Eq. FORCESTRUCTURE
+    // per pair): F[t][d] = sum_i w_i c_id rho^t(r + c_i) on the deviations (the
+    // reference part sums to zero), then a^s = -sum_{t != s} G_st F[t]
+    float F[NS][3];
+    static_for<NS>([&](auto tc) {
+        constexpr int t = decltype(tc)::value;
+        F[t][0] = F[t][1] = F[t][2] = 0.0f;
+    });
+    static_for<Q - 1>([&](auto kc) {
+        constexpr int i = decltype(kc)::value + 1;
+        constexpr float wi = (float)L::wd(i);
+        const float4 rn = __ldg(drho + nb.at(L::cx(i), L::cy(i), L::cz(i)));
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int cd = comp<L>(i, d);
+            if constexpr (cd != 0) {
+                constexpr float cw = (float)cd * wi;
+                static_for<NS>([&](auto tc) {
+                    constexpr int t = decltype(tc)::value;
+                    F[t][d] = fmaf(cw, get4(rn, t), F[t][d]);
+                });
+            }
+        });
+    });
+    float acc[NS][3];
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            float a = 0.0f;
+            static_for<NS>([&](auto tc) {
+                constexpr int t = decltype(tc)::value;
+                if constexpr (t != s) a = fmaf(p.G[s][t], F[t][d], a);
+            });
+            acc[s][d] = -a;
+        });
+    });
+
+    // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
+    float rt = 0.0f;
+    bool bad = false;
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        rt += rs[s];
+        bad |= !(rs[s] > 0.0f);
+    });
+    if (bad || !isfinite(rt)) atomicOr(status, kStatusNonFinite);
+    const float irt = __frcp_rn(rt);
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    static_for<D>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        float j = 0.0f;
+        static_for<NS>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            j += m[s][1 + d] + 0.5f * rs[s] * acc[s][d];
+        });
+        u[d] = j * irt;
+    });
+
+    // 4. Philox slot 0 of every species: modes 1 .. 3 (the momenta; for D2Q9
+    // also mode 3, kept for step 6).  Projected momentum noise.
+    float g0[NS][4], sq[NS];
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        slot_gaussians<0xE>((uint32_t)site, p.step, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
+        sq[s] = rs[s] * rsqrtf(rs[s]); // sqrt(rho^s); rho^s > 0 on every valid state
+    });
+    float xi[NS][3];
+    static_for<D>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        float sum = 0.0f;
+        static_for<NS>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            sum = fmaf(sq[s], g0[s][1 + d], sum);
+        });
+        const float cs = sum * irt;
+        static_for<NS>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            xi[s][d] = p.amp_d * fmaf(-rs[s], cs, sq[s] * g0[s][1 + d]);
+        });
+    });
+
+    // 5. momentum modes: common rate; species velocity for Phi (Eq. alg-mom)
+    float v[NS][3];
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        const float irs = __frcp_rn(rs[s]);
+        v[s][2] = 0.0f;
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int a = 1 + d;
+            const float R = p.lam_d * (rs[s] * u[d] - m[s][a]) + p.hlam_d * rs[s] * acc[s][d] + xi[s][d];
+            v[s][d] = (m[s][a] + 0.5f * R) * irs;
+            m[s][a] += R;
+        });
+    });
+
+    // 6. transport and ghost modes of each species, back-projection, mass
+    // closure on the stored values, streaming
+    float X[Q];
+    Closure<L>::eq(u, X);
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        float g[Q];
+        static_for<(Q + 3) / 4 - 1>([&](auto kc) {
+            constexpr int slot = decltype(kc)::value + 1;
+            constexpr int lanes = Q - 4 * slot < 4 ? Q - 4 * slot : 4;
+            constexpr int mask = (1 << lanes) - 1;
+            float gs[4];
+            slot_gaussians<mask>((uint32_t)site, p.step, (uint32_t)s, (uint32_t)slot, p.key0, p.key1, gs);
+            static_for<lanes>([&](auto lc) {
+                constexpr int l = decltype(lc)::value;
+                g[4 * slot + l] = gs[l];
+            });
+        });
+        if constexpr (D + 1 < 4) g[3] = g0[s][3];
+        float Y[Q];
+        Closure<L>::force(acc[s], v[s], Y);
+        float mu[Q], fo[Q];
+        mu[0] = m[s][0];
+        static_for<D>([&](auto dc) {
+            constexpr int a = decltype(dc)::value + 1;
+            constexpr float invN = (float)(1.0 / L::Nd(a));
+            mu[a] = invN * m[s][a];
+        });
+        static_for<Q - D - 1>([&](auto kc) {
+            constexpr int a = decltype(kc)::value + D + 1;
+            float t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * (sq[s] * g[a]));
+            if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
+            mu[a] = t;
+        });
+        float yv[Q];
+        Transform<L>::backward(mu, yv);
+        // the moving populations are stored first and replaced by the deviations
+        // their words load as; the rest population takes m0 minus what they hold
+        float word[Q];
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
+            constexpr float wi = (float)L::wd(i);
+            const float base = wi * p.rho0[s];
+            word[i] = __fmaf_rn(wi, yv[i], base);
+            fo[i] = __fsub_rn(word[i], base);
+        });
+        word[0] = __fadd_rn((float)L::wd(0) * p.rho0[s], Transform<L>::rest_closing_mass(fo, m[s][0]));
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            planes.template plane<L>(s, kern::write_slot<L, PARITY, i>())[kern::write_site<L, PARITY, i>(nb)] = word[i];
+        });
+    });
+}
+
+// Observables in double from the stored floats; the forces from the float
+// density deviations.  Per-block totals in a fixed-order tree.
+template <class L, int NS, int PARITY>
+__global__ void __launch_bounds__(kObsBlock) k_mobservables(const MStepParams p, const MPlanes<const float> planes,
+                                                            const float4 *__restrict__ drho, double *rho_out,
+                                                            double *u_out, double *partials)
+{
+    constexpr int Q = L::Q, D = L::D, NC = NS + 3;
+    __shared__ double sh[NC][kObsBlock];
+    const int site = blockIdx.x * kObsBlock + threadIdx.x;
+    double tot[NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) tot[k] = 0.0;
+    if (site < p.N) {
+        const int x = site % p.nx, y = (site / p.nx) % p.ny, z = site / (p.nx * p.ny);
+        const kern::Nbr nb = make_nbr(p, x, y, z);
+        double F[NS][3] = {};
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
+            const float4 rn = drho[nb.at(L::cx(i), L::cy(i), L::cz(i))];
+            static_for<NS>([&](auto tc) {
+                constexpr int t = decltype(tc)::value;
+                static_for<D>([&](auto dc) {
+                    constexpr int d = decltype(dc)::value;
+                    F[t][d] += L::wd(i) * comp<L>(i, d) * (double)get4(rn, t);
+                });
+            });
+        });
+        double rt = 0.0, j[3] = {0.0, 0.0, 0.0};
+        static_for<NS>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            double r = 0.0, js[3] = {0.0, 0.0, 0.0};
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                const double f = planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
+                r += f;
+                js[0] += L::cx(i) * f;
+                js[1] += L::cy(i) * f;
+                js[2] += L::cz(i) * f;
+            });
+            if (rho_out) rho_out[(size_t)s * p.N + site] = r;
+            tot[s] = r;
+            rt += r;
+            static_for<D>([&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                double a = 0.0;
+                static_for<NS>([&](auto tc) {
+                    constexpr int t = decltype(tc)::value;
+                    if constexpr (t != s) a -= (double)p.G[s][t] * F[t][d];
+                });
+                j[d] += js[d] + 0.5 * r * a;
+            });
+        });
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            if (u_out) u_out[(size_t)d * p.N + site] = j[d] / rt;
+            tot[NS + d] = j[d];
+        });
+    }
+#pragma unroll
+    for (int k = 0; k < NC; k++) sh[k][threadIdx.x] = tot[k];
+    __syncthreads();
+    for (int w = kObsBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < NC; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < NC) partials[(size_t)blockIdx.x * NC + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+template <class L, int NS, int PARITY>
+__global__ void k_mnatural(const MStepParams p, const MPlanes<const float> planes, float *__restrict__ out)
+{
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.N) return;
+    const int x = site % p.nx, y = (site / p.nx) % p.ny, z = site / (p.nx * p.ny);
+    const kern::Nbr nb = make_nbr(p, x, y, z);
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            out[(size_t)(s * L::Q + i) * p.N + site] =
+                planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
+        });
+    });
+}
+
+template <class L, int NS, int PARITY>
+__global__ void k_mgather(const MStepParams p, const MPlanes<const float> planes, const int64_t *__restrict__ sites,
+                          int64_t n, double *__restrict__ out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int site = (int)sites[k];
+    const int x = site % p.nx, y = (site / p.nx) % p.ny, z = site / (p.nx * p.ny);
+    const kern::Nbr nb = make_nbr(p, x, y, z);
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            out[(k * NS + s) * L::Q + i] =
+                planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
+        });
+    });
+}
+
+template <class L, int NS>
+__global__ void k_minit_rest(const MStepParams p, const float *__restrict__ rho, float *__restrict__ pop)
+{
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.N) return;
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        const float r = rho[(size_t)s * p.N + site];
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            pop[(size_t)(s * L::Q + i) * p.N + site] = __fmul_rn((float)L::wd(i), r);
+        });
+    });
+}
+
+template <class T> MPlanes<T> mplanes(T *pop, int ns, int Q, int N)
+{
+    MPlanes<T> t{};
+    for (int k = 0; k < ns * Q; k++) t.ptr[k] = pop + (size_t)k * (size_t)N;
+    return t;
+}
+
+inline dim3 msite_block(const MStepParams &p)
+{
+    const int wx = ((p.nx + 31) / 32) * 32;
+    return dim3(p.block_x < wx ? p.block_x : wx, p.block_y);
+}
+inline dim3 msite_grid(const MStepParams &p, dim3 b)
+{
+    return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz);
+}
+
+} // namespace mkern
+
+template <class L, int NS>
+cudaError_t MLaunch<L, NS>::density(int parity, const MStepParams &p, const float *pop, float4 *drho, cudaStream_t st)
+{
+    const dim3 b = mkern::msite_block(p), g = mkern::msite_grid(p, b);
+    const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
+    if (parity == 0) mkern::k_mdensity<L, NS, 0><<<g, b, 0, st>>>(p, planes, drho);
+    else mkern::k_mdensity<L, NS, 1><<<g, b, 0, st>>>(p, planes, drho);
+    return cudaGetLastError();
+}
+
+template <class L, int NS>
+cudaError_t MLaunch<L, NS>::collide(int parity, const MStepParams &p, float *pop, const float4 *drho,
+                                    unsigned *status, cudaStream_t st)
+{
+    const dim3 b = mkern::msite_block(p), g = mkern::msite_grid(p, b);
+    const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
+    if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, 0, st>>>(p, planes, drho, status);
+    else mkern::k_mcollide<L, NS, 1><<<g, b, 0, st>>>(p, planes, drho, status);
+    return cudaGetLastError();
+}
+
+template <class L, int NS>
+cudaError_t MLaunch<L, NS>::observables(int parity, const MStepParams &p, const float *pop, const float4 *drho,
+                                        double *rho, double *u, double *partials, int *nblocks, cudaStream_t st)
+{
+    const int nb = (p.N + mkern::kObsBlock - 1) / mkern::kObsBlock;
+    *nblocks = nb;
+    const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
+    if (parity == 0) mkern::k_mobservables<L, NS, 0><<<nb, mkern::kObsBlock, 0, st>>>(p, planes, drho, rho, u, partials);
+    else mkern::k_mobservables<L, NS, 1><<<nb, mkern::kObsBlock, 0, st>>>(p, planes, drho, rho, u, partials);
+    return cudaGetLastError();
+}
+
+template <class L, int NS>
+cudaError_t MLaunch<L, NS>::natural(int parity, const MStepParams &p, const float *pop, float *out, cudaStream_t st)
+{
+    const int nb = (p.N + 127) / 128;
+    const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
+    if (parity == 0) mkern::k_mnatural<L, NS, 0><<<nb, 128, 0, st>>>(p, planes, out);
+    else mkern::k_mnatural<L, NS, 1><<<nb, 128, 0, st>>>(p, planes, out);
+    return cudaGetLastError();
+}
+
+template <class L, int NS>
+cudaError_t MLaunch<L, NS>::gather(int parity, const MStepParams &p, const float *pop, const int64_t *sites,
+                                   int64_t n, double *out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
+    if (parity == 0) mkern::k_mgather<L, NS, 0><<<nb, 128, 0, st>>>(p, planes, sites, n, out);
+    else mkern::k_mgather<L, NS, 1><<<nb, 128, 0, st>>>(p, planes, sites, n, out);
+    return cudaGetLastError();
+}
+
+template <class L, int NS>
+cudaError_t MLaunch<L, NS>::init_rest(const MStepParams &p, const float *rho, float *pop, cudaStream_t st)
+{
+    mkern::k_minit_rest<L, NS><<<(p.N + 127) / 128, 128, 0, st>>>(p, rho, pop);
+    return cudaGetLastError();
+}
+
+#define FLBM_MULTI_EXTERN(L)                                                                             \
+    extern template struct MLaunch<L, 2>;                                                                \
+    extern template struct MLaunch<L, 3>;                                                                \
+    extern template struct MLaunch<L, 4>;
+FLBM_MULTI_EXTERN(D2Q9)
+FLBM_MULTI_EXTERN(D3Q19)
+#undef FLBM_MULTI_EXTERN
+
+} // namespace flbm

@@ -40,6 +40,7 @@ OPT_BLOCK_X = 17
 OPT_BLOCK_Y = 18
 SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
 OPT_LAMBDA_MODE = 1000
+OPT_RHO0_SPECIES = 2000
 OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
                 "rho0_a": OPT_RHO0_A, "rho0_b": OPT_RHO0_B, "noise_rho": OPT_NOISE_RHO,
                 "force_velocity": OPT_FORCE_VELOCITY, "sf_axis": OPT_SF_AXIS,
@@ -120,6 +121,20 @@ def lib():
             "flbm_batch_create": (i32, [i32, i32, ctypes.POINTER(RepParams), ctypes.POINTER(vp)]),
             "flbm_batch_replica": (i32, [vp, i32, ctypes.POINTER(vp)]),
             "flbm_batch_size": (i32, [vp, ctypes.POINTER(ctypes.c_int), i64p]),
+            "flbm_mcreate": (i32, [i32, i32, i32, i32, i32, dp, dbl, dp, u64, ctypes.POINTER(vp)]),
+            "flbm_mset_option": (i32, [vp, i32, dbl]),
+            "flbm_mset_stream": (i32, [vp, vp]),
+            "flbm_minit": (i32, [vp, dp]),
+            "flbm_mstep": (i32, [vp, i64]),
+            "flbm_msync": (i32, [vp]),
+            "flbm_mkernel_times": (i32, [vp, dp, i64p]),
+            "flbm_mget_step": (i32, [vp, i64p]),
+            "flbm_mmoments": (i32, [vp, dp, dp, dp]),
+            "flbm_mget_populations": (i32, [vp, dp]),
+            "flbm_mset_populations": (i32, [vp, dp, i64]),
+            "flbm_mget_site_populations": (i32, [vp, i64p, i64, dp]),
+            "flbm_mlast_error": (ctypes.c_char_p, [vp]),
+            "flbm_mdestroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -140,6 +155,12 @@ def version() -> str:
 def check(handle, status):
     if status != OK:
         msg = lib().flbm_last_error(handle).decode(errors="replace") if handle else ""
+        raise FlbmError(status, msg)
+
+
+def mcheck(handle, status):
+    if status != OK:
+        msg = lib().flbm_mlast_error(handle).decode(errors="replace") if handle else ""
         raise FlbmError(status, msg)
 
 
@@ -443,6 +464,113 @@ class Lattice(_Context):
     def close(self):
         if getattr(self, "_h", None):
             lib().flbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MultiLattice:
+    """One periodic box of 2 .. 4 species (App. C-D) on the GPU (a flbm_mctx):
+    per-species relaxation times ``tau``, symmetric couplings ``G``
+    (nspecies x nspecies, diagonal ignored).  The context owns its device
+    memory; the work runs on ``stream`` (a ``torch.cuda.Stream``; a dedicated
+    one by default)."""
+
+    def __init__(self, lattice, nspecies, nx, ny, nz=1, tau=None, kT=0.0, G=None, seed=1, rho0=None,
+                 device="cuda:0", stream=None, block=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device visible: flbm runs on the GPU only")
+        self.lattice, self.ns = int(lattice), int(nspecies)
+        self.nx, self.ny = int(nx), int(ny)
+        self.nz = 1 if self.lattice == D2Q9 else int(nz)
+        self.D = 2 if self.lattice == D2Q9 else 3
+        self.Q = 9 if self.lattice == D2Q9 else 19
+        self.N = self.nx * self.ny * self.nz
+        tau = np.ascontiguousarray(np.ones(self.ns) if tau is None else tau, dtype=np.float64)
+        G = np.ascontiguousarray(np.zeros((self.ns, self.ns)) if G is None else G, dtype=np.float64)
+        if tau.size != self.ns or G.size != self.ns * self.ns:
+            raise ValueError("tau needs one value per species and G nspecies x nspecies")
+        self._h = None
+        h = ctypes.c_void_p()
+        mcheck(None, lib().flbm_mcreate(self.lattice, self.ns, self.nx, self.ny, self.nz, _dp(tau), float(kT),
+                                        _dp(G.ravel()), int(seed) & (2**64 - 1), ctypes.byref(h)))
+        self._h = h
+        if rho0 is not None:
+            for s, r in enumerate(rho0):
+                self.set_option(OPT_RHO0_SPECIES + s, r)
+        if block is not None:
+            self.set_option(OPT_BLOCK_X, block[0])
+            self.set_option(OPT_BLOCK_Y, block[1])
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        mcheck(self._h, lib().flbm_mset_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def set_option(self, key, value):
+        mcheck(self._h, lib().flbm_mset_option(self._h, int(key), float(value)))
+
+    def init(self, rho=None):
+        """Rest state from host densities [nspecies][z][y][x] (None: the reference densities)."""
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).ravel()
+        if r is not None and r.size != self.ns * self.N:
+            raise ValueError("densities need nspecies values per site")
+        mcheck(self._h, lib().flbm_minit(self._h, _dp(r)))
+
+    def step(self, n=1):
+        mcheck(self._h, lib().flbm_mstep(self._h, int(n)))
+
+    def sync(self):
+        mcheck(self._h, lib().flbm_msync(self._h))
+
+    @property
+    def step_count(self):
+        v = ctypes.c_int64()
+        mcheck(self._h, lib().flbm_mget_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    def kernel_times(self):
+        ms = np.zeros(2)
+        n = np.zeros(2, dtype=np.int64)
+        mcheck(self._h, lib().flbm_mkernel_times(self._h, _dp(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return {"density": ms[0], "collide": ms[1]}, {"density": int(n[0]), "collide": int(n[1])}
+
+    def moments(self):
+        """(rho [nspecies][z][y][x], u [D][z][y][x], cons [nspecies + 3])"""
+        rho = np.empty(self.ns * self.N)
+        u = np.empty(self.D * self.N)
+        cons = np.empty(self.ns + 3)
+        mcheck(self._h, lib().flbm_mmoments(self._h, _dp(rho), _dp(u), _dp(cons)))
+        shp = (self.nz, self.ny, self.nx)
+        return rho.reshape((self.ns,) + shp), u.reshape((self.D,) + shp), cons
+
+    def get_populations(self):
+        f = np.empty(self.ns * self.Q * self.N)
+        mcheck(self._h, lib().flbm_mget_populations(self._h, _dp(f)))
+        return f.reshape(self.ns, self.Q, self.nz, self.ny, self.nx)
+
+    def site_populations(self, sites):
+        """Natural-layout populations [len(sites)][nspecies][Q] of the given site indices."""
+        sites = np.ascontiguousarray(sites, dtype=np.int64).ravel()
+        out = np.empty(sites.size * self.ns * self.Q)
+        mcheck(self._h, lib().flbm_mget_site_populations(
+            self._h, sites.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), sites.size, _dp(out)))
+        return out.reshape(sites.size, self.ns, self.Q)
+
+    def set_populations(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        if f.size != self.ns * self.Q * self.N:
+            raise ValueError("populations need nspecies * Q values per site")
+        mcheck(self._h, lib().flbm_mset_populations(self._h, _dp(f), int(step)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().flbm_mdestroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -138,3 +138,49 @@ def test_batch_create_validates_replicas(lib):
         lib.flbm_destroy(v)                             # a view is not destroyed on its own
     finally:
         lib.flbm_destroy(h)
+
+
+def _mcreate(lib, lat, ns, nx, ny, nz, tau, kT, G):
+    t = (ctypes.c_double * len(tau))(*tau)
+    g = (ctypes.c_double * len(G))(*G)
+    h = ctypes.c_void_p()
+    st = lib.flbm_mcreate(lat, ns, nx, ny, nz, t, kT, g, 7, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("lat,ns,nz,tau,kT,G", [
+    (0, 1, 1, [1.0], 1e-4, [0.0]),                                       # one species
+    (0, 5, 1, [1.0] * 5, 1e-4, [0.0] * 25),                              # more than four
+    (0, 3, 2, [1.0] * 3, 1e-4, [0.0] * 9),                               # D2Q9 needs nz = 1
+    (0, 3, 1, [1.0, 0.5, 1.0], 1e-4, [0.0] * 9),                         # tau <= 1/2
+    (0, 3, 1, [1.0] * 3, -1.0, [0.0] * 9),                               # kT < 0
+    (0, 3, 1, [1.0] * 3, 1e-4, [0, 0.1, 0, 0.2, 0, 0, 0, 0, 0]),         # G not symmetric
+    (0, 2, 1, [1.0] * 2, 1e-4, [0, float("inf"), float("inf"), 0]),      # G not finite
+    (3, 3, 1, [1.0] * 3, 1e-4, [0.0] * 9),                               # unknown lattice
+])
+def test_multi_create_rejects_invalid_arguments(lib, lat, ns, nz, tau, kT, G):
+    st, h = _mcreate(lib, lat, ns, 8, 8, nz, tau, kT, G)
+    assert st == F.EINVAL
+    assert not h.value
+
+
+def test_multi_options_and_order_are_validated(lib):
+    st, h = _mcreate(lib, 1, 3, 8, 6, 4, [1.0, 0.8, 1.2], 1e-4, [0, 0.1, 0.2, 0.1, 0, 0.3, 0.2, 0.3, 0])
+    assert st == F.OK
+    try:
+        assert lib.flbm_mset_option(h, F.OPT_RHO0_SPECIES + 2, 0.7) == F.OK
+        assert lib.flbm_mset_option(h, F.OPT_RHO0_SPECIES + 3, 0.7) == F.EINVAL   # only 3 species
+        assert lib.flbm_mset_option(h, F.OPT_RHO0_SPECIES, 0.0) == F.EINVAL
+        assert lib.flbm_mset_option(h, F.OPT_KERNEL_TIMING, 2) == F.EINVAL
+        assert lib.flbm_mset_option(h, F.OPT_BLOCK_X, 64) == F.OK
+        assert lib.flbm_mset_option(h, F.OPT_BLOCK_Y, 4) == F.EINVAL              # 64 x 4 > 128
+        assert lib.flbm_mset_option(h, F.OPT_STORAGE, 1) == F.EINVAL              # float storage only
+        assert b"unknown option" in lib.flbm_mlast_error(h)
+        assert lib.flbm_mstep(h, 1) == F.ESTATE                                    # before init
+        step = ctypes.c_int64(-1)
+        assert lib.flbm_mget_step(h, ctypes.byref(step)) == F.OK and step.value == 0
+    finally:
+        lib.flbm_mdestroy(h)
+    assert lib.flbm_mlast_error(None) == b""
+    assert lib.flbm_mstep(None, 1) == F.EINVAL
+    lib.flbm_mdestroy(None)

@@ -148,3 +148,38 @@ def test_three_species_structure_factors(g):
             cont = np.array([theory.multi_sk(kT, rhos, G, np.sinc(kk / np.pi))[s, t] for kk in k[low]]).mean()
             got = B[:, s, t, low].mean(axis=1)
             assert abs(got.mean() - cont) < 4 * got.std(ddof=1) / np.sqrt(len(got)) + 0.02 * scale
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q9, (1, 5, 7)), (oracle.D3Q19, (4, 5, 6))])
+def test_block_with_rng_origin_reproduces_the_large_box(lat, shape):
+    """A 3^D block updated with the noise indices of its place in a larger
+    box gives, for the block's centre site, exactly the large box's
+    post-collision values f_i(r + c_i)."""
+    nz, ny, nx = shape
+    ns = 3
+    c, w, T, N = oracle.tables(lat)
+    Q, D = len(w), (2 if lat == oracle.D2Q9 else 3)
+    G = np.array([[0, 0.3, 0.5], [0.3, 0, 0.2], [0.5, 0.2, 0]])
+    tau = [1.0, 0.8, 1.25]
+    f0 = _random_multi_state(lat, ns, shape, [1.0, 0.8, 0.6], 9)
+    big = oracle.MultiOracle(lat, ns, nx, ny, nz, tau, 1e-4, G, 5)
+    big.set_f(f0, step=17)
+    big.step(1)
+    fb_all = big.get_f()
+    z, y, x = (nz // 2 if D == 3 else 0), 2, 3
+    bz = 3 if D == 3 else 1
+    fb = np.zeros((ns, Q, bz, 3, 3))
+    for dz in (range(-1, 2) if D == 3 else (0,)):
+        for dy in range(-1, 2):
+            for dx in range(-1, 2):
+                fb[:, :, dz + 1 if D == 3 else 0, dy + 1, dx + 1] = f0[:, :, (z + dz) % nz, (y + dy) % ny, (x + dx) % nx]
+    blk = oracle.MultiOracle(lat, ns, 3, 3, bz, tau, 1e-4, G, 5)
+    blk.set_rng_origin(shape, ((z - 1) % nz if D == 3 else 0, (y - 1) % ny, (x - 1) % nx))
+    blk.set_f(fb, step=17)
+    blk.step(1)
+    fo = blk.get_f()
+    cz = 1 if D == 3 else 0
+    for i in range(Q):
+        got = fo[:, i, (cz + c[i, 2]) % bz, 1 + c[i, 1], 1 + c[i, 0]]
+        want = fb_all[:, i, (z + c[i, 2]) % nz, (y + c[i, 1]) % ny, (x + c[i, 0]) % nx]
+        assert np.array_equal(got, want), i
