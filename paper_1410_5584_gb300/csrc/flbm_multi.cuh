@@ -151,29 +151,64 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mdensity(const MStepParams p,
     drho[nb.at(0, 0, 0)] = make_float4(r[0], r[1], r[2], r[3]);
 }
 
+// Whether the collide kernel parks each site's moments in shared memory (three
+// or more species: the register footprint stays that of one species at a
+// time) or holds them in registers (two species, where that is faster).
+template <int NS> constexpr bool kParkMoments = NS >= 3;
+
+// Shared-memory bytes of one collide block of `threads` threads: the NS Q
+// moments of each thread's site, [s][a][thread] (consecutive threads on
+// consecutive banks); none when they stay in registers.
+template <class L, int NS> constexpr size_t collide_smem(int threads)
+{
+    return kParkMoments<NS> ? (size_t)NS * L::Q * threads * 4 : 0;
+}
+
+// One step of one site: the populations of all species are loaded once and
+// their moments computed; only each species' density and momentum stay in
+// registers, the rest is parked (or kept in registers for two species);
+// forces, the baricentric velocity and the projected momentum noise follow;
+// then each species in turn is collided and streamed.  No barrier: a thread
+// reads back only its own slots.
 template <class L, int NS, int PARITY>
-__global__ void __launch_bounds__(kSiteBlockMax) k_mcollide(const MStepParams p, const MPlanes<float> planes,
-                                                            const float4 *__restrict__ drho,
-                                                            unsigned *__restrict__ status)
+__global__ void __launch_bounds__(kSiteBlockMax, 4) // <= 128 registers: 16 warps an SM
+    k_mcollide(const MStepParams p, const MPlanes<float> planes, const float4 *__restrict__ drho,
+               unsigned *__restrict__ status)
 {
     constexpr int Q = L::Q, D = L::D;
+    constexpr bool PARK = kParkMoments<NS>;
+    extern __shared__ float park[];
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const kern::Nbr nb = make_nbr(p, x, y, blockIdx.z);
     const int site = nb.at(0, 0, 0);
 
-    // 1. moments of every species (Eq. modes-discrete); rho^s = rhobar^s
-    float m[NS][Q], rs[NS];
-    {
-        float d[NS][Q];
-        load_site<L, NS, PARITY>(p, planes, nb, d);
-        static_for<NS>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            Transform<L>::forward(d[s], m[s]);
-            rs[s] = p.rho0[s] + m[s][0];
+    // 1. loads and moments of every species (Eq. modes-discrete; the density
+    // with the same expression as the density kernel)
+    float mc[NS][4], rs[NS];
+    float mreg[PARK ? 1 : NS][Q];
+    static_for<NS>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        float d[Q], m[Q];
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            const float v = __ldg(planes.template plane<L>(s, kern::read_slot<L, PARITY, i>()) +
+                                  kern::read_site<L, PARITY, i>(nb));
+            d[i] = __fsub_rn(v, wi * p.rho0[s]);
         });
-    }
+        Transform<L>::forward(d, m);
+        static_for<Q>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            if constexpr (a <= D) mc[s][a] = m[a];
+            if constexpr (PARK) park[(s * Q + a) * nthr + tid] = m[a];
+            else mreg[PARK ? 0 : s][a] = m[a];
+        });
+        rs[s] = p.rho0[s] + m[0];
+    });
 
     // 2. mean-field forces between different species (App. D, Eq. FORCESTRUCTURE
     // per pair): F[t][d] = sum_i w_i c_id rho^t(r + c_i) on the deviations (the
@@ -202,6 +237,7 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mcollide(const MStepParams p,
     float acc[NS][3];
     static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
+        acc[s][2] = 0.0f;
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             float a = 0.0f;
@@ -229,55 +265,59 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mcollide(const MStepParams p,
         float j = 0.0f;
         static_for<NS>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            j += m[s][1 + d] + 0.5f * rs[s] * acc[s][d];
+            j += mc[s][1 + d] + 0.5f * rs[s] * acc[s][d];
         });
         u[d] = j * irt;
     });
 
     // 4. Philox slot 0 of every species: modes 1 .. 3 (the momenta; for D2Q9
     // also mode 3, kept for step 6).  Projected momentum noise.
-    float g0[NS][4], sq[NS];
-    static_for<NS>([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        slot_gaussians<0xE>((uint32_t)site, p.step, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
-        sq[s] = rs[s] * rsqrtf(rs[s]); // sqrt(rho^s); rho^s > 0 on every valid state
-    });
-    float xi[NS][3];
-    static_for<D>([&](auto dc) {
-        constexpr int d = decltype(dc)::value;
-        float sum = 0.0f;
+    float g3[NS], sq[NS], xi[NS][3];
+    {
+        float g0[NS][4];
         static_for<NS>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            sum = fmaf(sq[s], g0[s][1 + d], sum);
+            slot_gaussians<0xE>((uint32_t)site, p.step, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
+            sq[s] = rs[s] * rsqrtf(rs[s]); // sqrt(rho^s); rho^s > 0 on every valid state
+            g3[s] = g0[s][3];
         });
-        const float cs = sum * irt;
-        static_for<NS>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            xi[s][d] = p.amp_d * fmaf(-rs[s], cs, sq[s] * g0[s][1 + d]);
-        });
-    });
-
-    // 5. momentum modes: common rate; species velocity for Phi (Eq. alg-mom)
-    float v[NS][3];
-    static_for<NS>([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        const float irs = __frcp_rn(rs[s]);
-        v[s][2] = 0.0f;
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
-            constexpr int a = 1 + d;
-            const float R = p.lam_d * (rs[s] * u[d] - m[s][a]) + p.hlam_d * rs[s] * acc[s][d] + xi[s][d];
-            v[s][d] = (m[s][a] + 0.5f * R) * irs;
-            m[s][a] += R;
+            float sum = 0.0f;
+            static_for<NS>([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                sum = fmaf(sq[s], g0[s][1 + d], sum);
+            });
+            const float cs = sum * irt;
+            static_for<NS>([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                xi[s][d] = p.amp_d * fmaf(-rs[s], cs, sq[s] * g0[s][1 + d]);
+            });
         });
-    });
+    }
 
-    // 6. transport and ghost modes of each species, back-projection, mass
-    // closure on the stored values, streaming
+    // 5. each species: its moments back, momentum modes with the common rate
+    // (species velocity for Phi from Eq. alg-mom), then the transport and
+    // ghost modes, back-projection, mass closure on the stored values, streaming
     float X[Q];
     Closure<L>::eq(u, X);
     static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
+        float m[Q];
+        static_for<Q>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            if constexpr (PARK) m[a] = park[(s * Q + a) * nthr + tid];
+            else m[a] = mreg[PARK ? 0 : s][a];
+        });
+        const float irs = __frcp_rn(rs[s]);
+        float v[3] = {0.0f, 0.0f, 0.0f};
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int a = 1 + d;
+            const float R = p.lam_d * (rs[s] * u[d] - m[a]) + p.hlam_d * rs[s] * acc[s][d] + xi[s][d];
+            v[d] = (m[a] + 0.5f * R) * irs;
+            m[a] += R;
+        });
         float g[Q];
         static_for<(Q + 3) / 4 - 1>([&](auto kc) {
             constexpr int slot = decltype(kc)::value + 1;
@@ -290,19 +330,19 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mcollide(const MStepParams p,
                 g[4 * slot + l] = gs[l];
             });
         });
-        if constexpr (D + 1 < 4) g[3] = g0[s][3];
+        if constexpr (D + 1 < 4) g[3] = g3[s];
         float Y[Q];
-        Closure<L>::force(acc[s], v[s], Y);
+        Closure<L>::force(acc[s], v, Y);
         float mu[Q], fo[Q];
-        mu[0] = m[s][0];
+        mu[0] = m[0];
         static_for<D>([&](auto dc) {
             constexpr int a = decltype(dc)::value + 1;
             constexpr float invN = (float)(1.0 / L::Nd(a));
-            mu[a] = invN * m[s][a];
+            mu[a] = invN * m[a];
         });
         static_for<Q - D - 1>([&](auto kc) {
             constexpr int a = decltype(kc)::value + D + 1;
-            float t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * (sq[s] * g[a]));
+            float t = fmaf(p.cm[s][a], m[a], p.cxi[s][a] * (sq[s] * g[a]));
             if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
             mu[a] = t;
         });
@@ -318,7 +358,7 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mcollide(const MStepParams p,
             word[i] = __fmaf_rn(wi, yv[i], base);
             fo[i] = __fsub_rn(word[i], base);
         });
-        word[0] = __fadd_rn((float)L::wd(0) * p.rho0[s], Transform<L>::rest_closing_mass(fo, m[s][0]));
+        word[0] = __fadd_rn((float)L::wd(0) * p.rho0[s], Transform<L>::rest_closing_mass(fo, m[0]));
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             planes.template plane<L>(s, kern::write_slot<L, PARITY, i>())[kern::write_site<L, PARITY, i>(nb)] = word[i];
@@ -483,8 +523,9 @@ cudaError_t MLaunch<L, NS>::collide(int parity, const MStepParams &p, float *pop
 {
     const dim3 b = mkern::msite_block(p), g = mkern::msite_grid(p, b);
     const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
-    if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, 0, st>>>(p, planes, drho, status);
-    else mkern::k_mcollide<L, NS, 1><<<g, b, 0, st>>>(p, planes, drho, status);
+    const size_t smem = mkern::collide_smem<L, NS>(b.x * b.y);
+    if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, smem, st>>>(p, planes, drho, status);
+    else mkern::k_mcollide<L, NS, 1><<<g, b, smem, st>>>(p, planes, drho, status);
     return cudaGetLastError();
 }
 
