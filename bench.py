@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
     ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap"], default=None,
                     help="force one step schedule (implies --no-autotune)")
+    ap.add_argument("--form", choices=["species2", "species3", "species4"], default=None,
+                    help="time only this N-species form (--steps steps on a --form-box^3 D3Q19 box) and print it")
+    ap.add_argument("--form-box", type=int, default=256)
     return ap.parse_args()
 
 
@@ -578,6 +581,9 @@ def run_ours(args, wl):
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
+    if args.form:
+        print(json.dumps(multi_form(args.seed, "cuda:0", steps=args.steps, n=args.form_box, ns=int(args.form[-1]))))
+        return
     if args.impl == "reference":
         run_reference(args, wl)
     else:
