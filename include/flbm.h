@@ -59,7 +59,7 @@ typedef enum { FLBM_D2Q9 = 0, FLBM_D3Q19 = 1 } flbm_lattice;
 
 /* Population storage formats (option FLBM_OPT_STORAGE). */
 typedef enum {
-    FLBM_STORE_F32 = 0,  /* populations stored as float */
+    FLBM_STORE_F32 = 0,  /* stored as float deviations f_i - w_i * rho0^s; collided in float */
     FLBM_STORE_F16 = 1,  /* stored as half deviations from w_i * rho0^s; collided in float */
     FLBM_STORE_BF16 = 2  /* stored as bfloat16 deviations from w_i * rho0^s; collided in float */
 } flbm_storage;
@@ -92,13 +92,12 @@ enum {
                                     0: switched off ("no-sdf" control of Sec. VI A) */
     FLBM_OPT_RHO0_A = 4,         /* reference density of A, default 1: the uniform init value and
                                     the base of the stored deviations f_i - w_i rho0 (all storage
-                                    formats).  Set it near the mean density: then the deviations
-                                    are small, float subtraction of the base is exact and the
-                                    total mass only random-walks at the rounding of one
-                                    population per site and step.  Far from it (for instance
-                                    rho = rho0 / 2) the deviations are as large as the
-                                    populations and the mass drifts slowly at their rounding
-                                    (about 1e-10 relative per step). */
+                                    formats); fixed once the buffers exist.  Set it near the mean
+                                    density: the deviations are then small, their rounding is
+                                    small, and the total mass only random-walks at the rounding
+                                    of one population per site and step.  Far from it (for
+                                    instance rho = rho0 / 2) the deviations are as large as the
+                                    populations and the walk is correspondingly wider. */
     FLBM_OPT_RHO0_B = 5,         /* same for B */
     FLBM_OPT_NOISE_RHO = 7,      /* 0 (default): local densities in the noise amplitudes
                                     (Sec. VII); 1: the reference densities rho0 (Eq. new-noise,

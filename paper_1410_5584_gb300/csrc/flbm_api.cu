@@ -301,9 +301,9 @@ double raw_to_natural(const flbm_ctx *c, const std::vector<unsigned char> &raw, 
     const size_t idx = (size_t)(s * c->Q + slot) * (size_t)c->N + (size_t)src;
     const float base = (float)lat_w(c->lat, i) * (float)c->rho0[s];
     if (c->storage == FLBM_STORE_F32) {
-        float v;
-        std::memcpy(&v, raw.data() + idx * 4, 4);
-        return (double)v;
+        float dev;
+        std::memcpy(&dev, raw.data() + idx * 4, 4);
+        return (double)base + (double)dev;
     }
     uint16_t bits;
     std::memcpy(&bits, raw.data() + idx * 2, 2);
@@ -416,8 +416,7 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
         c->sdf = v != 0.0;
     } else if (key == FLBM_OPT_RHO0_A || key == FLBM_OPT_RHO0_B) {
         if (!(v > 0.0) || !std::isfinite(v)) return fail(c, FLBM_EINVAL, "reference densities must be positive");
-        if (c->pop && c->storage != FLBM_STORE_F32)
-            return fail(c, FLBM_ESTATE, "the deviation base of 16-bit storage is fixed once the buffers exist");
+        if (c->pop) return fail(c, FLBM_ESTATE, "the deviation base is fixed once the buffers exist");
         c->rho0[key == FLBM_OPT_RHO0_A ? 0 : 1] = v;
     } else if (key == FLBM_OPT_NOISE_RHO) {
         c->noise_ref = v != 0.0;
@@ -893,7 +892,7 @@ flbm_status flbm_set_populations(flbm_ctx *c, const double *f, int64_t step)
                 const double v = f[idx];
                 if (!std::isfinite(v)) return fail(c, FLBM_EINVAL, "non-finite population at index %zu", idx);
                 if (c->storage == FLBM_STORE_F32) {
-                    const float x = (float)v;
+                    const float x = (float)(v - (double)base);
                     std::memcpy(raw.data() + idx * 4, &x, 4);
                 } else if (c->storage == FLBM_STORE_F16) {
                     const __half h = __float2half_rn((float)(v - (double)base));

@@ -50,27 +50,29 @@ constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;   // a bounded device-side wait gave up
 
 // ---------------------------------------------------------------------------
-// Population storage.  Kernels work with deviations delta_i = f_i - w_i rho0^s:
-// for float storage the subtraction is (nearly always) exact and keeps the
-// small non-conserved moments free of cancellation; the 16-bit formats store
-// the deviation itself.
+// Population storage.  Every format stores the deviation delta_i = f_i -
+// w_i rho0^s from the reference state, and kernels work on deviations: the
+// small non-conserved moments stay free of cancellation, a stored value is
+// rounded relative to the deviation rather than to f_i, and no base has to be
+// added or subtracted on the device.
 // ---------------------------------------------------------------------------
 // encode() forms the stored word of a deviation, encode_w() that of the
 // deviation w y, and decode() the deviation a load of a word gives; each is a
 // fixed sequence of roundings without contraction, so a kernel can know
-// exactly what the next step will load.
+// exactly what the next step will load.  The base argument (w_i rho0^s) is
+// part of the interface for formats that might need it; none does.
 struct StoreF32 {
     using T = float;
-    __device__ __forceinline__ static T encode(float dev, float base) { return __fadd_rn(base, dev); }
-    __device__ __forceinline__ static T encode_w(float w, float y, float base) { return __fmaf_rn(w, y, base); }
-    __device__ __forceinline__ static float decode(T v, float base) { return __fsub_rn(v, base); }
-    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float base)
+    __device__ __forceinline__ static T encode(float dev, float) { return dev; }
+    __device__ __forceinline__ static T encode_w(float w, float y, float) { return __fmul_rn(w, y); }
+    __device__ __forceinline__ static float decode(T v, float) { return v; }
+    __device__ __forceinline__ static float load_dev(const T *p, size_t idx, float)
     {
-        return decode(__ldg(p + idx), base);
+        return __ldg(p + idx);
     }
-    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float base)
+    __device__ __forceinline__ static void store_dev(T *p, size_t idx, float dev, float)
     {
-        p[idx] = encode(dev, base);
+        p[idx] = dev;
     }
 };
 

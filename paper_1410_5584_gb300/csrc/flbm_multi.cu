@@ -65,6 +65,13 @@ flbm_status mfail(flbm_mctx *c, flbm_status st, const char *fmt, ...)
 
 double lat_N(int lat, int a) { return lat == FLBM_D2Q9 ? flbm::D2Q9::Nd(a) : flbm::D3Q19::Nd(a); }
 
+// w_i rho0^s as the kernels form it (float product): the base of the stored deviations
+float dev_base(const flbm_mctx *c, int s, int i)
+{
+    const float w = (float)(c->lat == FLBM_D2Q9 ? flbm::D2Q9::wd(i) : flbm::D3Q19::wd(i));
+    return w * (float)c->rho0[s];
+}
+
 MStepParams make_mparams(const flbm_mctx *c)
 {
     MStepParams p;
@@ -440,7 +447,12 @@ flbm_status flbm_mget_populations(flbm_mctx *c, double *f)
     MCUDA(c, e, "natural-layout copy");
     st = sync_and_check(c);
     if (st != FLBM_OK) return st;
-    for (size_t k = 0; k < n; k++) f[k] = h[k];
+    for (int s = 0; s < c->ns; s++)
+        for (int i = 0; i < c->Q; i++) {
+            const double base = dev_base(c, s, i);
+            const size_t off = ((size_t)s * c->Q + i) * (size_t)c->N;
+            for (int64_t k = 0; k < c->N; k++) f[off + k] = base + (double)h[off + k];
+        }
     return FLBM_OK;
 }
 
@@ -477,7 +489,15 @@ flbm_status flbm_mset_populations(flbm_mctx *c, const double *f, int64_t step)
     if (st != FLBM_OK) return st;
     const size_t n = pop_elems(c);
     std::vector<float> h(n);
-    for (size_t k = 0; k < n; k++) h[k] = (float)f[k];
+    for (int s = 0; s < c->ns; s++)
+        for (int i = 0; i < c->Q; i++) {
+            const double base = dev_base(c, s, i);
+            const size_t off = ((size_t)s * c->Q + i) * (size_t)c->N;
+            for (int64_t k = 0; k < c->N; k++) {
+                if (!std::isfinite(f[off + k])) return mfail(c, FLBM_EINVAL, "non-finite population");
+                h[off + k] = (float)(f[off + k] - base);
+            }
+        }
     MCUDA(c, cudaMemcpyAsync(c->pop, h.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy populations");
     MCUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "cudaMemset(status)");
     MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");

@@ -20,10 +20,10 @@
 // Box-Muller on Philox4x32-10 with counter (site, step, s, a/4), as in the
 // two-species kernels.
 //
-// Storage: float populations, the same in-place "AA" streaming and plane
-// layout [s][i][site] as the two-species kernels (flbm_kernels.cuh); the
-// kernels work on deviations f_i - w_i rho0^s.  The density field holds one
-// float4 per site: the deviations rho^s - rho0^s of up to four species.
+// Storage: the float deviations f_i - w_i rho0^s, with the same in-place "AA"
+// streaming and plane layout [s][i][site] as the two-species kernels
+// (flbm_kernels.cuh).  The density field holds one float4 per site: the
+// deviations rho^s - rho0^s of up to four species.
 #pragma once
 #include "flbm_internal.h"
 #include "flbm_kernels.cuh"
@@ -66,12 +66,12 @@ template <class L, int NS> struct MLaunch {
     // totals [nblocks][NS + 3] of (rho^s, jbar_t + F_t / 2); needs drho of the state
     static cudaError_t observables(int parity, const MStepParams &p, const float *pop, const float4 *drho,
                                    double *rho, double *u, double *partials, int *nblocks, cudaStream_t st);
-    // natural-layout copy [NS][Q][N] of the populations
+    // natural-layout copy [NS][Q][N] of the stored deviations
     static cudaError_t natural(int parity, const MStepParams &p, const float *pop, float *out, cudaStream_t st);
     // natural-layout populations of selected sites: out[k][s][i] (doubles)
     static cudaError_t gather(int parity, const MStepParams &p, const float *pop, const int64_t *sites, int64_t n,
                               double *out, cudaStream_t st);
-    // rest state f_i = w_i rho^s from float densities [NS][N]
+    // rest state f_i = w_i rho^s (stored as w_i (rho^s - rho0^s)) from float densities [NS][N]
     static cudaError_t init_rest(const MStepParams &p, const float *rho, float *pop, cudaStream_t st);
 };
 
@@ -115,17 +115,14 @@ __device__ __forceinline__ void slot_gaussians(uint32_t site, uint32_t step, uin
 
 // Loads of the NS Q pre-collision deviations of a site.
 template <class L, int NS, int PARITY, class P>
-__device__ __forceinline__ void load_site(const MStepParams &p, const P &planes, const kern::Nbr &nb,
-                                          float (&d)[NS][L::Q])
+__device__ __forceinline__ void load_site(const P &planes, const kern::Nbr &nb, float (&d)[NS][L::Q])
 {
     static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         static_for<L::Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            constexpr float wi = (float)L::wd(i);
-            const float v = __ldg(planes.template plane<L>(s, kern::read_slot<L, PARITY, i>()) +
-                                  kern::read_site<L, PARITY, i>(nb));
-            d[s][i] = __fsub_rn(v, wi * p.rho0[s]);
+            d[s][i] = __ldg(planes.template plane<L>(s, kern::read_slot<L, PARITY, i>()) +
+                            kern::read_site<L, PARITY, i>(nb));
         });
     });
 }
@@ -139,7 +136,7 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mdensity(const MStepParams p,
     if (x >= p.nx || y >= p.ny) return;
     const kern::Nbr nb = make_nbr(p, x, y, blockIdx.z);
     float d[NS][L::Q];
-    load_site<L, NS, PARITY>(p, planes, nb, d);
+    load_site<L, NS, PARITY>(planes, nb, d);
     float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
@@ -195,10 +192,8 @@ __global__ void __launch_bounds__(kSiteBlockMax, 4) // <= 128 registers: 16 warp
         float d[Q], m[Q];
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            constexpr float wi = (float)L::wd(i);
-            const float v = __ldg(planes.template plane<L>(s, kern::read_slot<L, PARITY, i>()) +
-                                  kern::read_site<L, PARITY, i>(nb));
-            d[i] = __fsub_rn(v, wi * p.rho0[s]);
+            d[i] = __ldg(planes.template plane<L>(s, kern::read_slot<L, PARITY, i>()) +
+                         kern::read_site<L, PARITY, i>(nb));
         });
         Transform<L>::forward(d, m);
         static_for<Q>([&](auto ac) {
@@ -348,17 +343,15 @@ __global__ void __launch_bounds__(kSiteBlockMax, 4) // <= 128 registers: 16 warp
         });
         float yv[Q];
         Transform<L>::backward(mu, yv);
-        // the moving populations are stored first and replaced by the deviations
-        // their words load as; the rest population takes m0 minus what they hold
+        // the moving deviations w_i y_i are rounded to the words stored; the rest
+        // population takes m0 minus what they hold, so no mass leaks
         float word[Q];
         static_for<Q - 1>([&](auto kc) {
             constexpr int i = decltype(kc)::value + 1;
-            constexpr float wi = (float)L::wd(i);
-            const float base = wi * p.rho0[s];
-            word[i] = __fmaf_rn(wi, yv[i], base);
-            fo[i] = __fsub_rn(word[i], base);
+            word[i] = __fmul_rn((float)L::wd(i), yv[i]);
+            fo[i] = word[i];
         });
-        word[0] = __fadd_rn((float)L::wd(0) * p.rho0[s], Transform<L>::rest_closing_mass(fo, m[0]));
+        word[0] = Transform<L>::rest_closing_mass(fo, m[0]);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             planes.template plane<L>(s, kern::write_slot<L, PARITY, i>())[kern::write_site<L, PARITY, i>(nb)] = word[i];
@@ -400,7 +393,9 @@ __global__ void __launch_bounds__(kObsBlock) k_mobservables(const MStepParams p,
             double r = 0.0, js[3] = {0.0, 0.0, 0.0};
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                const double f = planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
+                const float base = (float)L::wd(i) * p.rho0[s];
+                const double f = (double)base +
+                                 (double)planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
                 r += f;
                 js[0] += L::cx(i) * f;
                 js[1] += L::cy(i) * f;
@@ -467,8 +462,10 @@ __global__ void k_mgather(const MStepParams p, const MPlanes<const float> planes
         constexpr int s = decltype(sc)::value;
         static_for<L::Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
+            const float base = (float)L::wd(i) * p.rho0[s];
             out[(k * NS + s) * L::Q + i] =
-                planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
+                (double)base +
+                (double)planes.template plane<L>(s, kern::read_slot<L, PARITY, i>())[kern::read_site<L, PARITY, i>(nb)];
         });
     });
 }
@@ -480,10 +477,10 @@ __global__ void k_minit_rest(const MStepParams p, const float *__restrict__ rho,
     if (site >= p.N) return;
     static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        const float r = rho[(size_t)s * p.N + site];
+        const float dr = __fsub_rn(rho[(size_t)s * p.N + site], p.rho0[s]);
         static_for<L::Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            pop[(size_t)(s * L::Q + i) * p.N + site] = __fmul_rn((float)L::wd(i), r);
+            pop[(size_t)(s * L::Q + i) * p.N + site] = __fmul_rn((float)L::wd(i), dr);
         });
     });
 }

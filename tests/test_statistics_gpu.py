@@ -30,9 +30,7 @@ def test_ideal_mixture_64x64_flat_structure_factor():
     G = 0, seed 1): S_rho,rho = 3 kT rho0 at every k, S_rho,rho' = 0,
     <u_b^2> = kT / rho_t0 per component (Sec. VI A, Fig. 1)."""
     kT, rho0 = 1e-4, 0.5
-    g = Lattice(D2Q9, 64, 64, 1, 1.0, 1.0, kT, 0.0, 1)
-    g.set_option("rho0_a", rho0)
-    g.set_option("rho0_b", rho0)
+    g = Lattice(D2Q9, 64, 64, 1, 1.0, 1.0, kT, 0.0, 1, rho0_a=rho0, rho0_b=rho0)
     g.init()
     snaps = _snapshots(g, 2000, 2000, 20)
     m, se = theory.batch_means(snaps)
@@ -49,7 +47,8 @@ def test_ideal_mixture_64x64_flat_structure_factor():
     # mass of each species is conserved to float rounding over the 42,000 steps:
     # the rest population closes each site's balance on the deviations the other
     # stored words hold, so only its own store rounds, a random walk of
-    # 4096 x 42000 steps of <= ulp(0.22)/2 = 7.5e-9 (std ~5.6e-5); 4.1e-4 is 7 sigma
+    # 4096 x 42000 steps of at most half an ulp of the rest deviation (well below
+    # ulp(0.22)/2 = 7.5e-9, std < 5.6e-5); 4.1e-4 is over 7 sigma
     cons = g.moments(fields=False)
     assert cons[0] == pytest.approx(64 * 64 * rho0, rel=2e-7)
     assert cons[1] == pytest.approx(64 * 64 * rho0, rel=2e-7)
