@@ -812,6 +812,8 @@ typedef struct {
     long gnx, gny, gnz, ox, oy, oz;
 } orcm_t;
 
+void orcm_destroy(orcm_t *o);
+
 orcm_t *orcm_create(int lat, int ns, int nx, int ny, int nz, const double *tau, double kT, const double *G,
                     uint64_t seed)
 {
@@ -841,7 +843,10 @@ orcm_t *orcm_create(int lat, int ns, int nx, int ny, int nz, const double *tau, 
         o->f[s] = (double *)calloc((size_t)o->L.Q * o->N, sizeof(double));
         o->fn[s] = (double *)calloc((size_t)o->L.Q * o->N, sizeof(double));
         o->rho[s] = (double *)calloc((size_t)o->N, sizeof(double));
-        if (!o->f[s] || !o->fn[s] || !o->rho[s]) return NULL;
+        if (!o->f[s] || !o->fn[s] || !o->rho[s]) {
+            orcm_destroy(o); /* frees what was allocated (the rest is NULL) */
+            return NULL;
+        }
     }
     return o;
 }

@@ -134,17 +134,19 @@ flbm_status ensure_buffers(flbm_mctx *c)
         c->own_stream = true;
     }
     if (!c->pop) {
-        cudaError_t e = cudaMalloc((void **)&c->pop, pop_elems(c) * sizeof(float));
+        // both buffers or neither: a later call must never find one without the other
+        float *pop = nullptr;
+        float4 *drho = nullptr;
+        cudaError_t e = cudaMalloc((void **)&pop, pop_elems(c) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&drho, (size_t)c->N * sizeof(float4));
         if (e != cudaSuccess) {
-            c->pop = nullptr;
-            return mfail(c, FLBM_ENOMEM, "cudaMalloc of %zu population bytes failed: %s", pop_elems(c) * sizeof(float),
-                         cudaGetErrorString(e));
+            cudaFree(pop);
+            cudaGetLastError(); // clear the allocation error
+            return mfail(c, FLBM_ENOMEM, "cudaMalloc of %zu population bytes and the density field failed: %s",
+                         pop_elems(c) * sizeof(float), cudaGetErrorString(e));
         }
-        e = cudaMalloc((void **)&c->drho, (size_t)c->N * sizeof(float4));
-        if (e != cudaSuccess) {
-            c->drho = nullptr;
-            return mfail(c, FLBM_ENOMEM, "cudaMalloc of the density field failed: %s", cudaGetErrorString(e));
-        }
+        c->pop = pop;
+        c->drho = drho;
     }
     if (!c->d_status) {
         MCUDA(c, cudaMalloc((void **)&c->d_status, sizeof(unsigned)), "cudaMalloc(status)");
