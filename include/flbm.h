@@ -502,6 +502,21 @@ flbm_status flbm_mset_populations(flbm_mctx *ctx, const double *f, int64_t step)
  * Synchronising.  FLBM_EINVAL for an index out of range. */
 flbm_status flbm_mget_site_populations(flbm_mctx *ctx, const int64_t *sites, int64_t nsites, double *out);
 
+/* Axis structure factors of the N species (App. D: S_{sigma s}(k)).
+ * flbm_msf_sample adds one snapshot along `axis` (0 x, 1 y, 2 z; < D) to FP64
+ * accumulators: for k_m = 2 pi m / n_axis, m = 1 .. n_axis/2, and every pair
+ * (sigma, s): Re(rhohat^sigma conj rhohat^s) / N, with rhohat(k) = sum_r
+ * rho(r) e^{-i k r_axis} (the k = 0 mode, the conserved mass, is excluded).
+ * Each axis keeps its own accumulators.  Synchronising.
+ * flbm_mstructure_factor returns the means over the snapshots of `axis` for
+ * m = 1 .. nk (nk <= n_axis/2) into S = host [nspecies][nspecies][nk] doubles
+ * (may be NULL) and the snapshot count into *nsamples (may be NULL);
+ * FLBM_ESTATE before the first snapshot of that axis.
+ * flbm_msf_reset clears every axis. */
+flbm_status flbm_msf_sample(flbm_mctx *ctx, int axis);
+flbm_status flbm_mstructure_factor(flbm_mctx *ctx, int axis, int nk, double *S, int64_t *nsamples);
+flbm_status flbm_msf_reset(flbm_mctx *ctx);
+
 /* One-line reason of the last error ("" if none); never NULL. */
 const char *flbm_mlast_error(const flbm_mctx *ctx);
 

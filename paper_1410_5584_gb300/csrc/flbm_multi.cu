@@ -29,6 +29,10 @@ struct flbm_mctx {
     double *d_obs = nullptr;      // ns * N + D * N doubles
     double *d_partials = nullptr; // per-block totals
     size_t partials_cap = 0;
+    // axis structure factors (flbm_msf_*): per axis ns * ns * (n_axis / 2) FP64 sums
+    double *d_sf_acc[3] = {nullptr, nullptr, nullptr};
+    int64_t sf_count[3] = {0, 0, 0};
+    double *d_sf_prof = nullptr; // ns * max(nx, ny, nz) doubles of scratch
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     // per-kernel event timing
@@ -198,6 +202,8 @@ flbm_status drain_timing(flbm_mctx *c)
     c->ev_used = 0;
     return FLBM_OK;
 }
+
+int axis_len(const flbm_mctx *c, int axis) { return axis == 0 ? c->nx : (axis == 1 ? c->ny : c->nz); }
 
 // The density field of the current state.
 flbm_status density_now(flbm_mctx *c, const MStepParams &p)
@@ -510,6 +516,64 @@ flbm_status flbm_mset_populations(flbm_mctx *c, const double *f, int64_t step)
     return FLBM_OK;
 }
 
+flbm_status flbm_msf_sample(flbm_mctx *c, int axis)
+{
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    if (axis < 0 || axis >= c->D) return mfail(c, FLBM_EINVAL, "axis %d of a %dD box", axis, c->D);
+    const int n = axis_len(c, axis);
+    const size_t nacc = (size_t)c->ns * c->ns * (n / 2);
+    if (!c->d_sf_prof) {
+        const int nmax = c->nx > c->ny ? (c->nx > c->nz ? c->nx : c->nz) : (c->ny > c->nz ? c->ny : c->nz);
+        MCUDA(c, cudaMalloc((void **)&c->d_sf_prof, (size_t)c->ns * nmax * sizeof(double)), "cudaMalloc(profiles)");
+    }
+    if (!c->d_sf_acc[axis]) {
+        MCUDA(c, cudaMalloc((void **)&c->d_sf_acc[axis], nacc * sizeof(double)), "cudaMalloc(S(k) sums)");
+        MCUDA(c, cudaMemsetAsync(c->d_sf_acc[axis], 0, nacc * sizeof(double), c->stream), "cudaMemset(S(k) sums)");
+        c->sf_count[axis] = 0;
+    }
+    const MStepParams p = make_mparams(c);
+    st = density_now(c, p);
+    if (st != FLBM_OK) return st;
+    MCUDA(c, flbm::launch_msf_snapshot(c->ns, p, axis, c->drho, c->d_sf_prof, c->d_sf_acc[axis], c->stream),
+          "structure-factor kernels");
+    st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    c->sf_count[axis]++;
+    return FLBM_OK;
+}
+
+flbm_status flbm_mstructure_factor(flbm_mctx *c, int axis, int nk, double *S, int64_t *nsamples)
+{
+    if (!c) return FLBM_EINVAL;
+    if (axis < 0 || axis >= c->D) return mfail(c, FLBM_EINVAL, "axis %d of a %dD box", axis, c->D);
+    const int n = axis_len(c, axis);
+    if (nk < 0 || nk > n / 2) return mfail(c, FLBM_EINVAL, "nk = %d outside 0 .. %d", nk, n / 2);
+    if (!c->d_sf_acc[axis] || c->sf_count[axis] == 0)
+        return mfail(c, FLBM_ESTATE, "no structure-factor snapshot along axis %d", axis);
+    if (nsamples) *nsamples = c->sf_count[axis];
+    if (!S || nk == 0) return FLBM_OK;
+    const int nh = n / 2;
+    std::vector<double> h((size_t)c->ns * c->ns * nh);
+    MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    MCUDA(c, cudaMemcpy(h.data(), c->d_sf_acc[axis], h.size() * sizeof(double), cudaMemcpyDeviceToHost), "copy S(k)");
+    const double inv = 1.0 / (double)c->sf_count[axis];
+    for (int st2 = 0; st2 < c->ns * c->ns; st2++)
+        for (int m = 0; m < nk; m++) S[(size_t)st2 * nk + m] = h[(size_t)st2 * nh + m] * inv;
+    return FLBM_OK;
+}
+
+flbm_status flbm_msf_reset(flbm_mctx *c)
+{
+    if (!c) return FLBM_EINVAL;
+    for (int a = 0; a < 3; a++) {
+        if (c->d_sf_acc[a]) cudaFree(c->d_sf_acc[a]);
+        c->d_sf_acc[a] = nullptr;
+        c->sf_count[a] = 0;
+    }
+    return FLBM_OK;
+}
+
 const char *flbm_mlast_error(const flbm_mctx *c) { return c ? c->err : kNoError; }
 
 void flbm_mdestroy(flbm_mctx *c)
@@ -522,6 +586,8 @@ void flbm_mdestroy(flbm_mctx *c)
     cudaFree(c->d_status);
     cudaFree(c->d_obs);
     cudaFree(c->d_partials);
+    cudaFree(c->d_sf_prof);
+    for (int a = 0; a < 3; a++) cudaFree(c->d_sf_acc[a]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

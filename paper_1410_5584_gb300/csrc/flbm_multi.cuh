@@ -75,6 +75,14 @@ template <class L, int NS> struct MLaunch {
     static cudaError_t init_rest(const MStepParams &p, const float *rho, float *pop, cudaStream_t st);
 };
 
+// One axis structure-factor snapshot of the density deviations drho (float4 a
+// site): profiles prof[s][j] = sum over the plane at coordinate j along `axis`
+// (FP64, fixed order), then for k_m = 2 pi m / n, m = 1 .. n/2,
+// acc[s][t][m-1] += Re(rhohat^s conj rhohat^t) / N.  prof: NS n doubles of
+// scratch; acc: NS NS (n/2) doubles.
+cudaError_t launch_msf_snapshot(int ns, const MStepParams &p, int axis, const float4 *drho, double *prof,
+                                double *acc, cudaStream_t st);
+
 namespace mkern {
 
 constexpr int kObsBlock = 128;
@@ -483,6 +491,68 @@ __global__ void k_minit_rest(const MStepParams p, const float *__restrict__ rho,
             pop[(size_t)(s * L::Q + i) * p.N + site] = __fmul_rn((float)L::wd(i), dr);
         });
     });
+}
+
+// prof[s][j]: sum of drho^s over the plane j of `axis`, one block per j,
+// threads striding over the plane, fixed-order tree reduction.
+template <int NS>
+__global__ void __launch_bounds__(kObsBlock) k_mprofile(const MStepParams p, int axis, const float4 *__restrict__ drho,
+                                                        double *__restrict__ prof)
+{
+    __shared__ double sh[NS][kObsBlock];
+    const int j = blockIdx.x;
+    const int n_axis = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+    const int plane = p.N / n_axis;
+    double acc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) acc[s] = 0.0;
+    for (int k = threadIdx.x; k < plane; k += kObsBlock) {
+        int site;
+        if (axis == 0) site = k * p.nx + j;                                   // k = z ny + y
+        else if (axis == 1) site = ((k / p.nx) * p.ny + j) * p.nx + k % p.nx; // k = z nx + x
+        else site = j * p.nx * p.ny + k;                                      // k = y nx + x
+        const float4 r = drho[site];
+#pragma unroll
+        for (int s = 0; s < NS; s++) acc[s] += (double)get4(r, s);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) sh[s][threadIdx.x] = acc[s];
+    __syncthreads();
+    for (int w = kObsBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int s = 0; s < NS; s++) sh[s][threadIdx.x] += sh[s][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < NS) prof[(size_t)threadIdx.x * n_axis + j] = sh[threadIdx.x][0];
+}
+
+// One thread per wavevector m = 1 .. n/2: the DFT of every profile at k_m
+// (phase 2 pi ((m j) mod n) / n, FP64) and the products of every pair.
+template <int NS>
+__global__ void k_msf_accumulate(const double *__restrict__ prof, int n, double inv_sites, double *__restrict__ acc)
+{
+    const int nk = n / 2;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (m > nk) return;
+    double re[NS], im[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) re[s] = im[s] = 0.0;
+    for (int j = 0; j < n; j++) {
+        double sn, cs;
+        sincospi(2.0 * (double)(((long long)m * j) % n) / (double)n, &sn, &cs);
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            const double v = prof[(size_t)s * n + j];
+            re[s] += v * cs;
+            im[s] -= v * sn;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+#pragma unroll
+        for (int t = 0; t < NS; t++)
+            acc[((size_t)s * NS + t) * nk + (m - 1)] += (re[s] * re[t] + im[s] * im[t]) * inv_sites;
 }
 
 template <class T> MPlanes<T> mplanes(T *pop, int ns, int Q, int N)

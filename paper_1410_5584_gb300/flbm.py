@@ -133,6 +133,9 @@ def lib():
             "flbm_mget_populations": (i32, [vp, dp]),
             "flbm_mset_populations": (i32, [vp, dp, i64]),
             "flbm_mget_site_populations": (i32, [vp, i64p, i64, dp]),
+            "flbm_msf_sample": (i32, [vp, i32]),
+            "flbm_mstructure_factor": (i32, [vp, i32, i32, dp, i64p]),
+            "flbm_msf_reset": (i32, [vp]),
             "flbm_mlast_error": (ctypes.c_char_p, [vp]),
             "flbm_mdestroy": (None, [vp]),
         }
@@ -548,6 +551,22 @@ class MultiLattice:
         mcheck(self._h, lib().flbm_mmoments(self._h, _dp(rho), _dp(u), _dp(cons)))
         shp = (self.nz, self.ny, self.nx)
         return rho.reshape((self.ns,) + shp), u.reshape((self.D,) + shp), cons
+
+    def sf_sample(self, axis=0):
+        """Add one axis structure-factor snapshot of every species pair."""
+        mcheck(self._h, lib().flbm_msf_sample(self._h, int(axis)))
+
+    def structure_factor(self, axis=0, nk=None):
+        """(S [nspecies][nspecies][nk], snapshots): means at k_m = 2 pi m / n_axis, m = 1 .. nk."""
+        n = (self.nx, self.ny, self.nz)[axis]
+        nk = n // 2 if nk is None else int(nk)
+        S = np.empty(self.ns * self.ns * max(nk, 1))
+        cnt = ctypes.c_int64()
+        mcheck(self._h, lib().flbm_mstructure_factor(self._h, int(axis), nk, _dp(S), ctypes.byref(cnt)))
+        return S[:self.ns * self.ns * nk].reshape(self.ns, self.ns, nk), cnt.value
+
+    def sf_reset(self):
+        mcheck(self._h, lib().flbm_msf_reset(self._h))
 
     def get_populations(self):
         f = np.empty(self.ns * self.Q * self.N)

@@ -174,11 +174,66 @@ def test_nonpositive_density_is_reported():
         gp.sync()
 
 
+def _axis_sk_definition(rho, axis):
+    """S_st(k_m) = Re(rhohat_s conj rhohat_t) / N of one snapshot, from the
+    densities [ns][z][y][x] (Sec. IV A, App. D)."""
+    ax = 3 - axis
+    prof = rho.sum(axis=tuple(a for a in (1, 2, 3) if a != ax))
+    n = prof.shape[1]
+    f = np.fft.fft(prof, axis=1)[:, 1:n // 2 + 1]
+    return np.einsum("sk,tk->stk", f, np.conj(f)).real / rho[0].size
+
+
+@pytest.mark.parametrize("lat,ns,shape", [(D2Q9, 3, (1, 12, 20)), (D2Q9, 2, (1, 7, 33)), (D3Q19, 4, (6, 10, 8)),
+                                          (D3Q19, 3, (5, 7, 9))])
+def test_structure_factor_snapshot_matches_oracle(lat, ns, shape):
+    """One snapshot along every axis, in both streaming parities, against the
+    DFT definition on the oracle's densities of the same state."""
+    G = _couplings(ns, 0.5, seed=7)
+    f0 = _state(lat, ns, shape, eps=0.05, seed=11)
+    gp, o = _pair(lat, ns, shape, 1e-4, G, 3)
+    gp.set_populations(f0, step=0)
+    o.set_f(f0, step=0)
+    D = 2 if lat == D2Q9 else 3
+    for k in range(2):
+        rho_o = o.moments()[0]
+        for axis in range(D):
+            gp.sf_reset()
+            gp.sf_sample(axis)
+            S, n = gp.structure_factor(axis)
+            want = _axis_sk_definition(rho_o, axis)
+            assert n == 1 and S.shape == want.shape
+            assert np.max(np.abs(S - want)) <= 1e-4 * np.max(np.abs(want)), (k, axis)
+        gp.step(1)
+        o.step(1)
+
+
+def test_structure_factor_accumulates_means():
+    shape, ns = (1, 16, 24), 3
+    gp = MultiLattice(D2Q9, ns, 24, 16, 1, TAUS[:ns], 1e-4, _couplings(ns, 0.3), 5, rho0=RHOS[:ns])
+    gp.init()
+    got = []
+    for _ in range(3):
+        gp.step(7)
+        gp.sf_sample(1)
+        got.append(_axis_sk_definition(gp.moments()[0], 1))
+    S, n = gp.structure_factor(1, nk=5)
+    assert n == 3
+    assert np.allclose(S, np.mean(got, axis=0)[:, :, :5], rtol=1e-4, atol=1e-12)
+
+
 def test_runtime_argument_errors():
     gp = MultiLattice(D2Q9, 3, 8, 8, 1, TAUS[:3], 1e-4, _couplings(3, 0.3), 1)
     with pytest.raises(FlbmError, match="FLBM_ESTATE"):
         gp.step(1)
     gp.init()
+    with pytest.raises(FlbmError, match="FLBM_ESTATE"):
+        gp.structure_factor(0)                      # no snapshot yet
+    with pytest.raises(FlbmError, match="FLBM_EINVAL"):
+        gp.sf_sample(2)                             # no z axis in 2D
+    gp.sf_sample(0)
+    with pytest.raises(FlbmError, match="FLBM_EINVAL"):
+        gp.structure_factor(0, nk=5)                # nk > n_x / 2
     with pytest.raises(FlbmError, match="FLBM_EINVAL"):
         gp.site_populations([64])
     with pytest.raises(FlbmError, match="FLBM_EINVAL"):
@@ -242,8 +297,8 @@ def test_full_size_d2q9_four_species_sampled_parity():
 @pytest.mark.filterwarnings("ignore:An ill-conditioned matrix")
 def test_three_species_structure_factors_against_lattice_theory():
     """64 x 16 box, rho = (1, 0.8, 0.6), tau = (1, 0.8, 1.25), G = 0.3 between
-    all pairs: S_{s s'}(k_x) in bands of k against the linearised-lattice
-    covariance, 20 batches of 200 snapshots."""
+    all pairs: the device S_{s s'}(k_x) in bands of k against the
+    linearised-lattice covariance, 20 batches of 200 snapshots."""
     nx, ny, ns, kT = 64, 16, 3, 1e-4
     rhos, taus = np.array(RHOS[:ns]), TAUS[:ns]
     G = 0.3 * (1 - np.eye(ns))
@@ -252,14 +307,13 @@ def test_three_species_structure_factors_against_lattice_theory():
     gp.step(3000)
     batches = []
     for _ in range(20):
-        acc = np.zeros((ns, ns, nx // 2))
+        gp.sf_reset()
         for _ in range(200):
             gp.step(10)
-            rho, u, cons = gp.moments()
-            prof = rho.sum(axis=(1, 2))
-            f = np.fft.fft(prof - prof.mean(axis=1, keepdims=True), axis=1)[:, 1:nx // 2 + 1]
-            acc += np.einsum("sk,tk->stk", f, np.conj(f)).real
-        batches.append(acc / (200 * nx * ny))
+            gp.sf_sample(0)
+        S, n = gp.structure_factor(0)
+        assert n == 200
+        batches.append(S)
     B = np.array(batches)
     c, w, T, N = oracle.tables(D2Q9)
     k = 2 * np.pi * np.arange(1, nx // 2 + 1) / nx
