@@ -517,6 +517,15 @@ flbm_status flbm_msf_sample(flbm_mctx *ctx, int axis);
 flbm_status flbm_mstructure_factor(flbm_mctx *ctx, int axis, int nk, double *S, int64_t *nsamples);
 flbm_status flbm_msf_reset(flbm_mctx *ctx);
 
+/* Checkpoint of an N-species context: parameters, step counter, streaming
+ * parity and the stored populations as an opaque byte image (buf == NULL:
+ * *bytes receives the size needed).  Restoring into a context created with
+ * the same lattice, species count and box continues bit-identically (the
+ * noise is keyed on the step).  FLBM_EINVAL on a size or shape mismatch or a
+ * corrupt image; FLBM_ESTATE for a checkpoint before the state exists. */
+flbm_status flbm_mcheckpoint(flbm_mctx *ctx, void *buf, size_t *bytes);
+flbm_status flbm_mrestore(flbm_mctx *ctx, const void *buf, size_t bytes);
+
 /* One-line reason of the last error ("" if none); never NULL. */
 const char *flbm_mlast_error(const flbm_mctx *ctx);
 

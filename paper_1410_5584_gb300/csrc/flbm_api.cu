@@ -956,7 +956,7 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "FLBMCKP1", 8);
-    h.version = 1;
+    h.version = 2; // 2: float storage holds deviations f_i - w_i rho0
     h.lat = c->lat;
     h.nx = c->nx;
     h.ny = c->ny;
@@ -991,7 +991,7 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
     if (bytes < sizeof(CkptHeader)) return fail(c, FLBM_EINVAL, "checkpoint image too small");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 1) return fail(c, FLBM_EINVAL, "not a checkpoint image");
+    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 2) return fail(c, FLBM_EINVAL, "not a checkpoint image");
     if (h.lat != c->lat || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz)
         return fail(c, FLBM_EINVAL, "checkpoint lattice or box differs from this context");
     if (c->pop && h.storage != c->storage) return fail(c, FLBM_EINVAL, "checkpoint storage format differs");

@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "flbm_ctx.h"
 #include "flbm_multi.cuh"
 
 struct flbm_mctx {
@@ -571,6 +572,93 @@ flbm_status flbm_msf_reset(flbm_mctx *c)
         c->d_sf_acc[a] = nullptr;
         c->sf_count[a] = 0;
     }
+    return FLBM_OK;
+}
+
+namespace {
+// Checkpoint image: this header, then the stored deviations in the current
+// (parity-dependent) layout.
+struct MCkptHeader {
+    char magic[8]; // "FLBMMCK1"
+    uint32_t version, lat, ns, parity;
+    int32_t nx, ny, nz, pad;
+    int64_t step;
+    uint64_t seed, payload_bytes, payload_hash;
+    double tau[flbm::kMaxSpecies], kT, G[flbm::kMaxSpecies][flbm::kMaxSpecies], rho0[flbm::kMaxSpecies], lam_d;
+};
+} // namespace
+
+flbm_status flbm_mcheckpoint(flbm_mctx *c, void *buf, size_t *bytes)
+{
+    if (!c || !bytes) return FLBM_EINVAL;
+    const size_t payload = pop_elems(c) * sizeof(float);
+    const size_t need = sizeof(MCkptHeader) + payload;
+    if (!buf) {
+        *bytes = need;
+        return FLBM_OK;
+    }
+    if (*bytes < need) return mfail(c, FLBM_EINVAL, "checkpoint buffer too small: need %zu bytes", need);
+    flbm_status st = check_ready(c);
+    if (st != FLBM_OK) return st;
+    st = sync_and_check(c);
+    if (st != FLBM_OK) return st;
+    MCkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "FLBMMCK1", 8);
+    h.version = 1;
+    h.lat = (uint32_t)c->lat;
+    h.ns = (uint32_t)c->ns;
+    h.parity = (uint32_t)c->parity;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.nz = c->nz;
+    h.step = c->step;
+    h.seed = c->seed;
+    std::memcpy(h.tau, c->tau, sizeof(h.tau));
+    h.kT = c->kT;
+    std::memcpy(h.G, c->G, sizeof(h.G));
+    std::memcpy(h.rho0, c->rho0, sizeof(h.rho0));
+    h.lam_d = c->lam_d;
+    h.payload_bytes = payload;
+    unsigned char *dst = static_cast<unsigned char *>(buf);
+    MCUDA(c, cudaMemcpy(dst + sizeof(MCkptHeader), c->pop, payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
+    h.payload_hash = flbm::host::fnv1a(dst + sizeof(MCkptHeader), payload);
+    std::memcpy(dst, &h, sizeof(h));
+    *bytes = need;
+    return FLBM_OK;
+}
+
+flbm_status flbm_mrestore(flbm_mctx *c, const void *buf, size_t bytes)
+{
+    if (!c || !buf) return FLBM_EINVAL;
+    if (bytes < sizeof(MCkptHeader)) return mfail(c, FLBM_EINVAL, "checkpoint image too small");
+    MCkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, "FLBMMCK1", 8) != 0 || h.version != 1)
+        return mfail(c, FLBM_EINVAL, "not an N-species checkpoint image");
+    if ((int)h.lat != c->lat || (int)h.ns != c->ns || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz)
+        return mfail(c, FLBM_EINVAL, "checkpoint lattice, species count or box differs from this context");
+    const size_t payload = pop_elems(c) * sizeof(float);
+    if (h.payload_bytes != payload || bytes < sizeof(MCkptHeader) + payload || h.parity > 1)
+        return mfail(c, FLBM_EINVAL, "checkpoint image truncated");
+    const unsigned char *src = static_cast<const unsigned char *>(buf) + sizeof(MCkptHeader);
+    if (flbm::host::fnv1a(src, payload) != h.payload_hash)
+        return mfail(c, FLBM_EINVAL, "checkpoint image corrupt (hash mismatch)");
+    flbm_status st = ensure_buffers(c);
+    if (st != FLBM_OK) return st;
+    MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    MCUDA(c, cudaMemcpy(c->pop, src, payload, cudaMemcpyHostToDevice), "H2D checkpoint");
+    MCUDA(c, cudaMemset(c->d_status, 0, sizeof(unsigned)), "status reset");
+    std::memcpy(c->tau, h.tau, sizeof(h.tau));
+    c->kT = h.kT;
+    std::memcpy(c->G, h.G, sizeof(h.G));
+    std::memcpy(c->rho0, h.rho0, sizeof(h.rho0));
+    c->lam_d = h.lam_d;
+    c->seed = h.seed;
+    c->step = h.step;
+    c->parity = (int)h.parity;
+    c->faulted = false;
+    c->initialised = true;
     return FLBM_OK;
 }
 

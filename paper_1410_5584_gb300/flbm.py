@@ -136,6 +136,8 @@ def lib():
             "flbm_msf_sample": (i32, [vp, i32]),
             "flbm_mstructure_factor": (i32, [vp, i32, i32, dp, i64p]),
             "flbm_msf_reset": (i32, [vp]),
+            "flbm_mcheckpoint": (i32, [vp, vp, szp]),
+            "flbm_mrestore": (i32, [vp, vp, sz]),
             "flbm_mlast_error": (ctypes.c_char_p, [vp]),
             "flbm_mdestroy": (None, [vp]),
         }
@@ -567,6 +569,17 @@ class MultiLattice:
 
     def sf_reset(self):
         mcheck(self._h, lib().flbm_msf_reset(self._h))
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t()
+        mcheck(self._h, lib().flbm_mcheckpoint(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        mcheck(self._h, lib().flbm_mcheckpoint(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def restore(self, image: bytes):
+        buf = ctypes.create_string_buffer(bytes(image), len(image))
+        mcheck(self._h, lib().flbm_mrestore(self._h, buf, len(image)))
 
     def get_populations(self):
         f = np.empty(self.ns * self.Q * self.N)

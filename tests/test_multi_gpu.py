@@ -148,6 +148,32 @@ def test_launch_shapes_give_identical_results():
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
+@pytest.mark.parametrize("nsteps", [4, 5])
+def test_checkpoint_restore_is_bit_identical(nsteps):
+    """A checkpoint taken after an even or odd number of steps, restored into a
+    fresh context, continues bit-identically; a corrupt or mismatched image is
+    refused."""
+    shape, ns = (4, 6, 10), 3
+    G = _couplings(ns, 0.5, seed=9)
+    a = MultiLattice(D3Q19, ns, 10, 6, 4, TAUS[:ns], 1e-4, G, 8, rho0=RHOS[:ns])
+    a.set_populations(_state(D3Q19, ns, shape, seed=4), step=2)
+    a.step(nsteps)
+    img = a.checkpoint()
+    a.step(6)
+    b = MultiLattice(D3Q19, ns, 10, 6, 4, TAUS[:ns], 1e-4, G, 8, rho0=RHOS[:ns])
+    b.restore(img)
+    assert b.step_count == 2 + nsteps
+    b.step(6)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    bad = bytearray(img)
+    bad[-1] ^= 0x40
+    with pytest.raises(FlbmError, match="FLBM_EINVAL"):
+        b.restore(bytes(bad))
+    other = MultiLattice(D3Q19, ns, 10, 6, 5, TAUS[:ns], 1e-4, G, 8)
+    with pytest.raises(FlbmError, match="FLBM_EINVAL"):
+        other.restore(img)
+
+
 def test_two_species_without_noise_match_the_binary_context():
     """kT = 0: the N-species path with two species is the two-species update
     (lambdabar_d = 2 / (tau_A + tau_B) in both), to float rounding."""
