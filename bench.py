@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage and batching forms")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
     ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap"], default=None,
-                    help="force one step schedule (implies --no-autotune)")
+                    help="force one step schedule (implies --no-autotune; fused and overlap stream in place)")
+    ap.add_argument("--streaming", choices=["two_arrays", "in_place"], default="two_arrays",
+                    help="population streaming: two arrays (default) or one array updated in place")
     ap.add_argument("--form", choices=["species2", "species3", "species4"], default=None,
                     help="time only this N-species form (--steps steps on a --form-box^3 D3Q19 box) and print it")
     ap.add_argument("--form-box", type=int, default=256)
@@ -464,13 +466,15 @@ def run_ours(args, wl):
     nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
     sites = nx * ny * nz
     Q = 19 if wl["lattice"] == 1 else 9
+    from paper_1410_5584_gb300 import flbm as F
+    streaming = "in_place" if args.schedule in ("fused", "overlap") else args.streaming
     lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
-                  storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"])
+                  storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"],
+                  streaming=F.STREAMING[streaming])
     lat.init()
     # launch settings from the autotuner (untimed; the state is left as it was)
     launch = None
     if args.schedule:
-        from paper_1410_5584_gb300 import flbm as F
         lat.set_option("schedule", F.SCHEDULE[args.schedule])
         launch = {"schedule": F.SCHEDULE[args.schedule]}
     elif not args.no_autotune:
@@ -543,7 +547,7 @@ def run_ours(args, wl):
         "config": {"workload": wl["desc"], "lattice": "D3Q19" if wl["lattice"] == 1 else "D2Q9",
                    "nx": nx, "ny": ny, "nz": nz, "storage": wl["storage"], "replicas": world,
                    "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2",
-                   "launch": launch},
+                   "launch": launch, "streaming": streaming},
         "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},

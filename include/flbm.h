@@ -82,6 +82,17 @@ typedef enum {
                                       with fewer than 3 planes (rows) run the two-kernel schedule */
 } flbm_schedule;
 
+/* How populations stream (option FLBM_OPT_STREAMING). */
+typedef enum {
+    FLBM_STREAM_IN_PLACE = 0,   /* one population array updated in place ("AA" pattern: even steps swap
+                                   each site's slots, odd steps read and write the neighbours'); half the
+                                   memory of two arrays */
+    FLBM_STREAM_TWO_ARRAYS = 1  /* default: two population arrays; a step reads each site's populations
+                                   from one (natural layout) and writes f*_i to x + c_i in the other.  On
+                                   GB300 this moves data at the HBM copy rate, where updating one array in
+                                   place loses about a third of it.  Runs the two-kernel schedule */
+} flbm_streaming;
+
 /* Option keys for flbm_set_option. */
 enum {
     FLBM_OPT_STORAGE = 1,        /* flbm_storage; only before flbm_init / flbm_attach_buffers */
@@ -128,6 +139,9 @@ enum {
     FLBM_OPT_BLOCK_Y = 18,       /* ... and rows along y, 1 (default), 2 or 4; x * y <= 128.
                                     The shape changes speed only, never results.  Set one of the
                                     two first when the other would exceed the product limit */
+    FLBM_OPT_STREAMING = 19,     /* flbm_streaming; only before the buffers exist (it sets their
+                                    size, see flbm_buffer_bytes).  Both modes compute bitwise the
+                                    same update.  Batches and flbm_step_noalloc stream in place */
     FLBM_OPT_LAMBDA_MODE = 1000, /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
     FLBM_OPT_RHO0_SPECIES = 2000 /* N-species contexts only: + s, reference density of species s

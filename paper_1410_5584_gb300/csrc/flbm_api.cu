@@ -100,7 +100,23 @@ flbm_status ensure_stream(flbm_ctx *c)
     return FLBM_OK;
 }
 
-size_t pop_bytes_of(const flbm_ctx *c) { return (size_t)2 * c->Q * (size_t)c->N * storage_bytes(c->storage); }
+size_t array_bytes_of(const flbm_ctx *c) { return (size_t)2 * c->Q * (size_t)c->N * storage_bytes(c->storage); }
+size_t pop_bytes_of(const flbm_ctx *c)
+{
+    return array_bytes_of(c) * (c->streaming == FLBM_STREAM_TWO_ARRAYS && !c->batch ? 2 : 1);
+}
+bool two_arrays(const flbm_ctx *c) { return c->streaming == FLBM_STREAM_TWO_ARRAYS && !c->batch; }
+void *cur_pop(const flbm_ctx *c)
+{
+    if (!two_arrays(c) || c->parity == 0) return c->pop;
+    return static_cast<unsigned char *>(c->pop) + array_bytes_of(c);
+}
+void *next_pop(const flbm_ctx *c)
+{
+    if (!two_arrays(c)) return c->pop;
+    return static_cast<unsigned char *>(c->pop) + (c->parity == 0 ? array_bytes_of(c) : 0);
+}
+int layout_parity(const flbm_ctx *c) { return two_arrays(c) ? 0 : c->parity; }
 size_t rho_bytes_of(const flbm_ctx *c) { return (size_t)2 * (size_t)c->N * sizeof(float); }
 
 flbm_status ensure_status(flbm_ctx *c)
@@ -281,7 +297,8 @@ struct TimedLaunch {
 
 flbm_status density_now(flbm_ctx *c, const StepParams &p)
 {
-    FLBM_CUDA(c, launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream), "density kernel launch");
+    FLBM_CUDA(c, launch_density(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->rho, c->stream),
+              "density kernel launch");
     return FLBM_OK;
 }
 
@@ -290,7 +307,7 @@ double raw_to_natural(const flbm_ctx *c, const std::vector<unsigned char> &raw, 
 {
     int64_t src = site;
     int slot = i;
-    if (c->parity == 1) {
+    if (layout_parity(c) == 1) {
         const int x = (int)(site % c->nx), y = (int)((site / c->nx) % c->ny), z = (int)(site / ((int64_t)c->nx * c->ny));
         const int xs = (x - lat_c(c->lat, i, 0) + c->nx) % c->nx;
         const int ys = (y - lat_c(c->lat, i, 1) + c->ny) % c->ny;
@@ -429,6 +446,11 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
             free_sf(c);
             c->sf_axis = (int)v;
         }
+    } else if (key == FLBM_OPT_STREAMING) {
+        if (c->pop) return fail(c, FLBM_ESTATE, "the streaming mode is fixed once the buffers exist");
+        if (v != (double)FLBM_STREAM_IN_PLACE && v != (double)FLBM_STREAM_TWO_ARRAYS)
+            return fail(c, FLBM_EINVAL, "streaming must be 0 (in place) or 1 (two arrays)");
+        c->streaming = (int)v;
     } else if (key == FLBM_OPT_SCHEDULE) {
         if (v != (double)FLBM_SCHEDULE_FUSED && v != (double)FLBM_SCHEDULE_TWO_KERNELS &&
             v != (double)FLBM_SCHEDULE_OVERLAP)
@@ -489,6 +511,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_SF_AXIS: *value = c->sf_axis; break;
     case FLBM_OPT_KERNEL_TIMING: *value = c->timing ? 1.0 : 0.0; break;
     case FLBM_OPT_SCHEDULE: *value = c->schedule; break;
+    case FLBM_OPT_STREAMING: *value = c->batch ? FLBM_STREAM_IN_PLACE : c->streaming; break;
     case FLBM_OPT_WAIT_LIMIT_MS: *value = c->wait_limit_ms; break;
     case FLBM_OPT_TEST_STALL: *value = c->test_stall; break;
     case FLBM_OPT_PIPE_LAG: *value = c->pipe_lag; break;
@@ -664,7 +687,7 @@ flbm_status step_overlap(flbm_ctx *c, int64_t n, StepParams p)
     auto collide = [&](const StepParams &q) -> flbm_status {
         TimedLaunch tl{c, c->stream, 1};
         if ((st = tl.begin()) != FLBM_OK) return st;
-        cudaError_t e = launch_collide(c->lat, c->storage, c->parity, q, c->pop, c->rho, c->d_status, c->stream);
+        cudaError_t e = launch_collide(c->lat, c->storage, c->parity, q, c->pop, c->pop, c->rho, c->d_status, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
         return tl.end();
     };
@@ -713,6 +736,8 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
     if (n == 0) return FLBM_OK;
     StepParams p = make_params(c);
+    if (two_arrays(c) && c->schedule != FLBM_SCHEDULE_TWO_KERNELS)
+        return fail(c, FLBM_EUNSUPPORTED, "two-array streaming runs the two-kernel schedule only");
     if (c->schedule == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
     if (c->schedule == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
@@ -730,11 +755,15 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
                                               c->d_pipe, c->wait_limit_ms, c->test_stall, c->pipe_lag, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "fused step kernel launch");
         } else {
-            cudaError_t e = launch_density(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->stream);
+            cudaError_t e = launch_density(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->rho, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
             if ((st = t0.end()) != FLBM_OK) return st;
             if ((st = t1.begin()) != FLBM_OK) return st;
-            e = launch_collide(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status, c->stream);
+            if (two_arrays(c))
+                e = launch_collide(c->lat, c->storage, kStreamPush, p, cur_pop(c), next_pop(c), c->rho, c->d_status,
+                                   c->stream);
+            else
+                e = launch_collide(c->lat, c->storage, c->parity, p, c->pop, c->pop, c->rho, c->d_status, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
         }
         if ((st = t1.end()) != FLBM_OK) return st;
@@ -787,7 +816,7 @@ flbm_status flbm_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, d
     if ((st = density_now(c, p)) != FLBM_OK) return st;
     double *ra = c->d_obs, *rb = c->d_obs + c->N, *uu = c->d_obs + 2 * c->N;
     int nb = 0;
-    FLBM_CUDA(c, launch_observables(c->lat, c->storage, c->parity, p, c->pop, c->rho, rho_a ? ra : nullptr,
+    FLBM_CUDA(c, launch_observables(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->rho, rho_a ? ra : nullptr,
                                     rho_b ? rb : nullptr, u ? uu : nullptr, c->d_partials, &nb, c->stream),
               "observables kernel launch");
     FLBM_CUDA(c, launch_sum_partials(c->d_partials, nb, c->d_cons, c->stream), "reduction kernel launch");
@@ -810,7 +839,7 @@ flbm_status flbm_sf_sample(flbm_ctx *c)
     const StepParams p = make_params(c);
     if ((st = density_now(c, p)) != FLBM_OK) return st;
     int nb = 0;
-    FLBM_CUDA(c, launch_observables(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_obs, c->d_obs + c->N,
+    FLBM_CUDA(c, launch_observables(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->rho, c->d_obs, c->d_obs + c->N,
                                     c->d_obs + 2 * c->N, c->d_partials, &nb, c->stream),
               "observables kernel launch");
     FLBM_CUDA(c, launch_sf_accumulate(c->D, c->nx, c->ny, c->nz, c->sf_axis, c->d_obs, c->d_profile, c->d_sf, c->stream),
@@ -864,9 +893,9 @@ flbm_status flbm_get_populations(flbm_ctx *c, double *f)
     if (!c->initialised) return fail(c, FLBM_ESTATE, "no populations before flbm_init");
     flbm_status st = sync_and_check(c);
     if (st != FLBM_OK) return st;
-    const size_t bytes = pop_bytes_of(c);
+    const size_t bytes = array_bytes_of(c);
     std::vector<unsigned char> raw(bytes);
-    FLBM_CUDA(c, cudaMemcpy(raw.data(), c->pop, bytes, cudaMemcpyDeviceToHost), "D2H populations");
+    FLBM_CUDA(c, cudaMemcpy(raw.data(), cur_pop(c), bytes, cudaMemcpyDeviceToHost), "D2H populations");
     for (int s = 0; s < 2; s++)
         for (int i = 0; i < c->Q; i++)
             for (int64_t site = 0; site < c->N; site++)
@@ -930,7 +959,8 @@ flbm_status flbm_get_site_populations(flbm_ctx *c, const int64_t *sites, int64_t
     cudaError_t e = cudaMalloc((void **)&d_sites, nsites * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d_out, out_n * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(d_sites, sites, nsites * sizeof(int64_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_gather_sites(c->lat, c->storage, c->parity, make_params(c), c->pop, d_sites, nsites, d_out, c->stream);
+    if (e == cudaSuccess) e = launch_gather_sites(c->lat, c->storage, layout_parity(c), make_params(c), cur_pop(c), d_sites, nsites,
+                                                      d_out, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaMemcpy(out, d_out, out_n * sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(d_sites);
@@ -943,7 +973,7 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
 {
     if (!c || !bytes) return FLBM_EINVAL;
     if (is_batch(c)) return batch_checkpoint(c, buf, bytes);
-    const size_t payload = pop_bytes_of(c);
+    const size_t payload = array_bytes_of(c); // the current state only
     const size_t need = sizeof(CkptHeader) + payload;
     if (!buf) {
         *bytes = need;
@@ -962,7 +992,7 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     h.ny = c->ny;
     h.nz = c->nz;
     h.storage = c->storage;
-    h.parity = c->parity;
+    h.parity = layout_parity(c);
     h.sdf = c->sdf;
     h.noise_ref = c->noise_ref;
     h.force_velocity = c->force_velocity;
@@ -976,7 +1006,7 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     std::memcpy(h.lam, c->lam, sizeof(h.lam));
     h.payload_bytes = payload;
     unsigned char *dst = static_cast<unsigned char *>(buf);
-    FLBM_CUDA(c, cudaMemcpy(dst + sizeof(CkptHeader), c->pop, payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
+    FLBM_CUDA(c, cudaMemcpy(dst + sizeof(CkptHeader), cur_pop(c), payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
     h.payload_hash = fnv1a(dst + sizeof(CkptHeader), payload);
     std::memcpy(dst, &h, sizeof(h));
     *bytes = need;
@@ -998,6 +1028,8 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
     const size_t payload = (size_t)2 * c->Q * (size_t)c->N * storage_bytes(h.storage);
     if (h.payload_bytes != payload || bytes < sizeof(CkptHeader) + payload)
         return fail(c, FLBM_EINVAL, "checkpoint image truncated");
+    if (two_arrays(c) && h.parity != 0)
+        return fail(c, FLBM_EINVAL, "an in-place image in the swapped layout restores into an in-place context only");
     const unsigned char *src = static_cast<const unsigned char *>(buf) + sizeof(CkptHeader);
     if (fnv1a(src, payload) != h.payload_hash) return fail(c, FLBM_EINVAL, "checkpoint image corrupt (hash mismatch)");
     c->storage = h.storage;

@@ -172,6 +172,10 @@ flbm_status batch_set_option(flbm_ctx *c, int key, double v)
 {
     BatchState *b = B(c);
     if (key == FLBM_OPT_STORAGE && c->pop) return fail(c, FLBM_ESTATE, "the storage format is fixed once the buffers exist");
+    if (key == FLBM_OPT_STREAMING) {
+        if (v != (double)FLBM_STREAM_IN_PLACE) return fail(c, FLBM_EUNSUPPORTED, "batches stream in place");
+        return FLBM_OK;
+    }
     if (key == FLBM_OPT_GRAPH_STEPS) {
         if (!(v >= 0.0 && v <= 4096.0) || v != (double)(int)v)
             return fail(c, FLBM_EINVAL, "graph steps must be an integer in [0, 4096]");

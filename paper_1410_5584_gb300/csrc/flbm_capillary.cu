@@ -248,7 +248,7 @@ flbm_status flbm_cap_sample(flbm_ctx *c, int x_liquid, int x_gas)
     int *cols = reinterpret_cast<int *>(colsum + c->nx);
     const StepParams p = make_params(c);
     int nb = 0;
-    FLBM_CUDA(c, launch_sfk_fields(c->lat, c->storage, c->parity, p, c->pop, c->d_cap_z, c->d_partials, &nb, c->stream),
+    FLBM_CUDA(c, launch_sfk_fields(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->d_cap_z, c->d_partials, &nb, c->stream),
               "fields kernel launch");
     if (x_liquid < 0) k_cap_track<<<1, 256, 0, c->stream>>>(c->d_cap_z, c->nx, ny, colsum, cols);
     k_cap_bulk<<<1, 256, 0, c->stream>>>(c->d_cap_z, c->nx, ny, x_liquid, x_gas, cols, bulk);

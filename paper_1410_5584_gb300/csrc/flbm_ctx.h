@@ -21,13 +21,15 @@ struct flbm_ctx {
     double lam[2][flbm::kMaxQ] = {};
     int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
     int schedule = FLBM_SCHEDULE_TWO_KERNELS;
+    int streaming = FLBM_STREAM_TWO_ARRAYS; // FLBM_OPT_STREAMING
     double wait_limit_ms = 2000.0;
     int pipe_lag = 0;
     int test_stall = 0;
     double rho0[2] = {1.0, 1.0};
     // state
     int64_t step = 0;
-    int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
+    int parity = 0; // in place: 0 natural layout, 1 swapped layout (after an odd number of steps);
+                    // two arrays: which of the two holds the current (natural-layout) state
     bool initialised = false;
     bool faulted = false;
     bool timed_out = false;
@@ -104,6 +106,13 @@ flbm_status sync_and_check(flbm_ctx *c);
 flbm_status ensure_obs(flbm_ctx *c);
 flbm_status density_now(flbm_ctx *c, const StepParams &p);
 size_t pop_bytes_of(const flbm_ctx *c);
+// Where the current state is and how it is laid out: with two arrays the
+// current one (natural layout, read as parity 0); in place the one array in
+// the layout of its parity.  next_pop: where a two-array step writes.
+size_t array_bytes_of(const flbm_ctx *c);
+void *cur_pop(const flbm_ctx *c);
+void *next_pop(const flbm_ctx *c);
+int layout_parity(const flbm_ctx *c);
 size_t rho_bytes_of(const flbm_ctx *c);
 uint64_t fnv1a(const unsigned char *p, size_t n);
 } // namespace host

@@ -52,10 +52,10 @@ cudaError_t launch_density(int lat, int storage, int parity, const StepParams &p
     return dispatch<DensityF>(lat, storage, parity, p, pop, rho, stream);
 }
 
-cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop, const float *rho,
-                           unsigned *status, cudaStream_t stream)
+cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop, void *pop_out,
+                           const float *rho, unsigned *status, cudaStream_t stream)
 {
-    return dispatch<CollideF>(lat, storage, parity, p, pop, rho, status, stream);
+    return dispatch<CollideF>(lat, storage, parity, p, pop, pop_out, rho, status, stream);
 }
 
 cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams &p, void *pop, float *rho,

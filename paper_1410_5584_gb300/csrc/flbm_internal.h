@@ -122,8 +122,13 @@ inline size_t storage_bytes(int storage) { return storage == FLBM_STORE_F32 ? 4 
 cudaError_t launch_density(int lat, int storage, int parity, const StepParams &p, const void *pop,
                            float *rho, cudaStream_t stream);
 
-// Fused force + moment collision + noise + in-place streaming of one step.
-cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop,
+// Streaming mode of a collide launch: 0 / 1 = the even / odd in-place step on
+// one array; kStreamPush = read one array (natural layout), write the other.
+constexpr int kStreamPush = 2;
+
+// Fused force + moment collision + noise + streaming of one step: in place in
+// pop (parity 0 or 1), or from pop into pop_out (kStreamPush).
+cudaError_t launch_collide(int lat, int storage, int parity, const StepParams &p, void *pop, void *pop_out,
                            const float *rho, unsigned *status, cudaStream_t stream);
 
 // One whole step (densities and collision) as one persistent launch whose

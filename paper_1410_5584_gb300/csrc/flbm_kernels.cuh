@@ -52,14 +52,21 @@ __device__ __forceinline__ Nbr make_nbr(const StepParams &p, int x, int y, int z
 
 template <class L> __device__ __forceinline__ constexpr float wf(int i) { return (float)L::wd(i); }
 
+// Streaming modes (the PARITY template argument of the step kernels):
+//   0: in place, even step: read slot i of the site, write slot opp(i) of the site;
+//   1: in place, odd step:  read slot opp(i) of x - c_i, write slot i of x + c_i;
+//   kPush: two arrays: read slot i of the site in one array (natural layout),
+//          write slot i of x + c_i in the other (natural layout again).
+constexpr int kPush = kStreamPush;
+
 // slot and site of the population f_i(site) that the current step reads
 template <class L, int PARITY, int I> __device__ __forceinline__ constexpr int read_slot()
 {
-    return PARITY == 0 ? I : L::opp(I);
+    return PARITY == 1 ? L::opp(I) : I;
 }
 template <class L, int PARITY, int I> __device__ __forceinline__ unsigned read_site(const Nbr &nb)
 {
-    if constexpr (PARITY == 0) return (unsigned)nb.at(0, 0, 0);
+    if constexpr (PARITY != 1) return (unsigned)nb.at(0, 0, 0);
     else return (unsigned)nb.at(-L::cx(I), -L::cy(I), -L::cz(I));
 }
 // slot and site where the post-collision f*_i(site) is written
@@ -137,8 +144,9 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_density(const StepParams p,
 // earlier in the same kernel launch by other thread blocks.  STORE = false
 // computes without writing (an idle lane of a partial warp).  after_loads()
 // runs once the population loads are issued; returning false abandons the site.
-template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, class P, class Hook = bool (*)()>
-__device__ __forceinline__ void site_collide(const StepParams &p, const P &planes,
+template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, bool FULL = false, class P,
+          class Hook = bool (*)()>
+__device__ __forceinline__ void site_collide(const StepParams &p, const P &planes, const P &out,
                                              const float2 *__restrict__ rho, unsigned *__restrict__ status,
                                              const Nbr &nb, Hook &&after_loads)
 {
@@ -248,7 +256,11 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
         });
         static_for<Q - D - 1>([&](auto kc) {
             constexpr int a = decltype(kc)::value + D + 1;
-            float t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * g[s][a]);
+            // FULL: every cm is zero (lambdabar_a = 1), so the old moment drops out
+            // exactly and its projection is never formed
+            float t;
+            if constexpr (FULL) t = p.cxi[s][a] * g[s][a];
+            else t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * g[s][a]);
             if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
             mu[a] = t;
         });
@@ -270,13 +282,16 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
         word[0] = S::encode(Transform<L>::rest_closing_mass(fo, m[s][0]), (float)L::wd(0) * p.rho0[s]);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            if (STORE) planes.template plane<L>(s, write_slot<L, PARITY, i>())[write_site<L, PARITY, i>(nb)] = word[i];
+            if (STORE) out.template plane<L>(s, write_slot<L, PARITY, i>())[write_site<L, PARITY, i>(nb)] = word[i];
         });
     });
 }
 
-template <class L, class S, int PARITY>
+// planes: the slot planes read; out: the slot planes written (the same table
+// for the in-place modes, the other array for kPush).
+template <class L, class S, int PARITY, bool FULL>
 __global__ void __launch_bounds__(kSiteBlockMax) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
+                                                           const PlaneTable<typename S::T> out,
                                                            const float2 *__restrict__ rho,
                                                            unsigned *__restrict__ status)
 {
@@ -284,7 +299,17 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_collide(const StepParams p, c
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.yn) return;
     const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
-    site_collide<L, S, PARITY, false>(p, planes, rho, status, nb, [] { return true; });
+    site_collide<L, S, PARITY, false, true, FULL>(p, planes, out, rho, status, nb, [] { return true; });
+}
+
+// True when every non-conserved mode relaxes fully (lambdabar_a = 1, so cm = 0
+// exactly for both species): the collide can skip those modes' projections.
+template <class L> inline bool full_relaxation(const StepParams &p)
+{
+    for (int s = 0; s < 2; s++)
+        for (int a = L::D + 1; a < L::Q; a++)
+            if (p.cm[s][a] != 0.0f) return false;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -454,9 +479,11 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
             };
             bool alive = true;
             if (active) {
-                site_collide<L, S, PARITY, true, true>(p, planes, rho, status, nb, [&] { return alive = after_loads(); });
+                site_collide<L, S, PARITY, true, true>(p, planes, planes, rho, status, nb,
+                                                       [&] { return alive = after_loads(); });
             } else {
-                site_collide<L, S, PARITY, true, false>(p, planes, rho, status, nb, [&] { return alive = after_loads(); });
+                site_collide<L, S, PARITY, true, false>(p, planes, planes, rho, status, nb,
+                                                        [&] { return alive = after_loads(); });
             }
             if (!__shfl_sync(0xffffffffu, alive ? 1 : 0, 0)) return; // a wait gave up: the host sees the status bit
         }
@@ -519,7 +546,8 @@ __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict
     if (site >= sp.N) return;
     const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
     const Nbr nb = make_nbr(sp, x, y, z);
-    site_collide<L, S, PARITY, false>(sp, FlatPlanes<typename S::T>{pop + pop_off, (size_t)sp.N}, rho + rho_off, status, nb,
+    const FlatPlanes<typename S::T> fp{pop + pop_off, (size_t)sp.N};
+    site_collide<L, S, PARITY, false>(sp, fp, fp, rho + rho_off, status, nb,
                                       [] { return true; });
 }
 
@@ -731,14 +759,24 @@ cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *p
 }
 
 template <class L, class S>
-cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, const float *rho, unsigned *status,
-                                  cudaStream_t st)
+cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, void *pop_out, const float *rho,
+                                  unsigned *status, cudaStream_t st)
 {
     const dim3 b = kern::site_block(p), g = kern::site_grid(p, b);
     const auto planes = kern::plane_table(static_cast<typename S::T *>(pop), L::Q, p.N);
+    const auto out = parity == kern::kPush ? kern::plane_table(static_cast<typename S::T *>(pop_out), L::Q, p.N) : planes;
     auto *r2 = reinterpret_cast<const float2 *>(rho);
-    if (parity == 0) kern::k_collide<L, S, 0><<<g, b, 0, st>>>(p, planes, r2, status);
-    else kern::k_collide<L, S, 1><<<g, b, 0, st>>>(p, planes, r2, status);
+    const bool full = kern::full_relaxation<L>(p);
+    if (parity == 0) {
+        if (full) kern::k_collide<L, S, 0, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        else kern::k_collide<L, S, 0, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
+    } else if (parity == 1) {
+        if (full) kern::k_collide<L, S, 1, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        else kern::k_collide<L, S, 1, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
+    } else {
+        if (full) kern::k_collide<L, S, kern::kPush, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        else kern::k_collide<L, S, kern::kPush, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
+    }
     return cudaGetLastError();
 }
 

@@ -8,8 +8,9 @@ namespace flbm {
 
 template <class L, class S> struct Launch {
     static cudaError_t density(int parity, const StepParams &p, const void *pop, float *rho, cudaStream_t st);
-    static cudaError_t collide(int parity, const StepParams &p, void *pop, const float *rho, unsigned *status,
-                               cudaStream_t st);
+    // parity 0 / 1: in place in pop; kPush (2): read pop, write pop_out
+    static cudaError_t collide(int parity, const StepParams &p, void *pop, void *pop_out, const float *rho,
+                               unsigned *status, cudaStream_t st);
     static cudaError_t step_fused(int parity, const StepParams &p, void *pop, float *rho, unsigned *status,
                                   unsigned *counters, double wait_ms, int stall, int lag, cudaStream_t st);
     static cudaError_t batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,

@@ -64,7 +64,7 @@ extern "C" flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int par
     for (int64_t t = 0; t < n; t++) {
         p.step = (uint32_t)(step + t);
         if ((e = launch_density(v.lat, v.storage, parity, p, pop, rho, st)) != cudaSuccess) return cuda_error(e);
-        if ((e = launch_collide(v.lat, v.storage, parity, p, pop, rho, status, st)) != cudaSuccess) return cuda_error(e);
+        if ((e = launch_collide(v.lat, v.storage, parity, p, pop, pop, rho, status, st)) != cudaSuccess) return cuda_error(e);
         parity ^= 1;
     }
     unsigned h = 0;

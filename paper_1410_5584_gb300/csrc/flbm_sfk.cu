@@ -316,7 +316,7 @@ flbm_status flbm_sfk_sample(flbm_ctx *c)
     }
     const StepParams p = make_params(c);
     int nb = 0;
-    FLBM_CUDA(c, launch_sfk_fields(c->lat, c->storage, c->parity, p, c->pop, c->d_sfk_z, c->d_partials, &nb, c->stream),
+    FLBM_CUDA(c, launch_sfk_fields(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->d_sfk_z, c->d_partials, &nb, c->stream),
               "fields kernel launch");
     k_sfk_means<<<1, 256, 0, c->stream>>>(c->d_partials, nb, (long)c->N, c->d_sfk_mean);
     FLBM_CUDA(c, cudaGetLastError(), "means kernel launch");

@@ -164,8 +164,9 @@ std::string cache_key(const flbm_ctx *c)
         std::snprintf(buf, sizeof(buf), "%s|%d SMs|%s|%s|batch of %d|%lld sites", prop.name, prop.multiProcessorCount,
                       lat, storage_name(c->storage), nrep, (long long)sites);
     } else {
-        std::snprintf(buf, sizeof(buf), "%s|%d SMs|%s|%s|%dx%dx%d", prop.name, prop.multiProcessorCount, lat,
-                      storage_name(c->storage), c->nx, c->ny, c->nz);
+        std::snprintf(buf, sizeof(buf), "%s|%d SMs|%s|%s|%s|%dx%dx%d", prop.name, prop.multiProcessorCount, lat,
+                      storage_name(c->storage), c->streaming == FLBM_STREAM_IN_PLACE ? "in place" : "two arrays",
+                      c->nx, c->ny, c->nz);
     }
     return buf;
 }
@@ -269,10 +270,11 @@ std::vector<Settings> candidates(const flbm_ctx *c)
     }
     const int axis = c->lat == FLBM_D2Q9 ? c->ny : c->nz;
     const int shapes[3][2] = {{128, 1}, {64, 2}, {32, 4}};
+    const bool in_place = c->streaming == FLBM_STREAM_IN_PLACE; // two arrays: the two-kernel schedule only
     for (const auto &b : shapes) {
         out.push_back({{"schedule", (double)FLBM_SCHEDULE_TWO_KERNELS}, {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
         for (int k : {4, 8})
-            if (axis >= k)
+            if (in_place && axis >= k)
                 out.push_back({{"schedule", (double)FLBM_SCHEDULE_OVERLAP}, {"slabs", (double)k},
                                {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
     }

@@ -38,6 +38,8 @@ OPT_GRAPH_STEPS = 15
 OPT_SLABS = 16
 OPT_BLOCK_X = 17
 OPT_BLOCK_Y = 18
+OPT_STREAMING = 19
+STREAMING = {"in_place": 0, "two_arrays": 1}
 SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
 OPT_LAMBDA_MODE = 1000
 OPT_RHO0_SPECIES = 2000
@@ -47,7 +49,7 @@ OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF
                 "kernel_timing": OPT_KERNEL_TIMING, "schedule": OPT_SCHEDULE,
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
                 "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS,
-                "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y}
+                "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y, "streaming": OPT_STREAMING}
 
 
 class RepParams(ctypes.Structure):

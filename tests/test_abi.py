@@ -72,13 +72,14 @@ def test_options_are_validated(lib):
         assert lib.flbm_step(h, -1) == F.EINVAL
         pb, rb = ctypes.c_size_t(), ctypes.c_size_t()
         assert lib.flbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(rb)) == F.OK
-        assert pb.value == 2 * 9 * 64 * 4 and rb.value == 2 * 64 * 4
+        # two population arrays (the default streaming) of 2 species x 9 x 64 sites
+        assert pb.value == 2 * (2 * 9 * 64 * 4) and rb.value == 2 * 64 * 4
         assert lib.flbm_set_option(h, F.OPT_STORAGE, 2) == F.OK
         assert lib.flbm_buffer_bytes(h, ctypes.byref(pb), None) == F.OK
-        assert pb.value == 2 * 9 * 64 * 2
+        assert pb.value == 2 * (2 * 9 * 64 * 2)
         need = ctypes.c_size_t()
         assert lib.flbm_checkpoint(h, None, ctypes.byref(need)) == F.OK
-        assert need.value > pb.value
+        assert need.value > pb.value // 2  # a header and the current array
     finally:
         lib.flbm_destroy(h)
 
@@ -184,3 +185,22 @@ def test_multi_options_and_order_are_validated(lib):
     assert lib.flbm_mlast_error(None) == b""
     assert lib.flbm_mstep(None, 1) == F.EINVAL
     lib.flbm_mdestroy(None)
+
+
+def test_streaming_option_and_buffer_sizes(lib):
+    """Two-array streaming (the default) needs twice the population bytes of
+    in-place streaming; the option takes 0 or 1 (host logic only)."""
+    h = F.flbm_create(1, 8, 6, 4, 1.0, 1.0, 1e-4, 0.5, 1)
+    try:
+        v = ctypes.c_double()
+        assert lib.flbm_get_option(h, F.OPT_STREAMING, ctypes.byref(v)) == F.OK and v.value == 1
+        pb2, rb2 = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.flbm_buffer_bytes(h, ctypes.byref(pb2), ctypes.byref(rb2)) == F.OK
+        assert lib.flbm_set_option(h, F.OPT_STREAMING, 2) == F.EINVAL
+        assert lib.flbm_set_option(h, F.OPT_STREAMING, 0) == F.OK
+        pb1, rb1 = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.flbm_buffer_bytes(h, ctypes.byref(pb1), ctypes.byref(rb1)) == F.OK
+        assert pb2.value == 2 * pb1.value == 2 * 2 * 19 * 8 * 6 * 4 * 4
+        assert rb1.value == rb2.value
+    finally:
+        lib.flbm_destroy(h)

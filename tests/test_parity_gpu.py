@@ -316,7 +316,7 @@ def test_fused_and_two_kernel_schedules_agree(lat, shape):
     f0 = _random_state(lat, shape)
     out = []
     for sched in ("fused", "fused", "two_kernels"):
-        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
+        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6, streaming=F.STREAMING["in_place"])
         g.set_option("schedule", F.SCHEDULE[sched])
         g.set_populations(f0, step=3)
         g.step(5)
@@ -336,13 +336,13 @@ def test_overlap_schedule_matches_two_kernels_bitwise(lat, shape, slabs):
     two-kernel schedule.  Kernel timing does not change the result."""
     nz, ny, nx = shape
     f0 = _random_state(lat, shape)
-    ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
+    ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6, streaming=F.STREAMING["in_place"])
     ref.set_option("schedule", F.SCHEDULE["two_kernels"])
     ref.set_populations(f0, step=3)
     ref.step(8)
     want = ref.get_populations()
     for timing in (0, 1):
-        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
+        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6, streaming=F.STREAMING["in_place"])
         g.set_option("schedule", F.SCHEDULE["overlap"])
         g.set_option("slabs", slabs)
         g.set_option("kernel_timing", timing)
@@ -360,7 +360,7 @@ def test_fused_step_wait_timeout_is_reported():
     """Failure detection without a GPU fault: a dependency wait that can never
     be satisfied gives up after its time limit, the kernel returns, the host
     reads FLBM_ETIMEOUT, and re-initialising restores a usable context."""
-    g = Lattice(D3Q19, 16, 8, 6, 1.0, 1.0, 1e-4, 0.5, 1)
+    g = Lattice(D3Q19, 16, 8, 6, 1.0, 1.0, 1e-4, 0.5, 1, streaming=F.STREAMING["in_place"])
     g.set_option("schedule", F.SCHEDULE["fused"])
     g.init()
     g.set_option("wait_limit_ms", 50)
@@ -374,3 +374,75 @@ def test_fused_step_wait_timeout_is_reported():
     g.step(3)
     g.sync()
     assert g.moments(fields=False)[0] == pytest.approx(16 * 8 * 6, rel=1e-6)
+
+
+@pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 2, 37)), (D2Q9, (1, 17, 33)), (D3Q19, (2, 2, 2)),
+                                       (D3Q19, (5, 7, 45))])
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.0)])
+def test_streaming_modes_are_bitwise_identical(lat, shape, tau):
+    """In-place and two-array streaming compute the same update bit for bit:
+    populations after odd and even step counts split over several calls,
+    observables and the axis structure factor; with all rates 1 (the collide
+    that skips the non-conserved projections) and with general rates."""
+    nz, ny, nx = shape
+    f0 = _random_state(lat, shape)
+    runs = []
+    for mode in ("in_place", "two_arrays"):
+        g = Lattice(lat, nx, ny, nz, tau[0], tau[1], 1e-4, 0.7, 6, streaming=F.STREAMING[mode])
+        assert g.get_option("streaming") == F.STREAMING[mode]
+        g.set_populations(f0, step=3)
+        got = []
+        for n in (1, 2, 4):
+            g.step(n)
+            g.sf_sample()
+            got.append((g.get_populations(), g.moments()))
+        got.append(g.structure_factor(0))
+        runs.append(got)
+    for a, b in zip(runs[0][:-1], runs[1][:-1]):
+        assert np.array_equal(a[0], b[0])
+        for x, y in zip(a[1], b[1]):
+            assert np.array_equal(x, y)
+    for x, y in zip(runs[0][-1], runs[1][-1]):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_checkpoints_move_between_streaming_modes():
+    """An image holds the current state in its layout: a two-array image (always
+    the natural layout) restores into either mode and continues bitwise; an
+    in-place image taken after an odd step count (swapped layout) restores
+    into an in-place context only."""
+    shape = (4, 6, 10)
+    f0 = _random_state(D3Q19, shape)
+    mk = lambda mode: Lattice(D3Q19, 10, 6, 4, 0.8, 1.0, 1e-4, 0.7, 6, streaming=F.STREAMING[mode])
+    a = mk("two_arrays")
+    a.set_populations(f0, step=3)
+    a.step(3)
+    img = a.checkpoint()
+    a.step(4)
+    b = mk("in_place")
+    b.restore(img)
+    b.step(4)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    c = mk("in_place")
+    c.set_populations(f0, step=3)
+    c.step(1)
+    odd = c.checkpoint()
+    d = mk("two_arrays")
+    with pytest.raises(FlbmError, match="FLBM_EINVAL"):
+        d.restore(odd)
+    e = mk("in_place")
+    e.restore(odd)
+    assert np.array_equal(e.get_populations(), c.get_populations())
+
+
+def test_two_arrays_refuse_the_other_schedules():
+    g = Lattice(D2Q9, 16, 8, 1, 1.0, 1.0, 1e-4, 0.5, 1)
+    g.init()
+    for sched in ("fused", "overlap"):
+        g.set_option("schedule", F.SCHEDULE[sched])
+        with pytest.raises(FlbmError, match="FLBM_EUNSUPPORTED"):
+            g.step(1)
+    g.set_option("schedule", F.SCHEDULE["two_kernels"])
+    g.step(1)
+    with pytest.raises(FlbmError, match="FLBM_ESTATE"):
+        g.set_option("streaming", F.STREAMING["in_place"])  # the buffers exist

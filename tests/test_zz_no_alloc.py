@@ -34,7 +34,8 @@ def test_noalloc_matches_flbm_step(lat, shape):
     nz, ny, nx = shape
     c, w, T, N = oracle.tables(lat)
     f0 = inputs.random_populations(np.stack([w * 1.0, w * 0.9]), shape, 0.02, seed=21)
-    ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.7, 99)
+    # the caller's buffer holds one in-place array, like the reference context's
+    ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.7, 99, streaming=F.STREAMING["in_place"])
     ref.set_populations(f0, step=4)
     work = ref.pop_buffer.clone()  # caller-owned copy of the raw populations (parity 0)
     torch.cuda.synchronize()
