@@ -142,6 +142,10 @@ enum {
     FLBM_OPT_STREAMING = 19,     /* flbm_streaming; only before the buffers exist (it sets their
                                     size, see flbm_buffer_bytes).  Both modes compute bitwise the
                                     same update.  Batches and flbm_step_noalloc stream in place */
+    FLBM_OPT_TEST_GENERAL_COLLIDE = 20, /* test hook: 1 keeps the general collide kernel even when
+                                    every non-conserved rate is 1, where a kernel that skips those
+                                    modes' projections runs by default (the two agree to rounding;
+                                    each is deterministic); 0 default */
     FLBM_OPT_LAMBDA_MODE = 1000, /* + 100 * species + a, a > D: rate lambdabar_a of one
                                     non-conserved mode, 0 < value < 2; default 1/tau_species */
     FLBM_OPT_RHO0_SPECIES = 2000 /* N-species contexts only: + s, reference density of species s

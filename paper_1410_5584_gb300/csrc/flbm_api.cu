@@ -88,6 +88,7 @@ StepParams make_params(const flbm_ctx *c)
     p.key0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
     p.key1 = (uint32_t)(c->seed >> 32);
     p.step = (uint32_t)c->step;
+    p.general_collide = c->test_general;
     return p;
 }
 
@@ -478,6 +479,8 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
         c->pipe_lag = (int)v;
     } else if (key == FLBM_OPT_TEST_STALL) {
         c->test_stall = v != 0.0;
+    } else if (key == FLBM_OPT_TEST_GENERAL_COLLIDE) {
+        c->test_general = v != 0.0;
     } else if (key == FLBM_OPT_KERNEL_TIMING) {
         if (c->stream) {
             flbm_status st = drain_timing(c);
@@ -514,6 +517,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_STREAMING: *value = c->batch ? FLBM_STREAM_IN_PLACE : c->streaming; break;
     case FLBM_OPT_WAIT_LIMIT_MS: *value = c->wait_limit_ms; break;
     case FLBM_OPT_TEST_STALL: *value = c->test_stall; break;
+    case FLBM_OPT_TEST_GENERAL_COLLIDE: *value = c->test_general; break;
     case FLBM_OPT_PIPE_LAG: *value = c->pipe_lag; break;
     case FLBM_OPT_GRAPH_STEPS:
         if (!is_batch(c)) return FLBM_EUNSUPPORTED;

@@ -25,6 +25,7 @@ struct flbm_ctx {
     double wait_limit_ms = 2000.0;
     int pipe_lag = 0;
     int test_stall = 0;
+    int test_general = 0; // FLBM_OPT_TEST_GENERAL_COLLIDE
     double rho0[2] = {1.0, 1.0};
     // state
     int64_t step = 0;

@@ -35,6 +35,7 @@ struct StepParams {
     int force_velocity;        // 0: rho v = jbar + R_j/2 ; 1: v = vbar + a/2
     uint32_t key0, key1;       // Philox key (seed low, seed high)
     uint32_t step;             // noise counter word for this step
+    int general_collide;       // test hook: 1 keeps the general collide even when every rate is 1
 };
 
 // One replica of a batch: its step parameters and the offsets of its slices of

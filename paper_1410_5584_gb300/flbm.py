@@ -39,6 +39,7 @@ OPT_SLABS = 16
 OPT_BLOCK_X = 17
 OPT_BLOCK_Y = 18
 OPT_STREAMING = 19
+OPT_TEST_GENERAL_COLLIDE = 20
 STREAMING = {"in_place": 0, "two_arrays": 1}
 SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
 OPT_LAMBDA_MODE = 1000
@@ -49,7 +50,8 @@ OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF
                 "kernel_timing": OPT_KERNEL_TIMING, "schedule": OPT_SCHEDULE,
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
                 "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS,
-                "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y, "streaming": OPT_STREAMING}
+                "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y, "streaming": OPT_STREAMING,
+                "test_general_collide": OPT_TEST_GENERAL_COLLIDE}
 
 
 class RepParams(ctypes.Structure):
