@@ -94,14 +94,21 @@ KERNEL_SOURCES = ("flbm_internal.h", "flbm_kernels.cuh", "flbm_lattice.cuh", "fl
 
 
 def sources_digest():
+    """sha256 over the kernel sources' code: comments and whitespace are left
+    out, so that documentation edits keep a recorded capture valid."""
+    import re
+
     h = hashlib.sha256()
     files = set()
     for pat in KERNEL_SOURCES:
         files.update(glob.glob(os.path.join(ROOT, "paper_1410_5584_gb300", "csrc", pat)))
     for p in sorted(files):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
-            h.update(f.read())
+        with open(p, encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(os.path.basename(p).encode())
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -3,7 +3,9 @@
 //
 // The per-step update is the fluctuating two-species lattice Boltzmann
 // equation of arXiv 1410.5584 (Sec. V B, Eqs. algorithm and lattice
-// finalstep) with in-place "AA" streaming:
+// finalstep).  Streaming either pushes each site's post-collision f*_i to
+// x + c_i in a second array (two-array mode; both arrays stay in the natural
+// layout) or updates one array in place with the "AA" pattern:
 //   parity 0 (natural layout, A[s][i][x] = f_i(x)):   read A[s][i][x],
 //       write the post-collision f*_i(x) to A[s][opp i][x] (same site);
 //   parity 1 (swapped layout, A[s][opp i][x] = f*_i(x) of the previous step):
