@@ -89,8 +89,9 @@ typedef enum {
                                    memory of two arrays */
     FLBM_STREAM_TWO_ARRAYS = 1  /* default: two population arrays; a step reads each site's populations
                                    from one (natural layout) and writes f*_i to x + c_i in the other.  On
-                                   GB300 this moves data at the HBM copy rate, where updating one array in
-                                   place loses about a third of it.  Runs the two-kernel schedule */
+                                   GB300 a pure copy with these reads and writes runs at the HBM copy rate,
+                                   the in-place pattern at half of it or less; the collide gains a few
+                                   per cent.  Runs the two-kernel schedule */
 } flbm_streaming;
 
 /* Option keys for flbm_set_option. */
@@ -189,7 +190,9 @@ flbm_status flbm_get_option(const flbm_ctx *ctx, int key, double *value);
 flbm_status flbm_set_stream(flbm_ctx *ctx, void *stream);
 
 /* Bytes of device memory the context needs for its populations and its density
- * field, for the current storage option.  Either pointer may be NULL. */
+ * field, for the current storage and streaming options: one array holds
+ * 2 * Q * N populations; two-array streaming needs two.  Either pointer may be
+ * NULL. */
 flbm_status flbm_buffer_bytes(const flbm_ctx *ctx, size_t *pop_bytes, size_t *rho_bytes);
 
 /* Use caller-owned device buffers for the populations (pop_bytes as reported by
