@@ -479,8 +479,10 @@ typedef struct flbm_mctx flbm_mctx; /* opaque; created and freed by the library 
 flbm_status flbm_mcreate(flbm_lattice lat, int nspecies, int nx, int ny, int nz, const double *tau,
                          double kT, const double *G, uint64_t seed, flbm_mctx **out);
 
-/* Options: FLBM_OPT_KERNEL_TIMING, FLBM_OPT_BLOCK_X, FLBM_OPT_BLOCK_Y (as for
- * two species) and FLBM_OPT_RHO0_SPECIES + s.  FLBM_EINVAL otherwise. */
+/* Options: FLBM_OPT_KERNEL_TIMING, FLBM_OPT_BLOCK_X, FLBM_OPT_BLOCK_Y,
+ * FLBM_OPT_STREAMING (as for two species; two arrays by default, in place on
+ * request, bitwise the same update) and FLBM_OPT_RHO0_SPECIES + s.
+ * FLBM_EINVAL otherwise. */
 flbm_status flbm_mset_option(flbm_mctx *ctx, int key, double value);
 
 /* Run on a caller-owned cudaStream_t (NULL: a stream the context creates). */
@@ -488,8 +490,9 @@ flbm_status flbm_mset_stream(flbm_mctx *ctx, void *stream);
 
 /* Rest state f_i = w_i rho^s: rho = host [nspecies][N] doubles (positive,
  * finite) or NULL for rho^s = the reference densities.  Allocates the
- * populations (nspecies Q N floats) and the density field (16 bytes a site).
- * Resets the step counter.  Synchronising. */
+ * populations (nspecies Q N floats, twice that with two-array streaming) and
+ * the density field (16 bytes a site).  Resets the step counter.
+ * Synchronising. */
 flbm_status flbm_minit(flbm_mctx *ctx, const double *rho);
 
 /* Advance n >= 0 steps (asynchronous): per step a density kernel, then the

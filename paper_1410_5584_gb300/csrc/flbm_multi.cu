@@ -19,9 +19,11 @@ struct flbm_mctx {
     double lam_d = 1.0;
     uint64_t seed = 0;
     int block_x = 128, block_y = 1;
+    int streaming = FLBM_STREAM_TWO_ARRAYS; // FLBM_OPT_STREAMING
     // state
     int64_t step = 0;
-    int parity = 0; // 0: natural layout, 1: swapped layout (after an odd number of steps)
+    int parity = 0; // in place: 0 natural layout, 1 swapped layout (after an odd number of steps);
+                    // two arrays: which of the two holds the current (natural-layout) state
     bool initialised = false, faulted = false;
     // device buffers
     float *pop = nullptr;
@@ -130,7 +132,13 @@ template <class F> cudaError_t dispatch(const flbm_mctx *c, F &&f)
     return cudaErrorInvalidValue;
 }
 
-size_t pop_elems(const flbm_mctx *c) { return (size_t)c->ns * c->Q * (size_t)c->N; }
+size_t pop_elems(const flbm_mctx *c) { return (size_t)c->ns * c->Q * (size_t)c->N; } // one array
+bool two_arrays(const flbm_mctx *c) { return c->streaming == FLBM_STREAM_TWO_ARRAYS; }
+// the array holding the current state, the one a two-array step writes, and
+// the layout readers see (two arrays: always natural)
+float *cur_pop(const flbm_mctx *c) { return c->pop + (two_arrays(c) && c->parity ? pop_elems(c) : 0); }
+float *next_pop(const flbm_mctx *c) { return c->pop + (two_arrays(c) && !c->parity ? pop_elems(c) : 0); }
+int layout_parity(const flbm_mctx *c) { return two_arrays(c) ? 0 : c->parity; }
 
 flbm_status ensure_buffers(flbm_mctx *c)
 {
@@ -142,7 +150,7 @@ flbm_status ensure_buffers(flbm_mctx *c)
         // both buffers or neither: a later call must never find one without the other
         float *pop = nullptr;
         float4 *drho = nullptr;
-        cudaError_t e = cudaMalloc((void **)&pop, pop_elems(c) * sizeof(float));
+        cudaError_t e = cudaMalloc((void **)&pop, pop_elems(c) * (two_arrays(c) ? 2 : 1) * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void **)&drho, (size_t)c->N * sizeof(float4));
         if (e != cudaSuccess) {
             cudaFree(pop);
@@ -209,7 +217,9 @@ int axis_len(const flbm_mctx *c, int axis) { return axis == 0 ? c->nx : (axis ==
 // The density field of the current state.
 flbm_status density_now(flbm_mctx *c, const MStepParams &p)
 {
-    cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::density(c->parity, p, c->pop, c->drho, c->stream); });
+    cudaError_t e = dispatch(c, [&](auto l) {
+        return decltype(l)::density(layout_parity(c), p, cur_pop(c), c->drho, c->stream);
+    });
     MCUDA(c, e, "density kernel launch");
     return FLBM_OK;
 }
@@ -280,6 +290,13 @@ flbm_status flbm_mset_option(flbm_mctx *c, int key, double v)
             return mfail(c, FLBM_EINVAL, "block shape %d x %d: x in {32, 64, 128}, y in {1, 2, 4}, x y <= 128", bx, by);
         c->block_x = bx;
         c->block_y = by;
+        return FLBM_OK;
+    }
+    if (key == FLBM_OPT_STREAMING) {
+        if (c->pop) return mfail(c, FLBM_ESTATE, "the streaming mode is fixed once the buffers exist");
+        if (v != (double)FLBM_STREAM_IN_PLACE && v != (double)FLBM_STREAM_TWO_ARRAYS)
+            return mfail(c, FLBM_EINVAL, "streaming must be 0 (in place) or 1 (two arrays)");
+        c->streaming = (int)v;
         return FLBM_OK;
     }
     if (key >= FLBM_OPT_RHO0_SPECIES && key < FLBM_OPT_RHO0_SPECIES + c->ns) {
@@ -357,14 +374,16 @@ flbm_status flbm_mstep(flbm_mctx *c, int64_t n)
             if (!e0 || !e1 || !e2 || !e3) return mfail(c, FLBM_ECUDA, "cudaEventCreate failed");
             MCUDA(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
-        cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::density(parity, p, c->pop, c->drho, c->stream); });
+        float *cur = cur_pop(c), *nxt = next_pop(c);
+        const int lp = layout_parity(c), cp = two_arrays(c) ? flbm::kStreamPush : parity;
+        cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::density(lp, p, cur, c->drho, c->stream); });
         MCUDA(c, e, "density kernel launch");
         if (c->timing) {
             MCUDA(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
             MCUDA(c, cudaEventRecord(e2, c->stream), "cudaEventRecord");
         }
         e = dispatch(c, [&](auto l) {
-            return decltype(l)::collide(parity, p, c->pop, c->drho, c->d_status, c->stream);
+            return decltype(l)::collide(cp, p, cur, nxt, c->drho, c->d_status, c->stream);
         });
         MCUDA(c, e, "collide kernel launch");
         if (c->timing) MCUDA(c, cudaEventRecord(e3, c->stream), "cudaEventRecord");
@@ -421,7 +440,7 @@ flbm_status flbm_mmoments(flbm_mctx *c, double *rho, double *u, double *cons)
     double *d_rho = c->d_obs, *d_u = c->d_obs + (size_t)c->ns * c->N;
     int nb = 0;
     cudaError_t e = dispatch(c, [&](auto l) {
-        return decltype(l)::observables(c->parity, p, c->pop, c->drho, rho ? d_rho : nullptr, u ? d_u : nullptr,
+        return decltype(l)::observables(layout_parity(c), p, cur_pop(c), c->drho, rho ? d_rho : nullptr, u ? d_u : nullptr,
                                         c->d_partials, &nb, c->stream);
     });
     MCUDA(c, e, "observables kernel launch");
@@ -449,7 +468,8 @@ flbm_status flbm_mget_populations(flbm_mctx *c, double *f)
     const size_t n = pop_elems(c);
     float *d = nullptr;
     MCUDA(c, cudaMallocAsync((void **)&d, n * sizeof(float), c->stream), "cudaMallocAsync");
-    cudaError_t e = dispatch(c, [&](auto l) { return decltype(l)::natural(c->parity, p, c->pop, d, c->stream); });
+    cudaError_t e =
+        dispatch(c, [&](auto l) { return decltype(l)::natural(layout_parity(c), p, cur_pop(c), d, c->stream); });
     std::vector<float> h(n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     cudaFreeAsync(d, c->stream);
@@ -482,7 +502,9 @@ flbm_status flbm_mget_site_populations(flbm_mctx *c, const int64_t *sites, int64
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_sites, sites, (size_t)nsites * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = dispatch(c, [&](auto l) { return decltype(l)::gather(c->parity, p, c->pop, d_sites, nsites, d_out, c->stream); });
+        e = dispatch(c, [&](auto l) {
+            return decltype(l)::gather(layout_parity(c), p, cur_pop(c), d_sites, nsites, d_out, c->stream);
+        });
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, nout * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaFreeAsync(d_sites, c->stream);
     if (d_out) cudaFreeAsync(d_out, c->stream);
@@ -608,7 +630,7 @@ flbm_status flbm_mcheckpoint(flbm_mctx *c, void *buf, size_t *bytes)
     h.version = 1;
     h.lat = (uint32_t)c->lat;
     h.ns = (uint32_t)c->ns;
-    h.parity = (uint32_t)c->parity;
+    h.parity = (uint32_t)layout_parity(c);
     h.nx = c->nx;
     h.ny = c->ny;
     h.nz = c->nz;
@@ -621,7 +643,7 @@ flbm_status flbm_mcheckpoint(flbm_mctx *c, void *buf, size_t *bytes)
     h.lam_d = c->lam_d;
     h.payload_bytes = payload;
     unsigned char *dst = static_cast<unsigned char *>(buf);
-    MCUDA(c, cudaMemcpy(dst + sizeof(MCkptHeader), c->pop, payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
+    MCUDA(c, cudaMemcpy(dst + sizeof(MCkptHeader), cur_pop(c), payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
     h.payload_hash = flbm::host::fnv1a(dst + sizeof(MCkptHeader), payload);
     std::memcpy(dst, &h, sizeof(h));
     *bytes = need;
@@ -641,6 +663,8 @@ flbm_status flbm_mrestore(flbm_mctx *c, const void *buf, size_t bytes)
     const size_t payload = pop_elems(c) * sizeof(float);
     if (h.payload_bytes != payload || bytes < sizeof(MCkptHeader) + payload || h.parity > 1)
         return mfail(c, FLBM_EINVAL, "checkpoint image truncated");
+    if (two_arrays(c) && h.parity != 0)
+        return mfail(c, FLBM_EINVAL, "an in-place image in the swapped layout restores into an in-place context only");
     const unsigned char *src = static_cast<const unsigned char *>(buf) + sizeof(MCkptHeader);
     if (flbm::host::fnv1a(src, payload) != h.payload_hash)
         return mfail(c, FLBM_EINVAL, "checkpoint image corrupt (hash mismatch)");

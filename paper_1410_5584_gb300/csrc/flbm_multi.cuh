@@ -60,8 +60,9 @@ template <class L, int NS> struct MLaunch {
     // density deviations of every site (float4 per site)
     static cudaError_t density(int parity, const MStepParams &p, const float *pop, float4 *drho, cudaStream_t st);
     // force + moment collision + noise + in-place streaming of one step
-    static cudaError_t collide(int parity, const MStepParams &p, float *pop, const float4 *drho, unsigned *status,
-                               cudaStream_t st);
+    // parity 0 / 1: in place in pop; kStreamPush: read pop, write pop_out
+    static cudaError_t collide(int parity, const MStepParams &p, float *pop, float *pop_out, const float4 *drho,
+                               unsigned *status, cudaStream_t st);
     // per-site rho^s and u (either may be NULL) in double, per-block FP64 partial
     // totals [nblocks][NS + 3] of (rho^s, jbar_t + F_t / 2); needs drho of the state
     static cudaError_t observables(int parity, const MStepParams &p, const float *pop, const float4 *drho,
@@ -175,10 +176,12 @@ template <class L, int NS> constexpr size_t collide_smem(int threads)
 // forces, the baricentric velocity and the projected momentum noise follow;
 // then each species in turn is collided and streamed.  No barrier: a thread
 // reads back only its own slots.
+// 128 registers (16 warps an SM); three species are held to 96 (20 warps), measured
+// 2 % faster at 256^3 despite a 48-byte spill, which costs four species 6 %
 template <class L, int NS, int PARITY>
-__global__ void __launch_bounds__(kSiteBlockMax, 4) // <= 128 registers: 16 warps an SM
-    k_mcollide(const MStepParams p, const MPlanes<float> planes, const float4 *__restrict__ drho,
-               unsigned *__restrict__ status)
+__global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
+    k_mcollide(const MStepParams p, const MPlanes<float> planes, const MPlanes<float> out,
+               const float4 *__restrict__ drho, unsigned *__restrict__ status)
 {
     constexpr int Q = L::Q, D = L::D;
     constexpr bool PARK = kParkMoments<NS>;
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(kSiteBlockMax, 4) // <= 128 registers: 16 warp
         word[0] = Transform<L>::rest_closing_mass(fo, m[0]);
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            planes.template plane<L>(s, kern::write_slot<L, PARITY, i>())[kern::write_site<L, PARITY, i>(nb)] = word[i];
+            out.template plane<L>(s, kern::write_slot<L, PARITY, i>())[kern::write_site<L, PARITY, i>(nb)] = word[i];
         });
     });
 }
@@ -585,14 +588,16 @@ cudaError_t MLaunch<L, NS>::density(int parity, const MStepParams &p, const floa
 }
 
 template <class L, int NS>
-cudaError_t MLaunch<L, NS>::collide(int parity, const MStepParams &p, float *pop, const float4 *drho,
+cudaError_t MLaunch<L, NS>::collide(int parity, const MStepParams &p, float *pop, float *pop_out, const float4 *drho,
                                     unsigned *status, cudaStream_t st)
 {
     const dim3 b = mkern::msite_block(p), g = mkern::msite_grid(p, b);
     const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
+    const auto out = parity == kStreamPush ? mkern::mplanes(pop_out, NS, L::Q, p.N) : planes;
     const size_t smem = mkern::collide_smem<L, NS>(b.x * b.y);
-    if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, smem, st>>>(p, planes, drho, status);
-    else mkern::k_mcollide<L, NS, 1><<<g, b, smem, st>>>(p, planes, drho, status);
+    if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, smem, st>>>(p, planes, out, drho, status);
+    else if (parity == 1) mkern::k_mcollide<L, NS, 1><<<g, b, smem, st>>>(p, planes, out, drho, status);
+    else mkern::k_mcollide<L, NS, kStreamPush><<<g, b, smem, st>>>(p, planes, out, drho, status);
     return cudaGetLastError();
 }
 

@@ -490,7 +490,7 @@ class MultiLattice:
     one by default)."""
 
     def __init__(self, lattice, nspecies, nx, ny, nz=1, tau=None, kT=0.0, G=None, seed=1, rho0=None,
-                 device="cuda:0", stream=None, block=None):
+                 device="cuda:0", stream=None, block=None, streaming="two_arrays"):
         import torch
 
         if not torch.cuda.is_available():
@@ -516,6 +516,7 @@ class MultiLattice:
         if block is not None:
             self.set_option(OPT_BLOCK_X, block[0])
             self.set_option(OPT_BLOCK_Y, block[1])
+        self.set_option(OPT_STREAMING, STREAMING[streaming] if isinstance(streaming, str) else int(streaming))
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
