@@ -290,12 +290,13 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
 }
 
 // planes: the slot planes read; out: the slot planes written (the same table
-// for the in-place modes, the other array for kPush).  The full-relaxation
-// instance is held to 80 registers, six blocks an SM (measured 2 % faster at
-// 256^3 than its own 96 despite a 24-byte spill; the general instance is
-// fastest at the 128 the compiler picks).
+// for the in-place modes, the other array for kPush).  Register limits,
+// measured: D3Q19 full relaxation 80 (six blocks an SM, 2 % faster at 256^3
+// than its own 96 despite a 24-byte spill), D3Q19 general as compiled (128);
+// D2Q9, whose 18 loads a site leave it short of loads in flight, 64 and 80
+// (eight and six blocks, 5-6 % faster at 2048^2, no spill).
 template <class L, class S, int PARITY, bool FULL>
-__global__ void __launch_bounds__(kSiteBlockMax, FULL ? 6 : 1) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
+__global__ void __launch_bounds__(kSiteBlockMax, FULL ? (L::Q == 9 ? 8 : 6) : (L::Q == 9 ? 6 : 1)) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
                                                            const PlaneTable<typename S::T> out,
                                                            const float2 *__restrict__ rho,
                                                            unsigned *__restrict__ status)
