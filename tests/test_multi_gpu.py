@@ -397,3 +397,35 @@ def test_checkpoints_move_between_streaming_modes():
     c = mk("in_place")
     c.restore(odd)
     assert np.array_equal(c.get_populations(), b.get_populations())
+
+
+@pytest.mark.filterwarnings("ignore:An ill-conditioned matrix")
+def test_d3q19_three_species_structure_factors_against_lattice_theory():
+    """D3Q19, 24 x 6 x 6 box, rho = (1, 0.8, 0.6), tau = (1, 0.8, 1.25), G = 0.3
+    between all pairs: the device S_{s s'}(k_x) in bands of k against the
+    linearised-lattice covariance of the N-species D3Q19 update, 20 batches
+    of 300 snapshots."""
+    nx, ny, nz, ns, kT = 24, 6, 6, 3, 1e-4
+    rhos, taus = np.array(RHOS[:ns]), TAUS[:ns]
+    G = 0.3 * (1 - np.eye(ns))
+    gp = MultiLattice(D3Q19, ns, nx, ny, nz, taus, kT, G, 31, rho0=rhos)
+    gp.init()
+    gp.step(3000)
+    batches = []
+    for _ in range(20):
+        gp.sf_reset()
+        for _ in range(300):
+            gp.step(10)
+            gp.sf_sample(0)
+        batches.append(gp.structure_factor(0)[0])
+    B = np.array(batches)
+    c, w, T, N = oracle.tables(D3Q19)
+    k = 2 * np.pi * np.arange(1, nx // 2 + 1) / nx
+    lat = np.array([theory.multi_lattice_linear_sk(c, w, T, N, (kk, 0, 0), G, rhos, taus, kT) for kk in k])
+    for s in range(ns):
+        for t in range(ns):
+            scale = 3 * kT * np.sqrt(rhos[s] * rhos[t])
+            for band in (k < 1.0, (k >= 1.0) & (k < 2.2), k >= 2.2):
+                got = B[:, s, t, band].mean(axis=1)
+                m, se = got.mean(), got.std(ddof=1) / np.sqrt(len(got))
+                assert abs(m - lat[band, s, t].mean()) < 4 * se + 0.015 * scale, (s, t, m, lat[band, s, t].mean())
