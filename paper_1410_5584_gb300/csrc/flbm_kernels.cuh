@@ -216,13 +216,25 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     // for the other modes of species s (their per-mode factors are in cxi).
     // Square roots as x rsqrt(x): the densities are positive on every valid state
     // (a non-positive one has already raised the status flag).
+    // LATE (the general D3Q19 instance): only species 0's Philox slot 0 (the
+    // shared momentum noise) is drawn here, and each species draws the rest
+    // just before its own relaxation (step 6), which keeps them out of the
+    // registers meanwhile.  Measured at 256^3 with two arrays: 1.45 -> 1.13 ms
+    // for that instance, while the full-relaxation and D2Q9 instances are ~3 %
+    // faster drawing everything here.
+    constexpr bool LATE = L::Q == 19 && !FULL;
     const float n0 = p.noise_ref ? p.rho0[0] : rs[0];
     const float n1 = p.noise_ref ? p.rho0[1] : rs[1];
     const float hm = n0 * n1 * __frcp_rn(n0 + n1);
     const float amp_j = p.noise_amp_j * (hm * rsqrtf(hm));
-    float g[2][Q];
-    draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g[0]);
-    draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g[1]);
+    constexpr int kSlots = (Q + 3) / 4;
+    float g0[Q], g1[Q];
+    if constexpr (LATE) {
+        draw_gaussians<L, 0, 0, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
+    } else {
+        draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
+        draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g1);
+    }
 
     // 5. momentum modes: common rate, opposite noise; species velocity for Phi
     float v[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
@@ -232,7 +244,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             constexpr int a = 1 + d;
-            const float xi = s == 0 ? g[0][a] : -g[0][a];
+            const float xi = s == 0 ? g0[a] : -g0[a];
             const float R = p.lam_d * (rs[s] * u[d] - m[s][a]) + p.hlam_d * rs[s] * acc[s][d] + xi;
             v[s][d] = p.force_velocity ? m[s][a] * irs + 0.5f * acc[s][d] : (m[s][a] + 0.5f * R) * irs;
             m[s][a] += R;
@@ -247,6 +259,21 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     Closure<L>::eq(u, X);
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
+        float g[Q];
+        if constexpr (!LATE) {
+            static_for<Q>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                g[a] = s == 0 ? g0[a] : g1[a];
+            });
+        } else if constexpr (s == 0) {
+            draw_gaussians<L, 0, 1, kSlots>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g);
+            static_for<4>([&](auto ac) { // the non-momentum modes of slot 0, drawn in step 4
+                constexpr int a = decltype(ac)::value;
+                if constexpr (a > D && a < Q) g[a] = g0[a];
+            });
+        } else {
+            draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g);
+        }
         float Y[Q];
         Closure<L>::force(acc[s], v[s], Y);
         float mu[Q], fo[Q];
@@ -261,8 +288,8 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
             // FULL: every cm is zero (lambdabar_a = 1), so the old moment drops out
             // exactly and its projection is never formed
             float t;
-            if constexpr (FULL) t = p.cxi[s][a] * g[s][a];
-            else t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * g[s][a]);
+            if constexpr (FULL) t = p.cxi[s][a] * g[a];
+            else t = fmaf(p.cm[s][a], m[s][a], p.cxi[s][a] * g[a]);
             if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
             mu[a] = t;
         });
@@ -292,11 +319,11 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
 // planes: the slot planes read; out: the slot planes written (the same table
 // for the in-place modes, the other array for kPush).  Register limits,
 // measured: D3Q19 full relaxation 80 (six blocks an SM, 2 % faster at 256^3
-// than its own 96 despite a 24-byte spill), D3Q19 general as compiled (128);
-// D2Q9, whose 18 loads a site leave it short of loads in flight, 64 and 80
-// (eight and six blocks, 5-6 % faster at 2048^2, no spill).
+// than its own 96 despite a 24-byte spill), D3Q19 general 128 (it asks for
+// 176 otherwise); D2Q9, whose 18 loads a site leave it short of loads in
+// flight, 64 and 80 (eight and six blocks, 5-6 % faster at 2048^2, no spill).
 template <class L, class S, int PARITY, bool FULL>
-__global__ void __launch_bounds__(kSiteBlockMax, FULL ? (L::Q == 9 ? 8 : 6) : (L::Q == 9 ? 6 : 1)) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
+__global__ void __launch_bounds__(kSiteBlockMax, FULL ? (L::Q == 9 ? 8 : 6) : (L::Q == 9 ? 6 : 4)) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
                                                            const PlaneTable<typename S::T> out,
                                                            const float2 *__restrict__ rho,
                                                            unsigned *__restrict__ status)

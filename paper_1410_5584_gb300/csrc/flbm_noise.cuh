@@ -124,11 +124,12 @@ __device__ __forceinline__ void gaussian_pair(uint32_t wa, uint32_t wb, float sc
 }
 
 // Fill g[a] with the Gaussian of mode a, times its scale, for every mode
-// species S uses: counter (site, step, S, a/4), lane a mod 4.  The momentum
+// species S uses in the Philox slots [SLOT_LO, SLOT_HI) (all by default):
+// counter (site, step, S, a/4), lane a mod 4.  The momentum
 // modes (species 0 only) are scaled by scale_j, the others by scale.  Only the
 // needed Philox blocks and Box-Muller pairs are evaluated (decided at compile
 // time).
-template <class L, int S>
+template <class L, int S, int SLOT_LO = 0, int SLOT_HI = (L::Q + 3) / 4>
 __device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uint32_t k0, uint32_t k1,
                                                float scale_j, float scale, float (&g)[L::Q])
 {
@@ -136,7 +137,7 @@ __device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uin
         constexpr int slot = decltype(sc)::value;
         constexpr bool any = uses_mode<L, S>(4 * slot) || uses_mode<L, S>(4 * slot + 1) ||
                              uses_mode<L, S>(4 * slot + 2) || uses_mode<L, S>(4 * slot + 3);
-        if constexpr (any) {
+        if constexpr (any && slot >= SLOT_LO && slot < SLOT_HI) {
             const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)slot), k0, k1);
             gaussian_pair<L, S, 4 * slot>(x.x, x.y, scale_j, scale, g);
             gaussian_pair<L, S, 4 * slot + 2>(x.z, x.w, scale_j, scale, g);
