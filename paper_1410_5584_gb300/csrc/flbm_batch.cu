@@ -30,6 +30,7 @@ struct BatchState {
     cudaGraphExec_t graph[2] = {nullptr, nullptr}; // per parity at the start of the graph
     int graph_len[2] = {0, 0};
     bool internal = false; // batch code is calling the single-box functions on a view
+    bool full = false;     // every replica has rate 1 on all non-conserved modes
 };
 
 using namespace host;
@@ -89,10 +90,21 @@ flbm_status upload_tables(flbm_ctx *c)
     }
     if (b->reps_dirty) {
         std::vector<RepInfo> h(b->views.size());
+        bool full = true;
         for (size_t r = 0; r < h.size(); r++) {
             h[r].p = make_params(b->views[r]);
             h[r].pop_off = (unsigned long long)2 * c->Q * (unsigned long long)b->site_off[r];
             h[r].rho_off = (unsigned long long)b->site_off[r];
+            exact_divider((unsigned)h[r].p.nx, h[r].mul_nx, h[r].shift_nx);
+            exact_divider((unsigned)(h[r].p.nx * h[r].p.ny), h[r].mul_nxy, h[r].shift_nxy);
+            full = full && !h[r].p.general_collide;
+            for (int s = 0; s < 2; s++)
+                for (int a = c->D + 1; a < c->Q; a++) full = full && h[r].p.cm[s][a] == 0.0f;
+        }
+        if (full != b->full) {
+            // the captured graphs launch the collide instance of the old choice
+            drop_graphs(b);
+            b->full = full;
         }
         // the graphs read this array on the device, so it is updated in stream order
         FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -112,7 +124,7 @@ flbm_status launch_steps(flbm_ctx *c, int parity, int k0, int n)
     for (int k = 0; k < n; k++) {
         cudaError_t e = launch_batch_step(c->lat, c->storage, (parity + k) & 1, b->d_reps, b->d_tiles,
                                           (int)b->tiles_h.size(), c->pop, c->rho, c->d_status, b->d_step,
-                                          (unsigned)(k0 + k), c->stream);
+                                          (unsigned)(k0 + k), b->full, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched step launch");
     }
     cudaError_t e = launch_add_u32(b->d_step, (unsigned)n, c->stream);

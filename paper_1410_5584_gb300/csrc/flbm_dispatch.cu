@@ -67,9 +67,9 @@ cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams
 
 cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,
                               void *pop, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
-                              cudaStream_t stream)
+                              bool full, cudaStream_t stream)
 {
-    return dispatch<BatchF>(lat, storage, parity, reps, tiles, ntiles, pop, rho, status, step_base, k, stream);
+    return dispatch<BatchF>(lat, storage, parity, reps, tiles, ntiles, pop, rho, status, step_base, k, full, stream);
 }
 
 cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in, void *pop,

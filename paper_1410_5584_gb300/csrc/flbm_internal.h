@@ -44,7 +44,21 @@ struct RepInfo {
     StepParams p;
     unsigned long long pop_off;
     unsigned long long rho_off;
+    // site / nx and site / (nx ny) as (site * mul) >> shift, exact for sites < 2^31
+    unsigned long long mul_nx, mul_nxy;
+    unsigned shift_nx, shift_nxy;
 };
+
+// Multiplier and shift that divide every n < 2^31 by d exactly: with
+// l = ceil(log2 d), m = floor(2^(31+l) / d) + 1 gives floor(n m / 2^(31+l))
+// = floor(n / d) (Granlund and Montgomery, PLDI 1994, Thm. 4.2, N = 31).
+inline void exact_divider(unsigned d, unsigned long long &mul, unsigned &shift)
+{
+    unsigned l = 0;
+    while ((1ull << l) < d) l++;
+    mul = (1ull << (31 + l)) / d + 1;
+    shift = 31 + l;
+}
 
 // Device status bits (ORed by kernels, read by the host at sync points).
 constexpr unsigned kStatusNonFinite = 1u;
@@ -144,10 +158,11 @@ inline int pipeline_slices(int lat, int ny, int nz) { return lat == FLBM_D2Q9 ? 
 
 // One step of every replica of a batch (density then collide over the tile
 // work list: tiles[t] = (replica, first site of 128)); the noise counter of the
-// step is *step_base + k.
+// step is *step_base + k.  full: every replica relaxes each non-conserved
+// mode with rate 1 (the collide skips their projections).
 cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,
                               void *pop, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
-                              cudaStream_t stream);
+                              bool full, cudaStream_t stream);
 // *p += v and *p = v on the device (one thread), for the batch step counter.
 cudaError_t launch_add_u32(unsigned *p, unsigned v, cudaStream_t stream);
 cudaError_t launch_set_u32(unsigned *p, unsigned v, cudaStream_t stream);

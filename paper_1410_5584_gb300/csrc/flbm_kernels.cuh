@@ -532,21 +532,40 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
 // The step's noise counter is read from device memory (base + k), so a CUDA
 // graph of several steps can be replayed without changing its parameters.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void stage_params(const RepInfo *__restrict__ reps, int r, StepParams &sp,
-                                             unsigned long long &pop_off, unsigned long long &rho_off,
+// A replica's step parameters, offsets and exact dividers, staged in shared memory.
+struct StagedRep {
+    StepParams sp;
+    unsigned long long pop_off, rho_off, mul_nx, mul_nxy;
+    unsigned shift_nx, shift_nxy;
+    // (x, y, z) of a replica-local site without integer division
+    __device__ __forceinline__ void coords(int site, int &x, int &y, int &z) const
+    {
+        const unsigned row = (unsigned)(((unsigned long long)(unsigned)site * mul_nx) >> shift_nx);
+        const unsigned plane = (unsigned)(((unsigned long long)(unsigned)site * mul_nxy) >> shift_nxy);
+        x = site - (int)row * sp.nx;
+        y = (int)row - (int)plane * sp.ny;
+        z = (int)plane;
+    }
+};
+
+__device__ __forceinline__ void stage_params(const RepInfo *__restrict__ reps, int r, StagedRep &st,
                                              const unsigned *__restrict__ step_base, unsigned k)
 {
     constexpr int words = (int)(sizeof(StepParams) / sizeof(unsigned));
     static_assert(sizeof(StepParams) % sizeof(unsigned) == 0, "StepParams must be a whole number of words");
     const unsigned *src = reinterpret_cast<const unsigned *>(&reps[r].p);
-    unsigned *dst = reinterpret_cast<unsigned *>(&sp);
+    unsigned *dst = reinterpret_cast<unsigned *>(&st.sp);
     for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldg(src + w);
     if (threadIdx.x == 0) {
-        pop_off = reps[r].pop_off;
-        rho_off = reps[r].rho_off;
+        st.pop_off = reps[r].pop_off;
+        st.rho_off = reps[r].rho_off;
+        st.mul_nx = reps[r].mul_nx;
+        st.mul_nxy = reps[r].mul_nxy;
+        st.shift_nx = reps[r].shift_nx;
+        st.shift_nxy = reps[r].shift_nxy;
     }
     __syncthreads();
-    if (threadIdx.x == 0) sp.step = *step_base + k;
+    if (threadIdx.x == 0) st.sp.step = *step_base + k;
     __syncthreads();
 }
 
@@ -555,34 +574,34 @@ __global__ void __launch_bounds__(128) k_density_batch(const RepInfo *__restrict
                                                        typename S::T *__restrict__ pop, float2 *__restrict__ rho,
                                                        const unsigned *__restrict__ step_base, unsigned k)
 {
-    __shared__ StepParams sp;
-    __shared__ unsigned long long pop_off, rho_off;
+    __shared__ StagedRep st;
     const int2 t = tiles[blockIdx.x];
-    stage_params(reps, t.x, sp, pop_off, rho_off, step_base, k);
+    stage_params(reps, t.x, st, step_base, k);
     const int site = t.y + (int)threadIdx.x;
-    if (site >= sp.N) return;
-    const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
-    const Nbr nb = make_nbr(sp, x, y, z);
-    rho[rho_off + site] = site_density<L, S, PARITY>(sp, FlatPlanes<const typename S::T>{pop + pop_off, (size_t)sp.N}, nb);
+    if (site >= st.sp.N) return;
+    int x, y, z;
+    st.coords(site, x, y, z);
+    const Nbr nb = make_nbr(st.sp, x, y, z);
+    rho[st.rho_off + site] =
+        site_density<L, S, PARITY>(st.sp, FlatPlanes<const typename S::T>{pop + st.pop_off, (size_t)st.sp.N}, nb);
 }
 
-template <class L, class S, int PARITY>
+template <class L, class S, int PARITY, bool FULL>
 __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict__ reps, const int2 *__restrict__ tiles,
                                                        typename S::T *__restrict__ pop, const float2 *__restrict__ rho,
                                                        unsigned *__restrict__ status, const unsigned *__restrict__ step_base,
                                                        unsigned k)
 {
-    __shared__ StepParams sp;
-    __shared__ unsigned long long pop_off, rho_off;
+    __shared__ StagedRep st;
     const int2 t = tiles[blockIdx.x];
-    stage_params(reps, t.x, sp, pop_off, rho_off, step_base, k);
+    stage_params(reps, t.x, st, step_base, k);
     const int site = t.y + (int)threadIdx.x;
-    if (site >= sp.N) return;
-    const int x = site % sp.nx, y = (site / sp.nx) % sp.ny, z = site / (sp.nx * sp.ny);
-    const Nbr nb = make_nbr(sp, x, y, z);
-    const FlatPlanes<typename S::T> fp{pop + pop_off, (size_t)sp.N};
-    site_collide<L, S, PARITY, false>(sp, fp, fp, rho + rho_off, status, nb,
-                                      [] { return true; });
+    if (site >= st.sp.N) return;
+    int x, y, z;
+    st.coords(site, x, y, z);
+    const Nbr nb = make_nbr(st.sp, x, y, z);
+    const FlatPlanes<typename S::T> fp{pop + st.pop_off, (size_t)st.sp.N};
+    site_collide<L, S, PARITY, false, true, FULL>(st.sp, fp, fp, rho + st.rho_off, status, nb, [] { return true; });
 }
 
 // ---------------------------------------------------------------------------
@@ -866,17 +885,19 @@ cudaError_t Launch<L, S>::step_fused(int parity, const StepParams &p, void *pop,
 
 template <class L, class S>
 cudaError_t Launch<L, S>::batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,
-                                     float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                                     float *rho, unsigned *status, const unsigned *step_base, unsigned k, bool full,
                                      cudaStream_t st)
 {
     auto *ptr = static_cast<typename S::T *>(pop);
     auto *r2 = reinterpret_cast<float2 *>(rho);
     if (parity == 0) {
         kern::k_density_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-        kern::k_collide_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        if (full) kern::k_collide_batch<L, S, 0, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        else kern::k_collide_batch<L, S, 0, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
     } else {
         kern::k_density_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-        kern::k_collide_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        if (full) kern::k_collide_batch<L, S, 1, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        else kern::k_collide_batch<L, S, 1, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
     }
     return cudaGetLastError();
 }

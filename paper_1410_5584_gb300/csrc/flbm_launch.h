@@ -14,7 +14,7 @@ template <class L, class S> struct Launch {
     static cudaError_t step_fused(int parity, const StepParams &p, void *pop, float *rho, unsigned *status,
                                   unsigned *counters, double wait_ms, int stall, int lag, cudaStream_t st);
     static cudaError_t batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,
-                                  float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                                  float *rho, unsigned *status, const unsigned *step_base, unsigned k, bool full,
                                   cudaStream_t st);
     static cudaError_t init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st);
     static cudaError_t gather(int parity, const StepParams &p, const void *pop, const int64_t *sites, int64_t n,

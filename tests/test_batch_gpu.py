@@ -94,3 +94,30 @@ def test_batch_observables_checkpoint_and_views():
     with pytest.raises(FlbmError) as e:
         F.check(b.replicas[0]._h, F.lib().flbm_step(b.replicas[0]._h, 1))
     assert e.value.status == F.ESTATE
+
+
+@pytest.mark.parametrize("lat", [D2Q9, D3Q19])
+def test_full_relaxation_batch_matches_lone_contexts_and_the_general_collide(lat):
+    """Replicas with every rate 1 run the batch collide that skips the
+    non-conserved projections: each replica agrees with a lone context to
+    rounding, and with the batch forced onto the general collide (a test
+    hook) to rounding; the replica sizes exercise the exact dividers that
+    replace the per-site integer division (rows of 37, 129 and 2 sites)."""
+    reps = [dict(r, tau_a=1.0, tau_b=1.0) for r in _replicas(lat)]
+    states = _states(lat, reps, seed=6)
+    flat = np.concatenate([s.ravel() for s in states])
+    runs = []
+    for general in (0, 1):
+        b = Batch(lat, reps, graph_steps=4, test_general_collide=general)
+        b.set_populations(flat, step=2)
+        b.step(9)
+        runs.append([b.replicas[k].get_populations() for k in range(len(reps))])
+        b.close()
+    for k, r in enumerate(reps):
+        g = Lattice(lat, r["nx"], r["ny"], r["nz"], 1.0, 1.0, r["kT"], r["G"], r["seed"],
+                    rho0_a=r["rho0_a"], rho0_b=r["rho0_b"])
+        g.set_populations(states[k], step=2)
+        g.step(9)
+        ref = g.get_populations()
+        assert np.max(np.abs(runs[0][k] - ref)) <= 2e-6 * np.max(np.abs(ref)), k
+        assert np.max(np.abs(runs[0][k] - runs[1][k])) <= 2e-6 * np.max(np.abs(ref)), k
