@@ -296,9 +296,10 @@ def batched_form(seed, steps, device, nrep=64):
 def capillary_form(seed, device, steps=20000):
     """The capillary-fluctuation workload of Sec. VI B: a D2Q9 100 x 512 box
     with an A-rich stripe 50 wide (G = 1.5, kT = 1e-5, all rates 1): MLUPS of a
-    lone context and of the same box as a one-replica batch replayed from CUDA
-    graphs (51,200 sites are too few to hide launch latency), and the time of
-    one tracked height-spectrum snapshot."""
+    lone context launching each step, of the same context replaying 64-step
+    CUDA graphs, and of the box as a one-replica batch replayed from graphs
+    (51,200 sites are too few to hide launch latency), and the time of one
+    tracked height-spectrum snapshot."""
     import numpy as np
     import torch
 
@@ -322,6 +323,10 @@ def capillary_form(seed, device, steps=20000):
     g.init(ra, rb)
     g.step(2000)
     t_lone = timed(lambda: g.step(steps), g.stream)
+    g.set_option("graph_steps", 64)
+    g.step(128)
+    t_graph = timed(lambda: g.step(steps), g.stream)
+    g.set_option("graph_steps", 0)
     g.cap_sample(-1, -1)
     t_cap = timed(lambda: [g.cap_sample(-1, -1) for _ in range(100)], g.stream) / 100
     g.sync()
@@ -335,6 +340,7 @@ def capillary_form(seed, device, steps=20000):
     b.close()
     sites = nx * ny
     return {"unit": "MLUPS", "sites": sites, "steps": steps, "lone_context": sites * steps / t_lone / 1e6,
+            "lone_context_graphs_64": sites * steps / t_graph / 1e6,
             "one_replica_batch": sites * steps / t_batch / 1e6, "graph_steps": graph_steps,
             "ms_per_height_snapshot": t_cap * 1e3}
 

@@ -131,8 +131,11 @@ enum {
     FLBM_OPT_PIPE_LAG = 14,      /* fused schedule: how many slices the density work runs ahead of the
                                     collisions; 0 (default) = the smallest lag that keeps it ahead of
                                     the work in flight; else an integer >= 2 (results are identical) */
-    FLBM_OPT_GRAPH_STEPS = 15,   /* batches: steps per CUDA graph replayed by flbm_step (0 = launch each
-                                    step directly); default 16 */
+    FLBM_OPT_GRAPH_STEPS = 15,   /* steps per CUDA graph that flbm_step replays: batches (default 16)
+                                    and single boxes (default 0: each step launched directly; the
+                                    two-kernel schedule, kernel timing off).  A graph is captured per
+                                    starting parity and dropped by any option or stream change.
+                                    Same results; pays on small boxes whose steps are launch-bound */
     FLBM_OPT_SLABS = 16,         /* overlap schedule: number of slabs, 3 .. 256 (at most the number of
                                     planes, or rows for D2Q9); default 8 */
     FLBM_OPT_BLOCK_X = 17,       /* thread block of the density and collide kernels: sites along x,

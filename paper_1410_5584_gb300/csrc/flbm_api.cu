@@ -107,17 +107,27 @@ size_t pop_bytes_of(const flbm_ctx *c)
     return array_bytes_of(c) * (c->streaming == FLBM_STREAM_TWO_ARRAYS && !c->batch ? 2 : 1);
 }
 bool two_arrays(const flbm_ctx *c) { return c->streaming == FLBM_STREAM_TWO_ARRAYS && !c->batch; }
-void *cur_pop(const flbm_ctx *c)
+// the same for an explicit parity (a step captured ahead of time)
+void *cur_pop_at(const flbm_ctx *c, int parity)
 {
-    if (!two_arrays(c) || c->parity == 0) return c->pop;
+    if (!two_arrays(c) || parity == 0) return c->pop;
     return static_cast<unsigned char *>(c->pop) + array_bytes_of(c);
 }
-void *next_pop(const flbm_ctx *c)
+void *next_pop_at(const flbm_ctx *c, int parity)
 {
     if (!two_arrays(c)) return c->pop;
-    return static_cast<unsigned char *>(c->pop) + (c->parity == 0 ? array_bytes_of(c) : 0);
+    return static_cast<unsigned char *>(c->pop) + (parity == 0 ? array_bytes_of(c) : 0);
 }
+void *cur_pop(const flbm_ctx *c) { return cur_pop_at(c, c->parity); }
+void *next_pop(const flbm_ctx *c) { return next_pop_at(c, c->parity); }
 int layout_parity(const flbm_ctx *c) { return two_arrays(c) ? 0 : c->parity; }
+void drop_step_graphs(flbm_ctx *c)
+{
+    for (int k = 0; k < 2; k++) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+    }
+}
 size_t rho_bytes_of(const flbm_ctx *c) { return (size_t)2 * (size_t)c->N * sizeof(float); }
 
 flbm_status ensure_status(flbm_ctx *c)
@@ -422,6 +432,13 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
     if (is_batch(c)) return batch_set_option(c, key, v);
     if (c->is_view && key != FLBM_OPT_SF_AXIS && !view_call_allowed(c))
         return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
+    drop_step_graphs(c); // a captured step holds the parameters and launch settings by value
+    if (key == FLBM_OPT_GRAPH_STEPS) {
+        if (!(v >= 0.0 && v <= 4096.0) || v != (double)(int)v)
+            return fail(c, FLBM_EINVAL, "graph steps must be an integer in [0, 4096]");
+        c->graph_steps = (int)v;
+        return FLBM_OK;
+    }
     if (key == FLBM_OPT_STORAGE) {
         if (c->pop) return fail(c, FLBM_ESTATE, "the storage format is fixed once the buffers exist");
         if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, FLBM_EINVAL, "storage must be 0 (f32), 1 (f16) or 2 (bf16)");
@@ -519,10 +536,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_TEST_STALL: *value = c->test_stall; break;
     case FLBM_OPT_TEST_GENERAL_COLLIDE: *value = c->test_general; break;
     case FLBM_OPT_PIPE_LAG: *value = c->pipe_lag; break;
-    case FLBM_OPT_GRAPH_STEPS:
-        if (!is_batch(c)) return FLBM_EUNSUPPORTED;
-        *value = batch_graph_steps(c);
-        break;
+    case FLBM_OPT_GRAPH_STEPS: *value = is_batch(c) ? batch_graph_steps(c) : c->graph_steps; break;
     case FLBM_OPT_SLABS: *value = c->slabs; break;
     case FLBM_OPT_BLOCK_X: *value = c->block_x; break;
     case FLBM_OPT_BLOCK_Y: *value = c->block_y; break;
@@ -540,6 +554,7 @@ flbm_status flbm_set_stream(flbm_ctx *c, void *stream)
 {
     if (!c) return FLBM_EINVAL;
     if (!view_call_allowed(c)) return fail(c, FLBM_ESTATE, "a replica view can be observed, not changed; use its batch");
+    drop_step_graphs(c);
     if (c->own_stream && c->stream) {
         cudaStreamSynchronize(c->stream);
         cudaStreamDestroy(c->stream);
@@ -732,6 +747,45 @@ flbm_status step_overlap(flbm_ctx *c, int64_t n, StepParams p)
     return FLBM_OK;
 }
 
+// One CUDA graph of c->graph_steps two-kernel steps starting at `parity`: the
+// step kernels read the noise counter as *d_gstep + k, so the graph replays
+// for any starting step once d_gstep is set.
+flbm_status ensure_step_graph(flbm_ctx *c, int parity)
+{
+    if (c->graph[parity]) return FLBM_OK;
+    if (!c->d_gstep) FLBM_CUDA(c, cudaMalloc((void **)&c->d_gstep, sizeof(unsigned)), "cudaMalloc(graph step counter)");
+    StepParams p = make_params(c);
+    p.step_dev = c->d_gstep;
+    cudaGraph_t g = nullptr;
+    FLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < c->graph_steps && e == cudaSuccess; k++) {
+        const int par = (parity + k) & 1;
+        p.step = (uint32_t)k;
+        void *cur = cur_pop_at(c, par);
+        e = launch_density(c->lat, c->storage, two_arrays(c) ? 0 : par, p, cur, c->rho, c->stream);
+        if (e == cudaSuccess) {
+            if (two_arrays(c))
+                e = launch_collide(c->lat, c->storage, kStreamPush, p, cur, next_pop_at(c, par), c->rho, c->d_status,
+                                   c->stream);
+            else
+                e = launch_collide(c->lat, c->storage, par, p, c->pop, c->pop, c->rho, c->d_status, c->stream);
+        }
+    }
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e != cudaSuccess ? e : ee, "step graph capture");
+    }
+    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[parity] = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    return FLBM_OK;
+}
+
 flbm_status flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
@@ -739,9 +793,22 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
     if (is_batch(c)) return batch_step(c, n);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
     if (n == 0) return FLBM_OK;
-    StepParams p = make_params(c);
     if (two_arrays(c) && c->schedule != FLBM_SCHEDULE_TWO_KERNELS)
         return fail(c, FLBM_EUNSUPPORTED, "two-array streaming runs the two-kernel schedule only");
+    // whole graphs of graph_steps steps first (two-kernel schedule, timing off)
+    if (c->graph_steps > 0 && c->schedule == FLBM_SCHEDULE_TWO_KERNELS && !c->timing) {
+        while (n >= c->graph_steps) {
+            flbm_status st = ensure_step_graph(c, c->parity);
+            if (st != FLBM_OK) return st;
+            FLBM_CUDA(c, launch_set_u32(c->d_gstep, (unsigned)c->step, c->stream), "graph step counter");
+            FLBM_CUDA(c, cudaGraphLaunch(c->graph[c->parity], c->stream), "cudaGraphLaunch");
+            c->step += c->graph_steps;
+            c->parity = (c->parity + c->graph_steps) & 1;
+            n -= c->graph_steps;
+        }
+        if (n == 0) return FLBM_OK;
+    }
+    StepParams p = make_params(c);
     if (c->schedule == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
     if (c->schedule == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
@@ -1074,6 +1141,8 @@ void flbm_destroy(flbm_ctx *c)
         if (c->pop) cudaFree(c->pop);
         if (c->rho) cudaFree(c->rho);
     }
+    drop_step_graphs(c);
+    if (c->d_gstep) cudaFree(c->d_gstep);
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_pipe) cudaFree(c->d_pipe);
     if (c->d_obs) cudaFree(c->d_obs);

@@ -26,6 +26,11 @@ struct flbm_ctx {
     int pipe_lag = 0;
     int test_stall = 0;
     int test_general = 0; // FLBM_OPT_TEST_GENERAL_COLLIDE
+    // CUDA graphs of graph_steps two-kernel steps, one per starting parity
+    // (FLBM_OPT_GRAPH_STEPS on a single box; 0 = launch each step directly)
+    int graph_steps = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned *d_gstep = nullptr; // noise counter at the start of a graph replay
     double rho0[2] = {1.0, 1.0};
     // state
     int64_t step = 0;
@@ -114,6 +119,7 @@ size_t array_bytes_of(const flbm_ctx *c);
 void *cur_pop(const flbm_ctx *c);
 void *next_pop(const flbm_ctx *c);
 int layout_parity(const flbm_ctx *c);
+void drop_step_graphs(flbm_ctx *c); // after any change of what a step launches
 size_t rho_bytes_of(const flbm_ctx *c);
 uint64_t fnv1a(const unsigned char *p, size_t n);
 } // namespace host

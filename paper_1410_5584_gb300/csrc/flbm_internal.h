@@ -34,7 +34,8 @@ struct StepParams {
     int noise_ref;             // 1: noise amplitudes from rho0 instead of the local densities
     int force_velocity;        // 0: rho v = jbar + R_j/2 ; 1: v = vbar + a/2
     uint32_t key0, key1;       // Philox key (seed low, seed high)
-    uint32_t step;             // noise counter word for this step
+    uint32_t step;             // noise counter word for this step, or its offset from *step_dev
+    const unsigned *step_dev;  // NULL, or a device word the counter is read from (CUDA-graph replays)
     int general_collide;       // test hook: 1 keeps the general collide even when every rate is 1
 };
 

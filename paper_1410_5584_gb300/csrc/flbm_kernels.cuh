@@ -223,6 +223,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     // for that instance, while the full-relaxation and D2Q9 instances are ~3 %
     // faster drawing everything here.
     constexpr bool LATE = L::Q == 19 && !FULL;
+    const uint32_t nstep = p.step_dev ? __ldg(p.step_dev) + p.step : p.step; // noise counter of this step
     const float n0 = p.noise_ref ? p.rho0[0] : rs[0];
     const float n1 = p.noise_ref ? p.rho0[1] : rs[1];
     const float hm = n0 * n1 * __frcp_rn(n0 + n1);
@@ -230,10 +231,10 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     constexpr int kSlots = (Q + 3) / 4;
     float g0[Q], g1[Q];
     if constexpr (LATE) {
-        draw_gaussians<L, 0, 0, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
+        draw_gaussians<L, 0, 0, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
     } else {
-        draw_gaussians<L, 0>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
-        draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g1);
+        draw_gaussians<L, 0>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
+        draw_gaussians<L, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g1);
     }
 
     // 5. momentum modes: common rate, opposite noise; species velocity for Phi
@@ -266,13 +267,13 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
                 g[a] = s == 0 ? g0[a] : g1[a];
             });
         } else if constexpr (s == 0) {
-            draw_gaussians<L, 0, 1, kSlots>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g);
+            draw_gaussians<L, 0, 1, kSlots>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g);
             static_for<4>([&](auto ac) { // the non-momentum modes of slot 0, drawn in step 4
                 constexpr int a = decltype(ac)::value;
                 if constexpr (a > D && a < Q) g[a] = g0[a];
             });
         } else {
-            draw_gaussians<L, 1>((uint32_t)site, p.step, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g);
+            draw_gaussians<L, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g);
         }
         float Y[Q];
         Closure<L>::force(acc[s], v[s], Y);

@@ -272,11 +272,13 @@ std::vector<Settings> candidates(const flbm_ctx *c)
     const int shapes[3][2] = {{128, 1}, {64, 2}, {32, 4}};
     const bool in_place = c->streaming == FLBM_STREAM_IN_PLACE; // two arrays: the two-kernel schedule only
     for (const auto &b : shapes) {
-        out.push_back({{"schedule", (double)FLBM_SCHEDULE_TWO_KERNELS}, {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
+        for (int gs : {0, 16})
+            out.push_back({{"schedule", (double)FLBM_SCHEDULE_TWO_KERNELS}, {"graph_steps", (double)gs},
+                           {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
         for (int k : {4, 8})
             if (in_place && axis >= k)
-                out.push_back({{"schedule", (double)FLBM_SCHEDULE_OVERLAP}, {"slabs", (double)k},
-                               {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
+                out.push_back({{"schedule", (double)FLBM_SCHEDULE_OVERLAP}, {"graph_steps", 0.0},
+                               {"slabs", (double)k}, {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
     }
     return out;
 }
@@ -312,7 +314,9 @@ extern "C" flbm_status flbm_autotune(flbm_ctx *c, int steps, const char *cache_p
         flbm_status s = apply_settings(c, cand[k]);
         if (s != FLBM_OK) return s;
         double ms = 0.0;
-        if ((s = time_steps(c, 2, steps, &ms)) != FLBM_OK) return s;
+        // warm up past one graph length, so that a graph is captured before the timing
+        const int gs = is_batch(c) ? batch_graph_steps(c) : c->graph_steps;
+        if ((s = time_steps(c, 2 + gs, steps, &ms)) != FLBM_OK) return s;
         best_ms[k] = std::min(best_ms[k], ms);
         return snap.put_back();
     };

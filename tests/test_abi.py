@@ -100,7 +100,7 @@ def test_launch_settings_are_validated_and_read_back(lib):
         for key, want in ((F.OPT_BLOCK_X, 32), (F.OPT_BLOCK_Y, 4), (F.OPT_SCHEDULE, 2), (F.OPT_SLABS, 5),
                           (F.OPT_LAMBDA_MODE + 100 + 7, 1.0)):
             assert lib.flbm_get_option(h, key, ctypes.byref(v)) == F.OK and v.value == want, key
-        assert lib.flbm_get_option(h, F.OPT_GRAPH_STEPS, ctypes.byref(v)) == F.EUNSUPPORTED  # batches only
+        assert lib.flbm_get_option(h, F.OPT_GRAPH_STEPS, ctypes.byref(v)) == F.OK and v.value == 0  # off
         assert lib.flbm_get_option(h, 12345, ctypes.byref(v)) == F.EINVAL
         # the autotuner checks its arguments and the state before touching the GPU
         assert lib.flbm_autotune(h, 0, None) == F.EINVAL
@@ -202,5 +202,18 @@ def test_streaming_option_and_buffer_sizes(lib):
         assert lib.flbm_buffer_bytes(h, ctypes.byref(pb1), ctypes.byref(rb1)) == F.OK
         assert pb2.value == 2 * pb1.value == 2 * 2 * 19 * 8 * 6 * 4 * 4
         assert rb1.value == rb2.value
+    finally:
+        lib.flbm_destroy(h)
+
+
+def test_graph_steps_option_on_a_single_box(lib):
+    h = F.flbm_create(0, 16, 8, 1, 1.0, 1.0, 1e-4, 0.5, 1)
+    try:
+        v = ctypes.c_double(-1)
+        assert lib.flbm_get_option(h, F.OPT_GRAPH_STEPS, ctypes.byref(v)) == F.OK and v.value == 0
+        assert lib.flbm_set_option(h, F.OPT_GRAPH_STEPS, 16) == F.OK
+        assert lib.flbm_get_option(h, F.OPT_GRAPH_STEPS, ctypes.byref(v)) == F.OK and v.value == 16
+        assert lib.flbm_set_option(h, F.OPT_GRAPH_STEPS, -1) == F.EINVAL
+        assert lib.flbm_set_option(h, F.OPT_GRAPH_STEPS, 2.5) == F.EINVAL
     finally:
         lib.flbm_destroy(h)
