@@ -484,7 +484,8 @@ flbm_status flbm_mcreate(flbm_lattice lat, int nspecies, int nx, int ny, int nz,
 
 /* Options: FLBM_OPT_KERNEL_TIMING, FLBM_OPT_BLOCK_X, FLBM_OPT_BLOCK_Y,
  * FLBM_OPT_STREAMING (as for two species; two arrays by default, in place on
- * request, bitwise the same update) and FLBM_OPT_RHO0_SPECIES + s.
+ * request, bitwise the same update), FLBM_OPT_GRAPH_STEPS (as for a single
+ * two-species box, default 0) and FLBM_OPT_RHO0_SPECIES + s.
  * FLBM_EINVAL otherwise. */
 flbm_status flbm_mset_option(flbm_mctx *ctx, int key, double value);
 

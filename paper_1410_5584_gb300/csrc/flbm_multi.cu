@@ -20,6 +20,10 @@ struct flbm_mctx {
     uint64_t seed = 0;
     int block_x = 128, block_y = 1;
     int streaming = FLBM_STREAM_TWO_ARRAYS; // FLBM_OPT_STREAMING
+    // CUDA graphs of graph_steps steps, one per starting parity (FLBM_OPT_GRAPH_STEPS)
+    int graph_steps = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    unsigned *d_gstep = nullptr; // noise counter at the start of a replay
     // state
     int64_t step = 0;
     int parity = 0; // in place: 0 natural layout, 1 swapped layout (after an odd number of steps);
@@ -136,8 +140,17 @@ size_t pop_elems(const flbm_mctx *c) { return (size_t)c->ns * c->Q * (size_t)c->
 bool two_arrays(const flbm_mctx *c) { return c->streaming == FLBM_STREAM_TWO_ARRAYS; }
 // the array holding the current state, the one a two-array step writes, and
 // the layout readers see (two arrays: always natural)
-float *cur_pop(const flbm_mctx *c) { return c->pop + (two_arrays(c) && c->parity ? pop_elems(c) : 0); }
-float *next_pop(const flbm_mctx *c) { return c->pop + (two_arrays(c) && !c->parity ? pop_elems(c) : 0); }
+float *cur_pop_at(const flbm_mctx *c, int par) { return c->pop + (two_arrays(c) && par ? pop_elems(c) : 0); }
+float *next_pop_at(const flbm_mctx *c, int par) { return c->pop + (two_arrays(c) && !par ? pop_elems(c) : 0); }
+float *cur_pop(const flbm_mctx *c) { return cur_pop_at(c, c->parity); }
+float *next_pop(const flbm_mctx *c) { return next_pop_at(c, c->parity); }
+void drop_graphs(flbm_mctx *c)
+{
+    for (int k = 0; k < 2; k++) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+    }
+}
 int layout_parity(const flbm_mctx *c) { return two_arrays(c) ? 0 : c->parity; }
 
 flbm_status ensure_buffers(flbm_mctx *c)
@@ -271,6 +284,13 @@ flbm_status flbm_mcreate(flbm_lattice lat, int nspecies, int nx, int ny, int nz,
 flbm_status flbm_mset_option(flbm_mctx *c, int key, double v)
 {
     if (!c) return FLBM_EINVAL;
+    drop_graphs(c); // a captured step holds the parameters and launch settings by value
+    if (key == FLBM_OPT_GRAPH_STEPS) {
+        if (!(v >= 0.0 && v <= 4096.0) || v != (double)(int)v)
+            return mfail(c, FLBM_EINVAL, "graph steps must be an integer in [0, 4096]");
+        c->graph_steps = (int)v;
+        return FLBM_OK;
+    }
     if (key == FLBM_OPT_KERNEL_TIMING) {
         if (v != 0.0 && v != 1.0) return mfail(c, FLBM_EINVAL, "kernel timing is 0 or 1");
         if (c->stream) {
@@ -311,6 +331,7 @@ flbm_status flbm_mset_option(flbm_mctx *c, int key, double v)
 flbm_status flbm_mset_stream(flbm_mctx *c, void *stream)
 {
     if (!c) return FLBM_EINVAL;
+    drop_graphs(c);
     if (c->initialised) {
         MCUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     }
@@ -353,11 +374,55 @@ flbm_status flbm_minit(flbm_mctx *c, const double *rho)
     return FLBM_OK;
 }
 
+// One CUDA graph of graph_steps steps from `parity`; the collide reads the
+// noise counter as *d_gstep + k.
+flbm_status ensure_graph(flbm_mctx *c, int parity)
+{
+    if (c->graph[parity]) return FLBM_OK;
+    if (!c->d_gstep) MCUDA(c, cudaMalloc((void **)&c->d_gstep, sizeof(unsigned)), "cudaMalloc(graph step counter)");
+    MStepParams p = make_mparams(c);
+    p.step_dev = c->d_gstep;
+    cudaGraph_t g = nullptr;
+    MCUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < c->graph_steps && e == cudaSuccess; k++) {
+        const int par = (parity + k) & 1;
+        p.step = (uint32_t)k;
+        float *cur = cur_pop_at(c, par), *nxt = next_pop_at(c, par);
+        const int lp = two_arrays(c) ? 0 : par, cp = two_arrays(c) ? flbm::kStreamPush : par;
+        e = dispatch(c, [&](auto l) { return decltype(l)::density(lp, p, cur, c->drho, c->stream); });
+        if (e == cudaSuccess)
+            e = dispatch(c, [&](auto l) { return decltype(l)::collide(cp, p, cur, nxt, c->drho, c->d_status, c->stream); });
+    }
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return mfail(c, FLBM_ECUDA, "step graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[parity] = nullptr;
+        return mfail(c, FLBM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    return FLBM_OK;
+}
+
 flbm_status flbm_mstep(flbm_mctx *c, int64_t n)
 {
     flbm_status st = check_ready(c);
     if (st != FLBM_OK) return st;
     if (n < 0) return mfail(c, FLBM_EINVAL, "negative step count");
+    if (c->graph_steps > 0 && !c->timing) {
+        while (n >= c->graph_steps) {
+            if ((st = ensure_graph(c, c->parity)) != FLBM_OK) return st;
+            MCUDA(c, flbm::launch_set_u32(c->d_gstep, (unsigned)c->step, c->stream), "graph step counter");
+            MCUDA(c, cudaGraphLaunch(c->graph[c->parity], c->stream), "cudaGraphLaunch");
+            c->step += c->graph_steps;
+            c->parity = (c->parity + c->graph_steps) & 1;
+            n -= c->graph_steps;
+        }
+    }
     for (int64_t k = 0; k < n; k++) {
         const MStepParams p = make_mparams(c);
         const int parity = c->parity;
@@ -696,6 +761,8 @@ void flbm_mdestroy(flbm_mctx *c)
     cudaFree(c->pop);
     cudaFree(c->drho);
     cudaFree(c->d_status);
+    drop_graphs(c);
+    cudaFree(c->d_gstep);
     cudaFree(c->d_obs);
     cudaFree(c->d_partials);
     cudaFree(c->d_sf_prof);

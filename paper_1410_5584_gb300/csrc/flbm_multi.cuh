@@ -46,7 +46,8 @@ struct MStepParams {
     // m*_a / N_a = cm m_a + ceq m^eq_a + cphi Phi_a + cxi sqrt(rho^s) g_a
     float cm[kMaxSpecies][kMaxQ], ceq[kMaxSpecies][kMaxQ], cphi[kMaxSpecies][kMaxQ], cxi[kMaxSpecies][kMaxQ];
     float rho0[kMaxSpecies];           // reference densities (base of the stored deviations)
-    uint32_t key0, key1, step;
+    uint32_t key0, key1, step;        // step: the noise counter, or its offset from *step_dev
+    const unsigned *step_dev;         // NULL, or a device word the counter is read from (graph replays)
 };
 
 template <class T> struct MPlanes {
@@ -278,12 +279,13 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
 
     // 4. Philox slot 0 of every species: modes 1 .. 3 (the momenta; for D2Q9
     // also mode 3, kept for step 6).  Projected momentum noise.
+    const uint32_t nstep = p.step_dev ? __ldg(p.step_dev) + p.step : p.step; // noise counter of this step
     float g3[NS], sq[NS], xi[NS][3];
     {
         float g0[NS][4];
         static_for<NS>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            slot_gaussians<0xE>((uint32_t)site, p.step, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
+            slot_gaussians<0xE>((uint32_t)site, nstep, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
             sq[s] = rs[s] * rsqrtf(rs[s]); // sqrt(rho^s); rho^s > 0 on every valid state
             g3[s] = g0[s][3];
         });
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
             constexpr int lanes = Q - 4 * slot < 4 ? Q - 4 * slot : 4;
             constexpr int mask = (1 << lanes) - 1;
             float gs[4];
-            slot_gaussians<mask>((uint32_t)site, p.step, (uint32_t)s, (uint32_t)slot, p.key0, p.key1, gs);
+            slot_gaussians<mask>((uint32_t)site, nstep, (uint32_t)s, (uint32_t)slot, p.key0, p.key1, gs);
             static_for<lanes>([&](auto lc) {
                 constexpr int l = decltype(lc)::value;
                 g[4 * slot + l] = gs[l];

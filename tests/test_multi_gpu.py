@@ -429,3 +429,27 @@ def test_d3q19_three_species_structure_factors_against_lattice_theory():
                 got = B[:, s, t, band].mean(axis=1)
                 m, se = got.mean(), got.std(ddof=1) / np.sqrt(len(got))
                 assert abs(m - lat[band, s, t].mean()) < 4 * se + 0.015 * scale, (s, t, m, lat[band, s, t].mean())
+
+
+@pytest.mark.parametrize("mode", ["two_arrays", "in_place"])
+def test_graph_steps_match_direct_launches(mode):
+    """N-species steps replayed from CUDA graphs (4, then 3 steps a graph)
+    give the same bits as direct launches across calls of any length."""
+    from paper_1410_5584_gb300 import flbm as F
+    shape, ns = (1, 18, 26), 3
+    G = _couplings(ns, 0.5, seed=21)
+    f0 = _state(D2Q9, ns, shape, seed=22)
+    runs = []
+    for graphs in (0, 1):
+        gp = MultiLattice(D2Q9, ns, 26, 18, 1, TAUS[:ns], 1e-4, G, 4, streaming=mode)
+        if graphs:
+            gp.set_option(F.OPT_GRAPH_STEPS, 4)
+        gp.set_populations(f0, step=1)
+        for n in (5, 1, 8):
+            gp.step(n)
+        if graphs:
+            gp.set_option(F.OPT_GRAPH_STEPS, 3)
+        gp.step(7)
+        assert gp.step_count == 22
+        runs.append(gp.get_populations())
+    assert np.array_equal(runs[0], runs[1])
