@@ -217,3 +217,48 @@ def test_graph_steps_option_on_a_single_box(lib):
         assert lib.flbm_set_option(h, F.OPT_GRAPH_STEPS, 2.5) == F.EINVAL
     finally:
         lib.flbm_destroy(h)
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/flbm.h compiles as C99 with warnings as errors, and a C program
+    linked against the library runs its argument checks (no GPU needed)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi_check.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "flbm.h"
+int main(void)
+{
+    flbm_ctx *ctx = NULL;
+    if (flbm_create(FLBM_D2Q9, 16, 16, 2, 1.0, 1.0, 1e-4, 0.5, 1, &ctx) != FLBM_EINVAL || ctx) return 1;
+    if (flbm_create(FLBM_D3Q19, 8, 6, 4, 1.0, 0.8, 1e-4, 0.5, 7, &ctx) != FLBM_OK || !ctx) return 2;
+    if (flbm_set_option(ctx, FLBM_OPT_STREAMING, FLBM_STREAM_IN_PLACE) != FLBM_OK) return 3;
+    if (flbm_set_option(ctx, 12345, 1.0) != FLBM_EINVAL || strlen(flbm_last_error(ctx)) == 0) return 4;
+    size_t pop = 0, rho = 0;
+    if (flbm_buffer_bytes(ctx, &pop, &rho) != FLBM_OK || pop != (size_t)2 * 19 * 192 * 4) return 5;
+    if (flbm_step(ctx, 1) != FLBM_ESTATE) return 6;
+    flbm_destroy(ctx);
+    double tau[3] = {1.0, 0.8, 1.25}, G[9] = {0, .3, .3, .3, 0, .3, .3, .3, 0};
+    flbm_mctx *m = NULL;
+    if (flbm_mcreate(FLBM_D2Q9, 3, 16, 8, 1, tau, 1e-4, G, 3, &m) != FLBM_OK || !m) return 7;
+    if (flbm_mstep(m, 1) != FLBM_ESTATE) return 8;
+    flbm_mdestroy(m);
+    printf("%s\n", flbm_version());
+    return 0;
+}
+""")
+    exe = tmp_path / "abi_check"
+    libdir = os.path.dirname(F.library_path())
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+           "-o", str(exe), "-L", libdir, "-lflbm", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert "sm_103a" in out.stdout
