@@ -489,6 +489,9 @@ flbm_status flbm_mcreate(flbm_lattice lat, int nspecies, int nx, int ny, int nz,
  * FLBM_EINVAL otherwise. */
 flbm_status flbm_mset_option(flbm_mctx *ctx, int key, double value);
 
+/* Read one of those options back into *value; FLBM_EINVAL for another key. */
+flbm_status flbm_mget_option(const flbm_mctx *ctx, int key, double *value);
+
 /* Run on a caller-owned cudaStream_t (NULL: a stream the context creates). */
 flbm_status flbm_mset_stream(flbm_mctx *ctx, void *stream);
 

@@ -328,6 +328,19 @@ flbm_status flbm_mset_option(flbm_mctx *c, int key, double v)
     return mfail(c, FLBM_EINVAL, "unknown option %d for an N-species context", key);
 }
 
+flbm_status flbm_mget_option(const flbm_mctx *c, int key, double *value)
+{
+    if (!c || !value) return FLBM_EINVAL;
+    if (key == FLBM_OPT_KERNEL_TIMING) *value = c->timing ? 1.0 : 0.0;
+    else if (key == FLBM_OPT_BLOCK_X) *value = c->block_x;
+    else if (key == FLBM_OPT_BLOCK_Y) *value = c->block_y;
+    else if (key == FLBM_OPT_STREAMING) *value = c->streaming;
+    else if (key == FLBM_OPT_GRAPH_STEPS) *value = c->graph_steps;
+    else if (key >= FLBM_OPT_RHO0_SPECIES && key < FLBM_OPT_RHO0_SPECIES + c->ns) *value = c->rho0[key - FLBM_OPT_RHO0_SPECIES];
+    else return FLBM_EINVAL;
+    return FLBM_OK;
+}
+
 flbm_status flbm_mset_stream(flbm_mctx *c, void *stream)
 {
     if (!c) return FLBM_EINVAL;

@@ -127,6 +127,7 @@ def lib():
             "flbm_batch_size": (i32, [vp, ctypes.POINTER(ctypes.c_int), i64p]),
             "flbm_mcreate": (i32, [i32, i32, i32, i32, i32, dp, dbl, dp, u64, ctypes.POINTER(vp)]),
             "flbm_mset_option": (i32, [vp, i32, dbl]),
+            "flbm_mget_option": (i32, [vp, i32, dp]),
             "flbm_mset_stream": (i32, [vp, vp]),
             "flbm_minit": (i32, [vp, dp]),
             "flbm_mstep": (i32, [vp, i64]),
@@ -524,6 +525,11 @@ class MultiLattice:
 
     def set_option(self, key, value):
         mcheck(self._h, lib().flbm_mset_option(self._h, int(key), float(value)))
+
+    def get_option(self, key):
+        v = ctypes.c_double()
+        mcheck(self._h, lib().flbm_mget_option(self._h, int(key), ctypes.byref(v)))
+        return v.value
 
     def init(self, rho=None):
         """Rest state from host densities [nspecies][z][y][x] (None: the reference densities)."""

@@ -178,6 +178,11 @@ def test_multi_options_and_order_are_validated(lib):
         assert lib.flbm_mset_option(h, F.OPT_STORAGE, 1) == F.EINVAL              # float storage only
         assert b"unknown option" in lib.flbm_mlast_error(h)
         assert lib.flbm_mstep(h, 1) == F.ESTATE                                    # before init
+        v = ctypes.c_double()
+        for key, want in ((F.OPT_RHO0_SPECIES + 2, 0.7), (F.OPT_BLOCK_X, 64), (F.OPT_STREAMING, 1),
+                          (F.OPT_GRAPH_STEPS, 0), (F.OPT_KERNEL_TIMING, 0)):
+            assert lib.flbm_mget_option(h, key, ctypes.byref(v)) == F.OK and v.value == want, key
+        assert lib.flbm_mget_option(h, F.OPT_RHO0_SPECIES + 3, ctypes.byref(v)) == F.EINVAL
         step = ctypes.c_int64(-1)
         assert lib.flbm_mget_step(h, ctypes.byref(step)) == F.OK and step.value == 0
     finally:
