@@ -51,7 +51,7 @@ typedef enum {
     FLBM_ECUDA = 3,        /* a CUDA runtime call failed (reason in flbm_last_error) */
     FLBM_ENONFINITE = 4,   /* a density became non-positive or non-finite on the device */
     FLBM_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the state is not valid */
-    FLBM_EUNSUPPORTED = 6, /* valid request that this build does not support */
+    FLBM_EUNSUPPORTED = 6, /* valid request that this library does not support */
     FLBM_ESTATE = 7        /* call out of order (e.g. step before init) */
 } flbm_status;
 

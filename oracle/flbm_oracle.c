@@ -29,7 +29,7 @@
  *   7. fbar_i(r + c_i, n+1) = fbar_i(r, n) + w_i sum_a T_ai R_a / N_a   (Eq. algorithm)
  * Streaming is plain two-array push streaming on a fully periodic box.
  *
- * Readings where the paper is silent (each listed in the design notes):
+ * Readings where the paper is silent:
  *   - lambdabar = 1/tau per species for every non-conserved mode; the common
  *     momentum rate lambdabar_d = 2/(tau_A + tau_B) (Sec. III, Eq. diffusionrelaxation
  *     requires one common rate), overridable.

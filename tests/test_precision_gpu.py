@@ -3,8 +3,7 @@ bfloat16 deviations from w_i rho0, collided in float) against the FP64 oracle
 and the float-storage run, on a 32^3 D3Q19 Shan-Chen case: densities,
 velocities, the axis structure factors sampled along the same noise history,
 and mass drift.  Writes the measured errors to precision.json in the folder
-named by the FLBM_REPORT_DIR environment variable, when it is set (a record
-for the design notes)."""
+named by the FLBM_REPORT_DIR environment variable, when it is set."""
 import json
 import os
 
