@@ -149,7 +149,9 @@ def lattice_linear_sk(c, w, T, N, k_vec, G, rho=(1.0, 1.0), lam=(1.0, 1.0), lam_
         e[0:Q] += c[:, d] / rt
         e[Q:2 * Q] += c[:, d] / rt
         e += 0.5 * (rho[0] * acc[0][d] + rho[1] * acc[1][d]) / rt
-        suu += (e.conj() @ P @ e).real / D
+        # the Fourier velocity is the form e^T x, so its variance is e^T P conj(e)
+        # (P = <x x^H>); the force part of e is complex, so the order matters
+        suu += (e @ P @ e.conj()).real / D
     return (eA @ P @ eA).real, (eA @ P @ eB).real, (eB @ P @ eB).real, suu
 
 
