@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage and batching forms")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
     ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap"], default=None,
-                    help="force one step schedule (implies --no-autotune; fused and overlap stream in place)")
+                    help="force one step schedule (implies --no-autotune; fused streams in place)")
     ap.add_argument("--streaming", choices=["two_arrays", "in_place"], default="two_arrays",
                     help="population streaming: two arrays (default) or one array updated in place")
     ap.add_argument("--form", choices=["species2", "species3", "species4"], default=None,
@@ -493,7 +493,7 @@ def run_ours(args, wl):
     sites = nx * ny * nz
     Q = 19 if wl["lattice"] == 1 else 9
     from paper_1410_5584_gb300 import flbm as F
-    streaming = "in_place" if args.schedule in ("fused", "overlap") else args.streaming
+    streaming = "in_place" if args.schedule == "fused" else args.streaming
     lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
                   storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"],
                   streaming=F.STREAMING[streaming])

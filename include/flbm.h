@@ -79,7 +79,8 @@ typedef enum {
                                       second stream of higher priority, on every slab whose neighbours
                                       have been collided, so the memory-bound density pass overlaps the
                                       instruction-bound collision.  Ordered by CUDA events only.  Boxes
-                                      with fewer than 3 planes (rows) run the two-kernel schedule */
+                                      with fewer than 3 planes (rows) run the two-kernel schedule.
+                                      Either streaming mode */
 } flbm_schedule;
 
 /* How populations stream (option FLBM_OPT_STREAMING). */
@@ -91,7 +92,8 @@ typedef enum {
                                    from one (natural layout) and writes f*_i to x + c_i in the other.  On
                                    GB300 a pure copy with these reads and writes runs at the HBM copy rate,
                                    the in-place pattern at half of it or less; the collide gains a few
-                                   per cent.  Runs the two-kernel schedule */
+                                   per cent.  Runs the two-kernel and overlap schedules (the fused
+                                   one gives FLBM_EUNSUPPORTED) */
 } flbm_streaming;
 
 /* Option keys for flbm_set_option. */

@@ -676,7 +676,9 @@ flbm_status ensure_overlap(flbm_ctx *c, int K)
 
 // n steps of the overlap schedule.  With the AA layout every array slot belongs
 // to the read/write set of exactly one site, so launches over disjoint slabs
-// never touch the same slot, and the orderings that matter are:
+// never touch the same slot.  With two arrays a collision reads its own slab of
+// one array and pushes into slabs j-1, j, j+1 of the other, which no launch of
+// the same step reads.  In both modes the orderings that matter are:
 //  - the density of slab j for step t+1 reads the sets of slab j's sites, which
 //    the collisions of slabs j-1, j, j+1 at step t filled (streaming moves one
 //    plane at most);
@@ -696,17 +698,22 @@ flbm_status step_overlap(flbm_ctx *c, int64_t n, StepParams p)
     flbm_status st = ensure_overlap(c, K);
     if (st != FLBM_OK) return st;
     cudaEvent_t *evC = c->ev_dep.data(), *evD = c->ev_dep.data() + K;
+    const bool two = two_arrays(c);
     auto density = [&](cudaStream_t s, const StepParams &q, int parity) -> flbm_status {
         TimedLaunch tl{c, s, 0};
         if ((st = tl.begin()) != FLBM_OK) return st;
-        cudaError_t e = launch_density(c->lat, c->storage, parity, q, c->pop, c->rho, s);
+        cudaError_t e = two ? launch_density(c->lat, c->storage, 0, q, cur_pop_at(c, parity), c->rho, s)
+                            : launch_density(c->lat, c->storage, parity, q, c->pop, c->rho, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "density kernel launch");
         return tl.end();
     };
     auto collide = [&](const StepParams &q) -> flbm_status {
         TimedLaunch tl{c, c->stream, 1};
         if ((st = tl.begin()) != FLBM_OK) return st;
-        cudaError_t e = launch_collide(c->lat, c->storage, c->parity, q, c->pop, c->pop, c->rho, c->d_status, c->stream);
+        cudaError_t e = two ? launch_collide(c->lat, c->storage, kStreamPush, q, cur_pop(c), next_pop(c), c->rho,
+                                             c->d_status, c->stream)
+                            : launch_collide(c->lat, c->storage, c->parity, q, c->pop, c->pop, c->rho, c->d_status,
+                                             c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "collide kernel launch");
         return tl.end();
     };
@@ -793,8 +800,8 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
     if (is_batch(c)) return batch_step(c, n);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
     if (n == 0) return FLBM_OK;
-    if (two_arrays(c) && c->schedule != FLBM_SCHEDULE_TWO_KERNELS)
-        return fail(c, FLBM_EUNSUPPORTED, "two-array streaming runs the two-kernel schedule only");
+    if (two_arrays(c) && c->schedule == FLBM_SCHEDULE_FUSED)
+        return fail(c, FLBM_EUNSUPPORTED, "two-array streaming runs the two-kernel and overlap schedules only");
     // whole graphs of graph_steps steps first (two-kernel schedule, timing off)
     if (c->graph_steps > 0 && c->schedule == FLBM_SCHEDULE_TWO_KERNELS && !c->timing) {
         while (n >= c->graph_steps) {

@@ -270,13 +270,12 @@ std::vector<Settings> candidates(const flbm_ctx *c)
     }
     const int axis = c->lat == FLBM_D2Q9 ? c->ny : c->nz;
     const int shapes[3][2] = {{128, 1}, {64, 2}, {32, 4}};
-    const bool in_place = c->streaming == FLBM_STREAM_IN_PLACE; // two arrays: the two-kernel schedule only
     for (const auto &b : shapes) {
         for (int gs : {0, 16})
             out.push_back({{"schedule", (double)FLBM_SCHEDULE_TWO_KERNELS}, {"graph_steps", (double)gs},
                            {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
         for (int k : {4, 8})
-            if (in_place && axis >= k)
+            if (axis >= k)
                 out.push_back({{"schedule", (double)FLBM_SCHEDULE_OVERLAP}, {"graph_steps", 0.0},
                                {"slabs", (double)k}, {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
     }

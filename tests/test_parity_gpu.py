@@ -332,8 +332,9 @@ def test_overlap_schedule_matches_two_kernels_bitwise(lat, shape, slabs):
     """The slab-overlapped schedule runs the same per-site arithmetic as the
     two-kernel schedule, so after any number of steps, split into any calls
     (both streaming parities, both starting slabs of the alternation), the
-    states agree bit for bit; boxes with fewer than 3 planes fall back to the
-    two-kernel schedule.  Kernel timing does not change the result."""
+    states agree bit for bit, in place and with two arrays; boxes with fewer
+    than 3 planes fall back to the two-kernel schedule.  Kernel timing does
+    not change the result."""
     nz, ny, nx = shape
     f0 = _random_state(lat, shape)
     ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6, streaming=F.STREAMING["in_place"])
@@ -341,8 +342,8 @@ def test_overlap_schedule_matches_two_kernels_bitwise(lat, shape, slabs):
     ref.set_populations(f0, step=3)
     ref.step(8)
     want = ref.get_populations()
-    for timing in (0, 1):
-        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6, streaming=F.STREAMING["in_place"])
+    for timing, streaming in ((0, "in_place"), (1, "in_place"), (0, "two_arrays"), (1, "two_arrays")):
+        g = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6, streaming=F.STREAMING[streaming])
         g.set_option("schedule", F.SCHEDULE["overlap"])
         g.set_option("slabs", slabs)
         g.set_option("kernel_timing", timing)
@@ -435,13 +436,12 @@ def test_checkpoints_move_between_streaming_modes():
     assert np.array_equal(e.get_populations(), c.get_populations())
 
 
-def test_two_arrays_refuse_the_other_schedules():
+def test_two_arrays_refuse_the_fused_schedule():
     g = Lattice(D2Q9, 16, 8, 1, 1.0, 1.0, 1e-4, 0.5, 1)
     g.init()
-    for sched in ("fused", "overlap"):
-        g.set_option("schedule", F.SCHEDULE[sched])
-        with pytest.raises(FlbmError, match="FLBM_EUNSUPPORTED"):
-            g.step(1)
+    g.set_option("schedule", F.SCHEDULE["fused"])
+    with pytest.raises(FlbmError, match="FLBM_EUNSUPPORTED"):
+        g.step(1)
     g.set_option("schedule", F.SCHEDULE["two_kernels"])
     g.step(1)
     with pytest.raises(FlbmError, match="FLBM_ESTATE"):
