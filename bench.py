@@ -115,9 +115,10 @@ def sources_digest():
     return h.hexdigest()
 
 
-def recorded_traffic(workload, sites):
-    """DRAM bytes per collide launch from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def recorded_capture(workload, sites):
+    """DRAM bytes and executed warp-instructions per collide launch from the
+    committed ncu summary, scaled to `sites`, if it was taken on the current
+    kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -127,7 +128,12 @@ def recorded_traffic(workload, sites):
     rec = d.get(workload)
     if not rec or rec.get("sources_sha256") != sources_digest():
         return None
-    return rec["dram_bytes_per_launch"] * sites / rec["sites"]
+    scale = sites / rec["sites"]
+    inst = rec.get("warp_instructions_per_launch")
+    return {"traffic": rec["dram_bytes_per_launch"] * scale, "inst": None if inst is None else inst * scale}
+
+
+SMS, SCHEDULERS_PER_SM = 152, 4  # GB300: each scheduler issues at most one warp-instruction a cycle
 
 
 class ClockSampler:
@@ -562,10 +568,43 @@ def run_ours(args, wl):
         return
     peak, peak_kind = measured_peaks()
     bpp = BYTES_PER_POP[wl["storage"]]
-    alg_bytes = sites * 2 * Q * 2 * bpp  # populations read + written once per step
+    D = 3 if wl["lattice"] == 1 else 2
+    # Two arrays, the two-kernel schedule and full relaxation: the density pass
+    # also writes m_0 .. m_D of both species and the collide reads those
+    # instead of the populations (the moment-fed collide)
+    moment_fed = (streaming == "two_arrays" and all(t == 1.0 for t in wl["tau"])
+                  and (launch or {}).get("schedule", F.SCHEDULE["two_kernels"]) == F.SCHEDULE["two_kernels"])
+    mom_bytes = sites * 2 * (D + 1) * 4 if moment_fed else 0
+    # algorithmic bytes of the collide: its reads (populations, or the moment
+    # planes) and its population writes, once each
+    alg_bytes = (mom_bytes if moment_fed else sites * 2 * Q * bpp) + sites * 2 * Q * bpp
+    # and of the whole step: the density pass reads the populations once and
+    # writes rho (and the moment planes)
+    step_bytes = alg_bytes + sites * 2 * Q * bpp + sites * 8 + mom_bytes
     coll_ms = kms["collide"] / max(kn["collide"], 1)
     achieved = alg_bytes / (coll_ms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload, sites)
+    cap = recorded_capture(args.workload, sites)
+    traffic = cap["traffic"] if cap else None
+    hbm_view = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    clocks = clk.summary()
+    if moment_fed and cap and cap["inst"]:
+        # the moment-fed collide moves 184 B a site and is bound by instruction
+        # issue: executed warp-instructions (ncu count, scaled per site) over
+        # the event-timed launch, against one per scheduler per cycle
+        mhz = clocks["sm_mhz"] if clocks else 2070.0
+        issue_peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
+        ach = cap["inst"] / (coll_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_collide", "achieved": ach, "peak": issue_peak,
+                    "unit": "G warp-instructions/s", "frac": ach / issue_peak, "traffic": traffic,
+                    "peak_source": f"{SMS} SMs x {SCHEDULERS_PER_SM} schedulers x 1 warp-instruction a cycle "
+                                   f"at the median SM clock sampled during the run ({mhz:.0f} MHz)",
+                    "instructions_per_launch": cap["inst"], "algorithmic_bytes_per_launch": alg_bytes,
+                    "hbm": {k: hbm_view[k] for k in ("achieved", "peak", "unit", "frac", "peak_source")}}
+    else:
+        roofline = hbm_view
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
@@ -574,14 +613,12 @@ def run_ours(args, wl):
                    "nx": nx, "ny": ny, "nz": nz, "storage": wl["storage"], "replicas": world,
                    "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2",
                    "launch": launch, "streaming": streaming},
-        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
-        "step_hbm_frac": alg_bytes / (t_max / args.steps) / 1e9 / peak,
+        "roofline": roofline,
+        "step_hbm_frac": step_bytes / (t_max / args.steps) / 1e9 / peak,
+        "step_bytes_per_site": step_bytes // sites,
         "kernel_ms": {"density": kms["density"] / max(kn["density"], 1), "collide": coll_ms},
         "gpu_launches": kn["density"] + kn["collide"],
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": e2e,
     }
     if not args.no_forms:

@@ -754,6 +754,24 @@ flbm_status step_overlap(flbm_ctx *c, int64_t n, StepParams p)
     return FLBM_OK;
 }
 
+// The two-kernel step with two arrays at full relaxation (every lambdabar_a = 1,
+// the condition the collide's full-relaxation instance is chosen on): the
+// density pass also stores m_0 .. m_D of both species and the collide reads
+// those instead of the populations.  Sets p.mom when that applies.
+flbm_status use_moments(flbm_ctx *c, StepParams &p)
+{
+    p.mom = nullptr;
+    if (!two_arrays(c) || p.general_collide) return FLBM_OK;
+    for (int s = 0; s < 2; s++)
+        for (int a = c->D + 1; a < c->Q; a++)
+            if (p.cm[s][a] != 0.0f) return FLBM_OK;
+    if (!c->d_mom)
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_mom, (size_t)2 * (c->D + 1) * (size_t)c->N * sizeof(float)),
+                  "cudaMalloc(moment planes)");
+    p.mom = c->d_mom;
+    return FLBM_OK;
+}
+
 // One CUDA graph of c->graph_steps two-kernel steps starting at `parity`: the
 // step kernels read the noise counter as *d_gstep + k, so the graph replays
 // for any starting step once d_gstep is set.
@@ -763,6 +781,7 @@ flbm_status ensure_step_graph(flbm_ctx *c, int parity)
     if (!c->d_gstep) FLBM_CUDA(c, cudaMalloc((void **)&c->d_gstep, sizeof(unsigned)), "cudaMalloc(graph step counter)");
     StepParams p = make_params(c);
     p.step_dev = c->d_gstep;
+    if (flbm_status st = use_moments(c, p); st != FLBM_OK) return st;
     cudaGraph_t g = nullptr;
     FLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     cudaError_t e = cudaSuccess;
@@ -820,6 +839,8 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
     if (c->schedule == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
         if (st != FLBM_OK) return st;
+    } else if (flbm_status st = use_moments(c, p); st != FLBM_OK) {
+        return st;
     }
     for (int64_t t = 0; t < n; t++) {
         p.step = (uint32_t)c->step;
@@ -1150,6 +1171,7 @@ void flbm_destroy(flbm_ctx *c)
     }
     drop_step_graphs(c);
     if (c->d_gstep) cudaFree(c->d_gstep);
+    if (c->d_mom) cudaFree(c->d_mom);
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_pipe) cudaFree(c->d_pipe);
     if (c->d_obs) cudaFree(c->d_obs);

@@ -31,6 +31,7 @@ struct flbm_ctx {
     int graph_steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     unsigned *d_gstep = nullptr; // noise counter at the start of a graph replay
+    float *d_mom = nullptr;      // moment planes of the full-relaxation two-array step (StepParams::mom)
     double rho0[2] = {1.0, 1.0};
     // state
     int64_t step = 0;

@@ -37,6 +37,9 @@ struct StepParams {
     uint32_t step;             // noise counter word for this step, or its offset from *step_dev
     const unsigned *step_dev;  // NULL, or a device word the counter is read from (CUDA-graph replays)
     int general_collide;       // test hook: 1 keeps the general collide even when every rate is 1
+    float *mom;                // NULL, or 2 (D + 1) planes of N floats: m_0 .. m_D of each species,
+                               // written by the density pass and read by the full-relaxation collide
+                               // in place of the populations (two-array streaming)
 };
 
 // One replica of a batch: its step parameters and the offsets of its slices of

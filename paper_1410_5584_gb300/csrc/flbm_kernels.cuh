@@ -138,6 +138,43 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_density(const StepParams p,
     rho[nb.at(0, 0, 0)] = site_density<L, S, PARITY>(p, planes, nb);
 }
 
+// The density pass of a full-relaxation step (every lambdabar_a = 1): besides
+// rho it stores each species' density deviation m_0 and momentum m_1..m_D, the
+// only moments of the old populations that the collision then uses (Eq.
+// algorithm with lambdabar_a = 1), so that the collide reads these 2 (D + 1)
+// floats instead of 2 Q populations.  Same expressions as site_density and the
+// collide's own transform, so the results are bitwise those of the
+// population-reading collide.
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(kSiteBlockMax) k_moments(const StepParams p,
+                                                           const PlaneTable<const typename S::T> planes,
+                                                           float2 *__restrict__ rho)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.yn) return;
+    const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
+    const size_t site = (size_t)nb.at(0, 0, 0);
+    float r[2];
+    static_for<2>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        float d[L::Q], m[L::Q];
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            d[i] = S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()), read_site<L, PARITY, i>(nb),
+                               wi * p.rho0[s]);
+        });
+        Transform<L>::forward(d, m);
+        r[s] = p.rho0[s] + m[0];
+        static_for<L::D + 1>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            p.mom[(size_t)(s * (L::D + 1) + a) * (size_t)p.N + site] = m[a];
+        });
+    });
+    rho[site] = make_float2(r[0], r[1]);
+}
+
 // ---------------------------------------------------------------------------
 // fused force + moment collision + noise + streaming
 // ---------------------------------------------------------------------------
@@ -146,19 +183,33 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_density(const StepParams p,
 // earlier in the same kernel launch by other thread blocks.  STORE = false
 // computes without writing (an idle lane of a partial warp).  after_loads()
 // runs once the population loads are issued; returning false abandons the site.
-template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, bool FULL = false, class P,
-          class Hook = bool (*)()>
+template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, bool FULL = false, bool MOM = false,
+          class P, class Hook = bool (*)()>
 __device__ __forceinline__ void site_collide(const StepParams &p, const P &planes, const P &out,
                                              const float2 *__restrict__ rho, unsigned *__restrict__ status,
                                              const Nbr &nb, Hook &&after_loads)
 {
     constexpr int Q = L::Q, D = L::D;
+    static_assert(!MOM || FULL, "the moment-fed collide needs full relaxation");
     const int site = nb.at(0, 0, 0);
 
     // 1. moments of both species (Eq. modes-discrete), density rho = rhobar.
     // All loads are issued first; `after_loads` runs while they are in flight.
+    // MOM: the density pass stored m_0 .. m_D (k_moments), and with full
+    // relaxation no other moment of the old populations enters the update.
     float m[2][Q], rs[2];
-    {
+    if constexpr (MOM) {
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<D + 1>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                m[s][a] = __ldg(p.mom + (size_t)(s * (D + 1) + a) * (size_t)p.N + (size_t)site);
+            });
+        });
+        if (!after_loads()) return;
+        rs[0] = p.rho0[0] + m[0][0];
+        rs[1] = p.rho0[1] + m[1][0];
+    } else {
         float d[2][Q];
         static_for<2>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
@@ -318,13 +369,15 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
 }
 
 // planes: the slot planes read; out: the slot planes written (the same table
-// for the in-place modes, the other array for kPush).  Register limits,
-// measured: D3Q19 full relaxation 80 (six blocks an SM, 2 % faster at 256^3
-// than its own 96 despite a 24-byte spill), D3Q19 general 128 (it asks for
-// 176 otherwise); D2Q9, whose 18 loads a site leave it short of loads in
-// flight, 64 and 80 (eight and six blocks, 5-6 % faster at 2048^2, no spill).
-template <class L, class S, int PARITY, bool FULL>
-__global__ void __launch_bounds__(kSiteBlockMax, FULL ? (L::Q == 9 ? 8 : 6) : (L::Q == 9 ? 6 : 4)) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
+// for the in-place modes, the other array for kPush).  MOM: full relaxation
+// fed by the moment planes of k_moments instead of the populations.  Register
+// limits, measured: D3Q19 full relaxation 80 (six blocks an SM, 2 % faster at
+// 256^3 than its own 96 despite a 24-byte spill), moment-fed 96 (five blocks,
+// no spill, 2 % faster than at 80), D3Q19 general 128 (it asks for 176
+// otherwise); D2Q9, whose 18 loads a site leave it short of loads in flight,
+// 64 and 80 (eight and six blocks, 5-6 % faster at 2048^2, no spill).
+template <class L, class S, int PARITY, bool FULL, bool MOM = false>
+__global__ void __launch_bounds__(kSiteBlockMax, FULL ? (L::Q == 9 ? 8 : (MOM ? 5 : 6)) : (L::Q == 9 ? 6 : 4)) k_collide(const StepParams p, const PlaneTable<typename S::T> planes,
                                                            const PlaneTable<typename S::T> out,
                                                            const float2 *__restrict__ rho,
                                                            unsigned *__restrict__ status)
@@ -333,7 +386,7 @@ __global__ void __launch_bounds__(kSiteBlockMax, FULL ? (L::Q == 9 ? 8 : 6) : (L
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.yn) return;
     const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
-    site_collide<L, S, PARITY, false, true, FULL>(p, planes, out, rho, status, nb, [] { return true; });
+    site_collide<L, S, PARITY, false, true, FULL, MOM>(p, planes, out, rho, status, nb, [] { return true; });
 }
 
 // True when every non-conserved mode relaxes fully (lambdabar_a = 1, so cm = 0
@@ -807,7 +860,8 @@ cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *p
     const dim3 b = kern::site_block(p), g = kern::site_grid(p, b);
     const auto planes = kern::plane_table(static_cast<const typename S::T *>(pop), L::Q, p.N);
     auto *r2 = reinterpret_cast<float2 *>(rho);
-    if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
+    if (p.mom && parity == 0) kern::k_moments<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
+    else if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
     else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, planes, r2);
     return cudaGetLastError();
 }
@@ -828,7 +882,8 @@ cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, vo
         if (full) kern::k_collide<L, S, 1, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
         else kern::k_collide<L, S, 1, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
     } else {
-        if (full) kern::k_collide<L, S, kern::kPush, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        if (full && p.mom) kern::k_collide<L, S, kern::kPush, true, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        else if (full) kern::k_collide<L, S, kern::kPush, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
         else kern::k_collide<L, S, kern::kPush, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
     }
     return cudaGetLastError();
