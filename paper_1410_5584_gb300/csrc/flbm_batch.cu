@@ -31,6 +31,7 @@ struct BatchState {
     int graph_len[2] = {0, 0};
     bool internal = false; // batch code is calling the single-box functions on a view
     bool full = false;     // every replica has rate 1 on all non-conserved modes
+    float *d_mom = nullptr; // moment planes of all replicas (full relaxation: the moment-fed collide)
 };
 
 using namespace host;
@@ -105,6 +106,14 @@ flbm_status upload_tables(flbm_ctx *c)
             // the captured graphs launch the collide instance of the old choice
             drop_graphs(b);
             b->full = full;
+        }
+        if (full) {
+            // each replica's 2 (D + 1) moment planes of its N sites, in site order
+            const size_t sites = (size_t)b->site_off.back() + (size_t)b->views.back()->N;
+            if (!b->d_mom)
+                FLBM_CUDA(c, cudaMalloc((void **)&b->d_mom, (size_t)2 * (c->D + 1) * sites * sizeof(float)),
+                          "cudaMalloc(moment planes)");
+            for (size_t r = 0; r < h.size(); r++) h[r].p.mom = b->d_mom + (size_t)2 * (c->D + 1) * (size_t)b->site_off[r];
         }
         // the graphs read this array on the device, so it is updated in stream order
         FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -488,6 +497,7 @@ void batch_destroy(flbm_ctx *c)
     if (b->d_reps) cudaFree(b->d_reps);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_step) cudaFree(b->d_step);
+    if (b->d_mom) cudaFree(b->d_mom);
     for (flbm_ctx *v : b->views) {
         v->batch = nullptr;
         v->is_view = false;

@@ -144,16 +144,10 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_density(const StepParams p,
 // algorithm with lambdabar_a = 1), so that the collide reads these 2 (D + 1)
 // floats instead of 2 Q populations.  Same expressions as site_density and the
 // collide's own transform, so the results are bitwise those of the
-// population-reading collide.
-template <class L, class S, int PARITY>
-__global__ void __launch_bounds__(kSiteBlockMax) k_moments(const StepParams p,
-                                                           const PlaneTable<const typename S::T> planes,
-                                                           float2 *__restrict__ rho)
+// population-reading collide.  Returns the densities; writes p.mom.
+template <class L, class S, int PARITY, class P>
+__device__ __forceinline__ float2 site_moments(const StepParams &p, const P &planes, const Nbr &nb)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.yn) return;
-    const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
     const size_t site = (size_t)nb.at(0, 0, 0);
     float r[2];
     static_for<2>([&](auto sc) {
@@ -172,7 +166,19 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_moments(const StepParams p,
             p.mom[(size_t)(s * (L::D + 1) + a) * (size_t)p.N + site] = m[a];
         });
     });
-    rho[site] = make_float2(r[0], r[1]);
+    return make_float2(r[0], r[1]);
+}
+
+template <class L, class S, int PARITY>
+__global__ void __launch_bounds__(kSiteBlockMax) k_moments(const StepParams p,
+                                                           const PlaneTable<const typename S::T> planes,
+                                                           float2 *__restrict__ rho)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.yn) return;
+    const Nbr nb = make_nbr(p, x, y + p.y0, blockIdx.z + p.z0);
+    rho[nb.at(0, 0, 0)] = site_moments<L, S, PARITY>(p, planes, nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -623,7 +629,9 @@ __device__ __forceinline__ void stage_params(const RepInfo *__restrict__ reps, i
     __syncthreads();
 }
 
-template <class L, class S, int PARITY>
+// MOM: the replicas relax fully and their StepParams::mom point at their
+// moment planes (the moment-fed collide, as for a single box)
+template <class L, class S, int PARITY, bool MOM = false>
 __global__ void __launch_bounds__(128) k_density_batch(const RepInfo *__restrict__ reps, const int2 *__restrict__ tiles,
                                                        typename S::T *__restrict__ pop, float2 *__restrict__ rho,
                                                        const unsigned *__restrict__ step_base, unsigned k)
@@ -636,11 +644,12 @@ __global__ void __launch_bounds__(128) k_density_batch(const RepInfo *__restrict
     int x, y, z;
     st.coords(site, x, y, z);
     const Nbr nb = make_nbr(st.sp, x, y, z);
-    rho[st.rho_off + site] =
-        site_density<L, S, PARITY>(st.sp, FlatPlanes<const typename S::T>{pop + st.pop_off, (size_t)st.sp.N}, nb);
+    const FlatPlanes<const typename S::T> fp{pop + st.pop_off, (size_t)st.sp.N};
+    if constexpr (MOM) rho[st.rho_off + site] = site_moments<L, S, PARITY>(st.sp, fp, nb);
+    else rho[st.rho_off + site] = site_density<L, S, PARITY>(st.sp, fp, nb);
 }
 
-template <class L, class S, int PARITY, bool FULL>
+template <class L, class S, int PARITY, bool FULL, bool MOM = false>
 __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict__ reps, const int2 *__restrict__ tiles,
                                                        typename S::T *__restrict__ pop, const float2 *__restrict__ rho,
                                                        unsigned *__restrict__ status, const unsigned *__restrict__ step_base,
@@ -655,7 +664,7 @@ __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict
     st.coords(site, x, y, z);
     const Nbr nb = make_nbr(st.sp, x, y, z);
     const FlatPlanes<typename S::T> fp{pop + st.pop_off, (size_t)st.sp.N};
-    site_collide<L, S, PARITY, false, true, FULL>(st.sp, fp, fp, rho + st.rho_off, status, nb, [] { return true; });
+    site_collide<L, S, PARITY, false, true, FULL, MOM>(st.sp, fp, fp, rho + st.rho_off, status, nb, [] { return true; });
 }
 
 // ---------------------------------------------------------------------------
@@ -946,14 +955,24 @@ cudaError_t Launch<L, S>::batch_step(int parity, const RepInfo *reps, const int2
 {
     auto *ptr = static_cast<typename S::T *>(pop);
     auto *r2 = reinterpret_cast<float2 *>(rho);
+    // full: every replica relaxes fully and its StepParams::mom points at its
+    // moment planes, so the moment-fed pair of kernels runs
     if (parity == 0) {
-        kern::k_density_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-        if (full) kern::k_collide_batch<L, S, 0, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
-        else kern::k_collide_batch<L, S, 0, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        if (full) {
+            kern::k_density_batch<L, S, 0, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+            kern::k_collide_batch<L, S, 0, true, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        } else {
+            kern::k_density_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+            kern::k_collide_batch<L, S, 0, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        }
     } else {
-        kern::k_density_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-        if (full) kern::k_collide_batch<L, S, 1, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
-        else kern::k_collide_batch<L, S, 1, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        if (full) {
+            kern::k_density_batch<L, S, 1, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+            kern::k_collide_batch<L, S, 1, true, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        } else {
+            kern::k_density_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+            kern::k_collide_batch<L, S, 1, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+        }
     }
     return cudaGetLastError();
 }
