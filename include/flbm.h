@@ -197,8 +197,8 @@ flbm_status flbm_set_stream(flbm_ctx *ctx, void *stream);
 /* Bytes of device memory the context needs for its populations and its density
  * field, for the current storage and streaming options: one array holds
  * 2 * Q * N populations; two-array streaming needs two.  Either pointer may be
- * NULL.  Not included: with two arrays at full relaxation (every
- * non-conserved rate 1) the two-kernel step also keeps 2 (D + 1) float planes
+ * NULL.  Not included: at full relaxation (every non-conserved rate 1) the
+ * two-kernel step also keeps 2 (D + 1) float planes
  * of moment scratch (8 (D + 1) N bytes), allocated by the library on the first
  * such step and freed with the context; the collide then reads those moments
  * instead of the populations (same results bit for bit). */

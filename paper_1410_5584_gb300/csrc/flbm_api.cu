@@ -754,14 +754,15 @@ flbm_status step_overlap(flbm_ctx *c, int64_t n, StepParams p)
     return FLBM_OK;
 }
 
-// The two-kernel step with two arrays at full relaxation (every lambdabar_a = 1,
-// the condition the collide's full-relaxation instance is chosen on): the
-// density pass also stores m_0 .. m_D of both species and the collide reads
-// those instead of the populations.  Sets p.mom when that applies.
+// The two-kernel step at full relaxation (every lambdabar_a = 1, the condition
+// the collide's full-relaxation instance is chosen on), in either streaming
+// mode: the density pass also stores m_0 .. m_D of both species and the
+// collide reads those instead of the populations (in place it then only
+// writes).  Sets p.mom when that applies.
 flbm_status use_moments(flbm_ctx *c, StepParams &p)
 {
     p.mom = nullptr;
-    if (!two_arrays(c) || p.general_collide) return FLBM_OK;
+    if (p.general_collide) return FLBM_OK;
     for (int s = 0; s < 2; s++)
         for (int a = c->D + 1; a < c->Q; a++)
             if (p.cm[s][a] != 0.0f) return FLBM_OK;

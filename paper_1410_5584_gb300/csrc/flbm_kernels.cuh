@@ -870,6 +870,7 @@ cudaError_t Launch<L, S>::density(int parity, const StepParams &p, const void *p
     const auto planes = kern::plane_table(static_cast<const typename S::T *>(pop), L::Q, p.N);
     auto *r2 = reinterpret_cast<float2 *>(rho);
     if (p.mom && parity == 0) kern::k_moments<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
+    else if (p.mom) kern::k_moments<L, S, 1><<<g, b, 0, st>>>(p, planes, r2);
     else if (parity == 0) kern::k_density<L, S, 0><<<g, b, 0, st>>>(p, planes, r2);
     else kern::k_density<L, S, 1><<<g, b, 0, st>>>(p, planes, r2);
     return cudaGetLastError();
@@ -885,10 +886,12 @@ cudaError_t Launch<L, S>::collide(int parity, const StepParams &p, void *pop, vo
     auto *r2 = reinterpret_cast<const float2 *>(rho);
     const bool full = kern::full_relaxation<L>(p);
     if (parity == 0) {
-        if (full) kern::k_collide<L, S, 0, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        if (full && p.mom) kern::k_collide<L, S, 0, true, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        else if (full) kern::k_collide<L, S, 0, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
         else kern::k_collide<L, S, 0, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
     } else if (parity == 1) {
-        if (full) kern::k_collide<L, S, 1, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        if (full && p.mom) kern::k_collide<L, S, 1, true, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
+        else if (full) kern::k_collide<L, S, 1, true><<<g, b, 0, st>>>(p, planes, out, r2, status);
         else kern::k_collide<L, S, 1, false><<<g, b, 0, st>>>(p, planes, out, r2, status);
     } else {
         if (full && p.mom) kern::k_collide<L, S, kern::kPush, true, true><<<g, b, 0, st>>>(p, planes, out, r2, status);

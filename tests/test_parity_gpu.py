@@ -384,9 +384,9 @@ def test_streaming_modes_are_bitwise_identical(lat, shape, tau):
     """In-place and two-array streaming compute the same update bit for bit:
     populations after odd and even step counts split over several calls,
     observables and the axis structure factor; with all rates 1 (the collide
-    that skips the non-conserved projections, which with two arrays reads the
-    moments m_0 .. m_D that the density pass stored instead of the
-    populations) and with general rates."""
+    that skips the non-conserved projections and reads the moments m_0 .. m_D
+    that the density pass stored instead of the populations) and with general
+    rates."""
     nz, ny, nx = shape
     f0 = _random_state(lat, shape)
     runs = []
@@ -438,25 +438,29 @@ def test_checkpoints_move_between_streaming_modes():
     assert np.array_equal(e.get_populations(), c.get_populations())
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("lat,shape", [(D2Q9, (1, 9, 70)), (D3Q19, (4, 6, 33))])
-def test_moment_fed_collide_matches_in_place_for_16bit_storage(lat, shape, storage):
-    """At full relaxation the two-array step feeds the collide the moments the
-    density pass stored; with 16-bit storage too it gives bitwise the update
-    of the in-place collide, which reads the populations, directly and
-    replayed from CUDA graphs."""
+def test_moment_fed_collide_matches_the_population_reading_one(lat, shape, storage):
+    """At full relaxation the two-kernel step feeds the collide the moments
+    m_0 .. m_D that the density pass stored; the overlap schedule keeps the
+    collide that reads the populations.  Both give bitwise the same update, in
+    both streaming modes, launched directly and replayed from CUDA graphs."""
     nz, ny, nx = shape
     f0 = _random_state(lat, shape)
     out = []
-    for mode, graphs in (("in_place", 0), ("two_arrays", 0), ("two_arrays", 4)):
+    for mode, sched, graphs in (("two_arrays", "overlap", 0), ("in_place", "overlap", 0),
+                                ("two_arrays", "two_kernels", 0), ("in_place", "two_kernels", 0),
+                                ("two_arrays", "two_kernels", 4), ("in_place", "two_kernels", 4)):
         g = Lattice(lat, nx, ny, nz, 1.0, 1.0, 1e-4, 0.8, 9, storage=storage, streaming=F.STREAMING[mode])
+        g.set_option("schedule", F.SCHEDULE[sched])
+        g.set_option("slabs", 3)
         g.set_option("graph_steps", graphs)
         g.set_populations(f0, step=5)
         g.step(3)
         g.step(6)
         out.append(g.get_populations())
-    assert np.array_equal(out[0], out[1])
-    assert np.array_equal(out[0], out[2])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
 
 
 def test_two_arrays_refuse_the_fused_schedule():
