@@ -347,3 +347,39 @@ def test_interacting_mixture_structure_factor():
         assert abs(m[0, mi] - pred[0]) < 5 * se[0, mi] + 0.02 * pred[0], mi
         assert abs(m[1, mi] - pred[1]) < 5 * se[1, mi] + 0.02 * pred[0], mi
         assert abs(m[3, mi] - pred[3]) < 5 * se[3, mi] + 0.02 * pred[3], mi
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q9, (1, 6, 10)), (oracle.D3Q19, (3, 4, 5))])
+def test_full_relaxation_forgets_the_non_conserved_moments(lat, shape):
+    """With lambdabar_a = 1 on every non-conserved mode (and lambdabar_d = 1),
+    Eq. algorithm gives m*_a = m^eq_a + Phi_a/2 + xi_a: the old m_a drops out,
+    so a step depends on each species' populations only through rho^s and
+    jbar^s.  Adding to the populations anything orthogonal to the density and
+    momentum rows of T (a kernel vector of rows 0 .. D) leaves the state
+    after one step unchanged, to FP64 rounding.  At tau = 0.8 the same
+    change does alter the result (the check has teeth).  This is the
+    property the library's moment-fed collide relies on."""
+    nz, ny, nx = shape
+    c, w, T, N = oracle.tables(lat)
+    D, Q = DIMS[lat]
+    f0 = inputs.random_populations(_base(lat, 1.0, 0.8), shape, 0.02, seed=21)
+    rng = np.random.default_rng(5)
+    # project random vectors onto the complement of rows 0 .. D of T
+    C = np.asarray(T[:D + 1], dtype=float)                   # (D + 1) x Q
+    P = np.eye(Q) - C.T @ np.linalg.solve(C @ C.T, C)
+    delta = np.einsum("ij,sjzyx->sizyx", P, rng.normal(0.0, 3e-3, f0.shape))
+    assert np.max(np.abs(np.einsum("aj,sjzyx->sazyx", C, delta))) < 1e-15
+    f1 = f0 + delta
+    for tau, same in ((1.0, True), (0.8, False)):
+        out = []
+        for f in (f0, f1):
+            o = oracle.Oracle(lat, nx, ny, nz, tau, tau, 1e-4, 0.7, 13)
+            o.set_f(f, step=4)
+            o.step(1)
+            out.append(o.get_f())
+            o.close()
+        diff = np.max(np.abs(out[0] - out[1]))
+        if same:
+            assert diff < 1e-15, diff
+        else:
+            assert diff > 1e-5, diff
