@@ -33,9 +33,11 @@
  *   - lambdabar = 1/tau per species for every non-conserved mode; the common
  *     momentum rate lambdabar_d = 2/(tau_A + tau_B) (Sec. III, Eq. diffusionrelaxation
  *     requires one common rate), overridable.
- *   - noise generator: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed,
- *     counter (site, step, species, a/4), Gaussian = lane a mod 4 of a
- *     Box-Muller pair (the paper only says "Box-Muller", Sec. VI A).
+ *   - noise generator: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed;
+ *     the Gaussian of mode a >= 1 is Gaussian n = a - 1 of its species, from
+ *     counter (site, step, species, n / 6), whose four words are cut into six
+ *     21-bit uniforms and three Box-Muller pairs (the paper only says
+ *     "Box-Muller", Sec. VI A); see orc_gaussian.
  *   - D3Q19 basis: not in the paper; rows given in d3q19_tables() below.
  *
  * The orcm_* functions at the end hold the N-species update of App. C-D (more
@@ -241,32 +243,44 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[3] = x3;
 }
 
-/* Box-Muller: u1 = ((x >> 8) + 1) 2^-24 in (0, 1], u2 = (y >> 8) 2^-24 in
- * [0, 1); g0 = sqrt(-2 ln u1) cos(2 pi u2), g1 = sqrt(-2 ln u1) sin(2 pi u2). */
-static void box_muller(uint32_t x, uint32_t y, double *g0, double *g1)
+/* Box-Muller on two 21-bit uniforms U1, U2 in [0, 2^21): u1 = (U1 + 1) 2^-21
+ * in (0, 1], u2 = U2 2^-21 in [0, 1); g0 = sqrt(-2 ln u1) cos(2 pi u2),
+ * g1 = sqrt(-2 ln u1) sin(2 pi u2). */
+static void box_muller(uint32_t U1, uint32_t U2, double *g0, double *g1)
 {
-    const double two_m24 = 1.0 / 16777216.0;
-    double u1 = ((double)(x >> 8) + 1.0) * two_m24;
-    double u2 = (double)(y >> 8) * two_m24;
+    const double two_m21 = 1.0 / 2097152.0;
+    double u1 = ((double)U1 + 1.0) * two_m21;
+    double u2 = (double)U2 * two_m21;
     double r = sqrt(-2.0 * log(u1));
     double th = 2.0 * M_PI * u2;
     *g0 = r * cos(th);
     *g1 = r * sin(th);
 }
 
-/* The standard Gaussian used for mode a of species s at (site, step):
- * Philox counter (site, step, s, a/4), lane a mod 4; lanes (0,1) and (2,3)
- * form the two Box-Muller pairs.  Only the pair holding lane a is transformed. */
+/* The standard Gaussian used for mode a >= 1 of species s at (site, step).
+ * Mode a is Gaussian n = a - 1 of the species.  Philox counter
+ * (site, step, s, n / 6) gives four words x0 .. x3, cut into six 21-bit
+ * uniforms: U_k = x_k >> 11 for k = 0 .. 3, and from the low bits
+ * U4 = (x0 mod 2^11) 2^10 + (x1 mod 2^10), U5 = (x2 mod 2^11) 2^10 + (x3 mod 2^10).
+ * Gaussian n is the cosine (n even) or sine (n odd) output of Box-Muller on
+ * the pair (U_2q, U_2q+1), q = (n mod 6) / 2.  Mode 0 (the conserved density)
+ * has no Gaussian: NAN. */
 double orc_gaussian(uint64_t seed, uint32_t site, uint32_t step, uint32_t species, uint32_t a)
 {
-    uint32_t ctr[4] = {site, step, species, a / 4u};
+    if (a == 0u) return NAN;
+    const uint32_t n = a - 1u;
+    uint32_t ctr[4] = {site, step, species, n / 6u};
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
     uint32_t x[4];
     orc_philox4x32_10(ctr, key, x);
-    uint32_t lane = a % 4u, pair = lane / 2u;
+    uint32_t U[6];
+    for (int k = 0; k < 4; k++) U[k] = x[k] >> 11;
+    U[4] = ((x[0] & 0x7FFu) << 10) | (x[1] & 0x3FFu);
+    U[5] = ((x[2] & 0x7FFu) << 10) | (x[3] & 0x3FFu);
+    const uint32_t q = (n % 6u) / 2u;
     double g0, g1;
-    box_muller(x[2 * pair], x[2 * pair + 1], &g0, &g1);
-    return (lane % 2u == 0u) ? g0 : g1;
+    box_muller(U[2 * q], U[2 * q + 1], &g0, &g1);
+    return (n % 2u == 0u) ? g0 : g1;
 }
 
 /* ------------------------------------------------------------------------ */

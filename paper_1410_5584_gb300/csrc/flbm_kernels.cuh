@@ -273,10 +273,10 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     // for the other modes of species s (their per-mode factors are in cxi).
     // Square roots as x rsqrt(x): the densities are positive on every valid state
     // (a non-positive one has already raised the status flag).
-    // LATE (the general D3Q19 instance): only species 0's Philox slot 0 (the
-    // shared momentum noise) is drawn here, and each species draws the rest
-    // just before its own relaxation (step 6), which keeps them out of the
-    // registers meanwhile.  Measured at 256^3 with two arrays: 1.45 -> 1.13 ms
+    // LATE (the general D3Q19 instance): only species 0's Philox block 0 (the
+    // shared momentum noise, modes 1 .. 3, and modes 4 .. 6) is drawn here, and
+    // each species draws the rest just before its own relaxation (step 6),
+    // which keeps them out of the registers meanwhile.  Measured at 256^3 with two arrays: 1.45 -> 1.13 ms
     // for that instance, while the full-relaxation and D2Q9 instances are ~3 %
     // faster drawing everything here.
     constexpr bool LATE = L::Q == 19 && !FULL;
@@ -285,7 +285,6 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     const float n1 = p.noise_ref ? p.rho0[1] : rs[1];
     const float hm = n0 * n1 * __frcp_rn(n0 + n1);
     const float amp_j = p.noise_amp_j * (hm * rsqrtf(hm));
-    constexpr int kSlots = (Q + 3) / 4;
     float g0[Q], g1[Q];
     if constexpr (LATE) {
         draw_gaussians<L, 0, 0, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g0);
@@ -324,8 +323,8 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
                 g[a] = s == 0 ? g0[a] : g1[a];
             });
         } else if constexpr (s == 0) {
-            draw_gaussians<L, 0, 1, kSlots>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g);
-            static_for<4>([&](auto ac) { // the non-momentum modes of slot 0, drawn in step 4
+            draw_gaussians<L, 0, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n0 * rsqrtf(n0), g);
+            static_for<7>([&](auto ac) { // the non-momentum modes of block 0, drawn in step 4
                 constexpr int a = decltype(ac)::value;
                 if constexpr (a > D && a < Q) g[a] = g0[a];
             });

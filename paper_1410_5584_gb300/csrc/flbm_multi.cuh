@@ -16,9 +16,9 @@
 //     sqrt(rho^s) g^s, C = rho / rho_t, A = sqrt((2 lb_d - lb_d^2) kT), which
 //     has exactly that covariance and sums to zero over the species,
 //   - the other modes' noise with the per-species variances of Eq. new-noise.
-// Unit Gaussian g of mode a of species s at (site, step): lane a mod 4 of
-// Box-Muller on Philox4x32-10 with counter (site, step, s, a/4), as in the
-// two-species kernels.
+// Unit Gaussian g of mode a >= 1 of species s at (site, step): Gaussian
+// n = a - 1 of the species, position n mod 6 of Philox block n / 6 with
+// counter (site, step, s, n / 6), as in the two-species kernels.
 //
 // Storage: the float deviations f_i - w_i rho0^s, with the same in-place "AA"
 // streaming and plane layout [s][i][site] as the two-species kernels
@@ -111,16 +111,27 @@ __device__ __forceinline__ float get4(const float4 &v, int t)
     return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
 }
 
-// Unit Gaussians of the lanes of one Philox block (counter (site, step, s,
-// slot)) that MASK selects (bit l = lane l); lanes (0, 1) and (2, 3) are the
-// cosine and sine outputs of one Box-Muller pair each.
+// Unit Gaussians of the positions of one Philox block (counter (site, step, s,
+// b)) that MASK selects (bit l = position l, mode 6 b + l + 1); positions
+// (0, 1), (2, 3) and (4, 5) are the cosine and sine outputs of one Box-Muller
+// pair each, the third on the uniforms packed from the words' low bits.
 template <int MASK>
-__device__ __forceinline__ void slot_gaussians(uint32_t site, uint32_t step, uint32_t s, uint32_t slot, uint32_t k0,
-                                               uint32_t k1, float (&g)[4])
+__device__ __forceinline__ void block_gaussians(uint32_t site, uint32_t step, uint32_t s, uint32_t b, uint32_t k0,
+                                                uint32_t k1, float (&g)[6])
 {
-    const uint4 x = philox4x32_10(make_uint4(site, step, s, slot), k0, k1);
+    const uint4 x = philox4x32_10(make_uint4(site, step, s, b), k0, k1);
     if constexpr ((MASK & 3) != 0) box_muller(x.x, x.y, 1.0f, g[0], g[1]);
     if constexpr ((MASK & 12) != 0) box_muller(x.z, x.w, 1.0f, g[2], g[3]);
+    if constexpr ((MASK & 48) != 0) box_muller(low_bits_word(x.x, x.y), low_bits_word(x.z, x.w), 1.0f, g[4], g[5]);
+}
+
+// Positions of block b that hold a non-conserved mode (D < a < Q).
+template <int Q, int D> __host__ __device__ constexpr int other_modes_mask(int b)
+{
+    int m = 0;
+    for (int l = 0; l < 6; l++)
+        if (6 * b + l + 1 > D && 6 * b + l + 1 < Q) m |= 1 << l;
+    return m;
 }
 
 // Loads of the NS Q pre-collision deviations of a site.
@@ -277,29 +288,28 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
         u[d] = j * irt;
     });
 
-    // 4. Philox slot 0 of every species: modes 1 .. 3 (the momenta; for D2Q9
-    // also mode 3, kept for step 6).  Projected momentum noise.
+    // 4. the momentum Gaussians of every species: modes 1 .. D, positions
+    // 0 .. D-1 of Philox block 0.  Projected momentum noise.
     const uint32_t nstep = p.step_dev ? __ldg(p.step_dev) + p.step : p.step; // noise counter of this step
-    float g3[NS], sq[NS], xi[NS][3];
+    float sq[NS], xi[NS][3];
     {
-        float g0[NS][4];
+        float g0[NS][6];
         static_for<NS>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            slot_gaussians<0xE>((uint32_t)site, nstep, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
+            block_gaussians<(1 << D) - 1>((uint32_t)site, nstep, (uint32_t)s, 0u, p.key0, p.key1, g0[s]);
             sq[s] = rs[s] * rsqrtf(rs[s]); // sqrt(rho^s); rho^s > 0 on every valid state
-            g3[s] = g0[s][3];
         });
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             float sum = 0.0f;
             static_for<NS>([&](auto sc) {
                 constexpr int s = decltype(sc)::value;
-                sum = fmaf(sq[s], g0[s][1 + d], sum);
+                sum = fmaf(sq[s], g0[s][d], sum);
             });
             const float cs = sum * irt;
             static_for<NS>([&](auto sc) {
                 constexpr int s = decltype(sc)::value;
-                xi[s][d] = p.amp_d * fmaf(-rs[s], cs, sq[s] * g0[s][1 + d]);
+                xi[s][d] = p.amp_d * fmaf(-rs[s], cs, sq[s] * g0[s][d]);
             });
         });
     }
@@ -326,19 +336,21 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
             v[d] = (m[a] + 0.5f * R) * irs;
             m[a] += R;
         });
+        // the non-conserved modes' Gaussians (block 0 drawn again: its
+        // momentum positions were used in step 4)
         float g[Q];
-        static_for<(Q + 3) / 4 - 1>([&](auto kc) {
-            constexpr int slot = decltype(kc)::value + 1;
-            constexpr int lanes = Q - 4 * slot < 4 ? Q - 4 * slot : 4;
-            constexpr int mask = (1 << lanes) - 1;
-            float gs[4];
-            slot_gaussians<mask>((uint32_t)site, nstep, (uint32_t)s, (uint32_t)slot, p.key0, p.key1, gs);
-            static_for<lanes>([&](auto lc) {
-                constexpr int l = decltype(lc)::value;
-                g[4 * slot + l] = gs[l];
-            });
+        static_for<kNoiseBlocks<L>>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int mask = other_modes_mask<Q, D>(b);
+            if constexpr (mask != 0) {
+                float gs[6];
+                block_gaussians<mask>((uint32_t)site, nstep, (uint32_t)s, (uint32_t)b, p.key0, p.key1, gs);
+                static_for<6>([&](auto lc) {
+                    constexpr int l = decltype(lc)::value;
+                    if constexpr ((mask >> l) & 1) g[6 * b + l + 1] = gs[l];
+                });
+            }
         });
-        if constexpr (D + 1 < 4) g[3] = g3[s];
         float Y[Q];
         Closure<L>::force(acc[s], v, Y);
         float mu[Q], fo[Q];

@@ -5,7 +5,8 @@
 // 128-bit counter under a 64-bit key; each round multiplies two words by fixed
 // odd constants, swaps halves and mixes in the key, which is advanced by the
 // Weyl constants between rounds.  Gaussians come from the Box-Muller transform
-// (the paper's generator, Sec. VI A) on pairs of output words.
+// (the paper's generator, Sec. VI A) on pairs of 21-bit uniforms, six of which
+// are cut from the four output words of a block.
 #pragma once
 #include <cstdint>
 
@@ -68,23 +69,32 @@ __device__ __forceinline__ float minus_two_log_unit_interval(float u1)
     return u1 > 0.96875f ? near1 : far;
 }
 
-// Box-Muller on one pair of words, scaled: g0 = scale r cos(2 pi u2),
-// g1 = scale r sin(2 pi u2), r = sqrt(-2 ln u1), with u1 = ((a >> 8) + 1) 2^-24
-// in (0, 1] and u2 = (b >> 8) 2^-24 in [0, 1), both exact in float.  The angle
-// is taken in [-pi, pi), where the hardware sine and cosine have an absolute
-// error of about 2^-21: reading b as signed and shifting arithmetically gives
-// u2 for u2 < 1/2 and u2 - 1 above (the same sine and cosine).
+// Box-Muller on one pair of 21-bit uniforms held in the top bits of two words,
+// scaled: g0 = scale r cos(2 pi u2), g1 = scale r sin(2 pi u2),
+// r = sqrt(-2 ln u1), with u1 = ((a >> 11) + 1) 2^-21 in (0, 1] and
+// u2 = (b >> 11) 2^-21 in [0, 1), both exact in float.  The angle is taken in
+// [-pi, pi), where the hardware sine and cosine have an absolute error of about
+// 2^-21: reading b as signed and shifting arithmetically gives u2 for u2 < 1/2
+// and u2 - 1 above (the same sine and cosine).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float scale, float &g0, float &g1)
 {
-    const float u1 = fmaf((float)(a >> 8), 0x1.0p-24f, 0x1.0p-24f); // ((a >> 8) + 1) 2^-24, exact
+    const float u1 = fmaf((float)(a >> 11), 0x1.0p-21f, 0x1.0p-21f); // ((a >> 11) + 1) 2^-21, exact
     const float r = scale * sqrt_hw(minus_two_log_unit_interval(u1)); // u1 = 1 gives r = 0
-    // 2 pi t with t = (signed b >> 8) 2^-24: one rounding, as 2 pi 2^-24 is the
+    // 2 pi t with t = (signed b >> 11) 2^-21: one rounding, as 2 pi 2^-21 is the
     // float 2 pi times a power of two
-    const float ang = (float)((int32_t)b >> 8) * (6.28318530717958647692f * 0x1.0p-24f);
+    const float ang = (float)((int32_t)b >> 11) * (6.28318530717958647692f * 0x1.0p-21f);
     float s, c;
     sincos_hw(ang, s, c);
     g0 = r * c;
     g1 = r * s;
+}
+
+// The fifth and sixth uniforms of a Philox block, packed from the low bits of
+// its words into the top 21 bits of one word, as box_muller reads them:
+// ((hi mod 2^11) 2^10 + (lo mod 2^10)) 2^11.
+__device__ __forceinline__ uint32_t low_bits_word(uint32_t hi, uint32_t lo)
+{
+    return (hi << 21) | ((lo & 0x3FFu) << 11);
 }
 
 // Does species S use the Gaussian of mode a?  Non-conserved modes a > D of
@@ -123,24 +133,32 @@ __device__ __forceinline__ void gaussian_pair(uint32_t wa, uint32_t wb, float sc
     }
 }
 
+// Philox blocks per species: mode a >= 1 is Gaussian n = a - 1 of its
+// species, and block b holds Gaussians 6 b .. 6 b + 5.
+template <class L> constexpr int kNoiseBlocks = (L::Q + 4) / 6;
+
 // Fill g[a] with the Gaussian of mode a, times its scale, for every mode
-// species S uses in the Philox slots [SLOT_LO, SLOT_HI) (all by default):
-// counter (site, step, S, a/4), lane a mod 4.  The momentum
-// modes (species 0 only) are scaled by scale_j, the others by scale.  Only the
-// needed Philox blocks and Box-Muller pairs are evaluated (decided at compile
-// time).
-template <class L, int S, int SLOT_LO = 0, int SLOT_HI = (L::Q + 3) / 4>
+// species S uses in the Philox blocks [BLK_LO, BLK_HI) (all by default).  Block
+// b has counter (site, step, S, b); its words x0 .. x3 give six 21-bit
+// uniforms, the top 21 bits of each word and two packed from the low bits, and
+// three Box-Muller pairs: modes (6b+1, 6b+2) on (x0, x1), (6b+3, 6b+4) on
+// (x2, x3) and (6b+5, 6b+6) on the packed two.  The momentum modes (species 0
+// only) are scaled by scale_j, the others by scale.  Only the needed Philox
+// blocks and Box-Muller pairs are evaluated (decided at compile time).
+template <class L, int S, int BLK_LO = 0, int BLK_HI = kNoiseBlocks<L>>
 __device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uint32_t k0, uint32_t k1,
                                                float scale_j, float scale, float (&g)[L::Q])
 {
-    static_for<(L::Q + 3) / 4>([&](auto sc) {
-        constexpr int slot = decltype(sc)::value;
-        constexpr bool any = uses_mode<L, S>(4 * slot) || uses_mode<L, S>(4 * slot + 1) ||
-                             uses_mode<L, S>(4 * slot + 2) || uses_mode<L, S>(4 * slot + 3);
-        if constexpr (any && slot >= SLOT_LO && slot < SLOT_HI) {
-            const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)slot), k0, k1);
-            gaussian_pair<L, S, 4 * slot>(x.x, x.y, scale_j, scale, g);
-            gaussian_pair<L, S, 4 * slot + 2>(x.z, x.w, scale_j, scale, g);
+    static_for<kNoiseBlocks<L>>([&](auto bc) {
+        constexpr int b = decltype(bc)::value;
+        constexpr int a = 6 * b + 1; // first mode of the block
+        constexpr bool any = uses_mode<L, S>(a) || uses_mode<L, S>(a + 1) || uses_mode<L, S>(a + 2) ||
+                             uses_mode<L, S>(a + 3) || uses_mode<L, S>(a + 4) || uses_mode<L, S>(a + 5);
+        if constexpr (any && b >= BLK_LO && b < BLK_HI) {
+            const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)b), k0, k1);
+            gaussian_pair<L, S, a>(x.x, x.y, scale_j, scale, g);
+            gaussian_pair<L, S, a + 2>(x.z, x.w, scale_j, scale, g);
+            gaussian_pair<L, S, a + 4>(low_bits_word(x.x, x.y), low_bits_word(x.z, x.w), scale_j, scale, g);
         }
     });
 }

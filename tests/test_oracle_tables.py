@@ -142,31 +142,53 @@ def test_philox_known_answers():
 
 def test_gaussians_are_standard_normal():
     """Box-Muller over Philox output (Sec. VI A): a large sample is N(0, 1), with
-    independent lanes and no correlation between neighbouring counters."""
+    independent positions within a block (the third pair is built from the
+    words' low bits) and no correlation between neighbouring counters."""
     scipy_stats = pytest.importorskip("scipy.stats")
-    n = 40000
-    g = np.array([[oracle.gaussian(1234, s, 7, 0, a) for a in range(4)] for s in range(n)])
+    n = 30000
+    g = np.array([[oracle.gaussian(1234, s, 7, 0, a) for a in range(1, 7)] for s in range(n)])
     flat = g.ravel()
     assert abs(flat.mean()) < 4.0 / np.sqrt(flat.size)
     assert abs(flat.var() - 1.0) < 4.0 * np.sqrt(2.0 / flat.size)
     assert scipy_stats.kstest(flat, "norm").pvalue > 1e-3
+    for col in range(6):
+        assert scipy_stats.kstest(g[:, col], "norm").pvalue > 1e-4, col
     cc = np.corrcoef(g.T)
-    assert np.all(np.abs(cc - np.eye(4)) < 4.0 / np.sqrt(n))
+    assert np.all(np.abs(cc - np.eye(6)) < 4.0 / np.sqrt(n))
+    # the squared radius of a pair is -2 ln u1: exponential with mean 2
+    r2 = g[:, 4] ** 2 + g[:, 5] ** 2
+    assert scipy_stats.kstest(r2 / 2.0, "expon").pvalue > 1e-3
     lag = np.corrcoef(g[:-1, 0], g[1:, 0])[0, 1]
     assert abs(lag) < 4.0 / np.sqrt(n)
 
 
+def _uniforms(x):
+    """The six 21-bit uniforms of a Philox block, as the noise definition cuts
+    them: the top 21 bits of each word, then two from the low bits."""
+    return [w >> 11 for w in x] + [((x[0] & 0x7FF) << 10) | (x[1] & 0x3FF),
+                                   ((x[2] & 0x7FF) << 10) | (x[3] & 0x3FF)]
+
+
 def test_gaussian_counter_layout():
-    """Modes a and a+4 use different Philox counters; species and step enter the
-    counter; lanes a mod 4 of one counter come from one Philox block."""
+    """Mode a >= 1 is Gaussian n = a - 1 of its species: modes a and a + 6 use
+    different Philox counters (site, step, species, n / 6); species, step,
+    site and seed enter the key or counter; the three Box-Muller pairs of one
+    block share their words as stated, radius from the first uniform of the
+    pair and angle from the second (cosine for even n, sine for odd n)."""
     base = oracle.gaussian(9, 3, 5, 0, 1)
-    assert base != oracle.gaussian(9, 3, 5, 0, 5)
+    assert base != oracle.gaussian(9, 3, 5, 0, 7)
     assert base != oracle.gaussian(9, 3, 5, 1, 1)
     assert base != oracle.gaussian(9, 3, 6, 0, 1)
     assert base != oracle.gaussian(9, 4, 5, 0, 1)
     assert base != oracle.gaussian(10, 3, 5, 0, 1)
-    # the Box-Muller pair (lanes 0, 1) shares one radius
-    g0, g1 = oracle.gaussian(9, 3, 5, 0, 4), oracle.gaussian(9, 3, 5, 0, 5)
-    x = oracle.philox4x32_10([3, 5, 0, 1], [9, 0])
-    u1 = ((x[0] >> 8) + 1) * 2.0 ** -24
-    assert g0 ** 2 + g1 ** 2 == pytest.approx(-2.0 * np.log(u1), rel=1e-13)
+    assert np.isnan(oracle.gaussian(9, 3, 5, 0, 0))
+    for blk, a0 in ((0, 1), (1, 7), (2, 13)):
+        x = oracle.philox4x32_10([3, 5, 1, blk], [9, 0])
+        U = _uniforms(x)
+        for q in range(3):
+            g0 = oracle.gaussian(9, 3, 5, 1, a0 + 2 * q)
+            g1 = oracle.gaussian(9, 3, 5, 1, a0 + 2 * q + 1)
+            u1, u2 = (U[2 * q] + 1) * 2.0 ** -21, U[2 * q + 1] * 2.0 ** -21
+            r = np.sqrt(-2.0 * np.log(u1))
+            assert g0 == pytest.approx(r * np.cos(2 * np.pi * u2), rel=1e-12, abs=1e-14), (blk, q)
+            assert g1 == pytest.approx(r * np.sin(2 * np.pi * u2), rel=1e-12, abs=1e-14), (blk, q)
