@@ -167,10 +167,13 @@ enum {
  * temperature (k_B T, lattice units, >= 0).  G: inter-species coupling of
  * Eq. FORCESTRUCTURE (G > 0 repels).  seed: the 64-bit key of the
  * Philox4x32-10 noise generator.
- * Noise: the Gaussian for mode a of species s at (site, step n) is lane a mod 4
- * of Box-Muller on Philox4x32-10 with key (seed low, seed high) and counter
- * (site, n, s, a/4); u1 = ((x>>8)+1) 2^-24, u2 = (y>>8) 2^-24,
- * (g0, g1) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2) on lanes (0,1) and (2,3).
+ * Noise: the Gaussian for mode a >= 1 of species s at (site, step n) is its
+ * Gaussian k = a - 1, from Philox4x32-10 with key (seed low, seed high) and
+ * counter (site, n, s, k/6).  The block's words x0..x3 give six 21-bit
+ * uniforms U0..U3 = x0..x3 >> 11, U4 = (x0 mod 2^11) 2^10 + (x1 mod 2^10),
+ * U5 = (x2 mod 2^11) 2^10 + (x3 mod 2^10); Gaussian k is output k mod 2 of
+ * Box-Muller on (U2q, U2q+1), q = (k mod 6)/2: u1 = (U2q + 1) 2^-21,
+ * u2 = U2q+1 2^-21, (g0, g1) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
  * The species momenta use species 0's draws for B as well, with the opposite sign.
  * No device memory is allocated here.
  * Errors: FLBM_EINVAL if lat is unknown, nx/ny/nz < 2 (nz != 1 for D2Q9),
@@ -471,8 +474,8 @@ const char *flbm_version(void);
  *     C = rho / rho_t, A = sqrt((2 lb_d - lb_d^2) kT); it sums to zero over the
  *     species, so the total momentum is conserved;
  *   - the other modes' noise with the variances of Eq. new-noise per species.
- * g of mode a of species s at (site, n) is lane a mod 4 of Box-Muller on
- * Philox4x32-10 with counter (site, n, s, a/4), as for two species; every
+ * g of mode a of species s at (site, n) is drawn as for two species (counter
+ * (site, n, s, (a-1)/6), six 21-bit uniforms per block); every
  * species draws its own momentum Gaussians.  Populations are stored as float
  * in the natural layout [s][i][z][y][x] where exposed.  Conventions (errors,
  * asynchrony, site order, lattice units) are those of the two-species calls.
