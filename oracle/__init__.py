@@ -141,6 +141,9 @@ def philox4x32_10(ctr, key):
 
 
 def gaussian(seed: int, site: int, step: int, species: int, mode: int) -> float:
+    """The standard Gaussian of mode >= 1 of a species at (site, step): its
+    Gaussian n = mode - 1, from Philox4x32-10 block n // 6 cut into six 21-bit
+    uniforms (orc_gaussian in flbm_oracle.c); NaN for mode 0."""
     return lib().orc_gaussian(seed, site, step, species, mode)
 
 
