@@ -183,20 +183,33 @@ def test_theory_structure_functions_reduce_to_appendix_e():
 # second formulation: the update written in population space (Sec. V B)
 # --------------------------------------------------------------------------
 
-def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True):
+def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True, noise_rho0=None,
+                           force_velocity=False, lambda_d=None, mode_rates=None):
     """One step of the FLBE written with the MRT matrix
     Lambda_ij = w_i sum_a lambdabar_a T_ai T_aj / N_a (Sec. V B) acting on f^eq
     and (I - Lambda/2) acting on the Hermite forcing Phi_i, plus the noise mapped
     to populations, then np.roll streaming.  Shares only the tables and the noise
-    draws with the oracle."""
+    draws with the oracle.
+
+    Options, each the population-space statement of one oracle option:
+    sdf=False drops the shared momentum noise (the no-sdf control of Sec. VI A);
+    noise_rho0=(rA, rB) puts fixed reference densities in the amplitudes of
+    Eq. new-noise instead of the local ones; force_velocity=True takes the
+    species velocity inside Phi as v = jbar/rho + a/2 instead of
+    rho v = jbar + R_j/2 (Eq. 2system); lambda_d overrides the common momentum
+    rate (Sec. III); mode_rates {(s, a): lambdabar} overrides single modes."""
     c, w, T, N = oracle.tables(lat)
     D, Q = DIMS[lat]
     cf = c.astype(float)
     lam = np.zeros((2, Q))
     lam_d = 1.0 / tau[0] if tau[0] == tau[1] else 2.0 / (tau[0] + tau[1])
+    if lambda_d is not None:
+        lam_d = lambda_d
     for s in range(2):
         lam[s, 1:] = 1.0 / tau[s]
         lam[s, 1:D + 1] = lam_d
+    for (s, a), lb in (mode_rates or {}).items():
+        lam[s, a] = lb
     Lam = [np.einsum("i,a,ai,aj->ij", w, lam[s] / N, T, T) for s in range(2)]
     nz, ny, nx = f.shape[2:]
     rho = f.sum(axis=1)
@@ -225,14 +238,15 @@ def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True):
         for y in range(ny):
             for x in range(nx):
                 site = (z * ny + y) * nx + x
-                vj = (2 * lam_d - lam_d ** 2) * kT * rho[0, z, y, x] * rho[1, z, y, x] / rt[z, y, x]
+                nr = (rho[0, z, y, x], rho[1, z, y, x]) if noise_rho0 is None else noise_rho0
+                vj = (2 * lam_d - lam_d ** 2) * kT * nr[0] * nr[1] / (nr[0] + nr[1])
                 for a in range(1, D + 1):
                     g = oracle.gaussian(seed, site, step, 0, a)
                     xi[0, a, z, y, x] = (np.sqrt(vj) if sdf else 0.0) * g
                     xi[1, a, z, y, x] = -xi[0, a, z, y, x]
                 for s in range(2):
                     for a in range(D + 1, Q):
-                        var = (2 * lam[s, a] - lam[s, a] ** 2) * N[a] * 3 * kT * rho[s, z, y, x]
+                        var = (2 * lam[s, a] - lam[s, a] ** 2) * N[a] * 3 * kT * nr[s]
                         xi[s, a, z, y, x] = np.sqrt(var) * oracle.gaussian(seed, site, step, s, a)
     out = np.empty_like(f)
     I = np.eye(Q)
@@ -242,7 +256,7 @@ def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True):
         d1 = (np.einsum("ij,jxyz->ixyz", Lam[s], feq(rho[s], u) - f[s])
               + np.einsum("ij,jxyz->ixyz", I - Lam[s] / 2, force(rho[s], acc[s], zero)) + noise)
         Rj = np.einsum("ixyz,id->dxyz", d1, cf)
-        v = (j[s] + 0.5 * Rj) / rho[s]
+        v = j[s] / rho[s] + 0.5 * acc[s] if force_velocity else (j[s] + 0.5 * Rj) / rho[s]
         d = (np.einsum("ij,jxyz->ixyz", Lam[s], feq(rho[s], u) - f[s])
              + np.einsum("ij,jxyz->ixyz", I - Lam[s] / 2, force(rho[s], acc[s], v)) + noise)
         post = f[s] + d
@@ -251,20 +265,88 @@ def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True):
     return out
 
 
+# One entry per oracle option branch: (oracle options, mode-rate overrides,
+# keyword arguments of the population-space form).  The reference densities
+# (1.4, 0.5) differ from the state's local ones (about 1.0 and 0.8), so that a
+# wrong density in the noise amplitude shows.
+_OPTION_CASES = {
+    "default": ({}, {}, {}),
+    "no_sdf": ({"sdf": 0}, {}, {"sdf": False}),
+    "noise_rho_reference": ({"noise_rho": 1, "rho0_a": 1.4, "rho0_b": 0.5}, {},
+                            {"noise_rho0": (1.4, 0.5)}),
+    "force_velocity": ({"force_velocity": 1}, {}, {"force_velocity": True}),
+    "lambda_d": ({"lambda_d": 1.3}, {}, {"lambda_d": 1.3}),
+    "mode_rates": ({}, {(0, 4): 1.5, (1, 5): 0.6, (0, 8): 1.9, (1, 8): 0.3}, {}),
+    "all": ({"noise_rho": 1, "rho0_a": 1.4, "rho0_b": 0.5, "force_velocity": 1, "lambda_d": 0.9},
+            {(0, 6): 1.2, (1, 7): 1.7},
+            {"noise_rho0": (1.4, 0.5), "force_velocity": True, "lambda_d": 0.9}),
+}
+
+
 @pytest.mark.parametrize("lat,shape", [(oracle.D2Q9, (1, 4, 5)), (oracle.D3Q19, (3, 3, 4))])
-def test_moment_space_update_equals_population_space_form(lat, shape):
+@pytest.mark.parametrize("case", sorted(_OPTION_CASES))
+def test_moment_space_update_equals_population_space_form(lat, shape, case):
     """The oracle's moment-space update equals the population-space MRT form of
     Sec. V B (Lambda_ij, Hermite f^eq and Phi, noise mapped to populations) on a
-    random non-uniform state with G != 0, tau_A != tau_B, over three steps."""
+    random non-uniform state with G != 0, tau_A != tau_B, over three steps, for
+    the default update and for every option branch of the oracle: no shared
+    momentum noise (Sec. VI A), reference densities in Eq. new-noise, the
+    alternative species velocity inside Phi (Eq. 2system), an overridden
+    common momentum rate (Sec. III) and single-mode rates."""
     tau, kT, G, seed = (0.8, 1.1), 1e-3, 0.7, 99
+    opts, rates, kw = _OPTION_CASES[case]
     f = inputs.random_populations(_base(lat, 1.0, 0.8), shape, 0.05, seed=5)
-    o = oracle.Oracle(lat, shape[2], shape[1], shape[0], tau[0], tau[1], kT, G, seed)
+    o = oracle.Oracle(lat, shape[2], shape[1], shape[0], tau[0], tau[1], kT, G, seed, **opts)
+    for (s, a), lb in rates.items():
+        o.set_mode_rate(s, a, lb)
     o.set_f(f, step=10)
     ref = f.copy()
     for n in range(3):
-        ref = _population_space_step(ref, lat, tau, kT, G, seed, 10 + n)
+        ref = _population_space_step(ref, lat, tau, kT, G, seed, 10 + n, mode_rates=rates, **kw)
     o.step(3)
     assert np.max(np.abs(o.get_f() - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q9, (1, 64, 64)), (oracle.D3Q19, (12, 12, 12))])
+@pytest.mark.parametrize("noise_rho", [0, 1])
+def test_one_step_variances_follow_the_density_option(lat, shape, noise_rho):
+    """Eq. new-noise on a non-uniform state: with every rate 1 the
+    post-collision ghost moments are exactly the noise (m^eq = Phi = 0 on the
+    ghosts), so ghost_a(r) / sqrt(N_a 3 kT rho(r)) is a standard Gaussian over
+    sites when the local densities enter the amplitude, and
+    ghost_a(r) / sqrt(N_a 3 kT rho0) when the reference densities do.  The
+    densities vary by a factor of three across the box and rho0 sits far from
+    them, so the wrong density (or a wrong factor) moves the variance well
+    outside the bound."""
+    nz, ny, nx = shape
+    D, Q = DIMS[lat]
+    kT = 1e-4
+    rho0 = (2.5, 0.2)
+    rng = np.random.Generator(np.random.PCG64(17))
+    ra = rng.uniform(0.5, 1.5, size=shape)
+    rb = rng.uniform(0.3, 0.9, size=shape)
+    o = oracle.Oracle(lat, nx, ny, nz, 1.0, 1.0, kT, 0.0, 23, noise_rho=noise_rho,
+                      rho0_a=rho0[0], rho0_b=rho0[1])
+    o.init(ra, rb)
+    o.step(1)
+    c, w, T, N = oracle.tables(lat)
+    m = np.einsum("ai,sixyz->saxyz", T, _unstream(o.get_f(), c)).reshape(2, Q, -1)
+    nsite = m.shape[2]
+    tol = 5.0 * np.sqrt(2.0 / nsite)
+    ghosts = range(D + 1 + (3 if lat == oracle.D2Q9 else 6), Q)
+    for s, rho in enumerate((ra.ravel(), rb.ravel())):
+        amp_rho = np.full(nsite, rho0[s]) if noise_rho else rho
+        for a in ghosts:
+            z = m[s, a] / np.sqrt(N[a] * 3 * kT * amp_rho)
+            assert abs(z.var() - 1.0) < tol, (s, a, z.var())
+            assert abs(z.mean()) < 5.0 / np.sqrt(nsite)
+    # the shared momentum noise, G = 0 and rest state: R_j = xi exactly
+    nr = (np.full(nsite, rho0[0]), np.full(nsite, rho0[1])) if noise_rho else (ra.ravel(), rb.ravel())
+    vj = kT * nr[0] * nr[1] / (nr[0] + nr[1])
+    for a in range(1, D + 1):
+        z = m[0, a] / np.sqrt(vj)
+        assert abs(z.var() - 1.0) < tol
+        assert np.all(np.abs(m[0, a] + m[1, a]) < 1e-15)
 
 
 # --------------------------------------------------------------------------
