@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage and batching forms")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
     ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap"], default=None,
-                    help="force one step schedule (implies --no-autotune; fused streams in place)")
+                    help="force one step schedule (implies --no-autotune); fused with two arrays is the "
+                         "pipelined step, fused in place the in-place persistent step")
     ap.add_argument("--streaming", choices=["two_arrays", "in_place"], default="two_arrays",
                     help="population streaming: two arrays (default) or one array updated in place")
     ap.add_argument("--form", choices=["species2", "species3", "species4"], default=None,
@@ -92,7 +93,7 @@ def measured_peaks():
 
 # the files that define the step kernels (device code and the structures they
 # take); the host runtime around them can change without touching the kernels
-KERNEL_SOURCES = ("flbm_internal.h", "flbm_kernels.cuh", "flbm_lattice.cuh", "flbm_launch.h", "flbm_noise.cuh",
+KERNEL_SOURCES = ("flbm_internal.h", "flbm_kernels.cuh", "flbm_lattice.cuh", "flbm_launch.h", "flbm_noise.cuh", "flbm_pair.cuh",
                   "flbm_transform.cuh", "inst_d*.cu")
 
 
@@ -115,10 +116,11 @@ def sources_digest():
     return h.hexdigest()
 
 
-def recorded_capture(workload, sites):
-    """DRAM bytes and executed warp-instructions per collide launch from the
-    committed ncu summary, scaled to `sites`, if it was taken on the current
-    kernel sources; else None."""
+def recorded_capture(workload, sites, schedule=None):
+    """DRAM bytes and executed warp-instructions per step (all of the step's
+    kernels) from the committed ncu record, scaled to `sites`, if it was taken
+    on the current kernel sources (and, when given, the same schedule); else
+    None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -128,9 +130,11 @@ def recorded_capture(workload, sites):
     rec = d.get(workload)
     if not rec or rec.get("sources_sha256") != sources_digest():
         return None
+    if schedule is not None and rec.get("schedule") != schedule:
+        return None
     scale = sites / rec["sites"]
-    inst = rec.get("warp_instructions_per_launch")
-    return {"traffic": rec["dram_bytes_per_launch"] * scale, "inst": None if inst is None else inst * scale}
+    inst = rec.get("warp_instructions_per_step")
+    return {"traffic": rec["dram_bytes_per_step"] * scale, "inst": None if inst is None else inst * scale}
 
 
 SMS, SCHEDULERS_PER_SM = 152, 4  # GB300: each scheduler issues at most one warp-instruction a cycle
@@ -251,6 +255,53 @@ def storage_forms(wl, seed, steps, device):
     return out
 
 
+def recorded_precision():
+    """Errors of the FP32, FP16 and BF16 storage forms against the FP64
+    oracle, from the committed record that tests/precision_vs_oracle.py
+    writes on the GPU (profiles/precision_vs_oracle.json); None unless it was
+    taken on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "precision_vs_oracle.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("sources_sha256") != sources_digest():
+        return None
+    return rec
+
+
+def timed_step_form(wl, seed, steps, device, schedule=None):
+    """MLUPS of one workload's step (device-timed, CUDA events)."""
+    import torch
+
+    from paper_1410_5584_gb300 import Lattice
+    from paper_1410_5584_gb300 import flbm as F
+
+    nx, ny, nz = wl["nx"], wl["ny"], wl["nz"]
+    lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
+                  storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"])
+    if schedule is not None:
+        lat.set_option("schedule", F.SCHEDULE[schedule])
+    lat.init()
+    lat.step(10)
+    lat.sync()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(lat.stream)
+    lat.step(steps)
+    s1.record(lat.stream)
+    lat.sync()
+    t = s0.elapsed_time(s1) / 1e3
+    lat.close()
+    sites = nx * ny * nz
+    q = 19 if wl["lattice"] == 1 else 9
+    peak, _ = measured_peaks()
+    bps = 2 * q * 2 * BYTES_PER_POP[wl["storage"]]
+    return {"value": sites * steps / t / 1e6, "unit": "MLUPS", "steps": steps, "ms_per_step": t / steps * 1e3,
+            "schedule": schedule or "default", "workload": wl["desc"],
+            "hbm": {"achieved": bps * sites * steps / t / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": bps * sites * steps / t / 1e9 / peak, "bytes_per_site": bps}}
+
+
 def batched_form(seed, steps, device, nrep=64):
     """The batching form: nrep independent D2Q9 replicas, n_x and n_y drawn from
     {64, 128, 256, 512}, kT log-uniform in [1e-6, 1e-4], G rho0 uniform in
@@ -283,6 +334,7 @@ def batched_form(seed, steps, device, nrep=64):
     b.sync()
     t_batch = timed(lambda: b.step(steps), b.stream)
     b.sync()
+    ensemble = ensemble_structure_factor(b, cfg)
     b.close()
     stream = torch.cuda.Stream(device=device)
     lats = [Lattice(0, r["nx"], r["ny"], 1, 1.0, 1.0, r["kT"], r["G"], r["seed"], device=device, stream=stream)
@@ -294,9 +346,50 @@ def batched_form(seed, steps, device, nrep=64):
     for g in lats:
         g.sync()
         g.close()
+    peak, _ = measured_peaks()
+    ach = sites * steps * 2 * 9 * 4 * 2 / t_batch / 1e9
     return {"value": sites * steps / t_batch / 1e6, "unit": "MLUPS", "replicas": nrep, "sites": sites,
             "steps": steps, "graph_steps": graph_steps, "per_replica_launches_mlups": sites * steps / t_sep / 1e6,
-            "speedup_vs_per_replica_launches": t_sep / t_batch}
+            "speedup_vs_per_replica_launches": t_sep / t_batch,
+            "hbm": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "bytes_per_site": 144},
+            "ensemble_sk": ensemble}
+
+
+def ensemble_structure_factor(b, cfg, burn=2000, nsnap=100, every=20):
+    """Ensemble statistics of the batch from one submission: every replica's
+    axis structure factor S_AA(k) sampled together (one flbm_sf_sample call
+    per snapshot for all 64 replicas), divided by the continuum prediction of
+    Eq. str-bin-hom at that replica's kT and G (rho0 = 1, alpha = G sin k/k),
+    averaged over k bands per replica, then over replicas: mean and standard
+    error over the replicas (independent runs).  Below k = 0.5 the continuum
+    form and the lattice agree; above it the lattice corrections of the
+    update show as a departure from 1."""
+    import numpy as np
+
+    b.step(burn)
+    for _ in range(nsnap):
+        b.step(every)
+        b.sf_sample()
+    b.sync()
+    bands = [(0.0, 0.5), (0.5, 1.0), (1.0, 2.0), (2.0, np.pi + 1e-9)]
+    per = [[] for _ in bands]
+    for k, c in enumerate(cfg):
+        s_aa = np.asarray(b.replicas[k].structure_factor(0)[0])
+        n = c["nx"]
+        kk = 2 * np.pi * np.arange(1, len(s_aa) + 1) / n
+        alpha = c["G"] * np.sinc(kk / np.pi)
+        pred = 3.0 * c["kT"] / (1.0 - alpha ** 2)
+        er = s_aa / pred
+        for q, (lo, hi) in enumerate(bands):
+            sel = (kk >= lo) & (kk < hi)
+            if sel.any():
+                per[q].append(float(er[sel].mean()))
+    out = {"snapshots": nsnap, "every": every, "burn_in": burn, "quantity": "S_AA(k) / (3 kT / (1 - (G sin k / k)^2))"}
+    for (lo, hi), vals in zip(bands, per):
+        v = np.array(vals)
+        out[f"k_{lo:.1f}_{min(hi, np.pi):.2f}"] = {"mean": float(v.mean()), "se": float(v.std(ddof=1) / np.sqrt(len(v))),
+                                                   "replicas": len(v)}
+    return out
 
 
 def capillary_form(seed, device, steps=20000):
@@ -499,7 +592,7 @@ def run_ours(args, wl):
     sites = nx * ny * nz
     Q = 19 if wl["lattice"] == 1 else 9
     from paper_1410_5584_gb300 import flbm as F
-    streaming = "in_place" if args.schedule == "fused" else args.streaming
+    streaming = args.streaming
     lat = Lattice(wl["lattice"], nx, ny, nz, wl["tau"][0], wl["tau"][1], wl["kT"], wl["G"], seed,
                   storage=wl["storage"], device=device, rho0_a=wl["rho0"], rho0_b=wl["rho0"],
                   streaming=F.STREAMING[streaming])
@@ -569,42 +662,57 @@ def run_ours(args, wl):
     peak, peak_kind = measured_peaks()
     bpp = BYTES_PER_POP[wl["storage"]]
     D = 3 if wl["lattice"] == 1 else 2
-    # Two arrays, the two-kernel schedule and full relaxation: the density pass
-    # also writes m_0 .. m_D of both species and the collide reads those
-    # instead of the populations (the moment-fed collide)
-    moment_fed = (streaming == "two_arrays" and all(t == 1.0 for t in wl["tau"])
-                  and (launch or {}).get("schedule", F.SCHEDULE["two_kernels"]) == F.SCHEDULE["two_kernels"])
-    mom_bytes = sites * 2 * (D + 1) * 4 if moment_fed else 0
-    # algorithmic bytes of the collide: its reads (populations, or the moment
-    # planes) and its population writes, once each
-    alg_bytes = (mom_bytes if moment_fed else sites * 2 * Q * bpp) + sites * 2 * Q * bpp
-    # and of the whole step: the density pass reads the populations once and
-    # writes rho (and the moment planes)
-    step_bytes = alg_bytes + sites * 2 * Q * bpp + sites * 8 + mom_bytes
-    coll_ms = kms["collide"] / max(kn["collide"], 1)
-    achieved = alg_bytes / (coll_ms / 1e3) / 1e9
-    cap = recorded_capture(args.workload, sites)
+    sched = (launch or {}).get("schedule", F.SCHEDULE["two_kernels"])
+    # the pipelined step: the fused schedule with two arrays (one launch a step)
+    pipelined = streaming == "two_arrays" and sched == F.SCHEDULE["fused"] and kn["density"] == 0
+    full = all(t == 1.0 for t in wl["tau"])
+    moment_fed = streaming == "two_arrays" and full and sched == F.SCHEDULE["two_kernels"]
+    # Algorithmic bytes of one site update (every population of both species
+    # read once and written once), the roofline's numerator for the whole step
+    alg_site = 2 * Q * 2 * bpp
+    step_s = t_max / args.steps
+    achieved = alg_site * sites / step_s / 1e9
+    # the bytes the implementation moves by design: the pipelined step keeps
+    # its densities and moments in an L2-resident ring; the two-kernel step
+    # re-reads the populations for the densities (moment-fed: the collide
+    # reads m_0 .. m_D and rho instead of the populations)
+    if pipelined:
+        design = alg_site
+    elif moment_fed:
+        design = alg_site + 2 * (2 * (D + 1) * 4 + 8)
+    else:
+        design = alg_site + 2 * Q * bpp + 8 + 8
+    cap = recorded_capture(args.workload, sites, "pipelined" if pipelined else "two_kernels")
     traffic = cap["traffic"] if cap else None
-    hbm_view = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     clocks = clk.summary()
-    if moment_fed and cap and cap["inst"]:
-        # the moment-fed collide moves 184 B a site and is bound by instruction
-        # issue: executed warp-instructions (ncu count, scaled per site) over
-        # the event-timed launch, against one per scheduler per cycle
+    coll_ms = kms["collide"] / max(kn["collide"], 1)
+    den_ms = kms["density"] / max(kn["density"], 1) if kn["density"] else 0.0
+    roofline = {"bound": "hbm", "kernel": "k_step_pipe (one launch a step)" if pipelined
+                else "whole step (density pass + k_collide)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_site": alg_site, "algorithmic_bytes_per_launch": alg_site * sites,
+                "launches_per_step": 1 if pipelined else 2, "design_bytes_per_site": design,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    kernels = {"collide" if not pipelined else "k_step_pipe": {"ms": coll_ms}}
+    if not pipelined:
+        coll_bytes = (2 * (D + 1) * 4 + 8 if moment_fed else 2 * Q * bpp + 8) + 2 * Q * bpp
+        den_bytes = 2 * Q * bpp + 8 + (2 * (D + 1) * 4 if moment_fed else 0)
+        kernels["collide"].update(bytes_per_site=coll_bytes, gbs=coll_bytes * sites / (coll_ms / 1e3) / 1e9)
+        kernels["density"] = {"ms": den_ms, "bytes_per_site": den_bytes,
+                              "gbs": den_bytes * sites / (den_ms / 1e3) / 1e9 if den_ms else None}
+    if cap and cap.get("inst"):
+        # issue view of the step's kernels: executed warp-instructions per step
+        # (the recorded ncu count, scaled by the site count) over the event-timed
+        # kernel time, against one warp-instruction per scheduler per cycle
         mhz = clocks["sm_mhz"] if clocks else 2070.0
         issue_peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
-        ach = cap["inst"] / (coll_ms / 1e3) / 1e9
-        roofline = {"bound": "alu", "kernel": "k_collide", "achieved": ach, "peak": issue_peak,
-                    "unit": "G warp-instructions/s", "frac": ach / issue_peak, "traffic": traffic,
-                    "peak_source": f"{SMS} SMs x {SCHEDULERS_PER_SM} schedulers x 1 warp-instruction a cycle "
-                                   f"at the median SM clock sampled during the run ({mhz:.0f} MHz)",
-                    "instructions_per_launch": cap["inst"], "algorithmic_bytes_per_launch": alg_bytes,
-                    "hbm": {k: hbm_view[k] for k in ("achieved", "peak", "unit", "frac", "peak_source")}}
-    else:
-        roofline = hbm_view
+        ach_i = cap["inst"] / ((coll_ms + den_ms) / 1e3) / 1e9
+        roofline["issue"] = {"achieved": ach_i, "peak": issue_peak, "unit": "G warp-instructions/s",
+                             "frac": ach_i / issue_peak, "instructions_per_step": cap["inst"],
+                             "source": "ncu smsp__inst_executed of a recorded capture on the current kernel "
+                                       "sources, scaled by the site count; peak at the median SM clock sampled "
+                                       f"during the run ({mhz:.0f} MHz)"}
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
@@ -614,9 +722,10 @@ def run_ours(args, wl):
                    "l2": "inputs larger than L2" if sites * 2 * Q * bpp > 129e6 else "working set fits in L2",
                    "launch": launch, "streaming": streaming},
         "roofline": roofline,
-        "step_hbm_frac": step_bytes / (t_max / args.steps) / 1e9 / peak,
-        "step_bytes_per_site": step_bytes // sites,
-        "kernel_ms": {"density": kms["density"] / max(kn["density"], 1), "collide": coll_ms},
+        "step_hbm_frac": achieved / peak,
+        "step_bytes_per_site": alg_site,
+        "kernels": kernels,
+        "kernel_ms": {"density": den_ms, "collide": coll_ms},
         "gpu_launches": kn["density"] + kn["collide"],
         "clocks": clocks,
         "e2e": e2e,
@@ -638,6 +747,16 @@ def run_ours(args, wl):
                            "note": "S_aa, S_ab, S_bb at every wavevector: fluctuation fields, float line FFTs, FP64 sums"}
     if not args.no_forms and wl["storage"] == "f32":
         line["forms"] = storage_forms(wl, args.seed, max(50, args.steps // 4), device)
+        prec = recorded_precision()
+        for st in ("f16", "bf16"):
+            line["forms"][st]["error_vs_oracle"] = prec["forms"][st] if prec else None
+        line["forms"]["f32_error_vs_oracle"] = prec["forms"]["f32"] if prec else None
+        if prec:
+            line["forms"]["error_vs_oracle_case"] = prec["case"]
+        line["forms"]["general_tau"] = timed_step_form(
+            dict(wl, tau=(0.8, 1.0), desc=wl["desc"].replace("tau=1.0", "tau=0.8/1.0")), args.seed,
+            max(50, args.steps // 4), device, schedule=args.schedule)
+        line["forms"]["d2q9_512"] = timed_step_form(WORKLOADS["d2q9-512"], args.seed, 2000, device)
         line["forms"]["batched"] = batched_form(args.seed, 5000, device)
         line["forms"]["capillary"] = capillary_form(args.seed, device)
         line["forms"]["species3"] = multi_form(args.seed, device)

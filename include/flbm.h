@@ -373,11 +373,15 @@ flbm_status flbm_restore(flbm_ctx *ctx, const void *buf, size_t bytes);
  *   stream: cudaStream_t to run on (NULL = the legacy default stream).
  *   status_out: if non-NULL, receives the device status word (bit 0: a
  *           density was not positive and finite).
- * Synchronises `stream` before returning.  The first call on a device looks up
- * the array's device address; make that first call before any stream capture.
+ * Synchronises `stream` before returning.  Every call looks up the array's
+ * device address on the current device (so a device reset between calls is
+ * harmless); the first call on a device may load the library's device code,
+ * so make that first call before any stream capture.
  * All calls share the one array, which keeps the last call's contents: calls
  * that overlap on the GPU (other streams, other threads) race.
- * Errors: FLBM_EINVAL for bad arguments or a box above 2^21 sites;
+ * Errors: FLBM_EINVAL for bad arguments, a batch handle (from
+ * flbm_batch_create: step batches with flbm_step), `pop` not 256-byte aligned
+ * or a box above 2^21 sites, all found before anything is launched;
  * FLBM_ENONFINITE if the status bit is set; FLBM_ECUDA if a CUDA call fails.
  */
 flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int parity, int64_t step, int64_t n,

@@ -385,6 +385,7 @@ bool flbm::ctx_view(const flbm_ctx *c, CtxView *out)
     out->nx = c->nx;
     out->ny = c->ny;
     out->nz = c->nz;
+    out->batch = is_batch(c);
     out->N = c->N;
     out->params = make_params(c);
     return true;
@@ -813,6 +814,57 @@ flbm_status ensure_step_graph(flbm_ctx *c, int parity)
     return FLBM_OK;
 }
 
+// Full relaxation (every lambdabar_a = 1 on the non-conserved modes, the
+// condition of the collide's full-relaxation instance).
+bool full_relaxation(const flbm_ctx *c, const StepParams &p)
+{
+    if (p.general_collide) return false;
+    for (int s = 0; s < 2; s++)
+        for (int a = c->D + 1; a < c->Q; a++)
+            if (p.cm[s][a] != 0.0f) return false;
+    return true;
+}
+
+// n steps of the pipelined two-array step (the fused schedule with two
+// arrays).  *done = false, with nothing launched, when the box has too few
+// slices for the pipeline; the caller then runs the two-kernel step.
+flbm_status step_pipe(flbm_ctx *c, int64_t n, bool *done)
+{
+    *done = false;
+    StepParams p = make_params(c);
+    const bool mom = full_relaxation(c, p);
+    int lag = 0, slots = 0;
+    size_t floats = 0, ncount = 0;
+    FLBM_CUDA(c, pipe_geometry(c->lat, c->storage, p, mom, c->pipe_lag, &lag, &slots, &floats, &ncount),
+              "pipelined step geometry");
+    if (slots == 0) return FLBM_OK;
+    if (c->ring_floats < floats) {
+        if (c->d_ring) cudaFree(c->d_ring);
+        c->d_ring = nullptr;
+        c->ring_floats = 0;
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_ring, floats * sizeof(float)), "cudaMalloc(pipeline ring)");
+        c->ring_floats = floats;
+    }
+    if (!c->d_ring_cnt)
+        FLBM_CUDA(c, cudaMalloc((void **)&c->d_ring_cnt, ncount * sizeof(unsigned)), "cudaMalloc(pipeline counters)");
+    for (int64_t t = 0; t < n; t++) {
+        p.step = (uint32_t)c->step;
+        TimedLaunch t1{c, c->stream, 1};
+        flbm_status st;
+        if ((st = t1.begin()) != FLBM_OK) return st;
+        const cudaError_t e = launch_step_pipe(c->lat, c->storage, p, cur_pop(c), next_pop(c), c->d_ring,
+                                               c->d_ring_cnt, slots, lag, mom, c->d_status, c->wait_limit_ms,
+                                               c->test_stall, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pipelined step kernel launch");
+        if ((st = t1.end()) != FLBM_OK) return st;
+        if (c->timing) c->kernel_launches[1]++;
+        c->step++;
+        c->parity ^= 1;
+    }
+    *done = true;
+    return FLBM_OK;
+}
+
 flbm_status flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
@@ -820,10 +872,15 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
     if (is_batch(c)) return batch_step(c, n);
     if (!c->initialised) return fail(c, FLBM_ESTATE, "flbm_step before flbm_init");
     if (n == 0) return FLBM_OK;
-    if (two_arrays(c) && c->schedule == FLBM_SCHEDULE_FUSED)
-        return fail(c, FLBM_EUNSUPPORTED, "two-array streaming runs the two-kernel and overlap schedules only");
+    int sched = c->schedule;
+    if (two_arrays(c) && sched == FLBM_SCHEDULE_FUSED) {
+        bool done = false;
+        flbm_status st = step_pipe(c, n, &done);
+        if (st != FLBM_OK || done) return st;
+        sched = FLBM_SCHEDULE_TWO_KERNELS; // too few slices for the pipeline
+    }
     // whole graphs of graph_steps steps first (two-kernel schedule, timing off)
-    if (c->graph_steps > 0 && c->schedule == FLBM_SCHEDULE_TWO_KERNELS && !c->timing) {
+    if (c->graph_steps > 0 && sched == FLBM_SCHEDULE_TWO_KERNELS && !c->timing) {
         while (n >= c->graph_steps) {
             flbm_status st = ensure_step_graph(c, c->parity);
             if (st != FLBM_OK) return st;
@@ -836,8 +893,8 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
         if (n == 0) return FLBM_OK;
     }
     StepParams p = make_params(c);
-    if (c->schedule == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
-    if (c->schedule == FLBM_SCHEDULE_FUSED) {
+    if (sched == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
+    if (sched == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
         if (st != FLBM_OK) return st;
     } else if (flbm_status st = use_moments(c, p); st != FLBM_OK) {
@@ -848,7 +905,7 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
         flbm_status st;
         TimedLaunch t0{c, c->stream, 0}, t1{c, c->stream, 1};
         if ((st = t0.begin()) != FLBM_OK) return st;
-        if (c->schedule == FLBM_SCHEDULE_FUSED) {
+        if (sched == FLBM_SCHEDULE_FUSED) {
             if ((st = t0.end()) != FLBM_OK) return st;
             if ((st = t1.begin()) != FLBM_OK) return st;
             cudaError_t e = launch_step_fused(c->lat, c->storage, c->parity, p, c->pop, c->rho, c->d_status,
@@ -1175,6 +1232,8 @@ void flbm_destroy(flbm_ctx *c)
     if (c->d_mom) cudaFree(c->d_mom);
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_pipe) cudaFree(c->d_pipe);
+    if (c->d_ring) cudaFree(c->d_ring);
+    if (c->d_ring_cnt) cudaFree(c->d_ring_cnt);
     if (c->d_obs) cudaFree(c->d_obs);
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_cons) cudaFree(c->d_cons);

@@ -32,6 +32,11 @@ struct flbm_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     unsigned *d_gstep = nullptr; // noise counter at the start of a graph replay
     float *d_mom = nullptr;      // moment planes of the full-relaxation two-array step (StepParams::mom)
+    // pipelined two-array step (the fused schedule with two arrays): its ring
+    // of slice slots (L2-resident scratch) and two counters per slice
+    float *d_ring = nullptr;
+    size_t ring_floats = 0;
+    unsigned *d_ring_cnt = nullptr;
     double rho0[2] = {1.0, 1.0};
     // state
     int64_t step = 0;

@@ -28,6 +28,12 @@ template <class L, class S> struct CollideF {
 template <class L, class S> struct FusedF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::step_fused(a...); }
 };
+template <class L, class S> struct PipeGeomF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::pipe_geometry(a...); }
+};
+template <class L, class S> struct PipeF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::step_pipe(a...); }
+};
 template <class L, class S> struct BatchF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::batch_step(a...); }
 };
@@ -63,6 +69,20 @@ cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams
                               cudaStream_t stream)
 {
     return dispatch<FusedF>(lat, storage, parity, p, pop, rho, status, counters, wait_ms, stall, lag, stream);
+}
+
+cudaError_t pipe_geometry(int lat, int storage, const StepParams &p, bool mom, int lag_opt, int *lag, int *ring_slots,
+                          size_t *ring_floats, size_t *counters)
+{
+    return dispatch<PipeGeomF>(lat, storage, p, mom, lag_opt, lag, ring_slots, ring_floats, counters);
+}
+
+cudaError_t launch_step_pipe(int lat, int storage, const StepParams &p, const void *pop, void *pop_out, float *ring,
+                             unsigned *counters, int ring_slots, int lag, bool mom, unsigned *status, double wait_ms,
+                             int stall, cudaStream_t stream)
+{
+    return dispatch<PipeF>(lat, storage, p, pop, pop_out, ring, counters, ring_slots, lag, mom, status, wait_ms, stall,
+                           stream);
 }
 
 cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,

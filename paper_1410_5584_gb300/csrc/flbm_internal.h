@@ -160,6 +160,21 @@ cudaError_t launch_step_fused(int lat, int storage, int parity, const StepParams
                               cudaStream_t stream);
 inline int pipeline_slices(int lat, int ny, int nz) { return lat == FLBM_D2Q9 ? ny : nz; }
 
+// One whole two-array step as one persistent launch: the densities (and, mom,
+// the moments m_0 .. m_D of a full-relaxation step) of each slice go through
+// a ring of slice slots that stays in L2, so that the populations cross HBM
+// once each way.  pipe_geometry gives the lag, the ring's slot count (0 when
+// the box has too few slices; lag_opt >= 1 overrides the lag, which any
+// value >= 1 keeps correct), the ring's size in floats and the number of
+// counter words (two per slice and row in 3D, per slice in 2D), which the
+// launcher resets.  wait_ms bounds each dependency
+// wait; stall (test hook) makes every wait run out.
+cudaError_t pipe_geometry(int lat, int storage, const StepParams &p, bool mom, int lag_opt, int *lag, int *ring_slots,
+                          size_t *ring_floats, size_t *counters);
+cudaError_t launch_step_pipe(int lat, int storage, const StepParams &p, const void *pop, void *pop_out, float *ring,
+                             unsigned *counters, int ring_slots, int lag, bool mom, unsigned *status, double wait_ms,
+                             int stall, cudaStream_t stream);
+
 // One step of every replica of a batch (density then collide over the tile
 // work list: tiles[t] = (replica, first site of 128)); the noise counter of the
 // step is *step_base + k.  full: every replica relaxes each non-conserved
@@ -207,6 +222,7 @@ cudaError_t launch_gather_sites(int lat, int storage, int parity, const StepPara
 // Read-only view of a context for the other translation units of the library.
 struct CtxView {
     int lat, storage, D, Q, nx, ny, nz;
+    bool batch; // a batch of replicas (one handle over many boxes), not a single box
     int64_t N;
     StepParams params; // parameters of the context's next step
 };

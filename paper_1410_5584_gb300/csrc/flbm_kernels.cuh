@@ -17,6 +17,7 @@
 #include "flbm_lattice.cuh"
 #include "flbm_launch.h"
 #include "flbm_noise.cuh"
+#include "flbm_pair.cuh"
 #include "flbm_transform.cuh"
 
 namespace flbm {
@@ -184,16 +185,60 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_moments(const StepParams p,
 // ---------------------------------------------------------------------------
 // fused force + moment collision + noise + streaming
 // ---------------------------------------------------------------------------
-// Force + moment collision + noise + streaming of one site.  COHERENT_RHO: read
-// the density field through L2 only (ld.global.cg), for a density field written
-// earlier in the same kernel launch by other thread blocks.  STORE = false
+// Where a collide reads the densities of its force stencil and, moment-fed,
+// the moments m_0 .. m_D of its own site: the whole-box density field and
+// moment planes.  COHERENT: read the density field through L2 only
+// (ld.global.cg), for a field written earlier in the same launch by other
+// thread blocks.
+template <bool COHERENT> struct BoxSrc {
+    const float2 *rho;
+    const float *mom;
+    size_t N, site;
+    __device__ __forceinline__ float2 rho_at(const Nbr &nb, int dx, int dy, int dz) const
+    {
+        const float2 *rp = rho + nb.at(dx, dy, dz);
+        return COHERENT ? __ldcg(rp) : __ldg(rp);
+    }
+    __device__ __forceinline__ float mom_at(int plane) const { return __ldg(mom + (size_t)plane * N + site); }
+};
+
+// Stored words go out with a plain store, or with the streaming hint (evict
+// first: written once, not read again by this launch).
+template <bool CS, class T> __device__ __forceinline__ void put_word(T *p, T v)
+{
+    if constexpr (CS) __stcs(p, v);
+    else *p = v;
+}
+
+// Force + moment collision + noise + streaming of one site, reading the
+// density stencil (and, MOM, its own moments) from `src`.  STORE = false
 // computes without writing (an idle lane of a partial warp).  after_loads()
-// runs once the population loads are issued; returning false abandons the site.
+// runs once the population loads are issued; returning false abandons the
+// site.  before_stores() runs once every read of the site is done, just
+// before its first store.  CS: store with the streaming hint.  live = false
+// does what STORE = false does, decided at run time (every lane of a warp
+// then runs the same code).
+template <class L, class S, int PARITY, bool STORE, bool FULL, bool MOM, bool CS, class P, class Src, class Hook,
+          class Hook2>
+__device__ __forceinline__ void site_collide_src(const StepParams &p, const P &planes, const P &out, const Src &src,
+                                                 unsigned *__restrict__ status, const Nbr &nb, Hook &&after_loads,
+                                                 Hook2 &&before_stores, bool live = true);
+
 template <class L, class S, int PARITY, bool COHERENT_RHO, bool STORE = true, bool FULL = false, bool MOM = false,
           class P, class Hook = bool (*)()>
 __device__ __forceinline__ void site_collide(const StepParams &p, const P &planes, const P &out,
                                              const float2 *__restrict__ rho, unsigned *__restrict__ status,
                                              const Nbr &nb, Hook &&after_loads)
+{
+    const BoxSrc<COHERENT_RHO> src{rho, p.mom, (size_t)p.N, (size_t)nb.at(0, 0, 0)};
+    site_collide_src<L, S, PARITY, STORE, FULL, MOM, false>(p, planes, out, src, status, nb, after_loads, [] {});
+}
+
+template <class L, class S, int PARITY, bool STORE, bool FULL, bool MOM, bool CS, class P, class Src, class Hook,
+          class Hook2>
+__device__ __forceinline__ void site_collide_src(const StepParams &p, const P &planes, const P &out, const Src &src,
+                                                 unsigned *__restrict__ status, const Nbr &nb, Hook &&after_loads,
+                                                 Hook2 &&before_stores, bool live)
 {
     constexpr int Q = L::Q, D = L::D;
     static_assert(!MOM || FULL, "the moment-fed collide needs full relaxation");
@@ -209,7 +254,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
             constexpr int s = decltype(sc)::value;
             static_for<D + 1>([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
-                m[s][a] = __ldg(p.mom + (size_t)(s * (D + 1) + a) * (size_t)p.N + (size_t)site);
+                m[s][a] = src.mom_at(s * (D + 1) + a);
             });
         });
         if (!after_loads()) return;
@@ -236,27 +281,49 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
 
     // 2. Shan-Chen force from the other species' neighbour densities (Eq. FORCESTRUCTURE)
     float acc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-    static_for<Q - 1>([&](auto kc) {
-        constexpr int i = decltype(kc)::value + 1;
-        constexpr float wi = (float)L::wd(i);
-        const float2 *rp = rho + nb.at(L::cx(i), L::cy(i), L::cz(i));
-        const float2 rn = COHERENT_RHO ? __ldcg(rp) : __ldg(rp);
-        const float ra = rn.x, rb = rn.y;
+    if constexpr (FULL) {
+        // both species at once: lane lo sums c w rho_A (species B's force),
+        // lane hi c w rho_B (species A's), the same fused multiply-adds in the
+        // same order as the scalar form below
+        F2 ab[3] = {F2(0), F2(0), F2(0)};
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
+            constexpr float wi = (float)L::wd(i);
+            const float2 rn = src.rho_at(nb, L::cx(i), L::cy(i), L::cz(i));
+            const F2 r2(rn.x, rn.y);
+            static_for<D>([&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                constexpr int cd = comp<L>(i, d);
+                if constexpr (cd != 0) ab[d] = fma2(splat2((float)cd * wi), r2, ab[d]);
+            });
+        });
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
-            constexpr int cd = comp<L>(i, d);
-            if constexpr (cd != 0) {
-                constexpr float cw = (float)cd * wi;
-                acc[0][d] += cw * rb;
-                acc[1][d] += cw * ra;
-            }
+            acc[0][d] = ab[d].hi() * -p.G;
+            acc[1][d] = ab[d].lo() * -p.G;
         });
-    });
-    static_for<D>([&](auto dc) {
-        constexpr int d = decltype(dc)::value;
-        acc[0][d] *= -p.G;
-        acc[1][d] *= -p.G;
-    });
+    } else {
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
+            constexpr float wi = (float)L::wd(i);
+            const float2 rn = src.rho_at(nb, L::cx(i), L::cy(i), L::cz(i));
+            const float ra = rn.x, rb = rn.y;
+            static_for<D>([&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                constexpr int cd = comp<L>(i, d);
+                if constexpr (cd != 0) {
+                    constexpr float cw = (float)cd * wi;
+                    acc[0][d] += cw * rb;
+                    acc[1][d] += cw * ra;
+                }
+            });
+        });
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            acc[0][d] *= -p.G;
+            acc[1][d] *= -p.G;
+        });
+    }
 
     // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
     const float rt = rs[0] + rs[1];
@@ -266,7 +333,7 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
         constexpr int d = decltype(dc)::value;
         u[d] = (m[0][1 + d] + m[1][1 + d] + 0.5f * (rs[0] * acc[0][d] + rs[1] * acc[1][d])) * irt;
     });
-    if (STORE && (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt))) atomicOr(status, kStatusNonFinite);
+    if (STORE && live && (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt))) atomicOr(status, kStatusNonFinite);
 
     // 4. Gaussians scaled by the amplitudes of Eq. new-noise (local or reference
     // densities): sqrt(rho rho'/rho_t) for the shared momentum noise, sqrt(rho^s)
@@ -314,6 +381,59 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
     // the ghost modes (m^eq = Phi = 0) mu_a = cm m_a + cxi g_a.
     float X[Q];
     Closure<L>::eq(u, X);
+    if constexpr (FULL) {
+        // Full relaxation: mu_a = cxi g_a (+ rho (ceq X_a + cphi Y_a) on the
+        // transport modes) per species, then the back-projection, the weights
+        // and the mass balance of both species in packed pairs (lane lo A, hi B)
+        F2 mu2[Q];
+        float Y[2][Q];
+        Closure<L>::force(acc[0], v[0], Y[0]);
+        Closure<L>::force(acc[1], v[1], Y[1]);
+        mu2[0] = F2(m[0][0], m[1][0]);
+        static_for<D>([&](auto dc) {
+            constexpr int a = decltype(dc)::value + 1;
+            constexpr float invN = (float)(1.0 / L::Nd(a));
+            mu2[a] = F2(invN * m[0][a], invN * m[1][a]);
+        });
+        static_for<Q - D - 1>([&](auto kc) {
+            constexpr int a = decltype(kc)::value + D + 1;
+            float t0 = p.cxi[0][a] * g0[a], t1 = p.cxi[1][a] * g1[a];
+            if constexpr (a < Closure<L>::kGhost) {
+                t0 = fmaf(rs[0], fmaf(p.ceq[0][a], X[a], p.cphi[0][a] * Y[0][a]), t0);
+                t1 = fmaf(rs[1], fmaf(p.ceq[1][a], X[a], p.cphi[1][a] * Y[1][a]), t1);
+            }
+            mu2[a] = F2(t0, t1);
+        });
+        F2 y2[Q];
+        Transform<L>::backward(mu2, y2);
+        // Mass balance as in the scalar form below: the moving populations'
+        // words first, then the rest population takes m0 minus what they hold.
+        typename S::T word[2][Q];
+        F2 fo2[Q];
+        static_for<Q - 1>([&](auto kc) {
+            constexpr int i = decltype(kc)::value + 1;
+            const F2 wy = mul2(splat2((float)L::wd(i)), y2[i]); // __fmul_rn(w_i, y_i) per lane
+            word[0][i] = S::encode(wy.lo(), (float)L::wd(i) * p.rho0[0]);
+            word[1][i] = S::encode(wy.hi(), (float)L::wd(i) * p.rho0[1]);
+            fo2[i] = F2(S::decode(word[0][i], 0.0f), S::decode(word[1][i], 0.0f));
+        });
+        fo2[0] = F2(0);
+        const F2 rest = Transform<L>::rest_closing_mass(fo2, mu2[0]);
+        word[0][0] = S::encode(rest.lo(), (float)L::wd(0) * p.rho0[0]);
+        word[1][0] = S::encode(rest.hi(), (float)L::wd(0) * p.rho0[1]);
+        before_stores();
+        if (STORE && live) {
+            static_for<2>([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                static_for<Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    put_word<CS>(out.template plane<L>(s, write_slot<L, PARITY, i>()) + write_site<L, PARITY, i>(nb),
+                                 word[s][i]);
+                });
+            });
+        }
+        return;
+    }
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         float g[Q];
@@ -366,10 +486,14 @@ __device__ __forceinline__ void site_collide(const StepParams &p, const P &plane
             fo[i] = S::decode(word[i], base);
         });
         word[0] = S::encode(Transform<L>::rest_closing_mass(fo, m[s][0]), (float)L::wd(0) * p.rho0[s]);
-        static_for<Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            if (STORE) out.template plane<L>(s, write_slot<L, PARITY, i>())[write_site<L, PARITY, i>(nb)] = word[i];
-        });
+        if constexpr (s == 0) before_stores();
+        if (STORE && live) {
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                put_word<CS>(out.template plane<L>(s, write_slot<L, PARITY, i>()) + write_site<L, PARITY, i>(nb),
+                             word[i]);
+            });
+        }
     });
 }
 
@@ -580,6 +704,239 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
             }
             if (!__shfl_sync(0xffffffffu, alive ? 1 : 0, 0)) return; // a wait gave up: the host sees the status bit
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined step with two arrays: one persistent launch per step in which the
+// density pass of the force stencil reads each population once from HBM and
+// the collide writes each once, with nothing else of the step going to HBM.
+// The box is cut into slices along its outermost axis (z in 3D, y in 2D) and
+// each slice into warp tiles of 32 sites along x (T per slice).  Work items,
+// in order:
+//   prologue: D(k, t) for k = S-1, 0, 1, ..., L                 ((L+2) T items)
+//   main    : item (j, t) = D(j+L+1, t) if j+L+1 <= S-2, then C(j, t)  (S T items)
+// D(k, t) reads the populations of tile t of slice k (natural layout) and
+// stores the densities, and with MOM the moments m_0 .. m_D of both species,
+// into a ring of slice slots that stays in L2; C(j, t) collides tile t of slice
+// j from those slots (own moments, the density stencil of slices j-1 .. j+1)
+// and pushes f* into the other array.  Without MOM (some rate below 1) the
+// collide reads its own populations again, from L2 when the lag is short.
+// Slices 0 and S-1 keep slots 0 and 1 for the whole step (the periodic wrap
+// needs them at both ends); slice k of 1 .. S-2 uses slot 2 + (k-1) mod R.
+// Dependencies, counted per slice: C(j) needs every D tile of slices j-1, j,
+// j+1; D(k) reuses the slot of slice k-R and waits until every C tile of
+// slices k-R-1 .. k-R+1 (its readers) is done.  Warp w takes items w, w + W,
+// ...; all warps are resident (cooperative launch) and each wait is on items
+// of smaller index, so every wait ends; each is also bounded in time (the
+// warp sets a status bit and returns).  The per-site arithmetic is that of
+// the two-kernel step, so the update is the same.
+// ---------------------------------------------------------------------------
+struct PipeRing {
+    float2 *rho;       // slots x sp: (rho_A, rho_B) of the slice's sites
+    float *mom;        // slots x 2 (D + 1) planes x sp (MOM only)
+    unsigned *dcount;  // finished D tiles per unit (zero at launch)
+    unsigned *ccount;  // finished C tiles per unit (zero at launch)
+    int R;             // ring slots of slices 1 .. S-2
+    int sp;            // sites per slice
+    int slices, rows, tiles_per_slice, tiles_per_row, lag, prologue, total;
+    unsigned long long mul_T, mul_row, mul_R; // exact dividers by tiles_per_slice, tiles_per_row, R
+    unsigned shift_T, shift_row, shift_R;
+    unsigned target;            // tiles a unit needs before its readers run (tiles_per_row; one more tests timeouts)
+    unsigned long long wait_ns; // give-up time of one dependency wait
+};
+
+__device__ __forceinline__ int pipe_slot(const PipeRing &a, int k)
+{
+    if (k == 0) return 0;
+    if (k == a.slices - 1) return 1;
+    const unsigned q = (unsigned)(k - 1), d = (unsigned)(((unsigned long long)q * a.mul_R) >> a.shift_R);
+    return 2 + (int)(q - d * (unsigned)a.R);
+}
+
+__device__ __forceinline__ unsigned exact_div(unsigned n, unsigned long long mul, unsigned shift)
+{
+    return (unsigned)(((unsigned long long)n * mul) >> shift);
+}
+
+// item -> (D slice or -1, C slice or -1, tile)
+__device__ __forceinline__ void pipe_decode(const PipeRing &a, int item, int &dslice, int &cslice, unsigned &tile)
+{
+    const int Sl = a.slices;
+    if (item < a.prologue) {
+        const unsigned q = exact_div((unsigned)item, a.mul_T, a.shift_T);
+        tile = (unsigned)item - q * (unsigned)a.tiles_per_slice;
+        dslice = q == 0 ? Sl - 1 : (int)q - 1;
+        cslice = -1;
+    } else {
+        const unsigned r = (unsigned)(item - a.prologue);
+        const unsigned j = exact_div(r, a.mul_T, a.shift_T);
+        tile = r - j * (unsigned)a.tiles_per_slice;
+        cslice = (int)j;
+        dslice = (int)j + a.lag + 1 <= Sl - 2 ? (int)j + a.lag + 1 : -1;
+    }
+}
+
+// Counters are kept per unit: one row of tiles of a slice in 3D (slice k,
+// row y: unit k ny + y), one slice in 2D.  The units a tile of slice k, row y
+// depends on are those of slices k-1 .. k+1 and, in 3D, rows y-1 .. y+1
+// (periodic); lane q < 9 (3D) or < 3 (2D) watches unit q with acquire loads,
+// and the warp's later reads are ordered after them by the warp-wide vote.
+// On timeout: status bit, false for every lane.
+template <int D>
+__device__ __forceinline__ bool pipe_wait(const PipeRing &a, const unsigned *cnt, int k, int y, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    if (lane < (D == 3 ? 9 : 3)) {
+        const int dk = (D == 3 ? lane / 3 : lane) - 1, dy = D == 3 ? lane % 3 - 1 : 0;
+        const int kk = k + dk < 0 ? a.slices - 1 : (k + dk >= a.slices ? 0 : k + dk);
+        const int yy = y + dy < 0 ? a.rows - 1 : (y + dy >= a.rows ? 0 : y + dy);
+        const unsigned *c = cnt + (size_t)kk * a.rows + yy;
+        if (load_acquire(c) < a.target) {
+            const unsigned long long t0 = global_ns();
+            unsigned nap = 32;
+            while (load_acquire(c) < a.target) {
+                if (global_ns() - t0 > a.wait_ns) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(nap); // back off: a spinning warp takes issue slots from the working ones
+                nap = nap < 1024 ? 2 * nap : nap;
+            }
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        return false;
+    }
+    return true;
+}
+
+// Every lane's earlier memory accesses are ordered before the counts (one
+// per unit given, -1: none), which lane 0 adds.
+__device__ __forceinline__ void pipe_publish(unsigned *c0, long long u0, unsigned *c1, long long u1)
+{
+    fence_acq_rel();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        if (u0 >= 0) red_add_relaxed(c0 + u0, 1u);
+        if (u1 >= 0) red_add_relaxed(c1 + u1, 1u);
+    }
+}
+
+// The collide's view of the ring: density stencil from the slots of slices
+// j-1, j, j+1 (3D: by dz; 2D: by dy), own moments from slice j's slot.
+template <int D> struct RingSrc {
+    const float2 *rho[3];
+    const float *mom;
+    int sp, insite;
+    __device__ __forceinline__ float2 rho_at(const Nbr &nb, int dx, int dy, int dz) const
+    {
+        if constexpr (D == 3) return __ldcg(rho[dz + 1] + nb.ys[dy + 1] * nb.nx + nb.xs[dx + 1]);
+        else return __ldcg(rho[dy + 1] + nb.xs[dx + 1]);
+    }
+    __device__ __forceinline__ float mom_at(int plane) const { return __ldcg(mom + (size_t)plane * sp + insite); }
+};
+
+template <class L, class S, bool MOM>
+__global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4))
+    k_step_pipe(const StepParams p, const PlaneTable<typename S::T> in, const PlaneTable<typename S::T> out,
+                const PipeRing a, unsigned *__restrict__ status)
+{
+    constexpr int D = L::D, NM = 2 * (D + 1);
+    const int lane = threadIdx.x & 31;
+    const int W = (int)((gridDim.x * blockDim.x) >> 5);
+    const int Sl = a.slices;
+    int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int dslice = -1, cslice = -1;
+    unsigned tile = 0;
+    if (item < a.total) pipe_decode(a, item, dslice, cslice, tile);
+    for (; item < a.total; item += W) {
+        const unsigned row = exact_div(tile, a.mul_row, a.shift_row); // y of the tile (3D; 0 in 2D)
+        const int x = (int)(tile - row * (unsigned)a.tiles_per_row) * 32 + lane;
+        const bool active = x < p.nx;
+        const int insite = D == 3 ? (int)row * p.nx + x : x;
+        // the next item of this warp: its density tile is prefetched into L2 now
+        int ndslice = -1, ncslice = -1;
+        unsigned ntile = 0;
+        if (item + W < a.total) {
+            pipe_decode(a, item + W, ndslice, ncslice, ntile);
+            if (ndslice >= 0) {
+                const unsigned nrow = exact_div(ntile, a.mul_row, a.shift_row);
+                const int nx0 = (int)(ntile - nrow * (unsigned)a.tiles_per_row) * 32;
+                const size_t nsite = D == 3 ? (size_t)ndslice * a.sp + (size_t)nrow * p.nx + nx0
+                                            : (size_t)ndslice * p.nx + nx0;
+                // the slot planes are consecutive: plane q starts at in.ptr[0] + q N
+                for (int q = lane; q < 2 * L::Q; q += 32)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(in.ptr[0] + (size_t)q * p.N + nsite));
+            }
+        }
+        // unit counters of this item
+        const int yrow = D == 3 ? (int)row : 0;
+        const long long dunit = dslice >= 0 ? (long long)dslice * a.rows + yrow : -1;
+        const long long cunit = cslice >= 0 ? (long long)cslice * a.rows + yrow : -1;
+        // ---- D part: densities (and moments) of tile `tile` of slice dslice
+        if (dslice >= 0) {
+            // the slice that held this ring slot before (slices 0 and S-1 keep
+            // slots of their own)
+            const int prev = dslice - a.R;
+            if (dslice <= Sl - 2 && prev >= 1 && !pipe_wait<D>(a, a.ccount, prev, yrow, status)) return;
+            if (active) {
+                const int site = D == 3 ? dslice * a.sp + insite : dslice * p.nx + x;
+                const int slot = pipe_slot(a, dslice);
+                float r[2], mm[2][D + 1];
+                static_for<2>([&](auto sc) {
+                    constexpr int s = decltype(sc)::value;
+                    float d[L::Q], m[L::Q];
+                    static_for<L::Q>([&](auto ic) {
+                        constexpr int i = decltype(ic)::value;
+                        d[i] = S::decode(__ldcs(in.template plane<L>(s, i) + site), 0.0f);
+                    });
+                    // the same expressions as the density pass of the two-kernel step
+                    Transform<L>::forward(d, m);
+                    r[s] = p.rho0[s] + m[0];
+                    static_for<D + 1>([&](auto ac) {
+                        constexpr int q = decltype(ac)::value;
+                        mm[s][q] = m[q];
+                    });
+                });
+                a.rho[(size_t)slot * a.sp + insite] = make_float2(r[0], r[1]);
+                if constexpr (MOM) {
+                    static_for<NM>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        a.mom[((size_t)slot * NM + q) * a.sp + insite] = mm[q / (D + 1)][q % (D + 1)];
+                    });
+                }
+            }
+            if (cslice < 0) pipe_publish(a.dcount, dunit, a.ccount, -1);
+        }
+        // ---- C part: collide tile `tile` of slice cslice.  The counts of this
+        // item (its D tile, and its C tile for the slots' next users) are
+        // published once every ring read is done and before the population
+        // stores, so that the fence does not wait for those stores.
+        if (cslice >= 0) {
+            const int jm = cslice == 0 ? Sl - 1 : cslice - 1, jp = cslice == Sl - 1 ? 0 : cslice + 1;
+            if (!pipe_wait<D>(a, a.dcount, cslice, yrow, status)) return;
+            const int xc = active ? x : p.nx - 1; // idle lanes compute a real site without storing
+            const int y = D == 3 ? (int)row : cslice, z = D == 3 ? cslice : 0;
+            const Nbr nb = make_nbr(p, xc, y, z);
+            RingSrc<D> src;
+            const int sc = pipe_slot(a, cslice);
+            src.rho[0] = a.rho + (size_t)pipe_slot(a, jm) * a.sp;
+            src.rho[1] = a.rho + (size_t)sc * a.sp;
+            src.rho[2] = a.rho + (size_t)pipe_slot(a, jp) * a.sp;
+            src.mom = a.mom + (size_t)sc * NM * a.sp;
+            src.sp = a.sp;
+            src.insite = D == 3 ? (int)row * p.nx + xc : xc;
+            auto publish = [&] { pipe_publish(a.dcount, dunit, a.ccount, cunit); };
+            site_collide_src<L, S, kPush, true, MOM, MOM, true>(p, in, out, src, status, nb, [] { return true; },
+                                                               publish, active);
+        }
+        dslice = ndslice;
+        cslice = ncslice;
+        tile = ntile;
     }
 }
 
@@ -947,6 +1304,101 @@ cudaError_t Launch<L, S>::step_fused(int parity, const StepParams &p, void *pop,
     StepParams pc = p;
     void *args[] = {(void *)&pc, (void *)&ptr, (void *)&r2, (void *)&status, (void *)&a};
     const void *fn = parity == 0 ? (const void *)kern::k_step_fused<L, S, 0> : (const void *)kern::k_step_fused<L, S, 1>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, st);
+}
+
+// Resident blocks of the pipelined step on the current device (queried once
+// per instance).
+template <class L, class S> static cudaError_t pipe_blocks(bool mom, int *out)
+{
+    static int blocks[2] = {0, 0};
+    int &b = blocks[mom ? 1 : 0];
+    if (!b) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = mom ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern::k_step_pipe<L, S, true>, 128, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern::k_step_pipe<L, S, false>, 128, 0);
+        if (e != cudaSuccess) return e;
+        b = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::pipe_geometry(const StepParams &p, bool mom, int lag_opt, int *lag, int *ring_slots,
+                                        size_t *ring_floats, size_t *counters)
+{
+    int blocks = 0;
+    const cudaError_t e = pipe_blocks<L, S>(mom, &blocks);
+    if (e != cudaSuccess) return e;
+    const int S_ = L::D == 3 ? p.nz : p.ny;
+    const int tpr = (p.nx + 31) / 32;
+    const int T = L::D == 3 ? p.ny * tpr : tpr;
+    const int sp = L::D == 3 ? p.nx * p.ny : p.nx;
+    // rows of items in flight (one item per warp, W warps: a wave of W items
+    // spans `inflight` rows); the density work runs a whole wave and two rows
+    // ahead of the collisions (an item publishes its density tile only after
+    // its own collide part, and warps drift apart by a fraction of a wave),
+    // and a slot is reused only two waves after its last readers were due
+    const int inflight = (int)(((long long)blocks * 4 + T - 1) / T);
+    int l = 2 * inflight + 2, R = l + 3 + 2 * inflight;
+    if (lag_opt >= 1) { // any lag >= 1 (and ring of lag + 3 or more) is correct; a short one may wait more
+        l = lag_opt;
+        R = l + 6;
+    }
+    *lag = l;
+    *ring_slots = S_ >= 2 * (l + 2) + R ? R : 0; // 0: too few slices for the pipeline
+    *counters = 2 * (size_t)S_ * (L::D == 3 ? p.ny : 1);
+    *ring_floats = ((size_t)R + 2) * sp * (2 + (mom ? 2 * (L::D + 1) : 0));
+    return cudaSuccess;
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::step_pipe(const StepParams &p, const void *pop, void *pop_out, float *ring, unsigned *counters,
+                                    int ring_slots, int lag, bool mom, unsigned *status, double wait_ms, int stall,
+                                    cudaStream_t st)
+{
+    const int S_ = L::D == 3 ? p.nz : p.ny;
+    const int tpr = (p.nx + 31) / 32;
+    const int T = L::D == 3 ? p.ny * tpr : tpr;
+    const int sp = L::D == 3 ? p.nx * p.ny : p.nx;
+    int blocks = 0;
+    cudaError_t e = pipe_blocks<L, S>(mom, &blocks);
+    if (e != cudaSuccess) return e;
+    kern::PipeRing a;
+    a.R = ring_slots;
+    a.sp = sp;
+    a.slices = S_;
+    a.rows = L::D == 3 ? p.ny : 1;
+    a.tiles_per_slice = T;
+    a.tiles_per_row = tpr;
+    a.lag = lag;
+    a.prologue = (lag + 2) * T;
+    a.total = a.prologue + S_ * T;
+    exact_divider((unsigned)T, a.mul_T, a.shift_T);
+    exact_divider((unsigned)tpr, a.mul_row, a.shift_row);
+    exact_divider((unsigned)ring_slots, a.mul_R, a.shift_R);
+    a.target = (unsigned)tpr + (stall ? 1u : 0u);
+    a.wait_ns = (unsigned long long)(wait_ms * 1e6);
+    const size_t slots = (size_t)ring_slots + 2;
+    a.rho = reinterpret_cast<float2 *>(ring);
+    a.mom = ring + slots * sp * 2;
+    const size_t units = (size_t)S_ * a.rows;
+    a.dcount = counters;
+    a.ccount = counters + units;
+    e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * 2 * units, st);
+    if (e != cudaSuccess) return e;
+    int grid = blocks;
+    if ((long long)grid * 4 > a.total) grid = (a.total + 3) / 4;
+    const auto in = kern::plane_table(static_cast<typename S::T *>(const_cast<void *>(pop)), L::Q, p.N);
+    const auto out = kern::plane_table(static_cast<typename S::T *>(pop_out), L::Q, p.N);
+    StepParams pc = p;
+    unsigned *stat = status;
+    void *args[] = {(void *)&pc, (void *)&in, (void *)&out, (void *)&a, (void *)&stat};
+    const void *fn = mom ? (const void *)kern::k_step_pipe<L, S, true> : (const void *)kern::k_step_pipe<L, S, false>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, st);
 }
 

@@ -13,6 +13,13 @@ template <class L, class S> struct Launch {
                                unsigned *status, cudaStream_t st);
     static cudaError_t step_fused(int parity, const StepParams &p, void *pop, float *rho, unsigned *status,
                                   unsigned *counters, double wait_ms, int stall, int lag, cudaStream_t st);
+    // pipelined two-array step: lag and ring slots for this box (ring_slots = 0:
+    // too few slices), and the ring's size in floats
+    static cudaError_t pipe_geometry(const StepParams &p, bool mom, int lag_opt, int *lag, int *ring_slots,
+                                     size_t *ring_floats, size_t *counters);
+    static cudaError_t step_pipe(const StepParams &p, const void *pop, void *pop_out, float *ring, unsigned *counters,
+                                 int ring_slots, int lag, bool mom, unsigned *status, double wait_ms, int stall,
+                                 cudaStream_t st);
     static cudaError_t batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,
                                   float *rho, unsigned *status, const unsigned *step_base, unsigned k, bool full,
                                   cudaStream_t st);

@@ -7,7 +7,7 @@
 // needs besides the caller's populations -- the density field and the status
 // word -- lives in one file-scope __device__ array of fixed size, which every
 // GPU that loads this library holds until the process exits.
-#include <mutex>
+#include <cstdint>
 
 #include "flbm_internal.h"
 
@@ -19,24 +19,10 @@ constexpr size_t kScratchBytes = kStatusBytes + (size_t)kNoAllocMaxSites * 2 * s
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {}; // device address of g_noalloc_scratch, per device
-
 // The array's name in host code is only a host-side stand-in; its device
-// address is looked up once per device, with that device current.
-cudaError_t scratch_address(int dev, void **addr)
-{
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *addr = g_scratch_addr[dev];
-    return cudaSuccess;
-}
+// address is looked up on every call, with the calling device current, so a
+// device reset between calls (which gives the array a new address) is harmless.
+cudaError_t scratch_address(void **addr) { return cudaGetSymbolAddress(addr, g_noalloc_scratch); }
 
 flbm_status cuda_error(cudaError_t e) { return e == cudaSuccess ? FLBM_OK : FLBM_ECUDA; }
 
@@ -48,13 +34,12 @@ extern "C" flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int par
     using namespace flbm;
     CtxView v;
     if (!ctx_view(ctx, &v) || !pop || (parity != 0 && parity != 1) || step < 0 || n < 0) return FLBM_EINVAL;
+    if (v.batch) return FLBM_EINVAL;                 // one box per call: a batch steps through flbm_step
+    if (reinterpret_cast<uintptr_t>(pop) & 255u) return FLBM_EINVAL; // rejected here, not left to fault on the device
     if (v.N > kNoAllocMaxSites) return FLBM_EINVAL; // the box exceeds the static scratch (2^21 sites)
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_error(e);
-    if (dev < 0 || dev >= kMaxDevices) return FLBM_EUNSUPPORTED;
     void *base = nullptr;
-    if ((e = scratch_address(dev, &base)) != cudaSuccess) return cuda_error(e);
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) return cuda_error(e);
     unsigned *status = static_cast<unsigned *>(base);
     float *rho = reinterpret_cast<float *>(static_cast<unsigned char *>(base) + kStatusBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -1,11 +1,12 @@
 // flbm_tune.cu -- flbm_autotune: time candidate launch settings on a context's
 // own state, keep the fastest, and remember the choice in a JSON file.
 //
-// Every candidate computes bitwise the same update (the two-kernel and slab
-// overlap schedules run the same per-site arithmetic; the thread-block shape
-// and the CUDA-graph length only change how the same kernels are launched), so
-// tuning changes speed, never results.  The fused schedule, which agrees only
-// to rounding, is not a candidate.
+// Every candidate computes bitwise the same update (the two-kernel, slab
+// overlap and, with two arrays, pipelined schedules run the same per-site
+// arithmetic; the thread-block shape and the CUDA-graph length only change
+// how the same kernels are launched), so tuning changes speed, never results.
+// The in-place fused schedule, which agrees only to rounding, is not a
+// candidate.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -175,7 +176,8 @@ const std::pair<const char *, int> kKeys[] = {{"schedule", FLBM_OPT_SCHEDULE},
                                               {"slabs", FLBM_OPT_SLABS},
                                               {"block_x", FLBM_OPT_BLOCK_X},
                                               {"block_y", FLBM_OPT_BLOCK_Y},
-                                              {"graph_steps", FLBM_OPT_GRAPH_STEPS}};
+                                              {"graph_steps", FLBM_OPT_GRAPH_STEPS},
+                                              {"pipe_lag", FLBM_OPT_PIPE_LAG}};
 
 // apply settings through flbm_set_option (validated like a caller's); the
 // block shape goes through a narrow first shape so that x * y never exceeds
@@ -279,6 +281,11 @@ std::vector<Settings> candidates(const flbm_ctx *c)
                 out.push_back({{"schedule", (double)FLBM_SCHEDULE_OVERLAP}, {"graph_steps", 0.0},
                                {"slabs", (double)k}, {"block_x", (double)b[0]}, {"block_y", (double)b[1]}});
     }
+    // with two arrays the fused schedule is the pipelined step (one launch a
+    // step, bitwise the two-kernel update; boxes with too few slices for it
+    // run the two-kernel step)
+    if (c->streaming == FLBM_STREAM_TWO_ARRAYS)
+        out.push_back({{"schedule", (double)FLBM_SCHEDULE_FUSED}, {"graph_steps", 0.0}, {"pipe_lag", 0.0}});
     return out;
 }
 

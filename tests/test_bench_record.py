@@ -1,7 +1,8 @@
 """bench.py's use of the committed ncu record: the DRAM traffic and the
-executed instruction count of the collide are reported only while the kernel
-sources match the digest they were captured on, scaled by the site count, and
-documentation edits do not invalidate them (CPU only)."""
+executed instruction count of a step are reported only while the kernel
+sources match the digest they were captured on (and the schedule matches),
+scaled by the site count, and documentation edits do not invalidate them
+(CPU only)."""
 import json
 import os
 import sys
@@ -17,10 +18,11 @@ def test_committed_record_matches_the_current_kernel_sources():
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         rec = json.load(f)["d3q19-256"]
     assert rec["sources_sha256"] == bench.sources_digest()
-    cap = bench.recorded_capture("d3q19-256", 256 ** 3)
+    cap = bench.recorded_capture("d3q19-256", 256 ** 3, rec["schedule"])
     scale = 256 ** 3 / rec["sites"]
-    assert cap["traffic"] == rec["dram_bytes_per_launch"] * scale
-    assert cap["inst"] == rec["warp_instructions_per_launch"] * scale
+    assert cap["traffic"] == rec["dram_bytes_per_step"] * scale
+    assert cap["inst"] == rec["warp_instructions_per_step"] * scale
+    assert bench.recorded_capture("d3q19-256", 256 ** 3, "some other schedule") is None
 
 
 def test_record_is_ignored_for_other_sources(tmp_path, monkeypatch):

@@ -77,6 +77,20 @@ def batch_means(x, nbatch=20):
     return b.mean(axis=0), b.std(axis=0, ddof=1) / np.sqrt(nbatch)
 
 
+def family_sigma(ncomp, nbatch=20, level=0.0027):
+    """Multiplier of the batch-means standard error for ``ncomp`` simultaneous
+    comparisons held to the false-alarm rate of one 3-standard-error check
+    (level 0.27 %, two-sided) as a family: each comparison gets the Sidak
+    share 1 - (1 - level)^(1/ncomp), and since the standard error is itself
+    estimated from ``nbatch`` batch means, (mean - prediction)/SE follows
+    Student's t with nbatch - 1 degrees of freedom.  One comparison with 20
+    batches gives 3.45; twenty give 4.76."""
+    from scipy import stats
+
+    p = 1.0 - (1.0 - level) ** (1.0 / ncomp)
+    return float(stats.t.ppf(1.0 - p / 2.0, nbatch - 1))
+
+
 def lattice_linear_sk(c, w, T, N, k_vec, G, rho=(1.0, 1.0), lam=(1.0, 1.0), lam_d=1.0,
                       kT=1e-5, sdf=True):
     """Exact stationary structure factors of the *linearised lattice* update at
