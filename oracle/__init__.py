@@ -34,6 +34,7 @@ OPT_RHO0_A = 4
 OPT_RHO0_B = 5
 OPT_NOISE_RHO = 7
 OPT_FORCE_VELOCITY = 8
+OPT_GHOST_NOISE = 21
 OPT_LAMBDA_MODE = 1000  # + 100 * species + mode
 
 
@@ -319,7 +320,7 @@ class Oracle:
         if isinstance(key, str):
             key = {"lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF, "rho0_a": OPT_RHO0_A,
                    "rho0_b": OPT_RHO0_B, "noise_rho": OPT_NOISE_RHO,
-                   "force_velocity": OPT_FORCE_VELOCITY}[key]
+                   "force_velocity": OPT_FORCE_VELOCITY, "ghost_noise": OPT_GHOST_NOISE}[key]
         if lib().orc_set_option(self._h, int(key), float(value)) != 0:
             raise ValueError(f"bad oracle option {key}")
 

@@ -58,6 +58,7 @@
 #define ORC_OPT_RHO0_B 5
 #define ORC_OPT_NOISE_RHO 7
 #define ORC_OPT_FORCE_VELOCITY 8
+#define ORC_OPT_GHOST_NOISE 21
 #define ORC_OPT_LAMBDA_MODE 1000 /* + 100*species + a */
 
 typedef struct {
@@ -80,6 +81,8 @@ typedef struct {
     int sdf;
     int noise_ref;          /* 0: local densities in the noise, 1: reference rho0 */
     int force_velocity;     /* 0: rho v = jbar + R_j/2 ; 1: v = vbar + a/2 */
+    int ghost_noise;        /* 1: non-conserved noise from population-space draws at the
+                               destination densities (see collide_site) */
     double rho0[2];
     double *f[2];   /* f[s][i*N + site] */
     double *fn[2];  /* push-streaming target */
@@ -454,6 +457,8 @@ int orc_set_option(orc_t *o, int key, double value)
         o->noise_ref = value != 0.0;
     } else if (key == ORC_OPT_FORCE_VELOCITY) {
         o->force_velocity = value != 0.0;
+    } else if (key == ORC_OPT_GHOST_NOISE) {
+        o->ghost_noise = value != 0.0;
     } else if (key >= ORC_OPT_LAMBDA_MODE && key < ORC_OPT_LAMBDA_MODE + 200) {
         int s = (key - ORC_OPT_LAMBDA_MODE) / 100, a = (key - ORC_OPT_LAMBDA_MODE) % 100;
         if (a <= o->L.D || a >= o->L.Q) return 1;
@@ -591,13 +596,43 @@ static int collide_site(const orc_t *o, long site, double R[2][ORC_MAXQ])
             xi[1][1 + d] = -xi[0][1 + d];
         }
     }
-    for (int s = 0; s < 2; s++)
-        for (int a = D + 1; a < Q; a++) {
-            double lam = o->lam[s][a];
-            double var = (2.0 * lam - lam * lam) * L->N[a] * mu * nr[s];
-            double g = orc_gaussian(o->seed, rng_site(o, site), (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
-            xi[s][a] = sqrt(var) * g;
+    if (!o->ghost_noise) {
+        for (int s = 0; s < 2; s++)
+            for (int a = D + 1; a < Q; a++) {
+                double lam = o->lam[s][a];
+                double var = (2.0 * lam - lam * lam) * L->N[a] * mu * nr[s];
+                double g = orc_gaussian(o->seed, rng_site(o, site), (uint32_t)o->step, (uint32_t)s, (uint32_t)a);
+                xi[s][a] = sqrt(var) * g;
+            }
+    } else {
+        /* Off-diagonal noise of the non-conserved modes (the correction the
+         * paper describes after Eq. finalstep, Sec. V B, and leaves open in
+         * Sec. VII; reading in the design notes): population i of species s
+         * leaves r for r + c_i, where local equilibrium gives it the variance
+         * mu w_i rho^s(r + c_i).  One Gaussian eta_i per population, scaled so,
+         * projected on the non-conserved rows, with the factor
+         * (2 lambdabar_a - lambdabar_a^2)^(1/2) of Eq. new-noise:
+         *   xi_a = sqrt(2 lb_a - lb_a^2) sum_i T_ai sqrt(mu w_i rho^s(r + c_i)) eta_i,
+         * covariance (for equal rates) (2 lb - lb^2) mu sum_i T_ai T_bi w_i rho^s(r + c_i),
+         * which is Eq. new-noise (diagonal, N_a mu rho) wherever rho^s is
+         * uniform.  eta_i is Gaussian number i of species slot s + 2 (the
+         * slots of the mode draws are 0 and 1). */
+        for (int s = 0; s < 2; s++) {
+            double x[ORC_MAXQ];
+            for (int i = 0; i < Q; i++) {
+                const double ri = o->noise_ref ? o->rho0[s] : o->rho[s][neighbour(o, site, L->c[i])];
+                if (!(ri > 0.0) || !isfinite(ri)) return 1;
+                const double eta = orc_gaussian(o->seed, rng_site(o, site), (uint32_t)o->step, (uint32_t)(s + 2),
+                                                (uint32_t)(i + 1));
+                x[i] = sqrt(mu * L->w[i] * ri) * eta;
+            }
+            for (int a = D + 1; a < Q; a++) {
+                double lam = o->lam[s][a], t = 0.0;
+                for (int i = 0; i < Q; i++) t += L->T[a][i] * x[i];
+                xi[s][a] = sqrt(2.0 * lam - lam * lam) * t;
+            }
         }
+    }
     /* momentum modes: R_alpha (Eq. finalstep, m^eq_alpha = rho u_alpha, Phi_alpha = rho a_alpha) */
     double meq[2][ORC_MAXQ], phi[2][ORC_MAXQ], v[2][3];
     for (int s = 0; s < 2; s++) {

@@ -80,6 +80,11 @@ StepParams make_params(const flbm_ctx *c)
             p.cphi[s][a] = (float)((1.0 - 0.5 * lb) / Na);
             p.cxi[s][a] = (float)(std::sqrt((2.0 * lb - lb * lb) * Na * mu) / Na);
         }
+    for (int a = 0; a < kMaxQ; a++) {
+        p.pair_eq[a] = make_float2(p.ceq[0][a], p.ceq[1][a]);
+        p.pair_phi[a] = make_float2(p.cphi[0][a], p.cphi[1][a]);
+        p.pair_xi[a] = make_float2(p.cxi[0][a], p.cxi[1][a]);
+    }
     p.noise_amp_j = c->sdf ? (float)std::sqrt((2.0 * lb_d - lb_d * lb_d) * c->kT) : 0.0f;
     p.rho0[0] = (float)c->rho0[0];
     p.rho0[1] = (float)c->rho0[1];

@@ -29,6 +29,9 @@ struct StepParams {
     float ceq[2][kMaxQ];       // lambdabar_a / N_a
     float cphi[2][kMaxQ];      // (1 - lambdabar_a / 2) / N_a
     float cxi[2][kMaxQ];       // sqrt((2 lb_a - lb_a^2) N_a kT / c_s^2) / N_a  (Eq. new-noise)
+    float2 pair_eq[kMaxQ];     // (ceq[0][a], ceq[1][a]): the same constants species by species in
+    float2 pair_phi[kMaxQ];    // adjacent pairs, for the collide's packed (two-species) arithmetic
+    float2 pair_xi[kMaxQ];
     float noise_amp_j;         // sqrt((2 lb_d - lb_d^2) kT); times sqrt(rho rho'/rho_t); 0 = no-sdf
     float rho0[2];             // reference densities: 16-bit deviation base, noise reference
     int noise_ref;             // 1: noise amplitudes from rho0 instead of the local densities

@@ -210,6 +210,44 @@ template <bool CS, class T> __device__ __forceinline__ void put_word(T *p, T v)
     else *p = v;
 }
 
+// The end of a full-relaxation collision for both species at once (packed
+// pairs, lane lo A, hi B): y_i = sum_a T_ai mu_a, the stored words of the
+// moving populations (w_i y_i, rounded by the storage format), the rest
+// population closing each species' mass on what those words hold (so the
+// rounding of their stores cannot leak mass), then the stores.
+template <class L, class S, int PARITY, bool STORE, bool CS, class P, class Hook2>
+__device__ __forceinline__ void full_relaxation_stores(const StepParams &p, const P &out, const Nbr &nb,
+                                                       const F2 (&mu2)[L::Q], Hook2 &&before_stores, bool live)
+{
+    constexpr int Q = L::Q;
+    F2 y2[Q];
+    Transform<L>::backward(mu2, y2);
+    typename S::T word[2][Q];
+    F2 fo2[Q];
+    static_for<Q - 1>([&](auto kc) {
+        constexpr int i = decltype(kc)::value + 1;
+        const F2 wy = mul2(splat2((float)L::wd(i)), y2[i]); // __fmul_rn(w_i, y_i) per lane
+        word[0][i] = S::encode(wy.lo(), (float)L::wd(i) * p.rho0[0]);
+        word[1][i] = S::encode(wy.hi(), (float)L::wd(i) * p.rho0[1]);
+        fo2[i] = F2(S::decode(word[0][i], 0.0f), S::decode(word[1][i], 0.0f));
+    });
+    fo2[0] = F2(0);
+    const F2 rest = Transform<L>::rest_closing_mass(fo2, mu2[0]);
+    word[0][0] = S::encode(rest.lo(), (float)L::wd(0) * p.rho0[0]);
+    word[1][0] = S::encode(rest.hi(), (float)L::wd(0) * p.rho0[1]);
+    before_stores();
+    if (STORE && live) {
+        static_for<2>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                put_word<CS>(out.template plane<L>(s, write_slot<L, PARITY, i>()) + write_site<L, PARITY, i>(nb),
+                             word[s][i]);
+            });
+        });
+    }
+}
+
 // Force + moment collision + noise + streaming of one site, reading the
 // density stencil (and, MOM, its own moments) from `src`.  STORE = false
 // computes without writing (an idle lane of a partial warp).  after_loads()
@@ -360,6 +398,45 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
         draw_gaussians<L, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g1);
     }
 
+    float X[Q];
+    Closure<L>::eq(u, X);
+    if constexpr (FULL) {
+        // 5'. Full relaxation: the momentum modes and the forcing moments of both
+        // species in packed pairs (lane lo A, hi B), the same update as steps 5-6
+        // below: R = lambdabar_d (rho u - j) + (1 - lambdabar_d/2) rho a + xi,
+        // rho v = j + R/2 (or v = j/rho + a/2), j* = j + R.
+        const F2 rs2(rs[0], rs[1]);
+        const F2 irs2(__frcp_rn(rs[0]), __frcp_rn(rs[1]));
+        const F2 lrs2 = mul2(splat2(p.lam_d), rs2), hrs2 = mul2(splat2(p.hlam_d), rs2);
+        const F2 nlam = splat2(-p.lam_d), half = splat2(0.5f);
+        F2 acc2[3], v2[3], mu2[Q];
+        static_for<D>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int a = 1 + d;
+            constexpr float invN = (float)(1.0 / L::Nd(a));
+            acc2[d] = F2(acc[0][d], acc[1][d]);
+            const F2 m2(m[0][a], m[1][a]);
+            const F2 R2 = fma2(lrs2, splat2(u[d]), fma2(nlam, m2, fma2(hrs2, acc2[d], F2(g0[a], -g0[a]))));
+            if (p.force_velocity) v2[d] = fma2(m2, irs2, mul2(half, acc2[d]));
+            else v2[d] = mul2(fma2(half, R2, m2), irs2);
+            mu2[a] = mul2(splat2(invN), m2 + R2);
+        });
+        // 6'. mu_a = cxi g_a (+ rho (ceq X_a + cphi Y_a) on the transport modes);
+        // then the back-projection, the weights and the mass balance
+        F2 Y2[Q];
+        ClosurePair<L>::force(acc2, v2, Y2);
+        mu2[0] = F2(m[0][0], m[1][0]);
+        static_for<Q - D - 1>([&](auto kc) {
+            constexpr int a = decltype(kc)::value + D + 1;
+            F2 t = mul2(pair2(p.pair_xi[a]), F2(g0[a], g1[a]));
+            if constexpr (a < Closure<L>::kGhost)
+                t = fma2(rs2, fma2(pair2(p.pair_eq[a]), splat2(X[a]), mul2(pair2(p.pair_phi[a]), Y2[a])), t);
+            mu2[a] = t;
+        });
+        full_relaxation_stores<L, S, PARITY, STORE, CS>(p, out, nb, mu2, before_stores, live);
+        return;
+    }
+
     // 5. momentum modes: common rate, opposite noise; species velocity for Phi
     float v[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
     static_for<2>([&](auto sc) {
@@ -379,61 +456,6 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
     // mu_a = m*_a / N_a: m*_a = m_a + lambdabar_a (m^eq_a - m_a) + (1 - lambdabar_a/2)
     // Phi_a + xi_a, i.e. mu_a = cm m_a + rho (ceq X_a + cphi Y_a) + cxi g_a, and for
     // the ghost modes (m^eq = Phi = 0) mu_a = cm m_a + cxi g_a.
-    float X[Q];
-    Closure<L>::eq(u, X);
-    if constexpr (FULL) {
-        // Full relaxation: mu_a = cxi g_a (+ rho (ceq X_a + cphi Y_a) on the
-        // transport modes) per species, then the back-projection, the weights
-        // and the mass balance of both species in packed pairs (lane lo A, hi B)
-        F2 mu2[Q];
-        float Y[2][Q];
-        Closure<L>::force(acc[0], v[0], Y[0]);
-        Closure<L>::force(acc[1], v[1], Y[1]);
-        mu2[0] = F2(m[0][0], m[1][0]);
-        static_for<D>([&](auto dc) {
-            constexpr int a = decltype(dc)::value + 1;
-            constexpr float invN = (float)(1.0 / L::Nd(a));
-            mu2[a] = F2(invN * m[0][a], invN * m[1][a]);
-        });
-        static_for<Q - D - 1>([&](auto kc) {
-            constexpr int a = decltype(kc)::value + D + 1;
-            float t0 = p.cxi[0][a] * g0[a], t1 = p.cxi[1][a] * g1[a];
-            if constexpr (a < Closure<L>::kGhost) {
-                t0 = fmaf(rs[0], fmaf(p.ceq[0][a], X[a], p.cphi[0][a] * Y[0][a]), t0);
-                t1 = fmaf(rs[1], fmaf(p.ceq[1][a], X[a], p.cphi[1][a] * Y[1][a]), t1);
-            }
-            mu2[a] = F2(t0, t1);
-        });
-        F2 y2[Q];
-        Transform<L>::backward(mu2, y2);
-        // Mass balance as in the scalar form below: the moving populations'
-        // words first, then the rest population takes m0 minus what they hold.
-        typename S::T word[2][Q];
-        F2 fo2[Q];
-        static_for<Q - 1>([&](auto kc) {
-            constexpr int i = decltype(kc)::value + 1;
-            const F2 wy = mul2(splat2((float)L::wd(i)), y2[i]); // __fmul_rn(w_i, y_i) per lane
-            word[0][i] = S::encode(wy.lo(), (float)L::wd(i) * p.rho0[0]);
-            word[1][i] = S::encode(wy.hi(), (float)L::wd(i) * p.rho0[1]);
-            fo2[i] = F2(S::decode(word[0][i], 0.0f), S::decode(word[1][i], 0.0f));
-        });
-        fo2[0] = F2(0);
-        const F2 rest = Transform<L>::rest_closing_mass(fo2, mu2[0]);
-        word[0][0] = S::encode(rest.lo(), (float)L::wd(0) * p.rho0[0]);
-        word[1][0] = S::encode(rest.hi(), (float)L::wd(0) * p.rho0[1]);
-        before_stores();
-        if (STORE && live) {
-            static_for<2>([&](auto sc) {
-                constexpr int s = decltype(sc)::value;
-                static_for<Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    put_word<CS>(out.template plane<L>(s, write_slot<L, PARITY, i>()) + write_site<L, PARITY, i>(nb),
-                                 word[s][i]);
-                });
-            });
-        }
-        return;
-    }
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         float g[Q];

@@ -11,6 +11,8 @@
 #pragma once
 #include <utility>
 
+#include "flbm_pair.cuh"
+
 namespace flbm {
 
 // Compile-time loop: f(std::integral_constant<int, I>{}) for I = 0 .. N-1, so
@@ -212,6 +214,37 @@ template <> struct Closure<D3Q19> {
         Y[7] = a[0] * v[1] + a[1] * v[0];
         Y[8] = a[1] * v[2] + a[2] * v[1];
         Y[9] = a[0] * v[2] + a[2] * v[0];
+    }
+};
+
+// The forcing moments of Closure<L>::force for both species at once (packed
+// pairs, lane lo species A, hi species B; flbm_pair.cuh supplies F2).
+template <class L> struct ClosurePair;
+
+template <> struct ClosurePair<D2Q9> {
+    template <class F>
+    __device__ __forceinline__ static void force(const F *a, const F *v, F *Y)
+    {
+        const F axvx = mul2(a[0], v[0]), ayvy = mul2(a[1], v[1]);
+        Y[3] = mul2(splat2(6.0f), axvx + ayvy);
+        Y[4] = mul2(splat2(2.0f), axvx - ayvy);
+        Y[5] = fma2(a[0], v[1], mul2(a[1], v[0]));
+    }
+};
+
+template <> struct ClosurePair<D3Q19> {
+    template <class F>
+    __device__ __forceinline__ static void force(const F *a, const F *v, F *Y)
+    {
+        const F two = splat2(2.0f);
+        const F pxx = mul2(mul2(two, a[0]), v[0]), pyy = mul2(mul2(two, a[1]), v[1]), pzz = mul2(mul2(two, a[2]), v[2]);
+        const F pyz = pyy + pzz;
+        Y[4] = pxx + pyz;
+        Y[5] = mul2(two, pxx) - pyz;
+        Y[6] = pyy - pzz;
+        Y[7] = fma2(a[0], v[1], mul2(a[1], v[0]));
+        Y[8] = fma2(a[1], v[2], mul2(a[2], v[1]));
+        Y[9] = fma2(a[0], v[2], mul2(a[2], v[0]));
     }
 };
 

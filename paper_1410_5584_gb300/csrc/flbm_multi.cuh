@@ -120,9 +120,10 @@ __device__ __forceinline__ void block_gaussians(uint32_t site, uint32_t step, ui
                                                 uint32_t k1, float (&g)[6])
 {
     const uint4 x = philox4x32_10(make_uint4(site, step, s, b), k0, k1);
-    if constexpr ((MASK & 3) != 0) box_muller(x.x, x.y, 1.0f, g[0], g[1]);
-    if constexpr ((MASK & 12) != 0) box_muller(x.z, x.w, 1.0f, g[2], g[3]);
-    if constexpr ((MASK & 48) != 0) box_muller(low_bits_word(x.x, x.y), low_bits_word(x.z, x.w), 1.0f, g[4], g[5]);
+    if constexpr ((MASK & 3) != 0) box_muller(uniform_hi(x.x), uniform_hi_signed(x.y), 1.0f, g[0], g[1]);
+    if constexpr ((MASK & 12) != 0) box_muller(uniform_hi(x.z), uniform_hi_signed(x.w), 1.0f, g[2], g[3]);
+    if constexpr ((MASK & 48) != 0)
+        box_muller(uniform_lo(x.x, x.y), uniform_lo_signed(x.z, x.w), 1.0f, g[4], g[5]);
 }
 
 // Positions of block b that hold a non-conserved mode (D < a < Q).

@@ -51,50 +51,54 @@ __device__ __forceinline__ void sincos_hw(float x, float &s, float &c)
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
-// -2 ln u1 for u1 in (0, 1].  For u1 <= 31/32 the hardware log2 (absolute error
-// <= 2^-22 on [1/2, 2], 2 ulp below) is accurate to ~5e-6 relative since
-// |ln u1| >= 0.0317; nearer 1, where an absolute error would swamp the small
-// radius, the Mercator series -2 ln(1 - v) = 2 (v + v^2/2 + ... + v^5/5) with
-// v = 1 - u1 <= 1/32 (exact by Sterbenz's lemma) is used, truncation error
-// below 1e-8 relative.
+// -2 ln u1 for u1 in (0, 1].  Away from 1 the hardware log2 is used: its
+// absolute error (about 2^-22) puts an error of at most 3.3e-7 on -2 ln u1, so
+// at most 1.3e-6 on the radius r = sqrt(-2 ln u1) >= 0.125 there.  For
+// u1 > 1 - 2^-7, where that absolute error would swamp the small radius, the
+// Mercator series -2 ln(1 - v) = 2 v + v^2 + (2/3) v^3 + ..., v = 1 - u1 (exact
+// by Sterbenz's lemma), is cut after two terms: v (2 + v) leaves out at most
+// (2/3) v^3 <= 3.2e-7, again at most 1.3e-6 on r.  Either way a Gaussian is
+// within about 1.3e-6 of its exact value.
 __device__ __forceinline__ float minus_two_log_unit_interval(float u1)
 {
     const float v = 1.0f - u1;
-    float ps = fmaf(v, 0.4f, 0.5f);
-    ps = fmaf(v, ps, 0.666666667f);
-    ps = fmaf(v, ps, 1.0f);
-    ps = fmaf(v, ps, 2.0f);
-    const float near1 = v * ps;
+    const float near1 = v * (2.0f + v);
     const float far = lg2_hw(u1) * -1.38629436111989061883f; // -2 ln 2
-    return u1 > 0.96875f ? near1 : far;
+    return v < 0x1.0p-7f ? near1 : far;
 }
 
-// Box-Muller on one pair of 21-bit uniforms held in the top bits of two words,
-// scaled: g0 = scale r cos(2 pi u2), g1 = scale r sin(2 pi u2),
-// r = sqrt(-2 ln u1), with u1 = ((a >> 11) + 1) 2^-21 in (0, 1] and
-// u2 = (b >> 11) 2^-21 in [0, 1), both exact in float.  The angle is taken in
-// [-pi, pi), where the hardware sine and cosine have an absolute error of about
-// 2^-21: reading b as signed and shifting arithmetically gives u2 for u2 < 1/2
-// and u2 - 1 above (the same sine and cosine).
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float scale, float &g0, float &g1)
+// Box-Muller on one pair of 21-bit uniforms, scaled: g0 = scale r cos(2 pi u2),
+// g1 = scale r sin(2 pi u2), r = sqrt(-2 ln u1), with u1 = (U1 + 1) 2^-21 in
+// (0, 1] and u2 = U2 2^-21 in [0, 1), both exact in float.  T2 is U2 read as a
+// signed 21-bit number (U2 for U2 < 2^20, U2 - 2^21 above), so that the angle
+// is taken in [-pi, pi), where the hardware sine and cosine have an absolute
+// error of about 2^-21; the two readings give the same sine and cosine.
+__device__ __forceinline__ void box_muller(uint32_t U1, int32_t T2, float scale, float &g0, float &g1)
 {
-    const float u1 = fmaf((float)(a >> 11), 0x1.0p-21f, 0x1.0p-21f); // ((a >> 11) + 1) 2^-21, exact
+    const float u1 = fmaf((float)U1, 0x1.0p-21f, 0x1.0p-21f); // (U1 + 1) 2^-21, exact
     const float r = scale * sqrt_hw(minus_two_log_unit_interval(u1)); // u1 = 1 gives r = 0
-    // 2 pi t with t = (signed b >> 11) 2^-21: one rounding, as 2 pi 2^-21 is the
-    // float 2 pi times a power of two
-    const float ang = (float)((int32_t)b >> 11) * (6.28318530717958647692f * 0x1.0p-21f);
+    // 2 pi T2 2^-21: one rounding, as 2 pi 2^-21 is the float 2 pi times a power of two
+    const float ang = (float)T2 * (6.28318530717958647692f * 0x1.0p-21f);
     float s, c;
     sincos_hw(ang, s, c);
     g0 = r * c;
     g1 = r * s;
 }
 
-// The fifth and sixth uniforms of a Philox block, packed from the low bits of
-// its words into the top 21 bits of one word, as box_muller reads them:
-// ((hi mod 2^11) 2^10 + (lo mod 2^10)) 2^11.
-__device__ __forceinline__ uint32_t low_bits_word(uint32_t hi, uint32_t lo)
+// The six 21-bit uniforms of a Philox block x0 .. x3: U_k = x_k >> 11 for
+// k = 0 .. 3, U4 = (x0 mod 2^11) 2^10 + (x1 mod 2^10) and
+// U5 = (x2 mod 2^11) 2^10 + (x3 mod 2^10).  The angle uniforms (U1, U3, U5)
+// are taken signed (see box_muller).
+__device__ __forceinline__ uint32_t uniform_hi(uint32_t x) { return x >> 11; }
+__device__ __forceinline__ int32_t uniform_hi_signed(uint32_t x) { return (int32_t)x >> 11; }
+__device__ __forceinline__ uint32_t uniform_lo(uint32_t hi, uint32_t lo)
 {
-    return (hi << 21) | ((lo & 0x3FFu) << 11);
+    return ((hi << 10) & 0x1FFC00u) | (lo & 0x3FFu);
+}
+__device__ __forceinline__ int32_t uniform_lo_signed(uint32_t hi, uint32_t lo)
+{
+    // bit 10 of hi is the sign bit of the 21-bit value
+    return ((int32_t)(hi << 21) >> 11) | (int32_t)(lo & 0x3FFu);
 }
 
 // Does species S use the Gaussian of mode a?  Non-conserved modes a > D of
@@ -113,7 +117,7 @@ template <class L> __host__ __device__ constexpr int scale_kind(int a) { return 
 // used with different scales (D2Q9: momentum mode 2 beside mode 3) the radius
 // stays unscaled and each output takes its own scale.
 template <class L, int S, int a0>
-__device__ __forceinline__ void gaussian_pair(uint32_t wa, uint32_t wb, float scale_j, float scale, float (&g)[L::Q])
+__device__ __forceinline__ void gaussian_pair(uint32_t wa, int32_t wb, float scale_j, float scale, float (&g)[L::Q])
 {
     constexpr bool use0 = uses_mode<L, S>(a0), use1 = uses_mode<L, S>(a0 + 1);
     if constexpr (use0 || use1) {
@@ -156,9 +160,9 @@ __device__ __forceinline__ void draw_gaussians(uint32_t site, uint32_t step, uin
                              uses_mode<L, S>(a + 3) || uses_mode<L, S>(a + 4) || uses_mode<L, S>(a + 5);
         if constexpr (any && b >= BLK_LO && b < BLK_HI) {
             const uint4 x = philox4x32_10(make_uint4(site, step, (uint32_t)S, (uint32_t)b), k0, k1);
-            gaussian_pair<L, S, a>(x.x, x.y, scale_j, scale, g);
-            gaussian_pair<L, S, a + 2>(x.z, x.w, scale_j, scale, g);
-            gaussian_pair<L, S, a + 4>(low_bits_word(x.x, x.y), low_bits_word(x.z, x.w), scale_j, scale, g);
+            gaussian_pair<L, S, a>(uniform_hi(x.x), uniform_hi_signed(x.y), scale_j, scale, g);
+            gaussian_pair<L, S, a + 2>(uniform_hi(x.z), uniform_hi_signed(x.w), scale_j, scale, g);
+            gaussian_pair<L, S, a + 4>(uniform_lo(x.x, x.y), uniform_lo_signed(x.z, x.w), scale_j, scale, g);
         }
     });
 }

@@ -41,6 +41,8 @@ struct F2 {
 };
 
 __device__ __forceinline__ F2 splat2(float x) { return F2(F2::splat(x)); }
+// a float2 of the kernel parameters (or any 8-byte aligned pair) as one packed value
+__device__ __forceinline__ F2 pair2(const float2 &x) { return F2(*reinterpret_cast<const unsigned long long *>(&x)); }
 __device__ __forceinline__ F2 neg2(F2 a) { return F2(a.v ^ 0x8000000080000000ull); }
 
 __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)

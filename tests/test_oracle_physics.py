@@ -184,7 +184,7 @@ def test_theory_structure_functions_reduce_to_appendix_e():
 # --------------------------------------------------------------------------
 
 def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True, noise_rho0=None,
-                           force_velocity=False, lambda_d=None, mode_rates=None):
+                           force_velocity=False, lambda_d=None, mode_rates=None, ghost_noise=False):
     """One step of the FLBE written with the MRT matrix
     Lambda_ij = w_i sum_a lambdabar_a T_ai T_aj / N_a (Sec. V B) acting on f^eq
     and (I - Lambda/2) acting on the Hermite forcing Phi_i, plus the noise mapped
@@ -197,7 +197,10 @@ def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True, noise_rho0=
     Eq. new-noise instead of the local ones; force_velocity=True takes the
     species velocity inside Phi as v = jbar/rho + a/2 instead of
     rho v = jbar + R_j/2 (Eq. 2system); lambda_d overrides the common momentum
-    rate (Sec. III); mode_rates {(s, a): lambdabar} overrides single modes."""
+    rate (Sec. III); mode_rates {(s, a): lambdabar} overrides single modes;
+    ghost_noise=True draws the non-conserved noise as one Gaussian per
+    population, of variance mu w_i rho(r + c_i) (the density where the
+    population lands), mapped to the non-conserved modes."""
     c, w, T, N = oracle.tables(lat)
     D, Q = DIMS[lat]
     cf = c.astype(float)
@@ -245,7 +248,15 @@ def _population_space_step(f, lat, tau, kT, G, seed, step, sdf=True, noise_rho0=
                     xi[0, a, z, y, x] = (np.sqrt(vj) if sdf else 0.0) * g
                     xi[1, a, z, y, x] = -xi[0, a, z, y, x]
                 for s in range(2):
+                    if ghost_noise:
+                        eta = np.array([oracle.gaussian(seed, site, step, s + 2, i + 1) for i in range(Q)])
+                        dest = np.array([rho[s, (z + c[i, 2]) % nz, (y + c[i, 1]) % ny, (x + c[i, 0]) % nx]
+                                         if noise_rho0 is None else noise_rho0[s] for i in range(Q)])
+                        xs = np.sqrt(3 * kT * w * dest) * eta
                     for a in range(D + 1, Q):
+                        if ghost_noise:
+                            xi[s, a, z, y, x] = np.sqrt(2 * lam[s, a] - lam[s, a] ** 2) * (T[a] @ xs)
+                            continue
                         var = (2 * lam[s, a] - lam[s, a] ** 2) * N[a] * 3 * kT * nr[s]
                         xi[s, a, z, y, x] = np.sqrt(var) * oracle.gaussian(seed, site, step, s, a)
     out = np.empty_like(f)
@@ -277,6 +288,7 @@ _OPTION_CASES = {
     "force_velocity": ({"force_velocity": 1}, {}, {"force_velocity": True}),
     "lambda_d": ({"lambda_d": 1.3}, {}, {"lambda_d": 1.3}),
     "mode_rates": ({}, {(0, 4): 1.5, (1, 5): 0.6, (0, 8): 1.9, (1, 8): 0.3}, {}),
+    "ghost_noise": ({"ghost_noise": 1}, {(0, 4): 1.5, (1, 8): 0.6}, {"ghost_noise": True}),
     "all": ({"noise_rho": 1, "rho0_a": 1.4, "rho0_b": 0.5, "force_velocity": 1, "lambda_d": 0.9},
             {(0, 6): 1.2, (1, 7): 1.7},
             {"noise_rho0": (1.4, 0.5), "force_velocity": True, "lambda_d": 0.9}),
@@ -465,3 +477,53 @@ def test_full_relaxation_forgets_the_non_conserved_moments(lat, shape):
             assert diff < 1e-15, diff
         else:
             assert diff > 1e-5, diff
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q9, (1, 400, 8)), (oracle.D3Q19, (40, 40, 8))])
+@pytest.mark.parametrize("ghost", [0, 1])
+def test_non_conserved_noise_covariance_in_a_density_gradient(lat, shape, ghost):
+    """The off-diagonal noise of the non-conserved modes (the correction left
+    open after Eq. finalstep, Sec. V B and Sec. VII, in the reading of one
+    Gaussian per population at the density where it lands): one step from a
+    rest state (G = 0, every rate 1, so the post-collision non-conserved
+    modes are the noise alone) on a density that varies along x.  For each
+    column x the covariance of those modes over the sites of the column is
+    mu sum_i T_ai T_bi w_i rho(x + c_ix) with the option, and the diagonal
+    mu N_a rho(x) of Eq. new-noise without it; each entry is compared with
+    its own sampling error (family-wise 3 standard errors).  A wrong
+    neighbour (the source density instead of the destination), a missing
+    weight or a diagonal-only draw fails the option case, whose
+    off-diagonal correlations between modes reach 0.2 - 0.35 here."""
+    nz, ny, nx = shape
+    D, Q = DIMS[lat]
+    kT, mu = 1e-4, 3e-4
+    c, w, T, N = oracle.tables(lat)
+    xs = np.arange(nx)
+    prof = 1.0 + 0.6 * np.sin(2 * np.pi * xs / nx)
+    ra = np.broadcast_to(prof, shape).copy()
+    rb = np.broadcast_to(0.7 * prof[::-1], shape).copy()
+    o = oracle.Oracle(lat, nx, ny, nz, 1.0, 1.0, kT, 0.0, 31, ghost_noise=ghost)
+    o.init(ra, rb)
+    o.step(1)
+    m = np.einsum("ai,sizyx->sazyx", T, _unstream(o.get_f(), c))  # [s][a][z][y][x]
+    nc = list(range(D + 1, Q))
+    nsamp = ny * nz
+    npairs = len(nc) * (len(nc) + 1) // 2
+    zcrit = theory.family_sigma(2 * nx * npairs, nbatch=10 ** 6)  # Gaussian quantile for the whole family
+    worst_off = 0.0
+    for s, rho in enumerate((prof, 0.7 * prof[::-1])):
+        for x in range(nx):
+            dest = np.array([rho[(x + c[i, 0]) % nx] for i in range(Q)])
+            if ghost:
+                pred = mu * np.einsum("ai,bi,i->ab", T[nc], T[nc], w * dest)
+            else:
+                pred = mu * rho[x] * np.diag(N[nc])
+            v = m[s][nc][:, :, :, x].reshape(len(nc), -1)
+            cov = v @ v.T / nsamp  # the noise has mean zero
+            # standard error of a sample covariance of Gaussians: sqrt((C_aa C_bb + C_ab^2) / n)
+            se = np.sqrt((np.outer(np.diag(pred), np.diag(pred)) + pred ** 2) / nsamp)
+            assert np.all(np.abs(cov - pred) < zcrit * se), (s, x)
+            sd = np.sqrt(np.diag(pred))
+            worst_off = max(worst_off, np.max(np.abs(pred - np.diag(np.diag(pred))) / np.outer(sd, sd)))
+    if ghost:
+        assert worst_off > 0.1

@@ -377,7 +377,9 @@ def test_noise_itself_matches_oracle(lat, shape, tau):
         df = _unstream_np(res[side, kT] - res[side, 0.0], c)
         dm[side] = np.einsum("ai,sixyz->saxyz", T, df).reshape(2, Q, -1)
     ref, got = dm["oracle"], dm["gpu"]
-    assert np.max(np.abs(ref[:, 0])) < 1e-12 and np.max(np.abs(got[:, 0])) < 1e-8
+    # the noise carries no mass (R_0 = 0): exactly on the oracle, to the float
+    # rounding of the stored deviations on the GPU
+    assert np.max(np.abs(ref[:, 0])) < 1e-12 and np.max(np.abs(got[:, 0])) < 1e-6 * np.max(np.abs(got))
     for s in range(2):
         for a in range(1, Q):
             scale = np.max(np.abs(ref[s, a]))
