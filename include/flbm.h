@@ -148,6 +148,18 @@ enum {
     FLBM_OPT_STREAMING = 19,     /* flbm_streaming; only before the buffers exist (it sets their
                                     size, see flbm_buffer_bytes).  Both modes compute bitwise the
                                     same update.  Batches and flbm_step_noalloc stream in place */
+    FLBM_OPT_GHOST_NOISE = 21,   /* 1: the non-conserved modes' noise is drawn as one Gaussian per
+                                    population with the variance of local equilibrium at the site
+                                    the population streams to, mu w_i rho^s(r + c_i), projected on
+                                    the non-conserved modes (times (2 lb_a - lb_a^2)^(1/2) as in
+                                    Eq. new-noise): the off-diagonal noise between higher modes of a
+                                    non-homogeneous state that the paper leaves open (Sec. V B,
+                                    Sec. VII).  Equal to Eq. new-noise in distribution where the
+                                    density is uniform.  0 (default): the diagonal form of Eq.
+                                    new-noise.  Two-species contexts (not batches); it runs the
+                                    general collide, so it is slower than the default at tau = 1,
+                                    and the fused schedule with two arrays runs the two-kernel
+                                    step while it is on */
     FLBM_OPT_TEST_GENERAL_COLLIDE = 20, /* test hook: 1 keeps the general collide kernel even when
                                     every non-conserved rate is 1, where a kernel that skips those
                                     modes' projections runs by default (the two agree to rounding;

@@ -90,10 +90,11 @@ StepParams make_params(const flbm_ctx *c)
     p.rho0[1] = (float)c->rho0[1];
     p.noise_ref = c->noise_ref;
     p.force_velocity = c->force_velocity;
+    p.ghost_noise = c->ghost_noise;
     p.key0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
     p.key1 = (uint32_t)(c->seed >> 32);
     p.step = (uint32_t)c->step;
-    p.general_collide = c->test_general;
+    p.general_collide = c->test_general || c->ghost_noise; // the option lives in the general collide
     return p;
 }
 
@@ -366,7 +367,7 @@ uint64_t fnv1a(const unsigned char *p, size_t n)
 struct CkptHeader {
     char magic[8];
     uint32_t version;
-    int32_t lat, nx, ny, nz, storage, parity, sdf, noise_ref, force_velocity, sf_axis;
+    int32_t lat, nx, ny, nz, storage, parity, sdf, noise_ref, force_velocity, sf_axis, ghost_noise, pad_;
     int64_t step;
     uint64_t seed;
     double tau[2], kT, G, rho0[2];
@@ -463,6 +464,9 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
         c->noise_ref = v != 0.0;
     } else if (key == FLBM_OPT_FORCE_VELOCITY) {
         c->force_velocity = v != 0.0;
+    } else if (key == FLBM_OPT_GHOST_NOISE) {
+        if (c->batch) return fail(c, FLBM_EUNSUPPORTED, "the population-space noise is for single boxes");
+        c->ghost_noise = v != 0.0;
     } else if (key == FLBM_OPT_SF_AXIS) {
         if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, FLBM_EINVAL, "axis must be 0, 1 or 2");
         if ((int)v >= c->D) return fail(c, FLBM_EINVAL, "axis %d does not exist on this lattice", (int)v);
@@ -534,6 +538,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_RHO0_B: *value = c->rho0[1]; break;
     case FLBM_OPT_NOISE_RHO: *value = c->noise_ref; break;
     case FLBM_OPT_FORCE_VELOCITY: *value = c->force_velocity; break;
+    case FLBM_OPT_GHOST_NOISE: *value = c->ghost_noise; break;
     case FLBM_OPT_SF_AXIS: *value = c->sf_axis; break;
     case FLBM_OPT_KERNEL_TIMING: *value = c->timing ? 1.0 : 0.0; break;
     case FLBM_OPT_SCHEDULE: *value = c->schedule; break;
@@ -837,6 +842,9 @@ flbm_status step_pipe(flbm_ctx *c, int64_t n, bool *done)
 {
     *done = false;
     StepParams p = make_params(c);
+    // the population-space noise reads the density ring again after a tile has
+    // released its slots, so it runs the two-kernel step
+    if (p.ghost_noise) return FLBM_OK;
     const bool mom = full_relaxation(c, p);
     int lag = 0, slots = 0;
     size_t floats = 0, ncount = 0;
@@ -1148,7 +1156,7 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "FLBMCKP1", 8);
-    h.version = 2; // 2: float storage holds deviations f_i - w_i rho0
+    h.version = 3; // 2: float storage holds deviations f_i - w_i rho0; 3: with the ghost-noise option
     h.lat = c->lat;
     h.nx = c->nx;
     h.ny = c->ny;
@@ -1158,6 +1166,8 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     h.sdf = c->sdf;
     h.noise_ref = c->noise_ref;
     h.force_velocity = c->force_velocity;
+    h.ghost_noise = c->ghost_noise;
+    h.pad_ = 0;
     h.sf_axis = c->sf_axis;
     h.step = c->step;
     h.seed = c->seed;
@@ -1183,7 +1193,7 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
     if (bytes < sizeof(CkptHeader)) return fail(c, FLBM_EINVAL, "checkpoint image too small");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 2) return fail(c, FLBM_EINVAL, "not a checkpoint image");
+    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 3) return fail(c, FLBM_EINVAL, "not a checkpoint image");
     if (h.lat != c->lat || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz)
         return fail(c, FLBM_EINVAL, "checkpoint lattice or box differs from this context");
     if (c->pop && h.storage != c->storage) return fail(c, FLBM_EINVAL, "checkpoint storage format differs");
@@ -1211,6 +1221,7 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
     c->sdf = h.sdf;
     c->noise_ref = h.noise_ref;
     c->force_velocity = h.force_velocity;
+    c->ghost_noise = h.ghost_noise;
     std::memcpy(c->lam, h.lam, sizeof(h.lam));
     if (h.sf_axis != c->sf_axis) {
         free_sf(c);

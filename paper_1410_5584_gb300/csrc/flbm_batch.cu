@@ -193,6 +193,7 @@ flbm_status batch_set_option(flbm_ctx *c, int key, double v)
 {
     BatchState *b = B(c);
     if (key == FLBM_OPT_STORAGE && c->pop) return fail(c, FLBM_ESTATE, "the storage format is fixed once the buffers exist");
+    if (key == FLBM_OPT_GHOST_NOISE) return fail(c, FLBM_EUNSUPPORTED, "the population-space noise is for single boxes");
     if (key == FLBM_OPT_STREAMING) {
         if (v != (double)FLBM_STREAM_IN_PLACE) return fail(c, FLBM_EUNSUPPORTED, "batches stream in place");
         return FLBM_OK;

@@ -36,6 +36,8 @@ struct StepParams {
     float rho0[2];             // reference densities: 16-bit deviation base, noise reference
     int noise_ref;             // 1: noise amplitudes from rho0 instead of the local densities
     int force_velocity;        // 0: rho v = jbar + R_j/2 ; 1: v = vbar + a/2
+    int ghost_noise;           // 1: non-conserved noise from one Gaussian per population at the
+                               // density of the site it streams to (FLBM_OPT_GHOST_NOISE)
     uint32_t key0, key1;       // Philox key (seed low, seed high)
     uint32_t step;             // noise counter word for this step, or its offset from *step_dev
     const unsigned *step_dev;  // NULL, or a device word the counter is read from (CUDA-graph replays)

@@ -473,6 +473,29 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
         } else {
             draw_gaussians<L, 1>((uint32_t)site, nstep, p.key0, p.key1, amp_j, n1 * rsqrtf(n1), g);
         }
+        if (p.ghost_noise) {
+            // Population-space noise: g_a = N_a^(-1/2) sum_i T_ai (w_i rho^s(r + c_i))^(1/2) eta_i,
+            // which has the variance rho N_a / N_a = rho of the scaled mode draws where
+            // the density is uniform, and the off-diagonal covariances of a density
+            // gradient elsewhere (cxi then supplies (2 lb - lb^2) N_a mu as usual).
+            float eta[Q], xs[Q], pr[Q];
+            population_gaussians<Q>((uint32_t)site, nstep, 2u + (uint32_t)s, p.key0, p.key1, eta);
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                float ri = rs[s];
+                if constexpr (i > 0) {
+                    const float2 rn = src.rho_at(nb, L::cx(i), L::cy(i), L::cz(i));
+                    ri = s == 0 ? rn.x : rn.y;
+                }
+                if (p.noise_ref) ri = p.rho0[s];
+                xs[i] = sqrtf((float)L::wd(i) * ri) * eta[i];
+            });
+            Transform<L>::forward(xs, pr);
+            static_for<Q - D - 1>([&](auto kc) {
+                constexpr int a = decltype(kc)::value + D + 1;
+                g[a] = pr[a] * __frsqrt_rn((float)L::Nd(a));
+            });
+        }
         float Y[Q];
         Closure<L>::force(acc[s], v[s], Y);
         float mu[Q], fo[Q];

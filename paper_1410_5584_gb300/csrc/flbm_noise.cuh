@@ -101,6 +101,28 @@ __device__ __forceinline__ int32_t uniform_lo_signed(uint32_t hi, uint32_t lo)
     return ((int32_t)(hi << 21) >> 11) | (int32_t)(lo & 0x3FFu);
 }
 
+// Gaussians n = 0 .. Q-1 of species slot `slot` at (site, step), block b
+// holding n = 6 b .. 6 b + 5 in the layout of draw_gaussians below.  The
+// population-space noise (FLBM_OPT_GHOST_NOISE) draws Gaussian n = i for
+// population i in slots 2 and 3, which the mode draws (slots 0, 1) never use.
+template <int Q>
+__device__ __forceinline__ void population_gaussians(uint32_t site, uint32_t step, uint32_t slot, uint32_t k0,
+                                                     uint32_t k1, float (&eta)[Q])
+{
+    static_for<(Q + 5) / 6>([&](auto bc) {
+        constexpr int b = decltype(bc)::value;
+        const uint4 x = philox4x32_10(make_uint4(site, step, slot, (uint32_t)b), k0, k1);
+        float g[6];
+        box_muller(uniform_hi(x.x), uniform_hi_signed(x.y), 1.0f, g[0], g[1]);
+        box_muller(uniform_hi(x.z), uniform_hi_signed(x.w), 1.0f, g[2], g[3]);
+        box_muller(uniform_lo(x.x, x.y), uniform_lo_signed(x.z, x.w), 1.0f, g[4], g[5]);
+        static_for<6>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            if constexpr (6 * b + l < Q) eta[6 * b + l] = g[l];
+        });
+    });
+}
+
 // Does species S use the Gaussian of mode a?  Non-conserved modes a > D of
 // each species have their own draws; the momenta (1..D) are drawn once, for
 // species 0, and used with the opposite sign for species 1 (Sec. IV A).

@@ -40,6 +40,7 @@ OPT_BLOCK_X = 17
 OPT_BLOCK_Y = 18
 OPT_STREAMING = 19
 OPT_TEST_GENERAL_COLLIDE = 20
+OPT_GHOST_NOISE = 21
 STREAMING = {"in_place": 0, "two_arrays": 1}
 SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
 OPT_LAMBDA_MODE = 1000
@@ -51,7 +52,7 @@ OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
                 "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS,
                 "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y, "streaming": OPT_STREAMING,
-                "test_general_collide": OPT_TEST_GENERAL_COLLIDE}
+                "test_general_collide": OPT_TEST_GENERAL_COLLIDE, "ghost_noise": OPT_GHOST_NOISE}
 
 
 class RepParams(ctypes.Structure):
@@ -212,7 +213,8 @@ class _Context:
         optional JSON file of earlier choices."""
         path = None if cache is None else os.fsencode(cache)
         check(self._h, lib().flbm_autotune(self._h, int(steps), path))
-        keys = ("graph_steps",) if isinstance(self, Batch) else ("schedule", "slabs", "block_x", "block_y")
+        keys = ("graph_steps",) if isinstance(self, Batch) else ("schedule", "slabs", "block_x", "block_y",
+                                                                 "graph_steps")
         return {k: int(self.get_option(k)) for k in keys}
 
     def sf_sample(self):

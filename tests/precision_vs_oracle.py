@@ -9,7 +9,8 @@ relative to the largest velocity, the largest relative error of
 S_AA + S_BB, and each side's relative mass drift.  bench.py reads the record
 while the kernel sources match the digest stored in it.
 
-Run on a GPU:  python tests/precision_vs_oracle.py
+Run on a GPU:  python tests/precision_vs_oracle.py [output path]
+(default profiles/precision_vs_oracle.json)
 """
 import json
 import os
@@ -73,7 +74,7 @@ def main():
                    f"{STEPS} steps, axis S(k) every {EVERY}; GPU against the FP64 oracle from the same densities",
            "sources_sha256": bench.sources_digest(), "forms": forms,
            "command": "python tests/precision_vs_oracle.py"}
-    path = os.path.join(ROOT, "profiles", "precision_vs_oracle.json")
+    path = sys.argv[1] if len(sys.argv) > 1 else os.path.join(ROOT, "profiles", "precision_vs_oracle.json")
     with open(path, "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))
