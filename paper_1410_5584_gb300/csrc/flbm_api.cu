@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "flbm_ctx.h"
@@ -175,6 +177,68 @@ flbm_status ensure_pipe(flbm_ctx *c)
         const size_t n = 1 + (size_t)pipeline_slices(c->lat, c->ny, c->nz);
         FLBM_CUDA(c, cudaMalloc((void **)&c->d_pipe, n * sizeof(unsigned)), "cudaMalloc(pipeline counters)");
     }
+    return FLBM_OK;
+}
+
+// f(lo, hi) over [0, n) in contiguous pieces on up to eight host threads (one
+// piece when n is small): the host side of the copies between the caller's
+// buffers and the pinned staging buffer.
+template <class F> void host_parallel(size_t n, F &&f)
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    const unsigned t = std::min(8u, hw ? hw : 1u);
+    if (t <= 1 || n < ((size_t)1 << 18)) {
+        f((size_t)0, n);
+        return;
+    }
+    const size_t piece = (n + t - 1) / t;
+    std::vector<std::thread> pool;
+    for (unsigned k = 1; k < t; k++) {
+        const size_t lo = k * piece, hi = std::min(n, lo + piece);
+        if (lo < hi) pool.emplace_back([&f, lo, hi] { f(lo, hi); });
+    }
+    f((size_t)0, std::min(n, piece));
+    for (auto &th : pool) th.join();
+}
+
+// Device -> the caller's (pageable) host memory through the context's pinned
+// staging buffer: chunks alternate between its two halves, so the copy of
+// one chunk into the caller's buffer (on host threads) runs while the next
+// chunk crosses the bus on the context's stream.
+flbm_status d2h_staged(flbm_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    unsigned char *stage = reinterpret_cast<unsigned char *>(c->h_stage);
+    const size_t half = (((size_t)2 * c->N * sizeof(float)) / 2) & ~(size_t)255;
+    if (half == 0) {
+        FLBM_CUDA(c, cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost), "D2H");
+        return FLBM_OK;
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    for (int k = 0; k < 2; k++)
+        if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            if (ev[0]) cudaEventDestroy(ev[0]);
+            return fail(c, FLBM_ECUDA, "cudaEventCreate failed");
+        }
+    const size_t nchunk = (bytes + half - 1) / half;
+    auto issue = [&](size_t i) -> cudaError_t {
+        const size_t off = i * half, len = std::min(half, bytes - off);
+        cudaError_t e = cudaMemcpyAsync(stage + (i & 1) * half, static_cast<const unsigned char *>(src) + off, len,
+                                        cudaMemcpyDeviceToHost, c->stream);
+        return e == cudaSuccess ? cudaEventRecord(ev[i & 1], c->stream) : e;
+    };
+    cudaError_t e = issue(0);
+    for (size_t i = 0; i < nchunk && e == cudaSuccess; i++) {
+        if (i + 1 < nchunk) e = issue(i + 1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[i & 1]);
+        if (e != cudaSuccess) break;
+        const size_t off = i * half, len = std::min(half, bytes - off);
+        unsigned char *to = static_cast<unsigned char *>(dst) + off;
+        const unsigned char *from = stage + (i & 1) * half;
+        host_parallel(len, [&](size_t lo, size_t hi) { std::memcpy(to + lo, from + lo, hi - lo); });
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "staged D2H copy");
     return FLBM_OK;
 }
 
@@ -630,12 +694,30 @@ flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
     // previous asynchronous work may still read the staging buffer
     FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     const double *in[2] = {rho_a, rho_b};
-    for (int s = 0; s < 2; s++)
-        for (int64_t k = 0; k < c->N; k++) {
-            const double r = in[s] ? in[s][k] : c->rho0[s];
-            if (!(r > 0.0) || !std::isfinite(r)) return fail(c, FLBM_EINVAL, "initial density %g at site %lld is not positive", r, (long long)k);
-            c->h_stage[s * c->N + k] = (float)r;
+    for (int s = 0; s < 2; s++) {
+        // converted on host threads; the first bad site of each piece is kept
+        std::vector<int64_t> bad;
+        std::mutex bad_lock;
+        float *to = c->h_stage + s * c->N;
+        const double *from = in[s];
+        const double r0 = c->rho0[s];
+        host_parallel((size_t)c->N, [&](size_t lo, size_t hi) {
+            for (size_t k = lo; k < hi; k++) {
+                const double r = from ? from[k] : r0;
+                if (!(r > 0.0) || !std::isfinite(r)) {
+                    std::lock_guard<std::mutex> g(bad_lock);
+                    bad.push_back((int64_t)k);
+                    return;
+                }
+                to[k] = (float)r;
+            }
+        });
+        if (!bad.empty()) {
+            const int64_t k = *std::min_element(bad.begin(), bad.end());
+            return fail(c, FLBM_EINVAL, "initial density %g at site %lld is not positive", from ? from[k] : r0,
+                        (long long)k);
         }
+    }
     FLBM_CUDA(c, cudaMemcpyAsync(c->rho, c->h_stage, (size_t)2 * c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream), "H2D densities");
     const StepParams p = make_params(c);
     FLBM_CUDA(c, launch_init_rest(c->lat, c->storage, p, c->rho, c->pop, c->stream), "init kernel launch");
@@ -991,9 +1073,10 @@ flbm_status flbm_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, d
               "observables kernel launch");
     FLBM_CUDA(c, launch_sum_partials(c->d_partials, nb, c->d_cons, c->stream), "reduction kernel launch");
     if ((st = sync_and_check(c)) != FLBM_OK) return st;
-    if (rho_a) FLBM_CUDA(c, cudaMemcpy(rho_a, ra, c->N * sizeof(double), cudaMemcpyDeviceToHost), "D2H rho_a");
-    if (rho_b) FLBM_CUDA(c, cudaMemcpy(rho_b, rb, c->N * sizeof(double), cudaMemcpyDeviceToHost), "D2H rho_b");
-    if (u) FLBM_CUDA(c, cudaMemcpy(u, uu, (size_t)c->D * c->N * sizeof(double), cudaMemcpyDeviceToHost), "D2H u");
+    if ((st = ensure_stage(c)) != FLBM_OK) return st;
+    if (rho_a && (st = d2h_staged(c, rho_a, ra, c->N * sizeof(double))) != FLBM_OK) return st;
+    if (rho_b && (st = d2h_staged(c, rho_b, rb, c->N * sizeof(double))) != FLBM_OK) return st;
+    if (u && (st = d2h_staged(c, u, uu, (size_t)c->D * c->N * sizeof(double))) != FLBM_OK) return st;
     if (cons) FLBM_CUDA(c, cudaMemcpy(cons, c->d_cons, 5 * sizeof(double), cudaMemcpyDeviceToHost), "D2H cons");
     return FLBM_OK;
 }

@@ -769,13 +769,17 @@ __global__ void __launch_bounds__(128) k_step_fused(const StepParams p, typename
 // collide reads its own populations again, from L2 when the lag is short.
 // Slices 0 and S-1 keep slots 0 and 1 for the whole step (the periodic wrap
 // needs them at both ends); slice k of 1 .. S-2 uses slot 2 + (k-1) mod R.
-// Dependencies, counted per slice: C(j) needs every D tile of slices j-1, j,
-// j+1; D(k) reuses the slot of slice k-R and waits until every C tile of
-// slices k-R-1 .. k-R+1 (its readers) is done.  Warp w takes items w, w + W,
-// ...; all warps are resident (cooperative launch) and each wait is on items
-// of smaller index, so every wait ends; each is also bounded in time (the
-// warp sets a status bit and returns).  The per-site arithmetic is that of
-// the two-kernel step, so the update is the same.
+// Dependencies, counted per row of a slice: C(j) needs the D tiles of the
+// neighbouring rows of slices j-1, j, j+1; D(k) reuses the slot of slice k-R
+// and waits until the C tiles that read it (slices k-R-1 .. k-R+1) are done.
+// Items are drawn dynamically from interleaved work lanes (see kPipeLanes),
+// in increasing order within each lane.  Every wait is on an item of smaller
+// index; the smallest item that waits can only wait on a smaller one that
+// is being processed or is the next of its lane, whose resident warps
+// (cooperative launch) all hold smaller items still, so every wait ends; each
+// is also bounded in time (the warp sets a status bit and returns).  The
+// per-site arithmetic is that of the two-kernel step, so the update is the
+// same.
 // ---------------------------------------------------------------------------
 struct PipeRing {
     float2 *rho;       // slots x sp: (rho_A, rho_B) of the slice's sites
@@ -784,12 +788,27 @@ struct PipeRing {
     unsigned *ccount;  // finished C tiles per unit (zero at launch)
     int R;             // ring slots of slices 1 .. S-2
     int sp;            // sites per slice
-    int slices, rows, tiles_per_slice, tiles_per_row, lag, prologue, total;
+    int slices, rows, tiles_per_slice, tiles_per_row, lag, prologue, total; // tiles: kPipeTiles warp tiles each
     unsigned long long mul_T, mul_row, mul_R; // exact dividers by tiles_per_slice, tiles_per_row, R
     unsigned shift_T, shift_row, shift_R;
     unsigned target;            // tiles a unit needs before its readers run (tiles_per_row; one more tests timeouts)
     unsigned long long wait_ns; // give-up time of one dependency wait
+    unsigned *next;             // kPipeLanes work counters, kPipeStride words apart (zero at launch)
 };
+
+// Items are handed out dynamically, in order within each of kPipeLanes
+// interleaved lanes (lane c: items c, c + kPipeLanes, ...); warp w draws from
+// lane w mod kPipeLanes, so warps that run slower take fewer items instead of
+// holding back the ones that depend on theirs, and the lanes' counters sit on
+// separate cache lines.
+constexpr int kPipeLanes = 32;
+constexpr int kPipeStride = 32;
+// An item covers kPipeTiles consecutive warp tiles of a row.  Two tiles
+// spread the decoding, polls and publication over 64 sites (1,829 -> 1,666
+// warp-instructions per 32 sites) but serialise two rounds of loads in the
+// density part at the 96-register cap, and measured slower (1.43 -> 1.63 ms a
+// step at 256^3), so an item is one tile.
+constexpr int kPipeTiles = 1;
 
 __device__ __forceinline__ int pipe_slot(const PipeRing &a, int k)
 {
@@ -894,79 +913,97 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
     const int lane = threadIdx.x & 31;
     const int W = (int)((gridDim.x * blockDim.x) >> 5);
     const int Sl = a.slices;
-    int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    // the work lane of this warp and its first two items; a third is always
+    // requested one item ahead, so the counter's latency is hidden
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int wl = wid % kPipeLanes;
+    unsigned *ctr = a.next + wl * kPipeStride;
+    auto draw = [&]() -> int {
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(ctr, 1u);
+        return wl + kPipeLanes * (int)__shfl_sync(0xffffffffu, k, 0);
+    };
+    (void)W;
+    int item = draw();
+    int nitem = draw();
     int dslice = -1, cslice = -1;
     unsigned tile = 0;
     if (item < a.total) pipe_decode(a, item, dslice, cslice, tile);
-    for (; item < a.total; item += W) {
+    while (item < a.total) {
+        unsigned kreq = 0; // request for the item after next; read at the end of this one
+        if (lane == 0) kreq = atomicAdd(ctr, 1u);
         const unsigned row = exact_div(tile, a.mul_row, a.shift_row); // y of the tile (3D; 0 in 2D)
-        const int x = (int)(tile - row * (unsigned)a.tiles_per_row) * 32 + lane;
-        const bool active = x < p.nx;
-        const int insite = D == 3 ? (int)row * p.nx + x : x;
-        // the next item of this warp: its density tile is prefetched into L2 now
+        const int x0 = (int)(tile - row * (unsigned)a.tiles_per_row) * (32 * kPipeTiles) + lane;
+        // the next item of this warp: its density tiles are prefetched into L2 now
         int ndslice = -1, ncslice = -1;
         unsigned ntile = 0;
-        if (item + W < a.total) {
-            pipe_decode(a, item + W, ndslice, ncslice, ntile);
+        if (nitem < a.total) {
+            pipe_decode(a, nitem, ndslice, ncslice, ntile);
             if (ndslice >= 0) {
                 const unsigned nrow = exact_div(ntile, a.mul_row, a.shift_row);
-                const int nx0 = (int)(ntile - nrow * (unsigned)a.tiles_per_row) * 32;
+                const int nx0 = (int)(ntile - nrow * (unsigned)a.tiles_per_row) * (32 * kPipeTiles);
                 const size_t nsite = D == 3 ? (size_t)ndslice * a.sp + (size_t)nrow * p.nx + nx0
                                             : (size_t)ndslice * p.nx + nx0;
-                // the slot planes are consecutive: plane q starts at in.ptr[0] + q N
-                for (int q = lane; q < 2 * L::Q; q += 32)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(in.ptr[0] + (size_t)q * p.N + nsite));
+                // the slot planes are consecutive: plane q starts at in.ptr[0] + q N; a
+                // tile of a plane is one 128-byte line or less
+                for (int q = lane; q < 2 * L::Q * kPipeTiles; q += 32) {
+                    const int u = q % kPipeTiles, pl = q / kPipeTiles;
+                    if (nx0 + 32 * u < p.nx)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.ptr[0] + (size_t)pl * p.N + nsite + 32 * u));
+                }
             }
         }
         // unit counters of this item
         const int yrow = D == 3 ? (int)row : 0;
         const long long dunit = dslice >= 0 ? (long long)dslice * a.rows + yrow : -1;
         const long long cunit = cslice >= 0 ? (long long)cslice * a.rows + yrow : -1;
-        // ---- D part: densities (and moments) of tile `tile` of slice dslice
+        // ---- D part: densities (and moments) of the tiles of slice dslice
         if (dslice >= 0) {
             // the slice that held this ring slot before (slices 0 and S-1 keep
             // slots of their own)
             const int prev = dslice - a.R;
             if (dslice <= Sl - 2 && prev >= 1 && !pipe_wait<D>(a, a.ccount, prev, yrow, status)) return;
-            if (active) {
-                const int site = D == 3 ? dslice * a.sp + insite : dslice * p.nx + x;
-                const int slot = pipe_slot(a, dslice);
-                float r[2], mm[2][D + 1];
-                static_for<2>([&](auto sc) {
-                    constexpr int s = decltype(sc)::value;
-                    float d[L::Q], m[L::Q];
-                    static_for<L::Q>([&](auto ic) {
-                        constexpr int i = decltype(ic)::value;
-                        d[i] = S::decode(__ldcs(in.template plane<L>(s, i) + site), 0.0f);
+            const int slot = pipe_slot(a, dslice);
+            static_for<kPipeTiles>([&](auto uc) {
+                constexpr int u = decltype(uc)::value;
+                const int x = x0 + 32 * u;
+                if (x < p.nx) {
+                    const int insite = D == 3 ? (int)row * p.nx + x : x;
+                    const int site = D == 3 ? dslice * a.sp + insite : dslice * p.nx + x;
+                    float r[2], mm[2][D + 1];
+                    static_for<2>([&](auto sc) {
+                        constexpr int s = decltype(sc)::value;
+                        float d[L::Q], m[L::Q];
+                        static_for<L::Q>([&](auto ic) {
+                            constexpr int i = decltype(ic)::value;
+                            d[i] = S::decode(__ldcs(in.template plane<L>(s, i) + site), 0.0f);
+                        });
+                        // the same expressions as the density pass of the two-kernel step
+                        Transform<L>::forward(d, m);
+                        r[s] = p.rho0[s] + m[0];
+                        static_for<D + 1>([&](auto ac) {
+                            constexpr int q = decltype(ac)::value;
+                            mm[s][q] = m[q];
+                        });
                     });
-                    // the same expressions as the density pass of the two-kernel step
-                    Transform<L>::forward(d, m);
-                    r[s] = p.rho0[s] + m[0];
-                    static_for<D + 1>([&](auto ac) {
-                        constexpr int q = decltype(ac)::value;
-                        mm[s][q] = m[q];
-                    });
-                });
-                a.rho[(size_t)slot * a.sp + insite] = make_float2(r[0], r[1]);
-                if constexpr (MOM) {
-                    static_for<NM>([&](auto qc) {
-                        constexpr int q = decltype(qc)::value;
-                        a.mom[((size_t)slot * NM + q) * a.sp + insite] = mm[q / (D + 1)][q % (D + 1)];
-                    });
+                    a.rho[(size_t)slot * a.sp + insite] = make_float2(r[0], r[1]);
+                    if constexpr (MOM) {
+                        static_for<NM>([&](auto qc) {
+                            constexpr int q = decltype(qc)::value;
+                            a.mom[((size_t)slot * NM + q) * a.sp + insite] = mm[q / (D + 1)][q % (D + 1)];
+                        });
+                    }
                 }
-            }
+            });
             if (cslice < 0) pipe_publish(a.dcount, dunit, a.ccount, -1);
         }
-        // ---- C part: collide tile `tile` of slice cslice.  The counts of this
-        // item (its D tile, and its C tile for the slots' next users) are
-        // published once every ring read is done and before the population
-        // stores, so that the fence does not wait for those stores.
+        // ---- C part: collide the tiles of slice cslice.  The counts of this
+        // item (its D tiles, and its C tiles for the slots' next users) are
+        // published once every ring read is done, before the last tile's
+        // population stores, so that the fence does not wait for those.
         if (cslice >= 0) {
             const int jm = cslice == 0 ? Sl - 1 : cslice - 1, jp = cslice == Sl - 1 ? 0 : cslice + 1;
             if (!pipe_wait<D>(a, a.dcount, cslice, yrow, status)) return;
-            const int xc = active ? x : p.nx - 1; // idle lanes compute a real site without storing
-            const int y = D == 3 ? (int)row : cslice, z = D == 3 ? cslice : 0;
-            const Nbr nb = make_nbr(p, xc, y, z);
             RingSrc<D> src;
             const int sc = pipe_slot(a, cslice);
             src.rho[0] = a.rho + (size_t)pipe_slot(a, jm) * a.sp;
@@ -974,14 +1011,29 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
             src.rho[2] = a.rho + (size_t)pipe_slot(a, jp) * a.sp;
             src.mom = a.mom + (size_t)sc * NM * a.sp;
             src.sp = a.sp;
-            src.insite = D == 3 ? (int)row * p.nx + xc : xc;
-            auto publish = [&] { pipe_publish(a.dcount, dunit, a.ccount, cunit); };
-            site_collide_src<L, S, kPush, true, MOM, MOM, true>(p, in, out, src, status, nb, [] { return true; },
-                                                               publish, active);
+            const int y = D == 3 ? (int)row : cslice, z = D == 3 ? cslice : 0;
+            static_for<kPipeTiles>([&](auto uc) {
+                constexpr int u = decltype(uc)::value;
+                const int x = x0 + 32 * u;
+                const bool active = x < p.nx;
+                const int xc = active ? x : p.nx - 1; // idle lanes compute a real site without storing
+                const Nbr nb = make_nbr(p, xc, y, z);
+                src.insite = D == 3 ? (int)row * p.nx + xc : xc;
+                if constexpr (u == kPipeTiles - 1) {
+                    auto publish = [&] { pipe_publish(a.dcount, dunit, a.ccount, cunit); };
+                    site_collide_src<L, S, kPush, true, MOM, MOM, true>(p, in, out, src, status, nb,
+                                                                       [] { return true; }, publish, active);
+                } else {
+                    site_collide_src<L, S, kPush, true, MOM, MOM, true>(p, in, out, src, status, nb,
+                                                                       [] { return true; }, [] {}, active);
+                }
+            });
         }
         dslice = ndslice;
         cslice = ncslice;
         tile = ntile;
+        item = nitem;
+        nitem = wl + kPipeLanes * (int)__shfl_sync(0xffffffffu, kreq, 0);
     }
 }
 
@@ -1380,7 +1432,7 @@ cudaError_t Launch<L, S>::pipe_geometry(const StepParams &p, bool mom, int lag_o
     const cudaError_t e = pipe_blocks<L, S>(mom, &blocks);
     if (e != cudaSuccess) return e;
     const int S_ = L::D == 3 ? p.nz : p.ny;
-    const int tpr = (p.nx + 31) / 32;
+    const int tpr = (p.nx + 32 * kern::kPipeTiles - 1) / (32 * kern::kPipeTiles); // items per row
     const int T = L::D == 3 ? p.ny * tpr : tpr;
     const int sp = L::D == 3 ? p.nx * p.ny : p.nx;
     // rows of items in flight (one item per warp, W warps: a wave of W items
@@ -1396,7 +1448,7 @@ cudaError_t Launch<L, S>::pipe_geometry(const StepParams &p, bool mom, int lag_o
     }
     *lag = l;
     *ring_slots = S_ >= 2 * (l + 2) + R ? R : 0; // 0: too few slices for the pipeline
-    *counters = 2 * (size_t)S_ * (L::D == 3 ? p.ny : 1);
+    *counters = 2 * (size_t)S_ * (L::D == 3 ? p.ny : 1) + (size_t)kern::kPipeLanes * kern::kPipeStride;
     *ring_floats = ((size_t)R + 2) * sp * (2 + (mom ? 2 * (L::D + 1) : 0));
     return cudaSuccess;
 }
@@ -1407,7 +1459,7 @@ cudaError_t Launch<L, S>::step_pipe(const StepParams &p, const void *pop, void *
                                     cudaStream_t st)
 {
     const int S_ = L::D == 3 ? p.nz : p.ny;
-    const int tpr = (p.nx + 31) / 32;
+    const int tpr = (p.nx + 32 * kern::kPipeTiles - 1) / (32 * kern::kPipeTiles); // items per row
     const int T = L::D == 3 ? p.ny * tpr : tpr;
     const int sp = L::D == 3 ? p.nx * p.ny : p.nx;
     int blocks = 0;
@@ -1434,10 +1486,12 @@ cudaError_t Launch<L, S>::step_pipe(const StepParams &p, const void *pop, void *
     const size_t units = (size_t)S_ * a.rows;
     a.dcount = counters;
     a.ccount = counters + units;
-    e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * 2 * units, st);
+    a.next = counters + 2 * units;
+    e = cudaMemsetAsync(counters, 0, sizeof(unsigned) * (2 * units + (size_t)kern::kPipeLanes * kern::kPipeStride), st);
     if (e != cudaSuccess) return e;
     int grid = blocks;
     if ((long long)grid * 4 > a.total) grid = (a.total + 3) / 4;
+    if (grid * 4 < kern::kPipeLanes) grid = kern::kPipeLanes / 4; // every work lane needs a warp
     const auto in = kern::plane_table(static_cast<typename S::T *>(const_cast<void *>(pop)), L::Q, p.N);
     const auto out = kern::plane_table(static_cast<typename S::T *>(pop_out), L::Q, p.N);
     StepParams pc = p;

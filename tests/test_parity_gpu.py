@@ -599,3 +599,22 @@ def test_graph_steps_match_direct_launches(lat, shape, mode):
         assert g.step_count == 24
         runs.append(g.get_populations())
     assert np.array_equal(runs[0], runs[1])
+
+
+@pytest.mark.parametrize("shape", [(50, 60, 70), (3, 5, 7)])
+def test_moments_copy_out_through_the_staging_buffer(shape):
+    """flbm_moments hands the fields to the caller's (pageable) buffers through
+    the pinned staging buffer in alternating chunks, copied on host threads:
+    on a box whose fields span several chunks (210,000 sites) and on a tiny
+    one, the densities come back as the initial field (float-rounded) and the
+    velocity of the rest state with G = 0 is exactly zero."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(4)
+    ra = rng.uniform(0.5, 1.5, size=shape).astype(np.float32).astype(np.float64)
+    rb = rng.uniform(0.2, 0.9, size=shape).astype(np.float32).astype(np.float64)
+    g = Lattice(D3Q19, nx, ny, nz, 1.0, 1.0, 0.0, 0.0, 1, rho0_a=1.0, rho0_b=0.55)
+    g.init(ra, rb)
+    fa, fb, u, cons = g.moments()
+    assert np.max(np.abs(fa - ra)) <= 1e-6 and np.max(np.abs(fb - rb)) <= 1e-6
+    assert np.all(u == 0.0)
+    assert cons[0] == pytest.approx(ra.sum(), rel=1e-6) and cons[1] == pytest.approx(rb.sum(), rel=1e-6)
