@@ -43,6 +43,12 @@ WORKLOADS = {
     "d2q9-512": dict(lattice=0, nx=512, ny=512, nz=1, storage="f32", tau=(0.8, 1.0), kT=1e-5, G=0.9,
                      rho0=1.0, desc="D2Q9 512^2 periodic Shan-Chen mixture, FP32, G*rho0=0.9, tau=0.8/1.0, "
                                     "kT=1e-5 (fits in L2)"),
+    "d2q9-4096": dict(lattice=0, nx=4096, ny=4096, nz=1, storage="f32", tau=(1.0, 1.0), kT=1e-5, G=0.9,
+                      rho0=1.0, desc="D2Q9 4096^2 periodic Shan-Chen mixture, FP32, G*rho0=0.9, tau=1.0, "
+                                     "kT=1e-5 (as many sites as D3Q19 256^3; larger than L2)"),
+    "d2q9-2048": dict(lattice=0, nx=2048, ny=2048, nz=1, storage="f32", tau=(1.0, 1.0), kT=1e-5, G=0.9,
+                      rho0=1.0, desc="D2Q9 2048^2 mixture, FP32, tau=1.0 (profiling case: 302 MB of "
+                                     "populations, larger than L2)"),
 }
 BYTES_PER_POP = {"f32": 4, "f16": 2, "bf16": 2}
 FALLBACK_HBM_GBS = 6800.0
@@ -60,7 +66,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 storage and batching forms")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
-    ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap"], default=None,
+    ap.add_argument("--schedule", choices=["fused", "two_kernels", "overlap", "tiled"], default=None,
                     help="force one step schedule (implies --no-autotune); fused with two arrays is the "
                          "pipelined step, fused in place the in-place persistent step")
     ap.add_argument("--streaming", choices=["two_arrays", "in_place"], default="two_arrays",
@@ -307,10 +313,11 @@ def timed_step_form(wl, seed, steps, device, schedule=None, tune=False):
 def batched_form(seed, steps, device, nrep=64):
     """The batching form: nrep independent D2Q9 replicas, n_x and n_y drawn from
     {64, 128, 256, 512}, kT log-uniform in [1e-6, 1e-4], G rho0 uniform in
-    [0, 0.9], distinct Philox keys, rho = 1, tau = 1; one density and one
-    collide launch per step for all replicas, replayed from CUDA graphs whose
-    length the autotuner picks.  Compared with the same replicas stepped as
-    separate contexts, 5000 steps each (the batching workload's length)."""
+    [0, 0.9], distinct Philox keys, rho = 1, tau = 1, two arrays; every
+    replica in one tiled launch a step, or in one density and one collide
+    launch, replayed from CUDA graphs, as the autotuner picks.  Compared with
+    the same replicas stepped as separate contexts, 5000 steps each (the
+    batching workload's length)."""
     import torch
 
     from paper_1410_5584_gb300 import Batch, Lattice
@@ -331,7 +338,8 @@ def batched_form(seed, steps, device, nrep=64):
 
     b = Batch(0, reps, device=device)
     b.init()
-    graph_steps = b.autotune(steps=200)["graph_steps"]
+    tuned = b.autotune(steps=200)
+    graph_steps = tuned["graph_steps"]
     b.step(2 * max(graph_steps, 1))
     b.sync()
     t_batch = timed(lambda: b.step(steps), b.stream)
@@ -351,7 +359,9 @@ def batched_form(seed, steps, device, nrep=64):
     peak, _ = measured_peaks()
     ach = sites * steps * 2 * 9 * 4 * 2 / t_batch / 1e9
     return {"value": sites * steps / t_batch / 1e6, "unit": "MLUPS", "replicas": nrep, "sites": sites,
-            "steps": steps, "graph_steps": graph_steps, "per_replica_launches_mlups": sites * steps / t_sep / 1e6,
+            "steps": steps, "graph_steps": graph_steps,
+            "schedule": {1: "two_kernels", 3: "tiled"}.get(tuned["schedule"], tuned["schedule"]),
+            "per_replica_launches_mlups": sites * steps / t_sep / 1e6,
             "speedup_vs_per_replica_launches": t_sep / t_batch,
             "hbm": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "bytes_per_site": 144},
             "ensemble_sk": ensemble}
@@ -436,7 +446,8 @@ def capillary_form(seed, device, steps=20000):
     b = Batch(0, [dict(nx=nx, ny=ny, tau_a=1.0, tau_b=1.0, kT=1e-5, G=1.5, seed=seed, rho0_a=1.18, rho0_b=1.18)],
               device=device)
     b.init(ra, rb)
-    graph_steps = b.autotune(steps=2000)["graph_steps"]
+    tuned = b.autotune(steps=2000)
+    graph_steps = tuned["graph_steps"]
     b.step(2000)
     t_batch = timed(lambda: b.step(steps), b.stream)
     b.sync()
@@ -445,6 +456,7 @@ def capillary_form(seed, device, steps=20000):
     return {"unit": "MLUPS", "sites": sites, "steps": steps, "lone_context": sites * steps / t_lone / 1e6,
             "lone_context_graphs_64": sites * steps / t_graph / 1e6,
             "one_replica_batch": sites * steps / t_batch / 1e6, "graph_steps": graph_steps,
+            "batch_schedule": {1: "two_kernels", 3: "tiled"}.get(tuned["schedule"], tuned["schedule"]),
             "ms_per_height_snapshot": t_cap * 1e3}
 
 
@@ -669,6 +681,10 @@ def run_ours(args, wl):
     sched = (launch or {}).get("schedule", F.SCHEDULE["two_kernels"])
     # the pipelined step: the fused schedule with two arrays (one launch a step)
     pipelined = streaming == "two_arrays" and sched == F.SCHEDULE["fused"] and kn["density"] == 0
+    # the tiled step of a 2D box (one launch a step, densities in shared memory)
+    tiled = streaming == "two_arrays" and sched == F.SCHEDULE["tiled"] and kn["density"] == 0
+    one_launch = pipelined or tiled
+    one_name = "k_step_pipe" if pipelined else "k_step_tiled"
     full = all(t == 1.0 for t in wl["tau"])
     moment_fed = streaming == "two_arrays" and full and sched == F.SCHEDULE["two_kernels"]
     # Algorithmic bytes of one site update (every population of both species
@@ -677,29 +693,30 @@ def run_ours(args, wl):
     step_s = t_max / args.steps
     achieved = alg_site * sites / step_s / 1e9
     # the bytes the implementation moves by design: the pipelined step keeps
-    # its densities and moments in an L2-resident ring; the two-kernel step
-    # re-reads the populations for the densities (moment-fed: the collide
-    # reads m_0 .. m_D and rho instead of the populations)
-    if pipelined:
+    # its densities and moments in an L2-resident ring, the tiled step in shared
+    # memory (its ring of neighbouring sites is read again from L2); the
+    # two-kernel step re-reads the populations for the densities (moment-fed:
+    # the collide reads m_0 .. m_D and rho instead of the populations)
+    if one_launch:
         design = alg_site
     elif moment_fed:
         design = alg_site + 2 * (2 * (D + 1) * 4 + 8)
     else:
         design = alg_site + 2 * Q * bpp + 8 + 8
-    cap = recorded_capture(args.workload, sites, "pipelined" if pipelined else "two_kernels")
+    cap = recorded_capture(args.workload, sites, "pipelined" if pipelined else "tiled" if tiled else "two_kernels")
     traffic = cap["traffic"] if cap else None
     clocks = clk.summary()
     coll_ms = kms["collide"] / max(kn["collide"], 1)
     den_ms = kms["density"] / max(kn["density"], 1) if kn["density"] else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_step_pipe (one launch a step)" if pipelined
+    roofline = {"bound": "hbm", "kernel": one_name + " (one launch a step)" if one_launch
                 else "whole step (density pass + k_collide)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_site": alg_site, "algorithmic_bytes_per_launch": alg_site * sites,
-                "launches_per_step": 1 if pipelined else 2, "design_bytes_per_site": design,
+                "launches_per_step": 1 if one_launch else 2, "design_bytes_per_site": design,
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
-    kernels = {"collide" if not pipelined else "k_step_pipe": {"ms": coll_ms}}
-    if not pipelined:
+    kernels = {"collide" if not one_launch else one_name: {"ms": coll_ms}}
+    if not one_launch:
         coll_bytes = (2 * (D + 1) * 4 + 8 if moment_fed else 2 * Q * bpp + 8) + 2 * Q * bpp
         den_bytes = 2 * Q * bpp + 8 + (2 * (D + 1) * 4 if moment_fed else 0)
         kernels["collide"].update(bytes_per_site=coll_bytes, gbs=coll_bytes * sites / (coll_ms / 1e3) / 1e9)
@@ -761,6 +778,7 @@ def run_ours(args, wl):
             dict(wl, tau=(0.8, 1.0), desc=wl["desc"].replace("tau=1.0", "tau=0.8/1.0")), args.seed,
             max(50, args.steps // 4), device, schedule=args.schedule)
         line["forms"]["d2q9_512"] = timed_step_form(WORKLOADS["d2q9-512"], args.seed, 5000, device, tune=True)
+        line["forms"]["d2q9_4096"] = timed_step_form(WORKLOADS["d2q9-4096"], args.seed, 200, device, tune=True)
         line["forms"]["batched"] = batched_form(args.seed, 5000, device)
         line["forms"]["capillary"] = capillary_form(args.seed, device)
         line["forms"]["species3"] = multi_form(args.seed, device)

@@ -73,7 +73,7 @@ typedef enum {
                                       L2 by the collision (one HBM pass each way).  Slower on GB300 while
                                       the collision is instruction-bound */
     FLBM_SCHEDULE_TWO_KERNELS = 1, /* a density kernel over the box, then the collide kernel */
-    FLBM_SCHEDULE_OVERLAP = 2      /* the box cut into FLBM_OPT_SLABS slabs along its last axis (z;
+    FLBM_SCHEDULE_OVERLAP = 2,     /* the box cut into FLBM_OPT_SLABS slabs along its last axis (z;
                                       y for D2Q9): the collide kernel runs slab by slab on the
                                       context's stream while the next step's density kernel runs, on a
                                       second stream of higher priority, on every slab whose neighbours
@@ -81,6 +81,14 @@ typedef enum {
                                       instruction-bound collision.  Ordered by CUDA events only.  Boxes
                                       with fewer than 3 planes (rows) run the two-kernel schedule.
                                       Either streaming mode */
+    FLBM_SCHEDULE_TILED = 3        /* D2Q9 with two arrays: one launch per step.  Each thread block owns
+                                      a 32 x 16 tile; it forms the densities of the tile and of the
+                                      one-site ring around it (the force stencil, Eq. FORCESTRUCTURE)
+                                      in shared memory, and at full relaxation the tile's m_0 .. m_D,
+                                      then collides the tile and pushes f* into the other array.  No
+                                      density field goes through HBM; bitwise the two-kernel update.
+                                      D3Q19 or in place: runs the two-kernel schedule.  The one
+                                      schedule besides the two-kernel one that a batch accepts */
 } flbm_schedule;
 
 /* How populations stream (option FLBM_OPT_STREAMING). */
@@ -92,8 +100,8 @@ typedef enum {
                                    from one (natural layout) and writes f*_i to x + c_i in the other.  On
                                    GB300 a pure copy with these reads and writes runs at the HBM copy rate,
                                    the in-place pattern at half of it or less; the collide gains a few
-                                   per cent.  Runs the two-kernel and overlap schedules (the fused
-                                   one gives FLBM_EUNSUPPORTED) */
+                                   per cent.  Runs every schedule (the fused one as a pipelined step;
+                                   the tiled one on D2Q9) */
 } flbm_streaming;
 
 /* Option keys for flbm_set_option. */
@@ -406,8 +414,11 @@ flbm_status flbm_step_noalloc(const flbm_ctx *ctx, void *pop, int parity, int64_
  * and therefore its noise are replica-local -- so a replica of a batch and a
  * lone context with the same parameters and state give the same populations.
  * A step of the batch is one density launch and one collide launch over a work
- * list of 128-site tiles spanning every replica; flbm_step replays CUDA graphs of
- * FLBM_OPT_GRAPH_STEPS steps.
+ * list of 128-site tiles spanning every replica, or, under FLBM_SCHEDULE_TILED
+ * (D2Q9, two arrays), one launch over a work list of 32 x 16 tiles; flbm_step
+ * replays CUDA graphs of FLBM_OPT_GRAPH_STEPS steps.  Batches stream through
+ * two arrays by default (FLBM_OPT_STREAMING, set before the buffers exist) and
+ * accept FLBM_OPT_SCHEDULE 1 (two kernels, the default) or 3 (tiled).
  * On a batch context: flbm_set_option (applied to every replica),
  * flbm_set_stream, flbm_buffer_bytes, flbm_attach_buffers, flbm_init (host
  * densities concatenated replica by replica, or NULL), flbm_step, flbm_sync,
@@ -446,7 +457,10 @@ flbm_status flbm_batch_size(const flbm_ctx *batch, int *nrep, int64_t *sites);
  * keeps the fastest:
  *   single box: the two-kernel schedule and the overlap schedule with 4 or 8
  *               slabs, each with thread blocks of 128x1, 64x2 and 32x4 sites;
- *   batch:      FLBM_OPT_GRAPH_STEPS of 0, 4, 16 and 64.
+ *               with two arrays the fused (pipelined) schedule, and on D2Q9
+ *               the tiled schedule with and without 16-step graphs;
+ *   batch:      FLBM_OPT_GRAPH_STEPS of 0, 4, 16 and 64, and on D2Q9 with two
+ *               arrays the same graph lengths under the tiled schedule.
  * Every candidate computes bitwise the same update, so tuning changes speed,
  * never results.  Each candidate runs 2 untimed and `steps` timed steps
  * (1 .. 100000) from the same saved state: the populations are copied aside on

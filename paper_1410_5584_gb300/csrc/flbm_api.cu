@@ -110,21 +110,23 @@ flbm_status ensure_stream(flbm_ctx *c)
 }
 
 size_t array_bytes_of(const flbm_ctx *c) { return (size_t)2 * c->Q * (size_t)c->N * storage_bytes(c->storage); }
-size_t pop_bytes_of(const flbm_ctx *c)
+bool two_arrays(const flbm_ctx *c) { return c->streaming == FLBM_STREAM_TWO_ARRAYS; }
+// a replica view owns slices of its batch's arrays, not two arrays of its own
+size_t pop_bytes_of(const flbm_ctx *c) { return array_bytes_of(c) * (two_arrays(c) && !c->is_view ? 2 : 1); }
+static void *second_array(const flbm_ctx *c)
 {
-    return array_bytes_of(c) * (c->streaming == FLBM_STREAM_TWO_ARRAYS && !c->batch ? 2 : 1);
+    return c->pop_second ? c->pop_second : static_cast<unsigned char *>(c->pop) + array_bytes_of(c);
 }
-bool two_arrays(const flbm_ctx *c) { return c->streaming == FLBM_STREAM_TWO_ARRAYS && !c->batch; }
 // the same for an explicit parity (a step captured ahead of time)
 void *cur_pop_at(const flbm_ctx *c, int parity)
 {
     if (!two_arrays(c) || parity == 0) return c->pop;
-    return static_cast<unsigned char *>(c->pop) + array_bytes_of(c);
+    return second_array(c);
 }
 void *next_pop_at(const flbm_ctx *c, int parity)
 {
     if (!two_arrays(c)) return c->pop;
-    return static_cast<unsigned char *>(c->pop) + (parity == 0 ? array_bytes_of(c) : 0);
+    return parity == 0 ? second_array(c) : c->pop;
 }
 void *cur_pop(const flbm_ctx *c) { return cur_pop_at(c, c->parity); }
 void *next_pop(const flbm_ctx *c) { return next_pop_at(c, c->parity); }
@@ -545,8 +547,9 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
         c->streaming = (int)v;
     } else if (key == FLBM_OPT_SCHEDULE) {
         if (v != (double)FLBM_SCHEDULE_FUSED && v != (double)FLBM_SCHEDULE_TWO_KERNELS &&
-            v != (double)FLBM_SCHEDULE_OVERLAP)
-            return fail(c, FLBM_EINVAL, "schedule must be 0 (fused), 1 (two kernels) or 2 (overlap)");
+            v != (double)FLBM_SCHEDULE_OVERLAP && v != (double)FLBM_SCHEDULE_TILED)
+            return fail(c, FLBM_EINVAL, "schedule must be 0 (fused), 1 (two kernels), 2 (overlap) or 3 (tiled)");
+        if ((int)v != c->schedule) drop_step_graphs(c);
         c->schedule = (int)v;
     } else if (key == FLBM_OPT_BLOCK_X || key == FLBM_OPT_BLOCK_Y) {
         const int bx = key == FLBM_OPT_BLOCK_X ? (int)v : c->block_x;
@@ -606,7 +609,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_SF_AXIS: *value = c->sf_axis; break;
     case FLBM_OPT_KERNEL_TIMING: *value = c->timing ? 1.0 : 0.0; break;
     case FLBM_OPT_SCHEDULE: *value = c->schedule; break;
-    case FLBM_OPT_STREAMING: *value = c->batch ? FLBM_STREAM_IN_PLACE : c->streaming; break;
+    case FLBM_OPT_STREAMING: *value = c->streaming; break;
     case FLBM_OPT_WAIT_LIMIT_MS: *value = c->wait_limit_ms; break;
     case FLBM_OPT_TEST_STALL: *value = c->test_stall; break;
     case FLBM_OPT_TEST_GENERAL_COLLIDE: *value = c->test_general; break;
@@ -866,16 +869,22 @@ flbm_status use_moments(flbm_ctx *c, StepParams &p)
     return FLBM_OK;
 }
 
-// One CUDA graph of c->graph_steps two-kernel steps starting at `parity`: the
-// step kernels read the noise counter as *d_gstep + k, so the graph replays
-// for any starting step once d_gstep is set.
+// The tiled schedule runs where it applies: a 2D box with two arrays.
+bool tiled_applies(const flbm_ctx *c) { return two_arrays(c) && tiled_step_rows(c->lat) > 0; }
+
+// One CUDA graph of c->graph_steps steps of the two-kernel schedule (or, where
+// it applies, the tiled one) starting at `parity`: the step kernels read the
+// noise counter as *d_gstep + k, so the graph replays for any starting step
+// once d_gstep is set.
 flbm_status ensure_step_graph(flbm_ctx *c, int parity)
 {
     if (c->graph[parity]) return FLBM_OK;
     if (!c->d_gstep) FLBM_CUDA(c, cudaMalloc((void **)&c->d_gstep, sizeof(unsigned)), "cudaMalloc(graph step counter)");
     StepParams p = make_params(c);
     p.step_dev = c->d_gstep;
-    if (flbm_status st = use_moments(c, p); st != FLBM_OK) return st;
+    const bool tiled = c->schedule == FLBM_SCHEDULE_TILED && tiled_applies(c);
+    if (!tiled)
+        if (flbm_status st = use_moments(c, p); st != FLBM_OK) return st;
     cudaGraph_t g = nullptr;
     FLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     cudaError_t e = cudaSuccess;
@@ -883,6 +892,10 @@ flbm_status ensure_step_graph(flbm_ctx *c, int parity)
         const int par = (parity + k) & 1;
         p.step = (uint32_t)k;
         void *cur = cur_pop_at(c, par);
+        if (tiled) {
+            e = launch_step_tiled(c->lat, c->storage, p, cur, next_pop_at(c, par), c->d_status, c->stream);
+            continue;
+        }
         e = launch_density(c->lat, c->storage, two_arrays(c) ? 0 : par, p, cur, c->rho, c->stream);
         if (e == cudaSuccess) {
             if (two_arrays(c))
@@ -960,6 +973,25 @@ flbm_status step_pipe(flbm_ctx *c, int64_t n, bool *done)
     return FLBM_OK;
 }
 
+// n steps of the tiled schedule (one launch a step)
+flbm_status step_tiled(flbm_ctx *c, int64_t n)
+{
+    StepParams p = make_params(c);
+    for (int64_t t = 0; t < n; t++) {
+        p.step = (uint32_t)c->step;
+        TimedLaunch t1{c, c->stream, 1};
+        flbm_status st;
+        if ((st = t1.begin()) != FLBM_OK) return st;
+        const cudaError_t e = launch_step_tiled(c->lat, c->storage, p, cur_pop(c), next_pop(c), c->d_status, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "tiled step kernel launch");
+        if ((st = t1.end()) != FLBM_OK) return st;
+        if (c->timing) c->kernel_launches[1]++;
+        c->step++;
+        c->parity ^= 1;
+    }
+    return FLBM_OK;
+}
+
 flbm_status flbm_step(flbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return fail(c, FLBM_EINVAL, "negative step count");
@@ -974,8 +1006,9 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
         if (st != FLBM_OK || done) return st;
         sched = FLBM_SCHEDULE_TWO_KERNELS; // too few slices for the pipeline
     }
-    // whole graphs of graph_steps steps first (two-kernel schedule, timing off)
-    if (c->graph_steps > 0 && sched == FLBM_SCHEDULE_TWO_KERNELS && !c->timing) {
+    if (sched == FLBM_SCHEDULE_TILED && !tiled_applies(c)) sched = FLBM_SCHEDULE_TWO_KERNELS;
+    // whole graphs of graph_steps steps first (two-kernel or tiled schedule, timing off)
+    if (c->graph_steps > 0 && (sched == FLBM_SCHEDULE_TWO_KERNELS || sched == FLBM_SCHEDULE_TILED) && !c->timing) {
         while (n >= c->graph_steps) {
             flbm_status st = ensure_step_graph(c, c->parity);
             if (st != FLBM_OK) return st;
@@ -987,6 +1020,7 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
         }
         if (n == 0) return FLBM_OK;
     }
+    if (sched == FLBM_SCHEDULE_TILED) return step_tiled(c, n);
     StepParams p = make_params(c);
     if (sched == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
     if (sched == FLBM_SCHEDULE_FUSED) {

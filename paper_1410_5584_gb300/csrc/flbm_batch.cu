@@ -1,14 +1,16 @@
 // flbm_batch.cu -- many independent two-species boxes of uneven size, stepped
 // together: one density launch and one collide launch per step over a work list
-// of 128-site tiles that spans every replica, replayed from CUDA graphs of K
-// steps.  Each replica has its own box, parameters and Philox key; its site
-// index (and so its noise) is replica-local, exactly as a lone context with the
-// same parameters.
+// of 128-site tiles that spans every replica, or (tiled schedule, 2D, two
+// arrays) one launch per step over a work list of 32 x 16 tiles, replayed from
+// CUDA graphs of K steps.  Each replica has its own box, parameters and Philox
+// key; its site index (and so its noise) is replica-local, exactly as a lone
+// context with the same parameters.
 //
-// The replicas share one population array and one density field.  Each replica
-// is also exposed as a *view*: a context whose buffers are its slices of the
-// shared ones, on which the observation calls (flbm_moments, flbm_sf_sample,
-// flbm_structure_factor, flbm_get_populations, ...) work unchanged.
+// The replicas share the population arrays (two by default, or one updated in
+// place) and one density field.  Each replica is also exposed as a *view*: a
+// context whose buffers are its slices of the shared ones, on which the
+// observation calls (flbm_moments, flbm_sf_sample, flbm_structure_factor,
+// flbm_get_populations, ...) work unchanged.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -21,8 +23,11 @@ struct BatchState {
     std::vector<flbm_ctx *> views;
     std::vector<int64_t> site_off; // first site of each replica in the density field
     std::vector<int2> tiles_h;     // (replica, first site) per 128-site tile
+    std::vector<int4> tiles2_h;    // (replica, x0, y0, 0) per tile of the tiled step
     RepInfo *d_reps = nullptr;
     int2 *d_tiles = nullptr;
+    int4 *d_tiles2 = nullptr;
+    int schedule = FLBM_SCHEDULE_TWO_KERNELS; // or FLBM_SCHEDULE_TILED
     unsigned *d_step = nullptr; // noise counter of the next step
     bool reps_dirty = true;
     bool step_dirty = true;
@@ -38,7 +43,7 @@ using namespace host;
 
 namespace {
 
-BatchState *B(flbm_ctx *c) { return c->batch; }
+BatchState *B(const flbm_ctx *c) { return c->batch; }
 
 void drop_graphs(BatchState *b)
 {
@@ -49,6 +54,13 @@ void drop_graphs(BatchState *b)
     }
 }
 
+// the tiled step applies: a 2D lattice with two arrays
+bool tiled(const flbm_ctx *c)
+{
+    return B(c)->schedule == FLBM_SCHEDULE_TILED && c->streaming == FLBM_STREAM_TWO_ARRAYS &&
+           tiled_step_rows(c->lat) > 0;
+}
+
 // point every view at its slices of the shared buffers and the batch stream
 void bind_views(flbm_ctx *c)
 {
@@ -57,10 +69,15 @@ void bind_views(flbm_ctx *c)
     for (size_t r = 0; r < b->views.size(); r++) {
         flbm_ctx *v = b->views[r];
         v->storage = c->storage;
+        v->streaming = c->streaming;
         v->stream = c->stream;
         v->own_stream = false;
         if (c->pop) {
-            v->pop = static_cast<unsigned char *>(c->pop) + (size_t)2 * c->Q * (size_t)b->site_off[r] * bytes;
+            const size_t off = (size_t)2 * c->Q * (size_t)b->site_off[r] * bytes;
+            v->pop = static_cast<unsigned char *>(c->pop) + off;
+            v->pop_second = c->streaming == FLBM_STREAM_TWO_ARRAYS
+                                ? static_cast<unsigned char *>(c->pop) + array_bytes_of(c) + off
+                                : nullptr;
             v->rho = c->rho + 2 * b->site_off[r];
             v->pop_bytes = pop_bytes_of(v);
             v->rho_bytes = rho_bytes_of(v);
@@ -85,6 +102,18 @@ flbm_status upload_tables(flbm_ctx *c)
         FLBM_CUDA(c, cudaMalloc((void **)&b->d_tiles, b->tiles_h.size() * sizeof(int2)), "cudaMalloc(tiles)");
         FLBM_CUDA(c, cudaMemcpy(b->d_tiles, b->tiles_h.data(), b->tiles_h.size() * sizeof(int2), cudaMemcpyHostToDevice),
                   "H2D tiles");
+        // the tiles of the tiled step, where the lattice has one
+        const int rows = tiled_step_rows(c->lat);
+        if (rows > 0) {
+            for (size_t r = 0; r < b->views.size(); r++)
+                for (int y0 = 0; y0 < b->views[r]->ny; y0 += rows)
+                    for (int x0 = 0; x0 < b->views[r]->nx; x0 += kTiledStepX)
+                        b->tiles2_h.push_back(make_int4((int)r, x0, y0, 0));
+            FLBM_CUDA(c, cudaMalloc((void **)&b->d_tiles2, b->tiles2_h.size() * sizeof(int4)), "cudaMalloc(tiles)");
+            FLBM_CUDA(c, cudaMemcpy(b->d_tiles2, b->tiles2_h.data(), b->tiles2_h.size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice),
+                      "H2D tiles");
+        }
         FLBM_CUDA(c, cudaMalloc((void **)&b->d_reps, b->views.size() * sizeof(RepInfo)), "cudaMalloc(replicas)");
         FLBM_CUDA(c, cudaMalloc((void **)&b->d_step, sizeof(unsigned)), "cudaMalloc(step counter)");
         b->reps_dirty = b->step_dirty = true;
@@ -130,10 +159,18 @@ flbm_status upload_tables(flbm_ctx *c)
 flbm_status launch_steps(flbm_ctx *c, int parity, int k0, int n)
 {
     BatchState *b = B(c);
+    const bool two = c->streaming == FLBM_STREAM_TWO_ARRAYS, tl = tiled(c);
     for (int k = 0; k < n; k++) {
-        cudaError_t e = launch_batch_step(c->lat, c->storage, (parity + k) & 1, b->d_reps, b->d_tiles,
-                                          (int)b->tiles_h.size(), c->pop, c->rho, c->d_status, b->d_step,
-                                          (unsigned)(k0 + k), b->full, c->stream);
+        const int par = (parity + k) & 1;
+        cudaError_t e;
+        if (tl)
+            e = launch_batch_step_tiled(c->lat, c->storage, b->d_reps, b->d_tiles2, (int)b->tiles2_h.size(),
+                                        cur_pop_at(c, par), next_pop_at(c, par), c->d_status, b->d_step,
+                                        (unsigned)(k0 + k), b->full, c->stream);
+        else
+            e = launch_batch_step(c->lat, c->storage, two ? kStreamPush : par, b->d_reps, b->d_tiles,
+                                  (int)b->tiles_h.size(), cur_pop_at(c, par), next_pop_at(c, par), c->rho,
+                                  c->d_status, b->d_step, (unsigned)(k0 + k), b->full, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "batched step launch");
     }
     cudaError_t e = launch_add_u32(b->d_step, (unsigned)n, c->stream);
@@ -195,7 +232,20 @@ flbm_status batch_set_option(flbm_ctx *c, int key, double v)
     if (key == FLBM_OPT_STORAGE && c->pop) return fail(c, FLBM_ESTATE, "the storage format is fixed once the buffers exist");
     if (key == FLBM_OPT_GHOST_NOISE) return fail(c, FLBM_EUNSUPPORTED, "the population-space noise is for single boxes");
     if (key == FLBM_OPT_STREAMING) {
-        if (v != (double)FLBM_STREAM_IN_PLACE) return fail(c, FLBM_EUNSUPPORTED, "batches stream in place");
+        if (c->pop) return fail(c, FLBM_ESTATE, "the streaming mode is fixed once the buffers exist");
+        if (v != (double)FLBM_STREAM_IN_PLACE && v != (double)FLBM_STREAM_TWO_ARRAYS)
+            return fail(c, FLBM_EINVAL, "streaming must be 0 (in place) or 1 (two arrays)");
+        c->streaming = (int)v;
+        for (flbm_ctx *vw : b->views) vw->streaming = c->streaming;
+        drop_graphs(b);
+        return FLBM_OK;
+    }
+    if (key == FLBM_OPT_SCHEDULE) {
+        if (v != (double)FLBM_SCHEDULE_TWO_KERNELS && v != (double)FLBM_SCHEDULE_TILED)
+            return fail(c, FLBM_EUNSUPPORTED, "a batch runs the two-kernel (1) or the tiled (3) schedule");
+        if ((int)v != b->schedule) drop_graphs(b);
+        b->schedule = (int)v;
+        c->schedule = (int)v;
         return FLBM_OK;
     }
     if (key == FLBM_OPT_GRAPH_STEPS) {
@@ -205,8 +255,7 @@ flbm_status batch_set_option(flbm_ctx *c, int key, double v)
         drop_graphs(b);
         return FLBM_OK;
     }
-    if (key == FLBM_OPT_SF_AXIS || key == FLBM_OPT_KERNEL_TIMING || key == FLBM_OPT_SCHEDULE ||
-        key == FLBM_OPT_PIPE_LAG || key == FLBM_OPT_WAIT_LIMIT_MS || key == FLBM_OPT_TEST_STALL ||
+    if (key == FLBM_OPT_SF_AXIS || key == FLBM_OPT_KERNEL_TIMING || key == FLBM_OPT_PIPE_LAG || key == FLBM_OPT_WAIT_LIMIT_MS || key == FLBM_OPT_TEST_STALL ||
         key == FLBM_OPT_SLABS || key == FLBM_OPT_BLOCK_X || key == FLBM_OPT_BLOCK_Y) {
         if (key == FLBM_OPT_SF_AXIS) {
             for (flbm_ctx *vw : b->views) {
@@ -385,7 +434,7 @@ flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
 {
     BatchState *b = B(c);
     const size_t nrep = b->views.size();
-    const size_t payload = pop_bytes_of(c);
+    const size_t payload = array_bytes_of(c); // the current array
     const size_t need = sizeof(BatchCkptHeader) + nrep * sizeof(BatchCkptReplica) + payload;
     if (!buf) {
         *bytes = need;
@@ -403,7 +452,7 @@ flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     h.lat = c->lat;
     h.nrep = (int32_t)nrep;
     h.storage = c->storage;
-    h.parity = c->parity;
+    h.parity = layout_parity(c);
     h.sdf = c->sdf;
     h.noise_ref = c->noise_ref;
     h.force_velocity = c->force_velocity;
@@ -426,7 +475,7 @@ flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
         std::memcpy(reps + r * sizeof(q), &q, sizeof(q));
     }
     unsigned char *pl = reps + nrep * sizeof(BatchCkptReplica);
-    FLBM_CUDA(c, cudaMemcpy(pl, c->pop, payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
+    FLBM_CUDA(c, cudaMemcpy(pl, cur_pop(c), payload, cudaMemcpyDeviceToHost), "D2H checkpoint");
     h.payload_hash = fnv1a(pl, payload);
     std::memcpy(dst, &h, sizeof(h));
     *bytes = need;
@@ -455,6 +504,8 @@ flbm_status batch_restore(flbm_ctx *c, const void *buf, size_t bytes)
         return fail(c, FLBM_EINVAL, "checkpoint image truncated");
     const unsigned char *pl = reps + nrep * sizeof(BatchCkptReplica);
     if (fnv1a(pl, payload) != h.payload_hash) return fail(c, FLBM_EINVAL, "checkpoint image corrupt (hash mismatch)");
+    if (c->streaming == FLBM_STREAM_TWO_ARRAYS && h.parity != 0)
+        return fail(c, FLBM_EINVAL, "an in-place image in the swapped layout restores into an in-place batch only");
     c->storage = h.storage;
     for (size_t r = 0; r < nrep; r++) {
         BatchCkptReplica q;
@@ -497,6 +548,7 @@ void batch_destroy(flbm_ctx *c)
     drop_graphs(b);
     if (b->d_reps) cudaFree(b->d_reps);
     if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_tiles2) cudaFree(b->d_tiles2);
     if (b->d_step) cudaFree(b->d_step);
     if (b->d_mom) cudaFree(b->d_mom);
     for (flbm_ctx *v : b->views) {

@@ -49,6 +49,8 @@ struct flbm_ctx {
     // device buffers
     void *pop = nullptr;
     size_t pop_bytes = 0;
+    void *pop_second = nullptr; // a batch replica view with two arrays: its slice of the second array
+                                // (NULL: the second array follows the first in pop)
     float *rho = nullptr;
     size_t rho_bytes = 0;
     bool own_buffers = false;
@@ -125,6 +127,8 @@ size_t pop_bytes_of(const flbm_ctx *c);
 size_t array_bytes_of(const flbm_ctx *c);
 void *cur_pop(const flbm_ctx *c);
 void *next_pop(const flbm_ctx *c);
+void *cur_pop_at(const flbm_ctx *c, int parity); // the same for an explicit parity
+void *next_pop_at(const flbm_ctx *c, int parity);
 int layout_parity(const flbm_ctx *c);
 void drop_step_graphs(flbm_ctx *c); // after any change of what a step launches
 size_t rho_bytes_of(const flbm_ctx *c);

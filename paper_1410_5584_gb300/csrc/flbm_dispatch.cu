@@ -37,6 +37,12 @@ template <class L, class S> struct PipeF {
 template <class L, class S> struct BatchF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::batch_step(a...); }
 };
+template <class L, class S> struct TiledF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::step_tiled(a...); }
+};
+template <class L, class S> struct BatchTiledF {
+    template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::batch_step_tiled(a...); }
+};
 template <class L, class S> struct InitF {
     template <class... A> static cudaError_t run(A... a) { return Launch<L, S>::init_rest(a...); }
 };
@@ -86,11 +92,27 @@ cudaError_t launch_step_pipe(int lat, int storage, const StepParams &p, const vo
 }
 
 cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,
-                              void *pop, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
-                              bool full, cudaStream_t stream)
+                              void *pop, void *pop_out, float *rho, unsigned *status, const unsigned *step_base,
+                              unsigned k, bool full, cudaStream_t stream)
 {
-    return dispatch<BatchF>(lat, storage, parity, reps, tiles, ntiles, pop, rho, status, step_base, k, full, stream);
+    return dispatch<BatchF>(lat, storage, parity, reps, tiles, ntiles, pop, pop_out, rho, status, step_base, k, full,
+                            stream);
 }
+
+cudaError_t launch_step_tiled(int lat, int storage, const StepParams &p, const void *pop, void *pop_out,
+                              unsigned *status, cudaStream_t stream)
+{
+    return dispatch<TiledF>(lat, storage, p, pop, pop_out, status, stream);
+}
+
+cudaError_t launch_batch_step_tiled(int lat, int storage, const RepInfo *reps, const int4 *tiles, int ntiles,
+                                    const void *pop, void *pop_out, unsigned *status, const unsigned *step_base,
+                                    unsigned k, bool full, cudaStream_t stream)
+{
+    return dispatch<BatchTiledF>(lat, storage, reps, tiles, ntiles, pop, pop_out, status, step_base, k, full, stream);
+}
+
+int tiled_step_rows(int lat) { return lat == FLBM_D2Q9 ? Launch<D2Q9, StoreF32>::tile_rows() : 0; }
 
 cudaError_t launch_init_rest(int lat, int storage, const StepParams &p, const float *rho_in, void *pop,
                              cudaStream_t stream)

@@ -183,10 +183,24 @@ cudaError_t launch_step_pipe(int lat, int storage, const StepParams &p, const vo
 // One step of every replica of a batch (density then collide over the tile
 // work list: tiles[t] = (replica, first site of 128)); the noise counter of the
 // step is *step_base + k.  full: every replica relaxes each non-conserved
-// mode with rate 1 (the collide skips their projections).
+// mode with rate 1 (the collide skips their projections).  parity 0 / 1: in
+// place in pop; kStreamPush: read pop, write pop_out.
 cudaError_t launch_batch_step(int lat, int storage, int parity, const RepInfo *reps, const int2 *tiles, int ntiles,
-                              void *pop, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
-                              bool full, cudaStream_t stream);
+                              void *pop, void *pop_out, float *rho, unsigned *status, const unsigned *step_base,
+                              unsigned k, bool full, cudaStream_t stream);
+
+// The tiled two-array step of a 2D box: one launch; each thread block forms the
+// densities of a kTileX x tiled_step_rows(lat) tile and of the one-site ring
+// around it in shared memory, then collides the tile, reading pop and writing
+// pop_out.  cudaErrorNotSupported for D3Q19.  The batch form steps the work
+// list tiles[t] = (replica, x0, y0, unused) of every replica.
+cudaError_t launch_step_tiled(int lat, int storage, const StepParams &p, const void *pop, void *pop_out,
+                              unsigned *status, cudaStream_t stream);
+cudaError_t launch_batch_step_tiled(int lat, int storage, const RepInfo *reps, const int4 *tiles, int ntiles,
+                                    const void *pop, void *pop_out, unsigned *status, const unsigned *step_base,
+                                    unsigned k, bool full, cudaStream_t stream);
+constexpr int kTiledStepX = 32;   // tile width of the tiled step (sites along x)
+int tiled_step_rows(int lat);     // tile height (rows), 0 when the lattice has no tiled step
 // *p += v and *p = v on the device (one thread), for the batch step counter.
 cudaError_t launch_add_u32(unsigned *p, unsigned v, cudaStream_t stream);
 cudaError_t launch_set_u32(unsigned *p, unsigned v, cudaStream_t stream);

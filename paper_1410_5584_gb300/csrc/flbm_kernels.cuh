@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_density(const StepParams p,
 // collide's own transform, so the results are bitwise those of the
 // population-reading collide.  Returns the densities; writes p.mom.
 template <class L, class S, int PARITY, class P>
-__device__ __forceinline__ float2 site_moments(const StepParams &p, const P &planes, const Nbr &nb)
+__device__ __forceinline__ float2 site_moments_to(const StepParams &p, const P &planes, const Nbr &nb,
+                                                  float (&mm)[2][L::D + 1])
 {
-    const size_t site = (size_t)nb.at(0, 0, 0);
     float r[2];
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
@@ -164,10 +164,23 @@ __device__ __forceinline__ float2 site_moments(const StepParams &p, const P &pla
         r[s] = p.rho0[s] + m[0];
         static_for<L::D + 1>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
-            p.mom[(size_t)(s * (L::D + 1) + a) * (size_t)p.N + site] = m[a];
+            mm[s][a] = m[a];
         });
     });
     return make_float2(r[0], r[1]);
+}
+
+template <class L, class S, int PARITY, class P>
+__device__ __forceinline__ float2 site_moments(const StepParams &p, const P &planes, const Nbr &nb)
+{
+    const size_t site = (size_t)nb.at(0, 0, 0);
+    float mm[2][L::D + 1];
+    const float2 r = site_moments_to<L, S, PARITY>(p, planes, nb, mm);
+    static_for<2 * (L::D + 1)>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        p.mom[(size_t)q * (size_t)p.N + site] = mm[q / (L::D + 1)][q % (L::D + 1)];
+    });
+    return r;
 }
 
 template <class L, class S, int PARITY>
@@ -351,8 +364,8 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
                 constexpr int cd = comp<L>(i, d);
                 if constexpr (cd != 0) {
                     constexpr float cw = (float)cd * wi;
-                    acc[0][d] += cw * rb;
-                    acc[1][d] += cw * ra;
+                    acc[0][d] = __fmaf_rn(cw, rb, acc[0][d]);
+                    acc[1][d] = __fmaf_rn(cw, ra, acc[1][d]);
                 }
             });
         });
@@ -363,13 +376,16 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
         });
     }
 
-    // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
-    const float rt = rs[0] + rs[1];
+    // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep).
+    // Here and in step 5 every rounding is explicit, so that each kernel that
+    // inlines this function gives the same bits.
+    const float rt = __fadd_rn(rs[0], rs[1]);
     const float irt = __frcp_rn(rt);
     float u[3] = {0.0f, 0.0f, 0.0f};
     static_for<D>([&](auto dc) {
         constexpr int d = decltype(dc)::value;
-        u[d] = (m[0][1 + d] + m[1][1 + d] + 0.5f * (rs[0] * acc[0][d] + rs[1] * acc[1][d])) * irt;
+        const float ra = __fmaf_rn(rs[0], acc[0][d], __fmul_rn(rs[1], acc[1][d]));
+        u[d] = __fmul_rn(__fmaf_rn(0.5f, ra, __fadd_rn(m[0][1 + d], m[1][1 + d])), irt);
     });
     if (STORE && live && (!(rs[0] > 0.0f) || !(rs[1] > 0.0f) || !isfinite(rt))) atomicOr(status, kStatusNonFinite);
 
@@ -442,13 +458,16 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         const float irs = __frcp_rn(rs[s]);
+        const float lrs = __fmul_rn(p.lam_d, rs[s]), hrs = __fmul_rn(p.hlam_d, rs[s]);
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             constexpr int a = 1 + d;
             const float xi = s == 0 ? g0[a] : -g0[a];
-            const float R = p.lam_d * (rs[s] * u[d] - m[s][a]) + p.hlam_d * rs[s] * acc[s][d] + xi;
-            v[s][d] = p.force_velocity ? m[s][a] * irs + 0.5f * acc[s][d] : (m[s][a] + 0.5f * R) * irs;
-            m[s][a] += R;
+            // the operations of the packed form of step 5', one lane at a time
+            const float R = __fmaf_rn(lrs, u[d], __fmaf_rn(-p.lam_d, m[s][a], __fmaf_rn(hrs, acc[s][d], xi)));
+            v[s][d] = p.force_velocity ? __fmaf_rn(m[s][a], irs, __fmul_rn(0.5f, acc[s][d]))
+                                       : __fmul_rn(__fmaf_rn(0.5f, R, m[s][a]), irs);
+            m[s][a] = __fadd_rn(m[s][a], R);
         });
     });
 
@@ -1102,11 +1121,12 @@ __global__ void __launch_bounds__(128) k_density_batch(const RepInfo *__restrict
     else rho[st.rho_off + site] = site_density<L, S, PARITY>(st.sp, fp, nb);
 }
 
+// PARITY kPush: read pop, write pop_out (two arrays); otherwise in place in pop.
 template <class L, class S, int PARITY, bool FULL, bool MOM = false>
 __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict__ reps, const int2 *__restrict__ tiles,
-                                                       typename S::T *__restrict__ pop, const float2 *__restrict__ rho,
-                                                       unsigned *__restrict__ status, const unsigned *__restrict__ step_base,
-                                                       unsigned k)
+                                                       typename S::T *__restrict__ pop, typename S::T *__restrict__ pop_out,
+                                                       const float2 *__restrict__ rho, unsigned *__restrict__ status,
+                                                       const unsigned *__restrict__ step_base, unsigned k)
 {
     __shared__ StagedRep st;
     const int2 t = tiles[blockIdx.x];
@@ -1117,7 +1137,142 @@ __global__ void __launch_bounds__(128) k_collide_batch(const RepInfo *__restrict
     st.coords(site, x, y, z);
     const Nbr nb = make_nbr(st.sp, x, y, z);
     const FlatPlanes<typename S::T> fp{pop + st.pop_off, (size_t)st.sp.N};
-    site_collide<L, S, PARITY, false, true, FULL, MOM>(st.sp, fp, fp, rho + st.rho_off, status, nb, [] { return true; });
+    const FlatPlanes<typename S::T> fo{(PARITY == kPush ? pop_out : pop) + st.pop_off, (size_t)st.sp.N};
+    site_collide<L, S, PARITY, false, true, FULL, MOM>(st.sp, fp, fo, rho + st.rho_off, status, nb, [] { return true; });
+}
+
+// ---------------------------------------------------------------------------
+// Tiled two-array step (2D): one launch per step, no density field in HBM.
+// A thread block owns a tile of kTileX x TileGeom::Y sites.  It forms the
+// densities of the tile and of the one-site ring around it (periodic) into
+// shared memory, and, at full relaxation, each tile site's m_0 .. m_D; after
+// one barrier it collides the tile from there and pushes f* into the other
+// array.  The ring's densities are formed again by the neighbouring blocks
+// (about 20 % more density work at 32 x 16), but the populations cross HBM
+// once each way (the ring's reads hit L2) and the densities never leave the
+// SM.  The per-site expressions are those of the two-kernel step, so the
+// update is bitwise the same.  Reads only `in`, writes only `out`: no two
+// blocks touch the same word of either.
+// ---------------------------------------------------------------------------
+constexpr int kTileX = kTiledStepX;
+// NT threads (NT / 32 rows of lanes), R rows per thread
+template <int NT, int R> struct TileGeom {
+    static constexpr int Y = (NT / kTileX) * R;     // rows of the tile
+    static constexpr int W = kTileX + 2, H = Y + 2; // with the ring
+    static constexpr int RING = 2 * W + 2 * Y;      // ring sites
+    static constexpr int MOMS = Y * kTileX;         // floats of one moment plane
+};
+// blocks an SM is asked to hold (register budget): 1024 threads at full
+// relaxation, 768 otherwise
+template <int NT, bool FULL> constexpr int tile_min_blocks() { return (FULL ? 1024 : 768) / NT > 0 ? (FULL ? 1024 : 768) / NT : 1; }
+
+// periodic coordinate g in [-n, 2n + kTileX) brought into [0, n)
+__device__ __forceinline__ int wrap_coord(int g, int n)
+{
+    while (g >= n) g -= n;
+    while (g < 0) g += n;
+    return g;
+}
+
+// The collide's view of a tile: the density stencil and, MOM, the site's own
+// moments from shared memory.
+template <class G> struct TileSrc {
+    const float2 *rho; // (H x W) densities, ring included
+    const float *mom;  // 2 (D + 1) planes of Y x kTileX
+    int c, m;          // this site's cell in rho and in each moment plane
+    __device__ __forceinline__ float2 rho_at(const Nbr &, int dx, int dy, int) const { return rho[c + dy * G::W + dx]; }
+    __device__ __forceinline__ float mom_at(int plane) const { return mom[plane * G::MOMS + m]; }
+};
+
+// One tile: densities (and moments) into shared memory, a barrier, then the
+// collisions.
+template <class L, class S, bool FULL, bool MOM, int NT, int R, class P>
+__device__ __forceinline__ void tile_step(const StepParams &p, const P &in, const P &out, unsigned *__restrict__ status,
+                                          int x0, int y0, float2 *srho, float *smom)
+{
+    static_assert(L::D == 2, "the tiled step is two-dimensional");
+    using G = TileGeom<NT, R>;
+    constexpr int NM = 2 * (L::D + 1), LR = NT / kTileX;
+    const int tid = (int)threadIdx.x, tx = tid % kTileX, ty = tid / kTileX;
+    // densities (and moments) of the tile's own sites
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int ly = ty + LR * r;
+        const Nbr nb = make_nbr(p, wrap_coord(x0 + tx, p.nx), wrap_coord(y0 + ly, p.ny), 0);
+        float2 rr;
+        if constexpr (MOM) {
+            float mm[2][L::D + 1];
+            rr = site_moments_to<L, S, 0>(p, in, nb, mm);
+            static_for<NM>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                smom[q * G::MOMS + ly * kTileX + tx] = mm[q / (L::D + 1)][q % (L::D + 1)];
+            });
+        } else {
+            rr = site_density<L, S, 0>(p, in, nb);
+        }
+        srho[(ly + 1) * G::W + tx + 1] = rr;
+    }
+    // densities of the ring: the rows above and below (corners included), then
+    // the columns left and right
+    for (int h = tid; h < G::RING; h += NT) {
+        int sx, sy;
+        if (h < 2 * G::W) {
+            sx = h % G::W - 1;
+            sy = h < G::W ? -1 : G::Y;
+        } else {
+            sx = h < 2 * G::W + G::Y ? -1 : kTileX;
+            sy = (h - 2 * G::W) % G::Y;
+        }
+        const Nbr nb = make_nbr(p, wrap_coord(x0 + sx, p.nx), wrap_coord(y0 + sy, p.ny), 0);
+        srho[(sy + 1) * G::W + sx + 1] = site_density<L, S, 0>(p, in, nb);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < R; r++) {
+        const int ly = ty + LR * r;
+        const int x = x0 + tx, y = y0 + ly;
+        const bool active = x < p.nx && y < p.ny;
+        // idle lanes of a ragged tile compute a real site without storing
+        const Nbr nb = make_nbr(p, wrap_coord(x, p.nx), wrap_coord(y, p.ny), 0);
+        const TileSrc<G> src{srho, smom, (ly + 1) * G::W + tx + 1, ly * kTileX + tx};
+        site_collide_src<L, S, kPush, true, FULL, MOM, false>(p, in, out, src, status, nb, [] { return true; },
+                                                              [] {}, active);
+    }
+}
+
+// One tile a block (a grid of persistent blocks walking the tiles, with or
+// without an L2 prefetch of each next tile, measured slower).
+template <class L, class S, bool FULL, bool MOM, int NT, int R>
+__global__ void __launch_bounds__(NT, (tile_min_blocks<NT, FULL>()))
+    k_step_tiled(const StepParams p, const PlaneTable<typename S::T> in, const PlaneTable<typename S::T> out,
+                 unsigned *__restrict__ status)
+{
+    using G = TileGeom<NT, R>;
+    __shared__ float2 srho[G::H * G::W];
+    __shared__ float smom[MOM ? 2 * (L::D + 1) * G::MOMS : 1];
+    tile_step<L, S, FULL, MOM, NT, R>(p, in, out, status, (int)blockIdx.x * kTileX, (int)blockIdx.y * G::Y, srho,
+                                      smom);
+}
+
+// The tiled step of a batch: block b steps tile tiles[b] = (replica, x0, y0)
+// with that replica's staged parameters, on its slices of the two arrays.
+template <class L, class S, bool FULL, bool MOM, int NT, int R>
+__global__ void __launch_bounds__(NT, (tile_min_blocks<NT, FULL>()))
+    k_step_tiled_batch(const RepInfo *__restrict__ reps, const int4 *__restrict__ tiles,
+                       const typename S::T *__restrict__ pop, typename S::T *__restrict__ pop_out,
+                       unsigned *__restrict__ status, const unsigned *__restrict__ step_base, unsigned k)
+{
+    using G = TileGeom<NT, R>;
+    __shared__ StagedRep st;
+    __shared__ float2 srho[G::H * G::W];
+    __shared__ float smom[MOM ? 2 * (L::D + 1) * G::MOMS : 1];
+    const int4 t = tiles[blockIdx.x];
+    stage_params(reps, t.x, st, step_base, k);
+    // the input is only read; FlatPlanes<T> of a const pointer would give the
+    // two tables different types
+    const FlatPlanes<typename S::T> in{const_cast<typename S::T *>(pop) + st.pop_off, (size_t)st.sp.N};
+    const FlatPlanes<typename S::T> out{pop_out + st.pop_off, (size_t)st.sp.N};
+    tile_step<L, S, FULL, MOM, NT, R>(st.sp, in, out, status, t.y, t.z, srho, smom);
 }
 
 // ---------------------------------------------------------------------------
@@ -1503,32 +1658,78 @@ cudaError_t Launch<L, S>::step_pipe(const StepParams &p, const void *pop, void *
 
 template <class L, class S>
 cudaError_t Launch<L, S>::batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,
-                                     float *rho, unsigned *status, const unsigned *step_base, unsigned k, bool full,
-                                     cudaStream_t st)
+                                     void *pop_out, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                                     bool full, cudaStream_t st)
 {
     auto *ptr = static_cast<typename S::T *>(pop);
+    auto *po = static_cast<typename S::T *>(pop_out);
     auto *r2 = reinterpret_cast<float2 *>(rho);
     // full: every replica relaxes fully and its StepParams::mom points at its
-    // moment planes, so the moment-fed pair of kernels runs
-    if (parity == 0) {
+    // moment planes, so the moment-fed pair of kernels runs.  Two arrays
+    // (kPush): the density pass reads pop in the natural layout.
+    auto pair = [&](auto dpar, auto cpar) {
+        constexpr int DP = decltype(dpar)::value, CP = decltype(cpar)::value;
         if (full) {
-            kern::k_density_batch<L, S, 0, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-            kern::k_collide_batch<L, S, 0, true, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+            kern::k_density_batch<L, S, DP, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+            kern::k_collide_batch<L, S, CP, true, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, po, r2, status,
+                                                                                 step_base, k);
         } else {
-            kern::k_density_batch<L, S, 0><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-            kern::k_collide_batch<L, S, 0, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
+            kern::k_density_batch<L, S, DP><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
+            kern::k_collide_batch<L, S, CP, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, po, r2, status,
+                                                                            step_base, k);
         }
-    } else {
-        if (full) {
-            kern::k_density_batch<L, S, 1, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-            kern::k_collide_batch<L, S, 1, true, true><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
-        } else {
-            kern::k_density_batch<L, S, 1><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, step_base, k);
-            kern::k_collide_batch<L, S, 1, false><<<ntiles, 128, 0, st>>>(reps, tiles, ptr, r2, status, step_base, k);
-        }
-    }
+    };
+    if (parity == 0) pair(std::integral_constant<int, 0>{}, std::integral_constant<int, 0>{});
+    else if (parity == 1) pair(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
+    else pair(std::integral_constant<int, 0>{}, std::integral_constant<int, kern::kPush>{});
     return cudaGetLastError();
 }
+
+// threads and rows per thread of the tiled step's blocks: 32 x 16 tiles (measured against
+// 32 x 32 of 256 or 512 threads and 32 x 8 or 32 x 16 of two rows a thread)
+constexpr int kTileThreads = 128, kTileRowsPerThread = 4;
+
+template <class L, class S>
+cudaError_t Launch<L, S>::step_tiled(const StepParams &p, const void *pop, void *pop_out, unsigned *status,
+                                     cudaStream_t st)
+{
+    if constexpr (L::D != 2) {
+        return cudaErrorNotSupported;
+    } else {
+        constexpr int NT = kTileThreads, R = kTileRowsPerThread;
+        using G = kern::TileGeom<NT, R>;
+        const dim3 g((p.nx + kern::kTileX - 1) / kern::kTileX, (p.ny + G::Y - 1) / G::Y);
+        const auto in = kern::plane_table(const_cast<typename S::T *>(static_cast<const typename S::T *>(pop)), L::Q, p.N);
+        const auto out = kern::plane_table(static_cast<typename S::T *>(pop_out), L::Q, p.N);
+        if (kern::full_relaxation<L>(p)) kern::k_step_tiled<L, S, true, true, NT, R><<<g, NT, 0, st>>>(p, in, out, status);
+        else kern::k_step_tiled<L, S, false, false, NT, R><<<g, NT, 0, st>>>(p, in, out, status);
+        return cudaGetLastError();
+    }
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::batch_step_tiled(const RepInfo *reps, const int4 *tiles, int ntiles, const void *pop,
+                                           void *pop_out, unsigned *status, const unsigned *step_base, unsigned k,
+                                           bool full, cudaStream_t st)
+{
+    if constexpr (L::D != 2) {
+        return cudaErrorNotSupported;
+    } else {
+        constexpr int NT = kTileThreads, R = kTileRowsPerThread;
+        auto *in = static_cast<const typename S::T *>(pop);
+        auto *out = static_cast<typename S::T *>(pop_out);
+        if (full)
+            kern::k_step_tiled_batch<L, S, true, true, NT, R><<<ntiles, NT, 0, st>>>(reps, tiles, in, out, status,
+                                                                                  step_base, k);
+        else
+            kern::k_step_tiled_batch<L, S, false, false, NT, R><<<ntiles, NT, 0, st>>>(reps, tiles, in, out, status,
+                                                                                    step_base, k);
+        return cudaGetLastError();
+    }
+}
+
+// rows of the tiles of the tiled step (the host cuts boxes into kTileX x rows)
+template <class L, class S> int Launch<L, S>::tile_rows() { return kern::TileGeom<kTileThreads, kTileRowsPerThread>::Y; }
 
 template <class L, class S>
 cudaError_t Launch<L, S>::init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st)

@@ -20,9 +20,17 @@ template <class L, class S> struct Launch {
     static cudaError_t step_pipe(const StepParams &p, const void *pop, void *pop_out, float *ring, unsigned *counters,
                                  int ring_slots, int lag, bool mom, unsigned *status, double wait_ms, int stall,
                                  cudaStream_t st);
+    // parity 0 / 1: in place in pop; kPush: read pop, write pop_out
     static cudaError_t batch_step(int parity, const RepInfo *reps, const int2 *tiles, int ntiles, void *pop,
-                                  float *rho, unsigned *status, const unsigned *step_base, unsigned k, bool full,
+                                  void *pop_out, float *rho, unsigned *status, const unsigned *step_base, unsigned k,
+                                  bool full, cudaStream_t st);
+    // tiled two-array step (2D lattices; cudaErrorNotSupported otherwise)
+    static cudaError_t step_tiled(const StepParams &p, const void *pop, void *pop_out, unsigned *status,
                                   cudaStream_t st);
+    static cudaError_t batch_step_tiled(const RepInfo *reps, const int4 *tiles, int ntiles, const void *pop,
+                                        void *pop_out, unsigned *status, const unsigned *step_base, unsigned k,
+                                        bool full, cudaStream_t st);
+    static int tile_rows();
     static cudaError_t init_rest(const StepParams &p, const float *rho_in, void *pop, cudaStream_t st);
     static cudaError_t gather(int parity, const StepParams &p, const void *pop, const int64_t *sites, int64_t n,
                               double *out, cudaStream_t st);

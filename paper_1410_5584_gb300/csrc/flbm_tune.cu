@@ -2,8 +2,8 @@
 // own state, keep the fastest, and remember the choice in a JSON file.
 //
 // Every candidate computes bitwise the same update (the two-kernel, slab
-// overlap and, with two arrays, pipelined schedules run the same per-site
-// arithmetic; the thread-block shape and the CUDA-graph length only change
+// overlap and, with two arrays, pipelined and tiled schedules run the same
+// per-site arithmetic; the thread-block shape and the CUDA-graph length only change
 // how the same kernels are launched), so tuning changes speed, never results.
 // The in-place fused schedule, which agrees only to rounding, is not a
 // candidate.
@@ -266,8 +266,13 @@ flbm_status time_steps(flbm_ctx *c, int warm, int steps, double *ms)
 std::vector<Settings> candidates(const flbm_ctx *c)
 {
     std::vector<Settings> out;
+    const bool tiled = c->streaming == FLBM_STREAM_TWO_ARRAYS && c->lat == FLBM_D2Q9;
     if (is_batch(c)) {
-        for (int g : {0, 4, 16, 64}) out.push_back({{"graph_steps", (double)g}});
+        for (int g : {0, 4, 16, 64})
+            out.push_back({{"schedule", (double)FLBM_SCHEDULE_TWO_KERNELS}, {"graph_steps", (double)g}});
+        if (tiled)
+            for (int g : {0, 4, 16, 64})
+                out.push_back({{"schedule", (double)FLBM_SCHEDULE_TILED}, {"graph_steps", (double)g}});
         return out;
     }
     const int axis = c->lat == FLBM_D2Q9 ? c->ny : c->nz;
@@ -286,6 +291,9 @@ std::vector<Settings> candidates(const flbm_ctx *c)
     // run the two-kernel step)
     if (c->streaming == FLBM_STREAM_TWO_ARRAYS)
         out.push_back({{"schedule", (double)FLBM_SCHEDULE_FUSED}, {"graph_steps", 0.0}, {"pipe_lag", 0.0}});
+    // the tiled step of a 2D box (one launch a step; bitwise the two-kernel update)
+    if (tiled)
+        for (int gs : {0, 16}) out.push_back({{"schedule", (double)FLBM_SCHEDULE_TILED}, {"graph_steps", (double)gs}});
     return out;
 }
 

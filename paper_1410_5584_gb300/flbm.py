@@ -42,7 +42,7 @@ OPT_STREAMING = 19
 OPT_TEST_GENERAL_COLLIDE = 20
 OPT_GHOST_NOISE = 21
 STREAMING = {"in_place": 0, "two_arrays": 1}
-SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2}
+SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2, "tiled": 3}
 OPT_LAMBDA_MODE = 1000
 OPT_RHO0_SPECIES = 2000
 OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF,
@@ -213,8 +213,8 @@ class _Context:
         optional JSON file of earlier choices."""
         path = None if cache is None else os.fsencode(cache)
         check(self._h, lib().flbm_autotune(self._h, int(steps), path))
-        keys = ("graph_steps",) if isinstance(self, Batch) else ("schedule", "slabs", "block_x", "block_y",
-                                                                 "graph_steps")
+        keys = ("schedule", "graph_steps") if isinstance(self, Batch) else ("schedule", "slabs", "block_x",
+                                                                            "block_y", "graph_steps")
         return {k: int(self.get_option(k)) for k in keys}
 
     def sf_sample(self):

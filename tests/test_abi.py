@@ -90,7 +90,7 @@ def test_launch_settings_are_validated_and_read_back(lib):
     v = ctypes.c_double()
     try:
         for key, bad in ((F.OPT_BLOCK_X, 48), (F.OPT_BLOCK_X, 256), (F.OPT_BLOCK_Y, 3), (F.OPT_BLOCK_Y, 8),
-                         (F.OPT_SCHEDULE, 3), (F.OPT_SLABS, 2), (F.OPT_SLABS, 4.5)):
+                         (F.OPT_SCHEDULE, 4), (F.OPT_SLABS, 2), (F.OPT_SLABS, 4.5)):
             assert lib.flbm_set_option(h, key, bad) == F.EINVAL, (key, bad)
         assert lib.flbm_set_option(h, F.OPT_BLOCK_X, 32) == F.OK
         assert lib.flbm_set_option(h, F.OPT_BLOCK_Y, 4) == F.OK
@@ -139,6 +139,41 @@ def test_batch_create_validates_replicas(lib):
         lib.flbm_destroy(v)                             # a view is not destroyed on its own
     finally:
         lib.flbm_destroy(h)
+
+
+def test_batch_streaming_and_schedule_options(lib):
+    """Batches stream through two arrays by default (twice the population
+    bytes of in place), take the streaming mode before their buffers exist,
+    and accept the two-kernel (1) and tiled (3) schedules only; a schedule
+    outside the enum is rejected on single boxes too (host logic only)."""
+    arr = (F.RepParams * 2)(F.RepParams(8, 6, 1, 1.0, 1.0, 1e-4, 0.1, 3, 1.0, 1.0),
+                            F.RepParams(5, 7, 1, 0.9, 1.1, 1e-5, 0.2, 4, 1.0, 0.8))
+    h = ctypes.c_void_p()
+    assert lib.flbm_batch_create(0, 2, arr, ctypes.byref(h)) == F.OK
+    try:
+        v = ctypes.c_double()
+        assert lib.flbm_get_option(h, F.OPT_STREAMING, ctypes.byref(v)) == F.OK and v.value == 1
+        pb2, rb = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.flbm_buffer_bytes(h, ctypes.byref(pb2), ctypes.byref(rb)) == F.OK
+        assert pb2.value == 2 * 2 * 9 * (48 + 35) * 4
+        assert lib.flbm_set_option(h, F.OPT_STREAMING, 2) == F.EINVAL
+        assert lib.flbm_set_option(h, F.OPT_STREAMING, 0) == F.OK
+        pb1 = ctypes.c_size_t()
+        assert lib.flbm_buffer_bytes(h, ctypes.byref(pb1), ctypes.byref(rb)) == F.OK
+        assert 2 * pb1.value == pb2.value
+        assert lib.flbm_get_option(h, F.OPT_STREAMING, ctypes.byref(v)) == F.OK and v.value == 0
+        for sched, want in ((0, F.EUNSUPPORTED), (2, F.EUNSUPPORTED), (3, F.OK), (1, F.OK), (4, F.EUNSUPPORTED)):
+            assert lib.flbm_set_option(h, F.OPT_SCHEDULE, sched) == want, sched
+        assert lib.flbm_set_option(h, F.OPT_SCHEDULE, 3) == F.OK
+        assert lib.flbm_get_option(h, F.OPT_SCHEDULE, ctypes.byref(v)) == F.OK and v.value == 3
+    finally:
+        lib.flbm_destroy(h)
+    g = F.flbm_create(0, 8, 6, 1, 1.0, 1.0, 1e-4, 0.5, 1)
+    try:
+        assert lib.flbm_set_option(g, F.OPT_SCHEDULE, 3) == F.OK
+        assert lib.flbm_set_option(g, F.OPT_SCHEDULE, 4) == F.EINVAL
+    finally:
+        lib.flbm_destroy(g)
 
 
 def _mcreate(lib, lat, ns, nx, ny, nz, tau, kT, G):
