@@ -32,6 +32,7 @@ struct flbm_mctx {
     // device buffers
     float *pop = nullptr;
     float4 *drho = nullptr;
+    float *d_mom = nullptr; // ns (D + 1) planes: the moment-fed pair's m_0 .. m_D (MStepParams::mom)
     unsigned *d_status = nullptr;
     double *d_obs = nullptr;      // ns * N + D * N doubles
     double *d_partials = nullptr; // per-block totals
@@ -387,6 +388,24 @@ flbm_status flbm_minit(flbm_mctx *c, const double *rho)
     return FLBM_OK;
 }
 
+// With two arrays and every non-conserved rate 1 (the old non-conserved
+// moments drop out of Eq. algorithm) the density pass also stores m_0 .. m_D
+// of every species and the collide reads those instead of the populations:
+// sets p.mom then.
+static flbm_status use_mmoments(flbm_mctx *c, MStepParams &p)
+{
+    p.mom = nullptr;
+    if (!two_arrays(c)) return FLBM_OK;
+    for (int s = 0; s < c->ns; s++)
+        for (int a = c->D + 1; a < c->Q; a++)
+            if (p.cm[s][a] != 0.0f) return FLBM_OK;
+    if (!c->d_mom)
+        MCUDA(c, cudaMalloc((void **)&c->d_mom, (size_t)c->ns * (c->D + 1) * (size_t)c->N * sizeof(float)),
+              "cudaMalloc(moment planes)");
+    p.mom = c->d_mom;
+    return FLBM_OK;
+}
+
 // One CUDA graph of graph_steps steps from `parity`; the collide reads the
 // noise counter as *d_gstep + k.
 flbm_status ensure_graph(flbm_mctx *c, int parity)
@@ -395,6 +414,7 @@ flbm_status ensure_graph(flbm_mctx *c, int parity)
     if (!c->d_gstep) MCUDA(c, cudaMalloc((void **)&c->d_gstep, sizeof(unsigned)), "cudaMalloc(graph step counter)");
     MStepParams p = make_mparams(c);
     p.step_dev = c->d_gstep;
+    if (flbm_status st = use_mmoments(c, p); st != FLBM_OK) return st;
     cudaGraph_t g = nullptr;
     MCUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     cudaError_t e = cudaSuccess;
@@ -437,7 +457,8 @@ flbm_status flbm_mstep(flbm_mctx *c, int64_t n)
         }
     }
     for (int64_t k = 0; k < n; k++) {
-        const MStepParams p = make_mparams(c);
+        MStepParams p = make_mparams(c);
+        if ((st = use_mmoments(c, p)) != FLBM_OK) return st;
         const int parity = c->parity;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
         if (c->timing) {
@@ -761,6 +782,7 @@ flbm_status flbm_mrestore(flbm_mctx *c, const void *buf, size_t bytes)
     c->parity = (int)h.parity;
     c->faulted = false;
     c->initialised = true;
+    drop_graphs(c); // captured steps hold the old parameters by value
     return FLBM_OK;
 }
 
@@ -773,6 +795,7 @@ void flbm_mdestroy(flbm_mctx *c)
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     cudaFree(c->pop);
     cudaFree(c->drho);
+    cudaFree(c->d_mom);
     cudaFree(c->d_status);
     drop_graphs(c);
     cudaFree(c->d_gstep);

@@ -48,6 +48,10 @@ struct MStepParams {
     float rho0[kMaxSpecies];           // reference densities (base of the stored deviations)
     uint32_t key0, key1, step;        // step: the noise counter, or its offset from *step_dev
     const unsigned *step_dev;         // NULL, or a device word the counter is read from (graph replays)
+    float *mom;                       // NULL, or NS (D + 1) planes of N floats: m_0 .. m_D of each
+                                      // species, written by the density pass and read by the collide
+                                      // in place of the populations (every non-conserved rate 1, two
+                                      // arrays)
 };
 
 template <class T> struct MPlanes {
@@ -149,7 +153,9 @@ __device__ __forceinline__ void load_site(const P &planes, const kern::Nbr &nb, 
     });
 }
 
-template <class L, int NS, int PARITY>
+// MOM: also stores m_0 .. m_D of every species into p.mom (the moment-fed
+// collide's input).
+template <class L, int NS, int PARITY, bool MOM = false>
 __global__ void __launch_bounds__(kSiteBlockMax) k_mdensity(const MStepParams p, const MPlanes<const float> planes,
                                                             float4 *__restrict__ drho)
 {
@@ -166,6 +172,12 @@ __global__ void __launch_bounds__(kSiteBlockMax) k_mdensity(const MStepParams p,
         // the collide kernel computes its own densities with this same expression
         Transform<L>::forward(d[s], m);
         r[s] = m[0];
+        if constexpr (MOM) {
+            static_for<L::D + 1>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                p.mom[(size_t)(s * (L::D + 1) + a) * (size_t)p.N + nb.at(0, 0, 0)] = m[a];
+            });
+        }
     });
     drho[nb.at(0, 0, 0)] = make_float4(r[0], r[1], r[2], r[3]);
 }
@@ -190,14 +202,17 @@ template <class L, int NS> constexpr size_t collide_smem(int threads)
 // then each species in turn is collided and streamed.  No barrier: a thread
 // reads back only its own slots.
 // 128 registers (16 warps an SM); three species are held to 96 (20 warps), measured
-// 2 % faster at 256^3 despite a 48-byte spill, which costs four species 6 %
-template <class L, int NS, int PARITY>
+// 2 % faster at 256^3 despite a 48-byte spill, which costs four species 6 %.
+// MOM (every non-conserved rate 1, so that the old non-conserved moments drop
+// out of Eq. algorithm): m_0 .. m_D of every species come from the density
+// pass's planes p.mom instead of the populations, which are not read.
+template <class L, int NS, int PARITY, bool MOM = false>
 __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
     k_mcollide(const MStepParams p, const MPlanes<float> planes, const MPlanes<float> out,
                const float4 *__restrict__ drho, unsigned *__restrict__ status)
 {
     constexpr int Q = L::Q, D = L::D;
-    constexpr bool PARK = kParkMoments<NS>;
+    constexpr bool PARK = kParkMoments<NS> && !MOM;
     extern __shared__ float park[];
     const int nthr = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -210,8 +225,17 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
     // 1. loads and moments of every species (Eq. modes-discrete; the density
     // with the same expression as the density kernel)
     float mc[NS][4], rs[NS];
-    float mreg[PARK ? 1 : NS][Q];
-    static_for<NS>([&](auto sc) {
+    float mreg[PARK || MOM ? 1 : NS][Q];
+    if constexpr (MOM) {
+        static_for<NS>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            static_for<D + 1>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                mc[s][a] = __ldg(p.mom + (size_t)(s * (D + 1) + a) * (size_t)p.N + site);
+            });
+            rs[s] = p.rho0[s] + mc[s][0];
+        });
+    } else static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         float d[Q], m[Q];
         static_for<Q>([&](auto ic) {
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
             constexpr int a = decltype(ac)::value;
             if constexpr (a <= D) mc[s][a] = m[a];
             if constexpr (PARK) park[(s * Q + a) * nthr + tid] = m[a];
-            else mreg[PARK ? 0 : s][a] = m[a];
+            else mreg[PARK || MOM ? 0 : s][a] = m[a];
         });
         rs[s] = p.rho0[s] + m[0];
     });
@@ -268,12 +292,14 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
         });
     });
 
-    // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep)
+    // 3. baricentric velocity with the half-force shift (Eq. lattice finalstep).
+    // Here and in step 5 every rounding is explicit, so that the population-
+    // reading and the moment-fed instances give the same bits.
     float rt = 0.0f;
     bool bad = false;
     static_for<NS>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        rt += rs[s];
+        rt = __fadd_rn(rt, rs[s]);
         bad |= !(rs[s] > 0.0f);
     });
     if (bad || !isfinite(rt)) atomicOr(status, kStatusNonFinite);
@@ -284,9 +310,9 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
         float j = 0.0f;
         static_for<NS>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
-            j += mc[s][1 + d] + 0.5f * rs[s] * acc[s][d];
+            j = __fadd_rn(j, __fmaf_rn(__fmul_rn(0.5f, rs[s]), acc[s][d], mc[s][1 + d]));
         });
-        u[d] = j * irt;
+        u[d] = __fmul_rn(j, irt);
     });
 
     // 4. the momentum Gaussians of every species: modes 1 .. D, positions
@@ -325,17 +351,24 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
         float m[Q];
         static_for<Q>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
-            if constexpr (PARK) m[a] = park[(s * Q + a) * nthr + tid];
-            else m[a] = mreg[PARK ? 0 : s][a];
+            if constexpr (MOM) {
+                if constexpr (a <= D) m[a] = mc[s][a];
+            } else if constexpr (PARK) {
+                m[a] = park[(s * Q + a) * nthr + tid];
+            } else {
+                m[a] = mreg[PARK || MOM ? 0 : s][a];
+            }
         });
         const float irs = __frcp_rn(rs[s]);
+        const float lrs = __fmul_rn(p.lam_d, rs[s]), hrs = __fmul_rn(p.hlam_d, rs[s]);
         float v[3] = {0.0f, 0.0f, 0.0f};
         static_for<D>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
             constexpr int a = 1 + d;
-            const float R = p.lam_d * (rs[s] * u[d] - m[a]) + p.hlam_d * rs[s] * acc[s][d] + xi[s][d];
-            v[d] = (m[a] + 0.5f * R) * irs;
-            m[a] += R;
+            // R = lambdabar_d (rho^s u - j^s) + (1 - lambdabar_d / 2) rho^s a^s + xi^s
+            const float R = __fmaf_rn(lrs, u[d], __fmaf_rn(-p.lam_d, m[a], __fmaf_rn(hrs, acc[s][d], xi[s][d])));
+            v[d] = __fmul_rn(__fmaf_rn(0.5f, R, m[a]), irs);
+            m[a] = __fadd_rn(m[a], R);
         });
         // the non-conserved modes' Gaussians (block 0 drawn again: its
         // momentum positions were used in step 4)
@@ -363,7 +396,10 @@ __global__ void __launch_bounds__(kSiteBlockMax, NS == 3 ? 5 : 4)
         });
         static_for<Q - D - 1>([&](auto kc) {
             constexpr int a = decltype(kc)::value + D + 1;
-            float t = fmaf(p.cm[s][a], m[a], p.cxi[s][a] * (sq[s] * g[a]));
+            // MOM: cm = 0 (rate 1), so the old moment, never formed, drops out
+            float t;
+            if constexpr (MOM) t = p.cxi[s][a] * (sq[s] * g[a]);
+            else t = fmaf(p.cm[s][a], m[a], p.cxi[s][a] * (sq[s] * g[a]));
             if constexpr (a < Closure<L>::kGhost) t = fmaf(rs[s], fmaf(p.ceq[s][a], X[a], p.cphi[s][a] * Y[a]), t);
             mu[a] = t;
         });
@@ -597,7 +633,8 @@ cudaError_t MLaunch<L, NS>::density(int parity, const MStepParams &p, const floa
 {
     const dim3 b = mkern::msite_block(p), g = mkern::msite_grid(p, b);
     const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
-    if (parity == 0) mkern::k_mdensity<L, NS, 0><<<g, b, 0, st>>>(p, planes, drho);
+    if (p.mom && parity == 0) mkern::k_mdensity<L, NS, 0, true><<<g, b, 0, st>>>(p, planes, drho);
+    else if (parity == 0) mkern::k_mdensity<L, NS, 0><<<g, b, 0, st>>>(p, planes, drho);
     else mkern::k_mdensity<L, NS, 1><<<g, b, 0, st>>>(p, planes, drho);
     return cudaGetLastError();
 }
@@ -610,7 +647,10 @@ cudaError_t MLaunch<L, NS>::collide(int parity, const MStepParams &p, float *pop
     const auto planes = mkern::mplanes(pop, NS, L::Q, p.N);
     const auto out = parity == kStreamPush ? mkern::mplanes(pop_out, NS, L::Q, p.N) : planes;
     const size_t smem = mkern::collide_smem<L, NS>(b.x * b.y);
-    if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, smem, st>>>(p, planes, out, drho, status);
+    // the moment-fed pair runs with two arrays only
+    if (p.mom && parity == kStreamPush)
+        mkern::k_mcollide<L, NS, kStreamPush, true><<<g, b, 0, st>>>(p, planes, out, drho, status);
+    else if (parity == 0) mkern::k_mcollide<L, NS, 0><<<g, b, smem, st>>>(p, planes, out, drho, status);
     else if (parity == 1) mkern::k_mcollide<L, NS, 1><<<g, b, smem, st>>>(p, planes, out, drho, status);
     else mkern::k_mcollide<L, NS, kStreamPush><<<g, b, smem, st>>>(p, planes, out, drho, status);
     return cudaGetLastError();

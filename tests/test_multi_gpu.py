@@ -355,15 +355,22 @@ def test_three_species_structure_factors_against_lattice_theory():
 
 @pytest.mark.parametrize("lat,ns,shape", [(D2Q9, 3, (1, 17, 33)), (D2Q9, 2, (1, 2, 2)), (D3Q19, 4, (5, 7, 9)),
                                           (D3Q19, 3, (2, 2, 2))])
-def test_streaming_modes_are_bitwise_identical(lat, ns, shape):
+@pytest.mark.parametrize("full", [False, True])
+def test_streaming_modes_are_bitwise_identical(lat, ns, shape, full):
     """In-place and two-array streaming of the N-species update give the same
-    bits: populations after odd and even step counts, moments, S(k)."""
+    bits: populations after odd and even step counts, moments, S(k).  With
+    every rate 1 (full) the two-array run is the moment-fed pair (the collide
+    reads m_0 .. m_D from the density pass, not the populations) and the
+    in-place run the population-reading collide: the same update, bit for bit
+    on D2Q9 and to a few float roundings on D3Q19 (measured: up to 3e-8 on
+    populations of 0.3 after a step, as close to the oracle either way)."""
     nz, ny, nx = shape
     G = _couplings(ns, 0.6, seed=12)
     f0 = _state(lat, ns, shape, seed=13)
+    taus = [1.0] * ns if full else TAUS[:ns]
     runs = []
     for mode in ("in_place", "two_arrays"):
-        gp = MultiLattice(lat, ns, nx, ny, nz, TAUS[:ns], 1e-4, G, 5, streaming=mode)
+        gp = MultiLattice(lat, ns, nx, ny, nz, taus, 1e-4, G, 5, streaming=mode)
         gp.set_populations(f0, step=2)
         got = []
         for n in (1, 2, 4):
@@ -374,7 +381,13 @@ def test_streaming_modes_are_bitwise_identical(lat, ns, shape):
         runs.append(got)
     for a, b in zip(runs[0], runs[1]):
         for x, y in zip(a, b):
-            assert np.array_equal(x, y)
+            if full and lat == D3Q19:
+                # populations to 2e-7 of their size; velocities and S(k), small
+                # differences of large numbers, to 1e-4 of theirs
+                tol = 2e-7 if np.shape(x) == f0.shape else 1e-4
+                assert np.max(np.abs(x - y)) <= tol * np.max(np.abs(y))
+            else:
+                assert np.array_equal(x, y)
 
 
 def test_checkpoints_move_between_streaming_modes():
@@ -453,3 +466,19 @@ def test_graph_steps_match_direct_launches(mode):
         assert gp.step_count == 22
         runs.append(gp.get_populations())
     assert np.array_equal(runs[0], runs[1])
+
+
+@pytest.mark.parametrize("lat,ns,shape", [(D2Q9, 3, (1, 23, 37)), (D3Q19, 3, (7, 6, 13)), (D3Q19, 4, (5, 4, 6))])
+def test_moment_fed_pair_matches_oracle(lat, ns, shape):
+    """Every rate 1 with two arrays: the moment-fed pair against the FP64
+    oracle, element by element, 3 steps."""
+    nz, ny, nx = shape
+    G = _couplings(ns, 0.6, seed=21)
+    f0 = _state(lat, ns, shape, seed=22)
+    g = MultiLattice(lat, ns, nx, ny, nz, [1.0] * ns, 1e-4, G, 9)
+    o = oracle.MultiOracle(lat, ns, nx, ny, nz, [1.0] * ns, 1e-4, G, 9)
+    g.set_populations(f0, step=4)
+    o.set_f(f0, step=4)
+    g.step(3)
+    o.step(3)
+    assert _rel(g.get_populations(), o.get_f()) <= 3e-6
