@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <unistd.h>
 #include <vector>
 
 #include "flbm_ctx.h"
@@ -182,13 +183,13 @@ flbm_status ensure_pipe(flbm_ctx *c)
     return FLBM_OK;
 }
 
-// f(lo, hi) over [0, n) in contiguous pieces on up to eight host threads (one
-// piece when n is small): the host side of the copies between the caller's
-// buffers and the pinned staging buffer.
-template <class F> void host_parallel(size_t n, F &&f)
+// f(lo, hi) over [0, n) in contiguous pieces on up to `most` host threads
+// (one piece when n is small): the host side of the copies between the
+// caller's buffers and the pinned staging buffer, and of mapping pages.
+template <class F> void host_parallel(size_t n, F &&f, unsigned most = 8)
 {
     const unsigned hw = std::thread::hardware_concurrency();
-    const unsigned t = std::min(8u, hw ? hw : 1u);
+    const unsigned t = std::min(most, hw ? hw : 1u);
     if (t <= 1 || n < ((size_t)1 << 18)) {
         f((size_t)0, n);
         return;
@@ -242,6 +243,50 @@ flbm_status d2h_staged(flbm_ctx *c, void *dst, const void *src, size_t bytes)
     cudaEventDestroy(ev[1]);
     if (e != cudaSuccess) return cuda_fail(c, e, "staged D2H copy");
     return FLBM_OK;
+}
+
+// Whether kernels may store straight into the caller's pageable host memory:
+// on a CPU-GPU pair that shares page tables (cudaDevAttrPageableMemoryAccess
+// with host page tables, as Grace with Blackwell over NVLink-C2C) device
+// stores reach any mapped host page coherently.  Queried once per device.
+bool pageable_direct()
+{
+    static int cached[64];
+    static bool known[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!known[dev]) {
+        int a = 0, b = 0;
+        if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
+            cudaGetLastError();
+            a = b = 0;
+        }
+        cached[dev] = a && b;
+        known[dev] = true;
+    }
+    return cached[dev] != 0;
+}
+
+// Map every page of a host output buffer before a kernel stores into it: a
+// device store to a page the OS has not mapped yet goes through a slow fault
+// path (on GB300 about 50 times slower than into a mapped page), while host
+// threads map pages quickly.  One byte a page is written (the buffer is
+// output only).
+void map_pages(void *buf, size_t bytes)
+{
+    const long pg = sysconf(_SC_PAGESIZE);
+    const size_t page = pg > 0 ? (size_t)pg : 4096;
+    volatile unsigned char *b = static_cast<volatile unsigned char *>(buf);
+    host_parallel(bytes, [&](size_t lo, size_t hi) {
+        // the pages that start in [lo, hi), and the first byte's page
+        size_t k = lo == 0 ? 0 : ((lo + page - 1) / page) * page;
+        for (; k < hi; k += page) b[k] = 0;
+        if (hi == bytes && bytes > 0) b[bytes - 1] = 0; // the last page, when the buffer starts mid-page
+    }, 16);
 }
 
 flbm_status ensure_stage(flbm_ctx *c)
@@ -533,6 +578,9 @@ flbm_status flbm_set_option(flbm_ctx *c, int key, double v)
     } else if (key == FLBM_OPT_GHOST_NOISE) {
         if (c->batch) return fail(c, FLBM_EUNSUPPORTED, "the population-space noise is for single boxes");
         c->ghost_noise = v != 0.0;
+    } else if (key == FLBM_OPT_DIRECT_HOST) {
+        if (v != 0.0 && v != 1.0) return fail(c, FLBM_EINVAL, "direct host stores must be 0 or 1");
+        c->direct_host = (int)v;
     } else if (key == FLBM_OPT_SF_AXIS) {
         if (v != 0.0 && v != 1.0 && v != 2.0) return fail(c, FLBM_EINVAL, "axis must be 0, 1 or 2");
         if ((int)v >= c->D) return fail(c, FLBM_EINVAL, "axis %d does not exist on this lattice", (int)v);
@@ -606,6 +654,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_NOISE_RHO: *value = c->noise_ref; break;
     case FLBM_OPT_FORCE_VELOCITY: *value = c->force_velocity; break;
     case FLBM_OPT_GHOST_NOISE: *value = c->ghost_noise; break;
+    case FLBM_OPT_DIRECT_HOST: *value = c->direct_host; break;
     case FLBM_OPT_SF_AXIS: *value = c->sf_axis; break;
     case FLBM_OPT_KERNEL_TIMING: *value = c->timing ? 1.0 : 0.0; break;
     case FLBM_OPT_SCHEDULE: *value = c->schedule; break;
@@ -1022,7 +1071,13 @@ flbm_status flbm_step(flbm_ctx *c, int64_t n)
     }
     if (sched == FLBM_SCHEDULE_TILED) return step_tiled(c, n);
     StepParams p = make_params(c);
-    if (sched == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) return step_overlap(c, n, p);
+    if (sched == FLBM_SCHEDULE_OVERLAP && overlap_slabs(c) >= 3) {
+        // at full relaxation the slabs run the moment-fed pair: a density slab
+        // rewrites its moment planes only after the collisions that read them
+        // (those of its own slab) are done, as for its densities
+        if (flbm_status st = use_moments(c, p); st != FLBM_OK) return st;
+        return step_overlap(c, n, p);
+    }
     if (sched == FLBM_SCHEDULE_FUSED) {
         flbm_status st = ensure_pipe(c);
         if (st != FLBM_OK) return st;
@@ -1101,12 +1156,28 @@ flbm_status flbm_moments(flbm_ctx *c, double *rho_a, double *rho_b, double *u, d
     const StepParams p = make_params(c);
     if ((st = density_now(c, p)) != FLBM_OK) return st;
     double *ra = c->d_obs, *rb = c->d_obs + c->N, *uu = c->d_obs + 2 * c->N;
+    // with shared page tables the kernel stores the fields straight into the
+    // caller's buffers (their pages mapped first); otherwise into device
+    // scratch, copied out through the pinned staging buffer below
+    const bool direct = c->direct_host && pageable_direct();
+    if (direct) {
+        if (rho_a) map_pages(rho_a, c->N * sizeof(double));
+        if (rho_b) map_pages(rho_b, c->N * sizeof(double));
+        if (u) map_pages(u, (size_t)c->D * c->N * sizeof(double));
+        ra = rho_a;
+        rb = rho_b;
+        uu = u;
+    }
     int nb = 0;
     FLBM_CUDA(c, launch_observables(c->lat, c->storage, layout_parity(c), p, cur_pop(c), c->rho, rho_a ? ra : nullptr,
                                     rho_b ? rb : nullptr, u ? uu : nullptr, c->d_partials, &nb, c->stream),
               "observables kernel launch");
     FLBM_CUDA(c, launch_sum_partials(c->d_partials, nb, c->d_cons, c->stream), "reduction kernel launch");
     if ((st = sync_and_check(c)) != FLBM_OK) return st;
+    if (direct) {
+        if (cons) FLBM_CUDA(c, cudaMemcpy(cons, c->d_cons, 5 * sizeof(double), cudaMemcpyDeviceToHost), "D2H cons");
+        return FLBM_OK;
+    }
     if ((st = ensure_stage(c)) != FLBM_OK) return st;
     if (rho_a && (st = d2h_staged(c, rho_a, ra, c->N * sizeof(double))) != FLBM_OK) return st;
     if (rho_b && (st = d2h_staged(c, rho_b, rb, c->N * sizeof(double))) != FLBM_OK) return st;

@@ -21,6 +21,7 @@ struct flbm_ctx {
     double lam[2][flbm::kMaxQ] = {};
     int storage = FLBM_STORE_F32, sdf = 1, noise_ref = 0, force_velocity = 0, sf_axis = 0;
     int ghost_noise = 0; // FLBM_OPT_GHOST_NOISE
+    int direct_host = 1; // FLBM_OPT_DIRECT_HOST
     int schedule = FLBM_SCHEDULE_TWO_KERNELS;
     int streaming = FLBM_STREAM_TWO_ARRAYS; // FLBM_OPT_STREAMING
     double wait_limit_ms = 2000.0;

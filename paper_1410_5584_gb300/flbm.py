@@ -41,6 +41,7 @@ OPT_BLOCK_Y = 18
 OPT_STREAMING = 19
 OPT_TEST_GENERAL_COLLIDE = 20
 OPT_GHOST_NOISE = 21
+OPT_DIRECT_HOST = 22
 STREAMING = {"in_place": 0, "two_arrays": 1}
 SCHEDULE = {"fused": 0, "two_kernels": 1, "overlap": 2, "tiled": 3}
 OPT_LAMBDA_MODE = 1000
@@ -52,7 +53,8 @@ OPTION_NAMES = {"storage": OPT_STORAGE, "lambda_d": OPT_LAMBDA_D, "sdf": OPT_SDF
                 "wait_limit_ms": OPT_WAIT_LIMIT_MS, "test_stall": OPT_TEST_STALL,
                 "pipe_lag": OPT_PIPE_LAG, "graph_steps": OPT_GRAPH_STEPS, "slabs": OPT_SLABS,
                 "block_x": OPT_BLOCK_X, "block_y": OPT_BLOCK_Y, "streaming": OPT_STREAMING,
-                "test_general_collide": OPT_TEST_GENERAL_COLLIDE, "ghost_noise": OPT_GHOST_NOISE}
+                "test_general_collide": OPT_TEST_GENERAL_COLLIDE, "ghost_noise": OPT_GHOST_NOISE,
+                "direct_host": OPT_DIRECT_HOST}
 
 
 class RepParams(ctypes.Structure):

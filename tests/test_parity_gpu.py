@@ -5,6 +5,8 @@ Tolerances (element by element, relative to max |f|): 1e-6 per step and 1e-4
 after 1000 steps for float storage; the 16-bit formats are bounded by their
 rounding of the stored deviation (2^-11 relative for half, 2^-8 for bfloat16).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -602,19 +604,34 @@ def test_graph_steps_match_direct_launches(lat, shape, mode):
 
 
 @pytest.mark.parametrize("shape", [(50, 60, 70), (3, 5, 7)])
-def test_moments_copy_out_through_the_staging_buffer(shape):
+@pytest.mark.parametrize("direct", [0, 1])
+def test_moments_copy_out_through_the_staging_buffer(shape, direct):
     """flbm_moments hands the fields to the caller's (pageable) buffers through
-    the pinned staging buffer in alternating chunks, copied on host threads:
-    on a box whose fields span several chunks (210,000 sites) and on a tiny
-    one, the densities come back as the initial field (float-rounded) and the
-    velocity of the rest state with G = 0 is exactly zero."""
+    the pinned staging buffer in alternating chunks, copied on host threads
+    (direct_host 0), or, where the GPU shares the host's page tables, stored
+    by the kernel straight into them (direct_host 1, the default): on a box
+    whose fields span several chunks (210,000 sites) and on a tiny one, the
+    densities come back as the initial field (float-rounded), the velocity of
+    the rest state is exactly zero, and after a few noisy steps both routes
+    give the same bits, also into arrays viewed at an odd offset."""
     nz, ny, nx = shape
     rng = np.random.default_rng(4)
     ra = rng.uniform(0.5, 1.5, size=shape).astype(np.float32).astype(np.float64)
     rb = rng.uniform(0.2, 0.9, size=shape).astype(np.float32).astype(np.float64)
-    g = Lattice(D3Q19, nx, ny, nz, 1.0, 1.0, 0.0, 0.0, 1, rho0_a=1.0, rho0_b=0.55)
+    g = Lattice(D3Q19, nx, ny, nz, 1.0, 1.0, 1e-4, 0.0, 1, rho0_a=1.0, rho0_b=0.55, direct_host=direct)
     g.init(ra, rb)
     fa, fb, u, cons = g.moments()
     assert np.max(np.abs(fa - ra)) <= 1e-6 and np.max(np.abs(fb - rb)) <= 1e-6
     assert np.all(u == 0.0)
     assert cons[0] == pytest.approx(ra.sum(), rel=1e-6) and cons[1] == pytest.approx(rb.sum(), rel=1e-6)
+    # a few noisy steps; then the other route into buffers that start 8 bytes
+    # past an allocation (not page-aligned)
+    g.step(3)
+    a = g.moments()
+    g.set_option("direct_host", 1 - direct)
+    n = nx * ny * nz
+    big = np.zeros(5 * n + 3)
+    out = [big[1:1 + n], big[2 + n:2 + 2 * n], big[3 + 2 * n:3 + 5 * n], np.empty(5)]
+    F.check(g._h, F.lib().flbm_moments(g._h, *[o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for o in out]))
+    assert np.array_equal(out[0], a[0].ravel()) and np.array_equal(out[1], a[1].ravel())
+    assert np.array_equal(out[2], a[2].ravel()) and np.array_equal(out[3], a[3])
