@@ -2,6 +2,7 @@
 // ownership, the step loop, observables, checkpoints and error reporting.
 // Every entry point catches its own failures and returns an flbm_status.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -251,24 +252,22 @@ flbm_status d2h_staged(flbm_ctx *c, void *dst, const void *src, size_t bytes)
 // stores reach any mapped host page coherently.  Queried once per device.
 bool pageable_direct()
 {
-    static int cached[64];
-    static bool known[64];
+    static std::atomic<int> cached[64]; // 0 not asked yet, 1 no, 2 yes
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
         return false;
     }
-    if (!known[dev]) {
+    if (cached[dev].load() == 0) {
         int a = 0, b = 0;
         if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
             cudaGetLastError();
             a = b = 0;
         }
-        cached[dev] = a && b;
-        known[dev] = true;
+        cached[dev].store(a && b ? 2 : 1);
     }
-    return cached[dev] != 0;
+    return cached[dev].load() == 2;
 }
 
 // Map every page of a host output buffer before a kernel stores into it: a
