@@ -285,7 +285,7 @@ void map_pages(void *buf, size_t bytes)
         size_t k = lo == 0 ? 0 : ((lo + page - 1) / page) * page;
         for (; k < hi; k += page) b[k] = 0;
         if (hi == bytes && bytes > 0) b[bytes - 1] = 0; // the last page, when the buffer starts mid-page
-    }, 16);
+    });
 }
 
 flbm_status ensure_stage(flbm_ctx *c)
@@ -762,7 +762,7 @@ flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
                 }
                 to[k] = (float)r;
             }
-        });
+        }, 16);
         if (!bad.empty()) {
             const int64_t k = *std::min_element(bad.begin(), bad.end());
             return fail(c, FLBM_EINVAL, "initial density %g at site %lld is not positive", from ? from[k] : r0,
