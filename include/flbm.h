@@ -168,13 +168,14 @@ enum {
                                     general collide, so it is slower than the default at tau = 1,
                                     and the fused schedule with two arrays runs the two-kernel
                                     step while it is on */
-    FLBM_OPT_DIRECT_HOST = 22,   /* how flbm_moments hands its fields to the caller's buffers.
-                                    1 (default): where the GPU shares the host's page tables
-                                    (cudaDevAttrPageableMemoryAccess, as Grace with Blackwell), the
-                                    observables kernel stores them straight into the caller's
-                                    memory after host threads have mapped its pages; elsewhere as
-                                    0.  0: device scratch copied out through a pinned staging
-                                    buffer in alternating chunks */
+    FLBM_OPT_DIRECT_HOST = 22,   /* how flbm_init and flbm_moments move fields between the caller's
+                                    arrays and the device.  1 (default): where the GPU shares the
+                                    host's page tables (cudaDevAttrPageableMemoryAccess, as Grace with
+                                    Blackwell), kernels read the initial densities and store the
+                                    moments straight from and into the caller's memory (the output
+                                    arrays' pages mapped by host threads first); elsewhere as 0.
+                                    0: through a pinned staging buffer (conversion on host threads;
+                                    the moments in alternating chunks) */
     FLBM_OPT_TEST_GENERAL_COLLIDE = 20, /* test hook: 1 keeps the general collide kernel even when
                                     every non-conserved rate is 1, where a kernel that skips those
                                     modes' projections runs by default (the two agree to rounding;

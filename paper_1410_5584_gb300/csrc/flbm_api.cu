@@ -741,6 +741,32 @@ flbm_status flbm_init(flbm_ctx *c, const double *rho_a, const double *rho_b)
     if (is_batch(c)) return batch_init(c, rho_a, rho_b);
     flbm_status st = ensure_buffers(c);
     if (st != FLBM_OK) return st;
+    if (c->direct_host && pageable_direct()) {
+        // the densities read by a kernel straight from the caller's arrays and
+        // checked there; nothing of the state changes before they pass
+        if (!c->d_bad) FLBM_CUDA(c, cudaMalloc((void **)&c->d_bad, 2 * sizeof(unsigned long long)), "cudaMalloc");
+        FLBM_CUDA(c, cudaMemsetAsync(c->d_bad, 0xFF, 2 * sizeof(unsigned long long), c->stream), "cudaMemset");
+        FLBM_CUDA(c, launch_densities_from_host(rho_a, rho_b, c->rho0[0], c->rho0[1], c->N, c->rho, c->d_bad, c->stream),
+                  "density read kernel launch");
+        unsigned long long bad[2];
+        FLBM_CUDA(c, cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream), "D2H check");
+        FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        for (int s = 0; s < 2; s++)
+            if (bad[s] != ~0ull) {
+                const double *from = s == 0 ? rho_a : rho_b;
+                return fail(c, FLBM_EINVAL, "initial density %g at site %lld is not positive",
+                            from ? from[bad[s]] : c->rho0[s], (long long)bad[s]);
+            }
+        const StepParams p = make_params(c);
+        FLBM_CUDA(c, launch_init_rest(c->lat, c->storage, p, c->rho, c->pop, c->stream), "init kernel launch");
+        FLBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "status reset");
+        c->step = 0;
+        c->parity = 0;
+        c->faulted = false;
+        c->timed_out = false;
+        c->initialised = true;
+        return FLBM_OK;
+    }
     if ((st = ensure_stage(c)) != FLBM_OK) return st;
     // previous asynchronous work may still read the staging buffer
     FLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -1444,6 +1470,7 @@ void flbm_destroy(flbm_ctx *c)
     free_sfk(c);
     free_cap(c);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->d_bad) cudaFree(c->d_bad);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_dep) cudaEventDestroy(e);
     if (c->stream_d) cudaStreamDestroy(c->stream_d);

@@ -78,6 +78,7 @@ struct flbm_ctx {
     int64_t cap_count = 0;
     int cap_xl = 0, cap_xg = 0;
     float *h_stage = nullptr;     // pinned staging, 2 * N floats
+    unsigned long long *d_bad = nullptr; // first invalid initial density of each species (direct reads)
     // per-kernel event timing (FLBM_OPT_KERNEL_TIMING)
     struct TimingMark {
         size_t start, end; // ev_pool indices

@@ -94,6 +94,24 @@ __global__ void __launch_bounds__(256) k_dft_accumulate(int D, int n_axis, doubl
     }
 }
 
+// Float densities of both species from the caller's double arrays, read
+// straight from host memory (NULL: uniform rho0); the smallest index of a
+// value that is not positive and finite goes to *bad (left as it is when
+// there is none).
+__global__ void k_densities_from_host(const double *__restrict__ ra, const double *__restrict__ rb, double r0a,
+                                      double r0b, long long n, float *__restrict__ out,
+                                      unsigned long long *__restrict__ bad)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double a = ra ? ra[k] : r0a, b = rb ? rb[k] : r0b;
+        const bool oka = a > 0.0 && isfinite(a), okb = b > 0.0 && isfinite(b);
+        if (!oka) atomicMin(bad, (unsigned long long)k);
+        if (!okb) atomicMin(bad + 1, (unsigned long long)k);
+        out[k] = (float)a;
+        out[n + k] = (float)b;
+    }
+}
+
 __global__ void k_add_u32(unsigned *p, unsigned v) { *p += v; }
 __global__ void k_set_u32(unsigned *p, unsigned v) { *p = v; }
 
@@ -102,6 +120,19 @@ __global__ void k_set_u32(unsigned *p, unsigned v) { *p = v; }
 cudaError_t launch_add_u32(unsigned *p, unsigned v, cudaStream_t stream)
 {
     k_add_u32<<<1, 1, 0, stream>>>(p, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_densities_from_host(const double *rho_a, const double *rho_b, double rho0_a, double rho0_b,
+                                       int64_t n, float *out, unsigned long long *bad, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long want = (n + 255) / 256, most = (long long)sms * 8;
+    k_densities_from_host<<<(unsigned)(want < most ? (want > 0 ? want : 1) : most), 256, 0, stream>>>(
+        rho_a, rho_b, rho0_a, rho0_b, (long long)n, out, bad);
     return cudaGetLastError();
 }
 

@@ -635,3 +635,30 @@ def test_moments_copy_out_through_the_staging_buffer(shape, direct):
     F.check(g._h, F.lib().flbm_moments(g._h, *[o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for o in out]))
     assert np.array_equal(out[0], a[0].ravel()) and np.array_equal(out[1], a[1].ravel())
     assert np.array_equal(out[2], a[2].ravel()) and np.array_equal(out[3], a[3])
+
+
+@pytest.mark.parametrize("direct", [0, 1])
+def test_init_reads_the_densities_and_rejects_bad_ones(direct):
+    """flbm_init through either route (kernels reading the caller's arrays
+    directly, or host threads through the staging buffer) gives the same rest
+    state; a density that is not positive and finite is refused with the
+    first bad site of its species, leaving the state as it was."""
+    shape = (9, 10, 11)
+    ra = inputs.perturbed_density(shape, 1.0, 1e-3, 5, 0)
+    rb = inputs.perturbed_density(shape, 0.7, 1e-3, 5, 1)
+    ref = Lattice(D3Q19, 11, 10, 9, 1.0, 1.0, 1e-4, 0.9, 3, direct_host=1 - direct)
+    ref.init(ra, rb)
+    g = Lattice(D3Q19, 11, 10, 9, 1.0, 1.0, 1e-4, 0.9, 3, direct_host=direct)
+    g.init(ra, rb)
+    assert np.array_equal(g.get_populations(), ref.get_populations())
+    g.step(2)
+    before = g.get_populations()
+    for which, site, value in ((0, 17, -0.5), (0, 40, np.nan), (1, 5, 0.0), (1, 900, np.inf)):
+        a, b = ra.copy().ravel(), rb.copy().ravel()
+        (a if which == 0 else b)[site] = value
+        if site != 5:
+            (a if which == 0 else b)[site + 3] = -1.0  # a later bad site is not the one reported
+        with pytest.raises(FlbmError) as e:
+            g.init(a, b)
+        assert e.value.status == F.EINVAL and f"at site {site} " in str(e.value)
+        assert g.step_count == 2 and np.array_equal(g.get_populations(), before)
