@@ -137,6 +137,14 @@ size_t rho_bytes_of(const flbm_ctx *c);
 uint64_t fnv1a(const unsigned char *p, size_t n);
 } // namespace host
 
+// Float densities [2][n] (species A, then B) from the caller's double arrays
+// read straight from host memory (a device that shares the host's page
+// tables; NULL: uniform rho0), with the smallest index of a value that is not
+// positive and finite per species atomically lowered into bad[0..1]
+// (flbm_obs.cu).
+cudaError_t launch_densities_from_host(const double *rho_a, const double *rho_b, double rho0_a, double rho0_b,
+                                       int64_t n, float *out, unsigned long long *bad, cudaStream_t stream);
+
 // batch entry points used by the C-ABI functions when ctx->batch is set
 flbm_status batch_set_option(flbm_ctx *c, int key, double v);
 flbm_status batch_set_stream(flbm_ctx *c, void *stream);

@@ -201,12 +201,6 @@ cudaError_t launch_batch_step_tiled(int lat, int storage, const RepInfo *reps, c
                                     unsigned k, bool full, cudaStream_t stream);
 constexpr int kTiledStepX = 32;   // tile width of the tiled step (sites along x)
 int tiled_step_rows(int lat);     // tile height (rows), 0 when the lattice has no tiled step
-// Float densities [2][n] (species A, then B) from the caller's double arrays
-// read straight from host memory (a device that shares the host's page
-// tables; NULL: uniform rho0), with the smallest index of a value that is not
-// positive and finite per species atomically lowered into bad[0..1].
-cudaError_t launch_densities_from_host(const double *rho_a, const double *rho_b, double rho0_a, double rho0_b,
-                                       int64_t n, float *out, unsigned long long *bad, cudaStream_t stream);
 // *p += v and *p = v on the device (one thread), for the batch step counter.
 cudaError_t launch_add_u32(unsigned *p, unsigned v, cudaStream_t stream);
 cudaError_t launch_set_u32(unsigned *p, unsigned v, cudaStream_t stream);
