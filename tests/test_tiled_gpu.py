@@ -172,3 +172,49 @@ def test_batch_two_array_checkpoint_and_restore():
     with pytest.raises(F.FlbmError) as e:
         Batch(D2Q9, reps).restore(swapped)
     assert e.value.status == F.EINVAL
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_batch_tiled_step_sixteen_bit_storage(storage):
+    """The tiled batch step on 16-bit deviations is the batch's two-kernel
+    step bit for bit."""
+    reps = [dict(r, tau_a=1.0) for r in _batch_reps()]
+    flat = _batch_states(reps)
+    out = []
+    for sched in (3, 1):
+        b = Batch(D2Q9, reps, storage=storage, schedule=sched, graph_steps=4)
+        b.set_populations(flat, step=1)
+        b.step(7)
+        out.append(b.get_populations())
+        b.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_batch_views_follow_the_current_array():
+    """With two arrays a replica view reads whichever array holds the current
+    state: after odd and even step counts its populations and moments are
+    the batch's slice, and a lone context stepped alike agrees."""
+    reps = _batch_reps()
+    flat = _batch_states(reps, seed=7)
+    b = Batch(D2Q9, reps, schedule=3)
+    b.set_populations(flat, step=0)
+    sizes = [r["nx"] * r["ny"] for r in reps]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for n in (3, 4):
+        b.step(n)
+        f = b.get_populations()
+        ra, rb, u, cons = b.moments()
+        for k, r in enumerate(reps):
+            v = b.replicas[k]
+            fv = v.get_populations()
+            assert np.array_equal(fv.ravel(), f[2 * 9 * offs[k]:2 * 9 * offs[k + 1]])
+            va, vb, vu, _ = v.moments()
+            assert np.array_equal(va.ravel(), ra[offs[k]:offs[k + 1]])
+            assert np.array_equal(vb.ravel(), rb[offs[k]:offs[k + 1]])
+    k = 3
+    r = reps[k]
+    g = Lattice(D2Q9, r["nx"], r["ny"], 1, r["tau_a"], r["tau_b"], r["kT"], r["G"], r["seed"], rho0_a=r["rho0_a"],
+                rho0_b=r["rho0_b"])
+    g.set_populations(flat[2 * 9 * offs[k]:2 * 9 * offs[k + 1]].reshape(2, 9, 1, r["ny"], r["nx"]), step=0)
+    g.step(7)
+    assert np.max(np.abs(g.get_populations() - b.replicas[k].get_populations())) <= 2e-6

@@ -50,7 +50,7 @@ def test_autotune_keeps_the_state_and_the_results(lat, shape, tmp_path):
     chosen = g.autotune(steps=3, cache=str(cache))
     assert g.step_count == 6
     assert np.array_equal(g.get_populations(), before)
-    assert chosen["schedule"] in (0, 1, 2) and chosen["block_x"] * chosen["block_y"] <= 128
+    assert chosen["schedule"] in (0, 1, 2, 3) and chosen["block_x"] * chosen["block_y"] <= 128
     g.step(7)
     ref = Lattice(lat, nx, ny, nz, 0.8, 1.0, 1e-4, 0.9, 6)
     ref.set_populations(f0, step=3)
@@ -75,7 +75,7 @@ def test_batch_autotune_picks_a_graph_length_and_keeps_the_state(tmp_path):
     b.step(5)
     before = b.get_populations()
     chosen = b.autotune(steps=8, cache=str(tmp_path / "tune.json"))
-    assert chosen["graph_steps"] in (0, 4, 16, 64)
+    assert chosen["graph_steps"] in (0, 4, 16, 64) and chosen["schedule"] in (1, 3)
     assert b.step_count == 5
     assert np.array_equal(b.get_populations(), before)
     b.step(9)
