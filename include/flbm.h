@@ -227,7 +227,9 @@ flbm_status flbm_set_stream(flbm_ctx *ctx, void *stream);
 
 /* Bytes of device memory the context needs for its populations and its density
  * field, for the current storage and streaming options: one array holds
- * 2 * Q * N populations; two-array streaming needs two.  Either pointer may be
+ * 2 * Q * N populations, slot by slot, with the two species' words of a slot
+ * and site side by side (species s, slot i, site x at word (i N + x) 2 + s);
+ * two-array streaming needs two.  Either pointer may be
  * NULL.  Not included: at full relaxation (every non-conserved rate 1) the
  * two-kernel step also keeps 2 (D + 1) float planes
  * of moment scratch (8 (D + 1) N bytes), allocated by the library on the first

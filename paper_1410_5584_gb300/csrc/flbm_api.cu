@@ -442,7 +442,7 @@ double raw_to_natural(const flbm_ctx *c, const std::vector<unsigned char> &raw, 
         src = ((int64_t)zs * c->ny + ys) * c->nx + xs;
         slot = lat_opp(c->lat, i);
     }
-    const size_t idx = (size_t)(s * c->Q + slot) * (size_t)c->N + (size_t)src;
+    const size_t idx = pop_index(s, slot, (size_t)src, (size_t)c->N);
     const float base = (float)lat_w(c->lat, i) * (float)c->rho0[s];
     if (c->storage == FLBM_STORE_F32) {
         float dev;
@@ -1300,20 +1300,21 @@ flbm_status flbm_set_populations(flbm_ctx *c, const double *f, int64_t step)
         for (int i = 0; i < c->Q; i++) {
             const float base = (float)lat_w(c->lat, i) * (float)c->rho0[s];
             for (int64_t site = 0; site < c->N; site++) {
-                const size_t idx = ((size_t)s * c->Q + i) * c->N + site;
+                const size_t idx = ((size_t)s * c->Q + i) * c->N + site;          // caller's [s][i][site]
+                const size_t at = pop_index(s, i, (size_t)site, (size_t)c->N); // the device layout
                 const double v = f[idx];
                 if (!std::isfinite(v)) return fail(c, FLBM_EINVAL, "non-finite population at index %zu", idx);
                 if (c->storage == FLBM_STORE_F32) {
                     const float x = (float)(v - (double)base);
-                    std::memcpy(raw.data() + idx * 4, &x, 4);
+                    std::memcpy(raw.data() + at * 4, &x, 4);
                 } else if (c->storage == FLBM_STORE_F16) {
                     const __half h = __float2half_rn((float)(v - (double)base));
                     const __half_raw hr = h;
-                    std::memcpy(raw.data() + idx * 2, &hr.x, 2);
+                    std::memcpy(raw.data() + at * 2, &hr.x, 2);
                 } else {
                     const __nv_bfloat16 b = __float2bfloat16_rn((float)(v - (double)base));
                     const __nv_bfloat16_raw br = b;
-                    std::memcpy(raw.data() + idx * 2, &br.x, 2);
+                    std::memcpy(raw.data() + at * 2, &br.x, 2);
                 }
             }
         }
@@ -1369,7 +1370,8 @@ flbm_status flbm_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "FLBMCKP1", 8);
-    h.version = 3; // 2: float storage holds deviations f_i - w_i rho0; 3: with the ghost-noise option
+    h.version = 4; // 2: float storage holds deviations f_i - w_i rho0; 3: with the ghost-noise option;
+                   // 4: the two species' words of a slot side by side
     h.lat = c->lat;
     h.nx = c->nx;
     h.ny = c->ny;
@@ -1406,7 +1408,7 @@ flbm_status flbm_restore(flbm_ctx *c, const void *buf, size_t bytes)
     if (bytes < sizeof(CkptHeader)) return fail(c, FLBM_EINVAL, "checkpoint image too small");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 3) return fail(c, FLBM_EINVAL, "not a checkpoint image");
+    if (std::memcmp(h.magic, "FLBMCKP1", 8) != 0 || h.version != 4) return fail(c, FLBM_EINVAL, "not a checkpoint image");
     if (h.lat != c->lat || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz)
         return fail(c, FLBM_EINVAL, "checkpoint lattice or box differs from this context");
     if (c->pop && h.storage != c->storage) return fail(c, FLBM_EINVAL, "checkpoint storage format differs");

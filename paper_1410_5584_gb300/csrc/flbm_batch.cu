@@ -448,7 +448,7 @@ flbm_status batch_checkpoint(flbm_ctx *c, void *buf, size_t *bytes)
     BatchCkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, "FLBMBAT1", 8);
-    h.version = 2; // 2: float storage holds deviations f_i - w_i rho0
+    h.version = 3; // 2: float storage holds deviations f_i - w_i rho0; 3: species side by side
     h.lat = c->lat;
     h.nrep = (int32_t)nrep;
     h.storage = c->storage;
@@ -489,7 +489,7 @@ flbm_status batch_restore(flbm_ctx *c, const void *buf, size_t bytes)
     if (bytes < sizeof(BatchCkptHeader)) return fail(c, FLBM_EINVAL, "checkpoint image too small");
     BatchCkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "FLBMBAT1", 8) != 0 || h.version != 2) return fail(c, FLBM_EINVAL, "not a batch checkpoint image");
+    if (std::memcmp(h.magic, "FLBMBAT1", 8) != 0 || h.version != 3) return fail(c, FLBM_EINVAL, "not a batch checkpoint image");
     if (h.lat != c->lat || (size_t)h.nrep != nrep) return fail(c, FLBM_EINVAL, "checkpoint lattice or replica count differs");
     if (c->pop && h.storage != c->storage) return fail(c, FLBM_EINVAL, "checkpoint storage format differs");
     const unsigned char *reps = static_cast<const unsigned char *>(buf) + sizeof(h);

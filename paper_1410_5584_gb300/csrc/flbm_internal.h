@@ -85,6 +85,9 @@ constexpr unsigned kStatusTimeout = 2u;   // a bounded device-side wait gave up
 // fixed sequence of roundings without contraction, so a kernel can know
 // exactly what the next step will load.  The base argument (w_i rho0^s) is
 // part of the interface for formats that might need it; none does.
+// load_pair / store_pair move the two species' words of one slot and site
+// (adjacent, species A first: pop_index below) in one access; the _cs forms
+// carry the streaming hint (evict first).
 struct StoreF32 {
     using T = float;
     __device__ __forceinline__ static T encode(float dev, float) { return dev; }
@@ -98,10 +101,42 @@ struct StoreF32 {
     {
         p[idx] = dev;
     }
+    __device__ __forceinline__ static float2 load_pair(const T *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    __device__ __forceinline__ static float2 load_pair_cs(const T *p)
+    {
+        return __ldcs(reinterpret_cast<const float2 *>(p));
+    }
+    __device__ __forceinline__ static void store_pair(T *p, T a, T b)
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+    __device__ __forceinline__ static void store_pair_cs(T *p, T a, T b)
+    {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+    }
+};
+
+// The two 16-bit words of a pair as one 32-bit word, species A in the low half
+// (the lower address).
+template <class H, class R> struct Pair16 {
+    __device__ __forceinline__ static unsigned pack(H a, H b)
+    {
+        const R ra = a, rb = b;
+        return (unsigned)ra.x | ((unsigned)rb.x << 16);
+    }
+    __device__ __forceinline__ static void unpack(unsigned w, H &a, H &b)
+    {
+        R ra, rb;
+        ra.x = (unsigned short)(w & 0xFFFFu);
+        rb.x = (unsigned short)(w >> 16);
+        a = H(ra);
+        b = H(rb);
+    }
 };
 
 struct StoreF16 {
     using T = __half;
+    using P = Pair16<__half, __half_raw>;
     __device__ __forceinline__ static T encode(float dev, float) { return __float2half_rn(dev); }
     __device__ __forceinline__ static T encode_w(float w, float y, float) { return __float2half_rn(__fmul_rn(w, y)); }
     __device__ __forceinline__ static float decode(T v, float) { return __half2float(v); }
@@ -113,10 +148,27 @@ struct StoreF16 {
     {
         p[idx] = encode(dev, base);
     }
+    __device__ __forceinline__ static float2 unpair(unsigned w)
+    {
+        T a, b;
+        P::unpack(w, a, b);
+        return make_float2(decode(a, 0.0f), decode(b, 0.0f));
+    }
+    __device__ __forceinline__ static float2 load_pair(const T *p) { return unpair(__ldg(reinterpret_cast<const unsigned *>(p))); }
+    __device__ __forceinline__ static float2 load_pair_cs(const T *p)
+    {
+        return unpair(__ldcs(reinterpret_cast<const unsigned *>(p)));
+    }
+    __device__ __forceinline__ static void store_pair(T *p, T a, T b) { *reinterpret_cast<unsigned *>(p) = P::pack(a, b); }
+    __device__ __forceinline__ static void store_pair_cs(T *p, T a, T b)
+    {
+        __stcs(reinterpret_cast<unsigned *>(p), P::pack(a, b));
+    }
 };
 
 struct StoreBF16 {
     using T = __nv_bfloat16;
+    using P = Pair16<__nv_bfloat16, __nv_bfloat16_raw>;
     __device__ __forceinline__ static T encode(float dev, float) { return __float2bfloat16_rn(dev); }
     __device__ __forceinline__ static T encode_w(float w, float y, float)
     {
@@ -131,7 +183,32 @@ struct StoreBF16 {
     {
         p[idx] = encode(dev, base);
     }
+    __device__ __forceinline__ static float2 unpair(unsigned w)
+    {
+        T a, b;
+        P::unpack(w, a, b);
+        return make_float2(decode(a, 0.0f), decode(b, 0.0f));
+    }
+    __device__ __forceinline__ static float2 load_pair(const T *p) { return unpair(__ldg(reinterpret_cast<const unsigned *>(p))); }
+    __device__ __forceinline__ static float2 load_pair_cs(const T *p)
+    {
+        return unpair(__ldcs(reinterpret_cast<const unsigned *>(p)));
+    }
+    __device__ __forceinline__ static void store_pair(T *p, T a, T b) { *reinterpret_cast<unsigned *>(p) = P::pack(a, b); }
+    __device__ __forceinline__ static void store_pair_cs(T *p, T a, T b)
+    {
+        __stcs(reinterpret_cast<unsigned *>(p), P::pack(a, b));
+    }
 };
+
+// Population layout of a two-species array: slot j of both species at a site
+// sits side by side, word (s, j, site) at index (j N + site) 2 + s, so that one
+// vector access moves both species of a slot; slot j's pairs fill the j-th
+// 2 N words.
+__host__ __device__ __forceinline__ size_t pop_index(int s, int j, size_t site, size_t N)
+{
+    return ((size_t)j * N + site) * 2 + (size_t)s;
+}
 
 inline size_t storage_bytes(int storage) { return storage == FLBM_STORE_F32 ? 4 : 2; }
 

@@ -86,42 +86,52 @@ template <class L, int PARITY, int I> __device__ __forceinline__ unsigned write_
 template <class L, int PARITY, int I>
 __device__ __forceinline__ size_t read_index(const Nbr &nb, size_t NN, int s)
 {
-    return (size_t)(s * L::Q + read_slot<L, PARITY, I>()) * NN + read_site<L, PARITY, I>(nb);
+    return pop_index(s, read_slot<L, PARITY, I>(), read_site<L, PARITY, I>(nb), NN);
 }
 
-// Where the slot planes of the population array start: slot j of species s is
-// the plane pop + (s Q + j) N.  FlatPlanes computes it in the kernel;
-// PlaneTable carries the 2Q plane pointers in the kernel's parameter space, so
-// an access is a uniform pointer plus a 32-bit site offset.
+// Where a slot's words are (pop_index: the two species side by side): pair(j,
+// site) is species A's word of slot j at site, followed by species B's;
+// word(s, j, site) is species s's.  FlatPlanes computes it from the array
+// start; PlaneTable carries the Q slot planes' starts in the kernel's parameter
+// space, so an access is a uniform pointer plus a site offset.
 template <class T> struct FlatPlanes {
     T *pop;
     size_t N;
-    template <class L> __device__ __forceinline__ T *plane(int s, int j) const { return pop + (size_t)(s * L::Q + j) * N; }
+    __device__ __forceinline__ T *pair(int j, size_t site) const { return pop + pop_index(0, j, site, N); }
+    __device__ __forceinline__ T *word(int s, int j, size_t site) const { return pop + pop_index(s, j, site, N); }
 };
 template <class T> struct PlaneTable {
-    T *ptr[2 * kMaxQ];
-    template <class L> __device__ __forceinline__ T *plane(int s, int j) const { return ptr[s * L::Q + j]; }
+    T *ptr[kMaxQ]; // slot j's pairs
+    __device__ __forceinline__ T *pair(int j, size_t site) const { return ptr[j] + 2 * site; }
+    __device__ __forceinline__ T *word(int s, int j, size_t site) const { return ptr[j] + 2 * site + s; }
 };
 
 // ---------------------------------------------------------------------------
 // density pass
 // ---------------------------------------------------------------------------
 // densities (rho_A, rho_B) of one site from its pre-collision populations
+// the pre-collision deviations of both species at a site, one pair load a slot
+template <class L, class S, int PARITY, class P>
+__device__ __forceinline__ void load_site(const P &planes, const Nbr &nb, float (&d)[2][L::Q])
+{
+    static_for<L::Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const float2 v = S::load_pair(planes.pair(read_slot<L, PARITY, i>(), read_site<L, PARITY, i>(nb)));
+        d[0][i] = v.x;
+        d[1][i] = v.y;
+    });
+}
+
 template <class L, class S, int PARITY, class P>
 __device__ __forceinline__ float2 site_density(const StepParams &p, const P &planes, const Nbr &nb)
 {
-    float r[2];
+    float r[2], d[2][L::Q];
+    load_site<L, S, PARITY>(planes, nb, d);
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        float d[L::Q], m[L::Q];
-        static_for<L::Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            constexpr float wi = (float)L::wd(i);
-            d[i] = S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()), read_site<L, PARITY, i>(nb),
-                               wi * p.rho0[s]);
-        });
+        float m[L::Q];
         // the collide step computes its own density with this same expression
-        Transform<L>::forward(d, m);
+        Transform<L>::forward(d[s], m);
         r[s] = p.rho0[s] + m[0];
     });
     return make_float2(r[0], r[1]);
@@ -150,17 +160,12 @@ template <class L, class S, int PARITY, class P>
 __device__ __forceinline__ float2 site_moments_to(const StepParams &p, const P &planes, const Nbr &nb,
                                                   float (&mm)[2][L::D + 1])
 {
-    float r[2];
+    float r[2], d[2][L::Q];
+    load_site<L, S, PARITY>(planes, nb, d);
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        float d[L::Q], m[L::Q];
-        static_for<L::Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            constexpr float wi = (float)L::wd(i);
-            d[i] = S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()), read_site<L, PARITY, i>(nb),
-                               wi * p.rho0[s]);
-        });
-        Transform<L>::forward(d, m);
+        float m[L::Q];
+        Transform<L>::forward(d[s], m);
         r[s] = p.rho0[s] + m[0];
         static_for<L::D + 1>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
@@ -222,6 +227,11 @@ template <bool CS, class T> __device__ __forceinline__ void put_word(T *p, T v)
     if constexpr (CS) __stcs(p, v);
     else *p = v;
 }
+template <bool CS, class S> __device__ __forceinline__ void put_pair(typename S::T *p, typename S::T a, typename S::T b)
+{
+    if constexpr (CS) S::store_pair_cs(p, a, b);
+    else S::store_pair(p, a, b);
+}
 
 // The end of a full-relaxation collision for both species at once (packed
 // pairs, lane lo A, hi B): y_i = sum_a T_ai mu_a, the stored words of the
@@ -250,13 +260,9 @@ __device__ __forceinline__ void full_relaxation_stores(const StepParams &p, cons
     word[1][0] = S::encode(rest.hi(), (float)L::wd(0) * p.rho0[1]);
     before_stores();
     if (STORE && live) {
-        static_for<2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                put_word<CS>(out.template plane<L>(s, write_slot<L, PARITY, i>()) + write_site<L, PARITY, i>(nb),
-                             word[s][i]);
-            });
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            put_pair<CS, S>(out.pair(write_slot<L, PARITY, i>(), write_site<L, PARITY, i>(nb)), word[0][i], word[1][i]);
         });
     }
 }
@@ -313,15 +319,7 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
         rs[1] = p.rho0[1] + m[1][0];
     } else {
         float d[2][Q];
-        static_for<2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr float wi = (float)L::wd(i);
-                d[s][i] = S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()),
-                                      read_site<L, PARITY, i>(nb), wi * p.rho0[s]);
-            });
-        });
+        load_site<L, S, PARITY>(planes, nb, d);
         if (!after_loads()) return;
         static_for<2>([&](auto sc) {
             constexpr int s = decltype(sc)::value;
@@ -554,8 +552,7 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
         if (STORE && live) {
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                put_word<CS>(out.template plane<L>(s, write_slot<L, PARITY, i>()) + write_site<L, PARITY, i>(nb),
-                             word[i]);
+                put_word<CS>(out.word(s, write_slot<L, PARITY, i>(), write_site<L, PARITY, i>(nb)), word[i]);
             });
         }
     });
@@ -963,12 +960,13 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
                 const int nx0 = (int)(ntile - nrow * (unsigned)a.tiles_per_row) * (32 * kPipeTiles);
                 const size_t nsite = D == 3 ? (size_t)ndslice * a.sp + (size_t)nrow * p.nx + nx0
                                             : (size_t)ndslice * p.nx + nx0;
-                // the slot planes are consecutive: plane q starts at in.ptr[0] + q N; a
-                // tile of a plane is one 128-byte line or less
-                for (int q = lane; q < 2 * L::Q * kPipeTiles; q += 32) {
-                    const int u = q % kPipeTiles, pl = q / kPipeTiles;
-                    if (nx0 + 32 * u < p.nx)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.ptr[0] + (size_t)pl * p.N + nsite + 32 * u));
+                // a tile of a slot is 32 pairs: two 128-byte lines in float,
+                // one in 16-bit storage (LN lines of PL pairs each)
+                constexpr int LN = sizeof(typename S::T) == 4 ? 2 : 1, PL = 32 / LN;
+                for (int q = lane; q < L::Q * LN * kPipeTiles; q += 32) {
+                    const int k = q % LN, u = (q / LN) % kPipeTiles, j = q / (LN * kPipeTiles);
+                    if (nx0 + 32 * u + PL * k < p.nx)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.pair(j, nsite + 32 * u + PL * k)));
                 }
             }
         }
@@ -989,16 +987,18 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
                 if (x < p.nx) {
                     const int insite = D == 3 ? (int)row * p.nx + x : x;
                     const int site = D == 3 ? dslice * a.sp + insite : dslice * p.nx + x;
-                    float r[2], mm[2][D + 1];
+                    float r[2], mm[2][D + 1], d[2][L::Q];
+                    static_for<L::Q>([&](auto ic) {
+                        constexpr int i = decltype(ic)::value;
+                        const float2 v = S::load_pair_cs(in.pair(i, site));
+                        d[0][i] = v.x;
+                        d[1][i] = v.y;
+                    });
                     static_for<2>([&](auto sc) {
                         constexpr int s = decltype(sc)::value;
-                        float d[L::Q], m[L::Q];
-                        static_for<L::Q>([&](auto ic) {
-                            constexpr int i = decltype(ic)::value;
-                            d[i] = S::decode(__ldcs(in.template plane<L>(s, i) + site), 0.0f);
-                        });
+                        float m[L::Q];
                         // the same expressions as the density pass of the two-kernel step
-                        Transform<L>::forward(d, m);
+                        Transform<L>::forward(d[s], m);
                         r[s] = p.rho0[s] + m[0];
                         static_for<D + 1>([&](auto ac) {
                             constexpr int q = decltype(ac)::value;
@@ -1289,7 +1289,7 @@ __global__ void k_init_rest(const StepParams p, const float *__restrict__ rho_in
             static_for<L::Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr float wi = (float)L::wd(i);
-                S::store_dev(pop, (size_t)(s * L::Q + i) * NN + site, wi * (r - p.rho0[s]), wi * p.rho0[s]);
+                S::store_dev(pop, pop_index(s, i, site, NN), wi * (r - p.rho0[s]), wi * p.rho0[s]);
             });
         });
     }
@@ -1355,7 +1355,7 @@ __global__ void __launch_bounds__(kObsBlock) k_sfk_fields(const StepParams p,
             constexpr int s = decltype(sc)::value;
             static_for<L::Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                sum[s] += S::load_dev(planes.template plane<L>(s, read_slot<L, PARITY, i>()), read_site<L, PARITY, i>(nb),
+                sum[s] += S::load_dev(planes.word(s, read_slot<L, PARITY, i>(), read_site<L, PARITY, i>(nb)), 0,
                                       (float)L::wd(i) * p.rho0[s]);
             });
         });
@@ -1399,8 +1399,8 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
             constexpr int s = decltype(sc)::value;
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                const size_t idx = PARITY == 0 ? (size_t)(s * Q + i) * NN + site
-                                               : (size_t)(s * Q + L::opp(i)) * NN + at(-L::cx(i), -L::cy(i), -L::cz(i));
+                const size_t idx = PARITY == 0 ? pop_index(s, i, site, NN)
+                                               : pop_index(s, L::opp(i), at(-L::cx(i), -L::cy(i), -L::cz(i)), NN);
                 const float dv = S::load_dev(pop, idx, (float)L::wd(i) * p.rho0[s]);
                 sum[s] += dv;
                 static_for<3>([&](auto dc) {
@@ -1466,7 +1466,7 @@ namespace kern {
 template <class T> PlaneTable<T> plane_table(T *pop, int Q, int N)
 {
     PlaneTable<T> t{};
-    for (int k = 0; k < 2 * Q; k++) t.ptr[k] = pop + (size_t)k * (size_t)N;
+    for (int k = 0; k < Q; k++) t.ptr[k] = pop + (size_t)2 * k * (size_t)N;
     return t;
 }
 } // namespace kern
