@@ -472,9 +472,13 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
     // 6. transport and ghost modes, then back-projection and streaming.  With
     // mu_a = m*_a / N_a: m*_a = m_a + lambdabar_a (m^eq_a - m_a) + (1 - lambdabar_a/2)
     // Phi_a + xi_a, i.e. mu_a = cm m_a + rho (ceq X_a + cphi Y_a) + cxi g_a, and for
-    // the ghost modes (m^eq = Phi = 0) mu_a = cm m_a + cxi g_a.
+    // the ghost modes (m^eq = Phi = 0) mu_a = cm m_a + cxi g_a.  The stored
+    // words of species A wait for those of B, so that each slot's pair goes
+    // out in one store.
+    typename S::T words[2][Q];
     static_for<2>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
+        typename S::T(&word)[Q] = words[s];
         float g[Q];
         if constexpr (!LATE) {
             static_for<Q>([&](auto ac) {
@@ -539,7 +543,6 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
         // the deviations their stored words will load as; the rest population
         // then takes m0 minus what they hold, so the rounding of their stores
         // cannot leak mass.
-        typename S::T word[Q];
         static_for<Q - 1>([&](auto kc) {
             constexpr int i = decltype(kc)::value + 1;
             constexpr float wi = (float)L::wd(i);
@@ -548,14 +551,14 @@ __device__ __forceinline__ void site_collide_src(const StepParams &p, const P &p
             fo[i] = S::decode(word[i], base);
         });
         word[0] = S::encode(Transform<L>::rest_closing_mass(fo, m[s][0]), (float)L::wd(0) * p.rho0[s]);
-        if constexpr (s == 0) before_stores();
-        if (STORE && live) {
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                put_word<CS>(out.word(s, write_slot<L, PARITY, i>(), write_site<L, PARITY, i>(nb)), word[i]);
-            });
-        }
     });
+    before_stores();
+    if (STORE && live) {
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            put_pair<CS, S>(out.pair(write_slot<L, PARITY, i>(), write_site<L, PARITY, i>(nb)), words[0][i], words[1][i]);
+        });
+    }
 }
 
 // planes: the slot planes read; out: the slot planes written (the same table
