@@ -1286,14 +1286,12 @@ __global__ void k_init_rest(const StepParams p, const float *__restrict__ rho_in
 {
     const size_t NN = (size_t)p.N;
     for (size_t site = blockIdx.x * (size_t)blockDim.x + threadIdx.x; site < NN; site += (size_t)gridDim.x * blockDim.x) {
-        static_for<2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            const float r = rho_in[(size_t)s * NN + site];
-            static_for<L::Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr float wi = (float)L::wd(i);
-                S::store_dev(pop, pop_index(s, i, site, NN), wi * (r - p.rho0[s]), wi * p.rho0[s]);
-            });
+        const float ra = rho_in[site], rb = rho_in[NN + site];
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float wi = (float)L::wd(i);
+            S::store_pair(pop + pop_index(0, i, site, NN), S::encode(wi * (ra - p.rho0[0]), wi * p.rho0[0]),
+                          S::encode(wi * (rb - p.rho0[1]), wi * p.rho0[1]));
         });
     }
 }
@@ -1354,13 +1352,11 @@ __global__ void __launch_bounds__(kObsBlock) k_sfk_fields(const StepParams p,
     if (x < p.nx) {
         const Nbr nb = make_nbr(p, x, blockIdx.y, blockIdx.z);
         float sum[2] = {0.0f, 0.0f};
-        static_for<2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<L::Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                sum[s] += S::load_dev(planes.word(s, read_slot<L, PARITY, i>(), read_site<L, PARITY, i>(nb)), 0,
-                                      (float)L::wd(i) * p.rho0[s]);
-            });
+        static_for<L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            const float2 v = S::load_pair(planes.pair(read_slot<L, PARITY, i>(), read_site<L, PARITY, i>(nb)));
+            sum[0] += v.x;
+            sum[1] += v.y;
         });
         z[nb.at(0, 0, 0)] = make_float2(sum[0], sum[1]);
         tot[0] = sum[0];
@@ -1398,13 +1394,14 @@ __global__ void __launch_bounds__(kObsBlock) k_observables(const StepParams p, c
         // precision; this GPU's FP64 rate is a small fraction of its FP32 rate)
         float sum[2] = {0.0f, 0.0f}, j[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
         float a[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
-        static_for<2>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                const size_t idx = PARITY == 0 ? pop_index(s, i, site, NN)
-                                               : pop_index(s, L::opp(i), at(-L::cx(i), -L::cy(i), -L::cz(i)), NN);
-                const float dv = S::load_dev(pop, idx, (float)L::wd(i) * p.rho0[s]);
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            const size_t idx = PARITY == 0 ? pop_index(0, i, site, NN)
+                                           : pop_index(0, L::opp(i), at(-L::cx(i), -L::cy(i), -L::cz(i)), NN);
+            const float2 v = S::load_pair(pop + idx);
+            static_for<2>([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                const float dv = s == 0 ? v.x : v.y;
                 sum[s] += dv;
                 static_for<3>([&](auto dc) {
                     constexpr int d = decltype(dc)::value;
