@@ -953,26 +953,11 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
         if (lane == 0) kreq = atomicAdd(ctr, 1u);
         const unsigned row = exact_div(tile, a.mul_row, a.shift_row); // y of the tile (3D; 0 in 2D)
         const int x0 = (int)(tile - row * (unsigned)a.tiles_per_row) * (32 * kPipeTiles) + lane;
-        // the next item of this warp: its density tiles are prefetched into L2 now
+        // the next item of this warp (an L2 prefetch of its density tiles here
+        // measured 4 % slower once the species' words sat side by side)
         int ndslice = -1, ncslice = -1;
         unsigned ntile = 0;
-        if (nitem < a.total) {
-            pipe_decode(a, nitem, ndslice, ncslice, ntile);
-            if (ndslice >= 0) {
-                const unsigned nrow = exact_div(ntile, a.mul_row, a.shift_row);
-                const int nx0 = (int)(ntile - nrow * (unsigned)a.tiles_per_row) * (32 * kPipeTiles);
-                const size_t nsite = D == 3 ? (size_t)ndslice * a.sp + (size_t)nrow * p.nx + nx0
-                                            : (size_t)ndslice * p.nx + nx0;
-                // a tile of a slot is 32 pairs: two 128-byte lines in float,
-                // one in 16-bit storage (LN lines of PL pairs each)
-                constexpr int LN = sizeof(typename S::T) == 4 ? 2 : 1, PL = 32 / LN;
-                for (int q = lane; q < L::Q * LN * kPipeTiles; q += 32) {
-                    const int k = q % LN, u = (q / LN) % kPipeTiles, j = q / (LN * kPipeTiles);
-                    if (nx0 + 32 * u + PL * k < p.nx)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(in.pair(j, nsite + 32 * u + PL * k)));
-                }
-            }
-        }
+        if (nitem < a.total) pipe_decode(a, nitem, ndslice, ncslice, ntile);
         // unit counters of this item
         const int yrow = D == 3 ? (int)row : 0;
         const long long dunit = dslice >= 0 ? (long long)dslice * a.rows + yrow : -1;
@@ -1590,17 +1575,25 @@ cudaError_t Launch<L, S>::pipe_geometry(const StepParams &p, bool mom, int lag_o
     const int tpr = (p.nx + 32 * kern::kPipeTiles - 1) / (32 * kern::kPipeTiles); // items per row
     const int T = L::D == 3 ? p.ny * tpr : tpr;
     const int sp = L::D == 3 ? p.nx * p.ny : p.nx;
-    // rows of items in flight (one item per warp, W warps: a wave of W items
-    // spans `inflight` rows); the density work runs a whole wave and two rows
-    // ahead of the collisions (an item publishes its density tile only after
-    // its own collide part, and warps drift apart by a fraction of a wave),
-    // and a slot is reused only two waves after its last readers were due
+    // slices of items in flight (one item per warp, W warps: a wave of W items
+    // spans `inflight` slices).  By default the density work runs two waves
+    // and two slices ahead of the collisions, but no further than the
+    // populations of about 40 MB of slices (which the collisions re-read from
+    // L2) allow, and never less than a wave and a slice; a slot is reused two
+    // waves and two slices after its last readers were due.  Measured, ms a
+    // step at full relaxation (two kernels / pipeline):
+    //   128^3 (a wave = 6 slices of 2.5 MB): lag 14, 29 slots: 0.158 / 0.159
+    //   192^3 (3 slices of 5.6 MB): lag 6, 14 slots: 0.535 / 0.501
+    //   256^3 (2 slices of 10 MB): lag 3, 9 slots: 1.162 / 1.183
+    // while lag 6 with 13 slots took 1.201 at 256^3, lag 7 with 21 slots 0.219
+    // at 128^3 and 4 slots of margin (lag 6, 10 slots) 1.338 at 256^3.  Any
+    // lag >= 1 with a ring of lag + 3 slots or more is correct (shorter ones
+    // wait more); an explicitly given lag gets lag + 6 slots.
     const int inflight = (int)(((long long)blocks * 4 + T - 1) / T);
-    int l = 2 * inflight + 2, R = l + 3 + 2 * inflight;
-    if (lag_opt >= 1) { // any lag >= 1 (and ring of lag + 3 or more) is correct; a short one may wait more
-        l = lag_opt;
-        R = l + 6;
-    }
+    const double slice_bytes = (double)sp * L::Q * 2 * sizeof(typename S::T);
+    const int l_fit = (int)(40e6 / slice_bytes) - 1;
+    const int l = lag_opt >= 1 ? lag_opt : std::max(inflight + 1, std::min(2 * inflight + 2, l_fit));
+    const int R = lag_opt >= 1 ? l + 6 : l + 2 * inflight + 2;
     *lag = l;
     *ring_slots = S_ >= 2 * (l + 2) + R ? R : 0; // 0: too few slices for the pipeline
     *counters = 2 * (size_t)S_ * (L::D == 3 ? p.ny : 1) + (size_t)kern::kPipeLanes * kern::kPipeStride;
