@@ -675,10 +675,16 @@ def run_ours(args, wl):
         t1 = time.perf_counter()
         barrier()
         te, ue = aggregate(t1 - t0, sites * args.steps, device=device)
-        h2d = 2 * sites * 4  # the two density planes, as float, from pinned staging
+        # the two density planes: read as doubles by a kernel straight from the
+        # caller's arrays where the GPU shares the host's page tables, else
+        # converted to float on the host and copied from pinned staging
+        direct = lat.get_option("direct_host") == 1
+        h2d = 2 * sites * (8 if direct else 4)
         d2h = (2 + D) * sites * 8 + 5 * 8
         e2e = {"value": ue / te / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps,
+               "route": "direct (kernels read and write the caller's pageable arrays)" if direct
+               else "pinned staging",
                "note": "flbm_init from host densities + K steps + flbm_moments to host, per-step averages"}
 
     if rank != 0:

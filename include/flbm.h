@@ -175,7 +175,8 @@ enum {
                                     moments straight from and into the caller's memory (the output
                                     arrays' pages mapped by host threads first); elsewhere as 0.
                                     0: through a pinned staging buffer (conversion on host threads;
-                                    the moments in alternating chunks) */
+                                    the moments in alternating chunks).  flbm_get_option reads the
+                                    route in effect: 1 only where the direct route is taken */
     FLBM_OPT_TEST_GENERAL_COLLIDE = 20, /* test hook: 1 keeps the general collide kernel even when
                                     every non-conserved rate is 1, where a kernel that skips those
                                     modes' projections runs by default (the two agree to rounding;

@@ -653,7 +653,7 @@ flbm_status flbm_get_option(const flbm_ctx *c, int key, double *value)
     case FLBM_OPT_NOISE_RHO: *value = c->noise_ref; break;
     case FLBM_OPT_FORCE_VELOCITY: *value = c->force_velocity; break;
     case FLBM_OPT_GHOST_NOISE: *value = c->ghost_noise; break;
-    case FLBM_OPT_DIRECT_HOST: *value = c->direct_host; break;
+    case FLBM_OPT_DIRECT_HOST: *value = c->direct_host && pageable_direct() ? 1.0 : 0.0; break; // the route in effect
     case FLBM_OPT_SF_AXIS: *value = c->sf_axis; break;
     case FLBM_OPT_KERNEL_TIMING: *value = c->timing ? 1.0 : 0.0; break;
     case FLBM_OPT_SCHEDULE: *value = c->schedule; break;

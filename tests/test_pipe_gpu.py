@@ -85,6 +85,20 @@ def test_pipeline_matches_oracle():
     assert np.max(np.abs(g.get_populations() - fo)) <= 2e-6 * np.max(np.abs(fo))
 
 
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.0)])
+def test_default_geometry_is_bitwise_the_two_kernel_step(tau):
+    """The automatic lag and ring on a box whose slices hold 5 MB of
+    populations (256 x 128 sites): the lag is cut by the L2 budget below two
+    waves; the pipelined kernel runs (one launch a step) and gives the
+    two-kernel step's bits."""
+    shape = (40, 128, 256)
+    f0 = _state(D3Q19, shape, eps=0.01)
+    a, launches = _run(D3Q19, shape, tau, "fused", f0, 3, timing=True)
+    b, _ = _run(D3Q19, shape, tau, "two_kernels", f0, 3)
+    assert launches == {"density": 0, "collide": 3}
+    assert np.array_equal(a, b)
+
+
 def test_small_boxes_fall_back_to_two_kernels():
     """A box with too few slices for the pipeline runs the two-kernel step."""
     shape = (6, 5, 40)
