@@ -930,7 +930,6 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
 {
     constexpr int D = L::D, NM = 2 * (D + 1);
     const int lane = threadIdx.x & 31;
-    const int W = (int)((gridDim.x * blockDim.x) >> 5);
     const int Sl = a.slices;
     // the work lane of this warp and its first two items; a third is always
     // requested one item ahead, so the counter's latency is hidden
@@ -942,7 +941,6 @@ __global__ void __launch_bounds__(128, L::Q == 9 ? (MOM ? 8 : 6) : (MOM ? 5 : 4)
         if (lane == 0) k = atomicAdd(ctr, 1u);
         return wl + kPipeLanes * (int)__shfl_sync(0xffffffffu, k, 0);
     };
-    (void)W;
     int item = draw();
     int nitem = draw();
     int dslice = -1, cslice = -1;
@@ -1578,9 +1576,10 @@ cudaError_t Launch<L, S>::pipe_geometry(const StepParams &p, bool mom, int lag_o
     // slices of items in flight (one item per warp, W warps: a wave of W items
     // spans `inflight` slices).  By default the density work runs two waves
     // and two slices ahead of the collisions, but no further than the
-    // populations of about 40 MB of slices (which the collisions re-read from
-    // L2) allow, and never less than a wave and a slice; a slot is reused two
-    // waves and two slices after its last readers were due.  Measured, ms a
+    // populations of about 40 MB of slices (a third of the 129 MB L2; the
+    // collisions re-read them from there) allow, and never less than a wave
+    // and a slice; a slot is reused two waves and two slices after its last
+    // readers were due.  Measured, ms a
     // step at full relaxation (two kernels / pipeline):
     //   128^3 (a wave = 6 slices of 2.5 MB): lag 14, 29 slots: 0.158 / 0.159
     //   192^3 (3 slices of 5.6 MB): lag 6, 14 slots: 0.535 / 0.501
