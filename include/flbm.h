@@ -82,7 +82,8 @@ typedef enum {
                                       with fewer than 3 planes (rows) run the two-kernel schedule.
                                       Either streaming mode */
     FLBM_SCHEDULE_TILED = 3        /* D2Q9 with two arrays: one launch per step.  Each thread block owns
-                                      a 32 x 16 tile; it forms the densities of the tile and of the
+                                      a 32 x 16 tile (32 x 4 on a box of at most 512 tiles of 32 x 16,
+                                      so that more blocks share it); it forms the densities of the tile and of the
                                       one-site ring around it (the force stencil, Eq. FORCESTRUCTURE)
                                       in shared memory, and at full relaxation the tile's m_0 .. m_D,
                                       then collides the tile and pushes f* into the other array.  No

@@ -1681,6 +1681,18 @@ cudaError_t Launch<L, S>::batch_step(int parity, const RepInfo *reps, const int2
 // 32 x 32 of 256 or 512 threads and 32 x 8 or 32 x 16 of two rows a thread)
 constexpr int kTileThreads = 128, kTileRowsPerThread = 4;
 
+// rows a thread of a single box's tiled step: 4 (32 x 16 tiles), or 1 (32 x 4
+// tiles, four times the blocks) on a box of at most 512 such tiles, which
+// would not fill half the GPU.  Measured (us a step, tau = 1 / 0.8/1.0, rows
+// a thread 4 / 1): 256^2 8.7 / 5.0 and 9.2 / 5.3; 512^2 13.4 / 10.9 and
+// 14.7 / 12.9; 2048^2 141 / 138 and 155 / 166; 4096^2 514 / 536 and 590 /
+// 646 (two rows a thread was never the best by more than 1 %).
+inline int tiled_rows_per_thread(int nx, int ny)
+{
+    const long long tiles = (long long)((nx + kern::kTileX - 1) / kern::kTileX) * ((ny + 15) / 16);
+    return tiles <= 512 ? 1 : kTileRowsPerThread;
+}
+
 template <class L, class S>
 cudaError_t Launch<L, S>::step_tiled(const StepParams &p, const void *pop, void *pop_out, unsigned *status,
                                      cudaStream_t st)
@@ -1688,13 +1700,19 @@ cudaError_t Launch<L, S>::step_tiled(const StepParams &p, const void *pop, void 
     if constexpr (L::D != 2) {
         return cudaErrorNotSupported;
     } else {
-        constexpr int NT = kTileThreads, R = kTileRowsPerThread;
-        using G = kern::TileGeom<NT, R>;
-        const dim3 g((p.nx + kern::kTileX - 1) / kern::kTileX, (p.ny + G::Y - 1) / G::Y);
+        constexpr int NT = kTileThreads;
         const auto in = kern::plane_table(const_cast<typename S::T *>(static_cast<const typename S::T *>(pop)), L::Q, p.N);
         const auto out = kern::plane_table(static_cast<typename S::T *>(pop_out), L::Q, p.N);
-        if (kern::full_relaxation<L>(p)) kern::k_step_tiled<L, S, true, true, NT, R><<<g, NT, 0, st>>>(p, in, out, status);
-        else kern::k_step_tiled<L, S, false, false, NT, R><<<g, NT, 0, st>>>(p, in, out, status);
+        const bool full = kern::full_relaxation<L>(p);
+        auto launch = [&](auto rc) {
+            constexpr int R = decltype(rc)::value;
+            using G = kern::TileGeom<NT, R>;
+            const dim3 g((p.nx + kern::kTileX - 1) / kern::kTileX, (p.ny + G::Y - 1) / G::Y);
+            if (full) kern::k_step_tiled<L, S, true, true, NT, R><<<g, NT, 0, st>>>(p, in, out, status);
+            else kern::k_step_tiled<L, S, false, false, NT, R><<<g, NT, 0, st>>>(p, in, out, status);
+        };
+        if (tiled_rows_per_thread(p.nx, p.ny) == 1) launch(std::integral_constant<int, 1>{});
+        else launch(std::integral_constant<int, kTileRowsPerThread>{});
         return cudaGetLastError();
     }
 }

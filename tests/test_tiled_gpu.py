@@ -1,6 +1,7 @@
 """The tiled two-array step of D2Q9 boxes (FLBM_SCHEDULE_TILED): one launch a
-step in which each thread block forms the densities of its 32 x 16 tile and of
-the one-site ring around it in shared memory, then collides the tile.  It runs
+step in which each thread block forms the densities of its tile (32 x 16 sites,
+or 32 x 4 on boxes of at most 512 such tiles) and of the one-site ring around
+it in shared memory, then collides the tile.  It runs
 the per-site arithmetic of the two-kernel step, so the two must agree bit for
 bit on every box shape (tiles cut by the box edges, boxes smaller than a tile
 whose ring wraps more than once), rate set, storage format and option; the
@@ -58,6 +59,19 @@ def test_tiled_step_is_bitwise_the_two_kernel_step(shape, tau):
     a, launches = _run(D2Q9, shape, tau, "tiled", f0, 5, timing=True)
     b, _ = _run(D2Q9, shape, tau, "two_kernels", f0, 5)
     assert launches == {"density": 0, "collide": 5}
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.8, 1.0)])
+def test_tiled_step_on_a_box_of_many_tiles(tau):
+    """Boxes of more than 512 tiles of 32 x 16 take the 32 x 16 tiles (four
+    rows a thread), smaller ones 32 x 4 tiles (one row a thread): a ragged box
+    of the first kind, bitwise the two-kernel step and one launch a step."""
+    shape = (1, 601, 1030)
+    f0 = _state(D2Q9, shape, eps=0.01)
+    a, launches = _run(D2Q9, shape, tau, "tiled", f0, 3, timing=True)
+    b, _ = _run(D2Q9, shape, tau, "two_kernels", f0, 3)
+    assert launches == {"density": 0, "collide": 3}
     assert np.array_equal(a, b)
 
 
