@@ -140,8 +140,10 @@ enum {
                                     fused step wait for work that never comes, so it runs out after
                                     the wait limit; 0 (default) off */
     FLBM_OPT_PIPE_LAG = 14,      /* fused schedule: how many slices the density work runs ahead of the
-                                    collisions; 0 (default) = the smallest lag that keeps it ahead of
-                                    the work in flight; else an integer >= 2 (results are identical) */
+                                    collisions; 0 (default) = two waves of work in flight and two
+                                    slices, cut to what about 40 MB of slices' populations allow (the
+                                    collisions re-read them from L2), never below one wave and a
+                                    slice; else an integer >= 2 (results are identical) */
     FLBM_OPT_GRAPH_STEPS = 15,   /* steps per CUDA graph that flbm_step replays: batches (default 16)
                                     and single boxes (default 0: each step launched directly; the
                                     two-kernel schedule, kernel timing off).  A graph is captured per
