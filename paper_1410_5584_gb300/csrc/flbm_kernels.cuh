@@ -1686,7 +1686,8 @@ constexpr int kTileThreads = 128, kTileRowsPerThread = 4;
 // would not fill half the GPU.  Measured (us a step, tau = 1 / 0.8/1.0, rows
 // a thread 4 / 1): 256^2 8.7 / 5.0 and 9.2 / 5.3; 512^2 13.4 / 10.9 and
 // 14.7 / 12.9; 2048^2 141 / 138 and 155 / 166; 4096^2 514 / 536 and 590 /
-// 646 (two rows a thread was never the best by more than 1 %).
+// 646 (two rows a thread was best only at tau = 0.8/1.0 on 384^2 and 768^2,
+// by 2-3 %).
 inline int tiled_rows_per_thread(int nx, int ny)
 {
     const long long tiles = (long long)((nx + kern::kTileX - 1) / kern::kTileX) * ((ny + 15) / 16);
